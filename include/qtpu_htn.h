@@ -1,0 +1,162 @@
+/*
+ * qtpu_htn.h -- C ABI for contracting hybrid tensor networks (h-TNs) on one
+ * NVIDIA B300 (sm_103a).
+ *
+ * What is computed (arXiv 2410.15080, section 4.1 and section 2.2): after the
+ * quantum tensors (QTs) of a cut circuit have been evaluated into classical
+ * tensors of subcircuit expectation values, the circuit's expectation value
+ * <O> is the contraction of a tensor network made of those tensors and the
+ * QPD coefficient tensors (CTs: a 6-vector per gate cut, the 4x4 tensor of
+ * Eq. wire-tensor per wire cut).  An index shared by two or more tensors is
+ * summed once (hyper-indices allowed, section 2.2); indices named as output
+ * (for instance a batch of observables) are kept.  Section 4.2: the value
+ * does not depend on the pairwise contraction order, the cost does; section
+ * 6.1 steps 3 and 4 plan that order and then contract.
+ *
+ * Flow: create -> add_tensor (xN) -> set_output -> plan -> contract (xM).
+ *
+ * Ownership: tensor memory is BORROWED.  The caller keeps every device
+ * buffer passed to add_tensor alive and unmodified until the stream work of
+ * every contract call that reads it has completed.  The library owns its
+ * plan, its device workspace and its status word; destroy frees them.  The
+ * output is always FP64, written densely in the order of the output ids.
+ *
+ * Errors: every call returns a qtpu_status and nothing is thrown across the
+ * ABI.  qtpu_last_error(h) returns a NUL-terminated message describing the
+ * last failure on that handle (valid until the next call on it).  A handle
+ * is not thread-safe; the network is immutable after a successful plan.
+ */
+#ifndef QTPU_HTN_H
+#define QTPU_HTN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qtpu_htn qtpu_htn; /* opaque, library-owned */
+
+typedef enum {
+  QTPU_OK = 0,
+  QTPU_EINVAL = 1,   /* bad argument: null pointer, rank/dim/stride/id error   */
+  QTPU_ENOMEM = 2,   /* host or device allocation failed                      */
+  QTPU_ECUDA = 3,    /* a CUDA runtime/driver call failed                     */
+  QTPU_ESTATE = 4,   /* call out of order (e.g. contract before plan)         */
+  QTPU_ETIMEOUT = 5, /* a bounded device-side wait gave up (status word)      */
+  QTPU_ENOTSUP = 6,  /* unsupported (e.g. a size above 2^255, no GPU)         */
+  QTPU_ELIMIT = 7    /* the peak-intermediate limit cannot be met by slicing  */
+} qtpu_status;
+
+typedef enum { QTPU_F32 = 0, QTPU_F64 = 1 } qtpu_dtype;
+
+/* Arithmetic of the large pairwise GEMMs.  All other steps (CT absorption,
+ * small or skinny contractions, dot products, the slice sum and the final
+ * reduction) always run in FP64 on the CUDA cores. */
+typedef enum {
+  QTPU_PREC_FP64 = 0,   /* every step in FP64 on the CUDA cores               */
+  QTPU_PREC_TF32 = 1,   /* tensor cores, operands rounded to TF32 (1 product) */
+  QTPU_PREC_3XTF32 = 2, /* tensor cores, 2-piece TF32 split, 3 products       */
+  QTPU_PREC_BF16X3 = 3  /* tensor cores, 3-piece BF16 split, 6 products       */
+} qtpu_prec;
+
+typedef enum { QTPU_QT = 0, QTPU_CT = 1 } qtpu_kind; /* informational */
+
+typedef struct {
+  uint64_t max_intermediate_bytes; /* 0 = no limit; 8 bytes per entry         */
+  uint32_t n_slices;               /* minimum slice count; 0 or 1 = minimal   */
+  uint32_t slice_dim;              /* only slice indices of this dim; 0 = any */
+  qtpu_prec prec;
+  int cost_model;                  /* 0 = exact FLOP cost (greedy)            */
+  uint64_t seed;                   /* reserved for randomised planners        */
+  const char* autotune_table;      /* reserved; may be NULL                   */
+} qtpu_plan_opts;
+
+/* Create an empty network bound to CUDA device `device` and the CUDA stream
+ * `cuda_stream` (a cudaStream_t; NULL = legacy default stream).  device = -1
+ * creates a host-only handle that can plan and report its plan but not
+ * contract (contract returns QTPU_ENOTSUP).  Fails with QTPU_EINVAL on a null
+ * `out`, QTPU_ECUDA if the device cannot be selected. */
+qtpu_status qtpu_htn_create(qtpu_htn** out, int device, void* cuda_stream);
+
+/* Add one tensor (a QT or a CT; contraction treats both alike).
+ *   rank       number of axes, 0..16
+ *   index_ids  rank index ids (any int64 >= 0); an id names one index of the
+ *              network; ids must be distinct within a tensor
+ *   dims       rank extents, each >= 1; every occurrence of an id must have
+ *              the same extent (else QTPU_EINVAL)
+ *   dtype      QTPU_F32 or QTPU_F64
+ *   dev_ptr    device pointer to the data (borrowed, see Ownership); may be
+ *              NULL on a host-only handle
+ *   strides    rank element strides (>= 0), or NULL for C row-major
+ *   tensor_id  receives the tensor's id (0, 1, 2, ... in call order); may be
+ *              NULL
+ * QTPU_ESTATE after plan. */
+qtpu_status qtpu_htn_add_tensor(qtpu_htn* h, qtpu_kind kind, int rank,
+                                const int64_t* index_ids, const int64_t* dims,
+                                qtpu_dtype dtype, const void* dev_ptr,
+                                const int64_t* strides, int* tensor_id);
+
+/* Name the output indices, in output order (n = 0: scalar output).  Every id
+ * must occur on some tensor (checked by plan).  Default: scalar. */
+qtpu_status qtpu_htn_set_output(qtpu_htn* h, int n, const int64_t* index_ids);
+
+/* Plan the contraction (host only): greedy pairwise order on exact 256-bit
+ * integer costs, then slicing until the peak intermediate fits
+ * max_intermediate_bytes and the slice count reaches n_slices.  opts may be
+ * NULL (defaults: no limit, no slicing, BF16X3).  QTPU_ESTATE with no
+ * tensors, QTPU_EINVAL on an unknown output id, QTPU_ELIMIT if the limit
+ * cannot be met, QTPU_ENOTSUP on a size of 2^255 or more. */
+qtpu_status qtpu_htn_plan(qtpu_htn* h, const qtpu_plan_opts* opts);
+
+/* Canonical plan text (order, index groups, per-slice sizes and FLOPs,
+ * slices, totals).  Writes at most len bytes including the NUL; *needed (if
+ * not NULL) receives the full length + 1.  QTPU_ESTATE before plan. */
+qtpu_status qtpu_htn_plan_info(const qtpu_htn* h, char* buf, size_t len,
+                               size_t* needed);
+
+/* Number of FP64 entries of the output (product of output dims). */
+qtpu_status qtpu_htn_output_size(const qtpu_htn* h, int64_t* n);
+
+/* Useful FLOPs of the planned contraction (2 per multiply-add, all slices),
+ * as a double, and the number of steps that run on the tensor cores. */
+qtpu_status qtpu_htn_plan_stats(const qtpu_htn* h, double* flops_total,
+                                int* n_steps, int* n_tensor_core_steps,
+                                uint64_t* workspace_bytes);
+
+/* Contract: enqueue the whole contraction on the handle's stream and write
+ * the FP64 result (output_size entries) to the device buffer dev_out.
+ * Asynchronous: returns after enqueueing.  Device-side failures (a bounded
+ * wait that timed out) are reported by qtpu_htn_sync.  QTPU_ESTATE before
+ * plan, QTPU_ENOTSUP on a host-only handle. */
+qtpu_status qtpu_htn_contract(qtpu_htn* h, double* dev_out);
+
+/* End-to-end form with HOST buffers: copies host_ptrs[t] (one per tensor,
+ * dense row-major in the tensor's dtype, ideally pinned) into the device
+ * buffers given to add_tensor, contracts, copies the FP64 result to host_out
+ * and waits for the stream.  Returns the device status like qtpu_htn_sync. */
+qtpu_status qtpu_htn_contract_host(qtpu_htn* h, const void* const* host_ptrs,
+                                   double* host_out);
+
+/* Contract n planned networks (possibly of different shapes) and write
+ * dev_out[i] for each, all enqueued on cuda_stream (NULL = each handle's own
+ * stream).  Handles must share one device. */
+qtpu_status qtpu_htn_contract_batch(qtpu_htn* const* hs, int n,
+                                    double* const* dev_out, void* cuda_stream);
+
+/* Wait for the handle's stream and read its device status word: QTPU_OK, or
+ * QTPU_ETIMEOUT if a bounded device-side wait gave up, or QTPU_ECUDA. */
+qtpu_status qtpu_htn_sync(qtpu_htn* h);
+
+qtpu_status qtpu_htn_destroy(qtpu_htn* h);
+
+/* Message of the last failure on h (or of the last failed create when h is
+ * NULL).  Never NULL. */
+const char* qtpu_last_error(const qtpu_htn* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QTPU_HTN_H */

@@ -1,0 +1,279 @@
+// C ABI of the h-TN contraction library (declared in include/qtpu_htn.h).
+//
+// Holds the network description (borrowed device tensors with their index
+// ids), runs the host planner, and hands the plan to the executor.  Every
+// entry point validates its arguments and returns a status; messages are
+// kept per handle.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "../../include/qtpu_htn.h"
+#include "exec.h"
+#include "planner.h"
+
+using namespace qtpu;
+
+struct qtpu_htn {
+  int device = -1;
+  cudaStream_t stream = nullptr;
+  bool host_only = true;
+  std::vector<Leaf> leaves;
+  Inds output;
+  DimMap dims;
+  bool planned = false;
+  Plan plan;
+  qtpu_plan_opts opts{};
+  Executor ex;
+  bool built = false;
+  std::string err;
+};
+
+static std::string g_create_err = "no error";
+
+static qtpu_status fail(qtpu_htn* h, qtpu_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+extern "C" {
+
+qtpu_status qtpu_htn_create(qtpu_htn** out, int device, void* cuda_stream) {
+  if (!out) {
+    g_create_err = "out is NULL";
+    return QTPU_EINVAL;
+  }
+  *out = nullptr;
+  qtpu_htn* h = new (std::nothrow) qtpu_htn();
+  if (!h) {
+    g_create_err = "host allocation failed";
+    return QTPU_ENOMEM;
+  }
+  h->device = device;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->host_only = device < 0;
+  if (!h->host_only) {
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || device >= n) {
+      cudaGetLastError();
+      g_create_err = std::string("device ") + std::to_string(device) + " not available: " +
+                     (e != cudaSuccess ? cudaGetErrorString(e) : "index out of range");
+      delete h;
+      return QTPU_ECUDA;
+    }
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+      g_create_err = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
+      delete h;
+      return QTPU_ECUDA;
+    }
+    h->ex.device = device;
+    h->ex.stream = h->stream;
+  }
+  *out = h;
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_add_tensor(qtpu_htn* h, qtpu_kind kind, int rank, const int64_t* index_ids,
+                                const int64_t* dims, qtpu_dtype dtype, const void* dev_ptr,
+                                const int64_t* strides, int* tensor_id) {
+  if (!h) return QTPU_EINVAL;
+  if (h->planned) return fail(h, QTPU_ESTATE, "add_tensor after plan");
+  if (kind != QTPU_QT && kind != QTPU_CT) return fail(h, QTPU_EINVAL, "bad kind");
+  if (rank < 0 || rank > 16) return fail(h, QTPU_EINVAL, "rank must be 0..16");
+  if (rank > 0 && (!index_ids || !dims)) return fail(h, QTPU_EINVAL, "index_ids/dims NULL");
+  if (dtype != QTPU_F32 && dtype != QTPU_F64) return fail(h, QTPU_EINVAL, "bad dtype");
+  if (!dev_ptr && !h->host_only) return fail(h, QTPU_EINVAL, "dev_ptr NULL");
+  Leaf L;
+  std::set<int64_t> seen;
+  for (int a = 0; a < rank; ++a) {
+    if (index_ids[a] < 0) return fail(h, QTPU_EINVAL, "negative index id");
+    if (dims[a] < 1) return fail(h, QTPU_EINVAL, "dim < 1");
+    if (!seen.insert(index_ids[a]).second) return fail(h, QTPU_EINVAL, "repeated index id within a tensor");
+    int64_t d = h->dims.get(index_ids[a]);
+    if (d >= 0 && d != dims[a])
+      return fail(h, QTPU_EINVAL,
+                  "index " + std::to_string(index_ids[a]) + ": dim " + std::to_string(dims[a]) +
+                      " != " + std::to_string(d));
+    if (strides && strides[a] < 0) return fail(h, QTPU_EINVAL, "negative stride");
+  }
+  for (int a = 0; a < rank; ++a) h->dims.set(index_ids[a], dims[a]);
+  L.ids.assign(index_ids, index_ids + rank);
+  L.dims.assign(dims, dims + rank);
+  L.strides.resize(rank);
+  int64_t st = 1;
+  for (int a = rank - 1; a >= 0; --a) {
+    L.strides[a] = strides ? strides[a] : st;
+    st *= dims[a];
+  }
+  L.dt = dtype == QTPU_F64 ? DT_F64 : DT_F32;
+  L.ptr = dev_ptr;
+  h->leaves.push_back(L);
+  if (tensor_id) *tensor_id = (int)h->leaves.size() - 1;
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_set_output(qtpu_htn* h, int n, const int64_t* index_ids) {
+  if (!h) return QTPU_EINVAL;
+  if (h->planned) return fail(h, QTPU_ESTATE, "set_output after plan");
+  if (n < 0 || (n > 0 && !index_ids)) return fail(h, QTPU_EINVAL, "bad output list");
+  std::set<int64_t> seen;
+  for (int a = 0; a < n; ++a)
+    if (!seen.insert(index_ids[a]).second) return fail(h, QTPU_EINVAL, "repeated output id");
+  h->output.assign(index_ids, index_ids + n);
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_plan(qtpu_htn* h, const qtpu_plan_opts* opts) {
+  if (!h) return QTPU_EINVAL;
+  if (h->planned) return fail(h, QTPU_ESTATE, "already planned");
+  if (h->leaves.empty()) return fail(h, QTPU_ESTATE, "plan before any tensor");
+  qtpu_plan_opts o{};
+  o.prec = QTPU_PREC_BF16X3;
+  if (opts) o = *opts;
+  if (o.prec < QTPU_PREC_FP64 || o.prec > QTPU_PREC_BF16X3) return fail(h, QTPU_EINVAL, "bad precision");
+  if (o.cost_model != 0) return fail(h, QTPU_ENOTSUP, "only the exact cost model is available");
+  for (int64_t i : h->output)
+    if (!h->dims.has(i)) return fail(h, QTPU_EINVAL, "output index " + std::to_string(i) + " is on no tensor");
+  std::vector<Inds> li;
+  for (auto& L : h->leaves) li.push_back(L.ids);
+  int r = make_plan(li, h->dims, h->output, o.max_intermediate_bytes, o.n_slices, o.slice_dim, &h->plan);
+  if (r == PLAN_OVERFLOW) return fail(h, QTPU_ENOTSUP, "a contraction size reaches 2^255");
+  if (r == PLAN_LIMIT) return fail(h, QTPU_ELIMIT, "the peak-intermediate limit cannot be met by slicing");
+  h->opts = o;
+  if (!h->host_only) {
+    int code = QTPU_OK;
+    std::string m = exec_build(&h->ex, h->plan, h->leaves, h->dims, (int)o.prec, &code);
+    if (code != QTPU_OK) return fail(h, (qtpu_status)code, m);
+    h->built = true;
+  }
+  h->planned = true;
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_plan_info(const qtpu_htn* h, char* buf, size_t len, size_t* needed) {
+  if (!h) return QTPU_EINVAL;
+  if (!h->planned) return QTPU_ESTATE;
+  std::string t = plan_text(h->plan);
+  if (needed) *needed = t.size() + 1;
+  if (buf && len) {
+    size_t n = std::min(len - 1, t.size());
+    memcpy(buf, t.data(), n);
+    buf[n] = 0;
+  }
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_output_size(const qtpu_htn* h, int64_t* n) {
+  if (!h || !n) return QTPU_EINVAL;
+  int64_t s = 1;
+  for (int64_t i : h->output) s *= h->dims.get(i);
+  *n = s;
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_plan_stats(const qtpu_htn* h, double* flops_total, int* n_steps, int* n_tc,
+                                uint64_t* ws) {
+  if (!h) return QTPU_EINVAL;
+  if (!h->planned) return QTPU_ESTATE;
+  if (flops_total) *flops_total = h->plan.flops_total.to_double();
+  if (n_steps) *n_steps = (int)h->plan.steps.size();
+  if (n_tc) *n_tc = h->built ? h->ex.n_tc_steps : 0;
+  if (ws) *ws = h->built ? (uint64_t)h->ex.workspace_bytes() : 0;
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_contract(qtpu_htn* h, double* dev_out) {
+  if (!h) return QTPU_EINVAL;
+  if (!h->planned) return fail(h, QTPU_ESTATE, "contract before plan");
+  if (h->host_only) return fail(h, QTPU_ENOTSUP, "host-only handle cannot contract");
+  if (!dev_out) return fail(h, QTPU_EINVAL, "dev_out NULL");
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
+  int code = QTPU_OK;
+  std::string m = exec_run(&h->ex, h->leaves, dev_out, h->stream, &code);
+  if (code != QTPU_OK) return fail(h, (qtpu_status)code, m);
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_sync(qtpu_htn* h) {
+  if (!h) return QTPU_EINVAL;
+  if (h->host_only || !h->built) return QTPU_OK;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
+  uint32_t st = 0;
+  e = cudaMemcpy(&st, h->ex.status, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
+  if (st & (ST_TIMEOUT_TMA | ST_TIMEOUT_MMA | ST_TIMEOUT_EPI | ST_TIMEOUT_DEP))
+    return fail(h, QTPU_ETIMEOUT, "a bounded device-side wait gave up (status 0x" + std::to_string(st) + ")");
+  if (st) return fail(h, QTPU_ECUDA, "device status word " + std::to_string(st));
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_contract_host(qtpu_htn* h, const void* const* host_ptrs, double* host_out) {
+  if (!h) return QTPU_EINVAL;
+  if (!h->planned) return fail(h, QTPU_ESTATE, "contract before plan");
+  if (h->host_only) return fail(h, QTPU_ENOTSUP, "host-only handle cannot contract");
+  if (!host_ptrs || !host_out) return fail(h, QTPU_EINVAL, "NULL host buffer");
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
+  for (size_t t = 0; t < h->leaves.size(); ++t) {
+    const Leaf& L = h->leaves[t];
+    if (!host_ptrs[t]) return fail(h, QTPU_EINVAL, "NULL host buffer");
+    int64_t n = 1;
+    for (int64_t d : L.dims) n *= d;
+    e = cudaMemcpyAsync((void*)L.ptr, host_ptrs[t], (size_t)n * (L.dt == DT_F64 ? 8 : 4), cudaMemcpyHostToDevice,
+                        h->stream);
+    if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
+  }
+  int64_t no = 1;
+  qtpu_htn_output_size(h, &no);
+  double* dout = h->ex.out_stage;  // allocated with the workspace by plan
+  qtpu_status s = qtpu_htn_contract(h, dout);
+  if (s != QTPU_OK) return s;
+  e = cudaMemcpyAsync(host_out, dout, (size_t)no * 8, cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
+  return qtpu_htn_sync(h);
+}
+
+qtpu_status qtpu_htn_contract_batch(qtpu_htn* const* hs, int n, double* const* dev_out, void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!hs || !dev_out))) return QTPU_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    qtpu_htn* h = hs[i];
+    if (!h) return QTPU_EINVAL;
+    if (!h->planned) return fail(h, QTPU_ESTATE, "contract before plan");
+    if (h->host_only) return fail(h, QTPU_ENOTSUP, "host-only handle cannot contract");
+    if (h->device != hs[0]->device) return fail(h, QTPU_EINVAL, "handles on different devices");
+  }
+  for (int i = 0; i < n; ++i) {
+    qtpu_htn* h = hs[i];
+    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : h->stream;
+    int code = QTPU_OK;
+    std::string m = exec_run(&h->ex, h->leaves, dev_out[i], st, &code);
+    if (code != QTPU_OK) return fail(h, (qtpu_status)code, m);
+  }
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_destroy(qtpu_htn* h) {
+  if (!h) return QTPU_EINVAL;
+  if (h->built) {
+    cudaSetDevice(h->device);
+    exec_free(&h->ex);
+  }
+  delete h;
+  return QTPU_OK;
+}
+
+const char* qtpu_last_error(const qtpu_htn* h) {
+  if (!h) return g_create_err.c_str();
+  return h->err.empty() ? "no error" : h->err.c_str();
+}
+
+}  // extern "C"

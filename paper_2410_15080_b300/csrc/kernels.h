@@ -1,0 +1,75 @@
+// Launch interfaces of the h-TN kernels (host side).
+#pragma once
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace qtpu {
+
+constexpr int kMaxModes = 12;
+
+// device status word bits (OR-ed in by any thread that gives up)
+enum : uint32_t {
+  ST_TIMEOUT_TMA = 1u << 0,   // producer waited too long for a free stage
+  ST_TIMEOUT_MMA = 1u << 1,   // MMA issuer waited too long for data / accumulator
+  ST_TIMEOUT_EPI = 1u << 2,   // epilogue waited too long for an accumulator
+  ST_TIMEOUT_DEP = 1u << 3,   // a dependency counter never completed
+  ST_BAD_ARG = 1u << 8,       // a kernel saw inconsistent arguments and did nothing
+};
+
+// A group of tensor modes (outermost first) with element strides into two
+// operands.  A stride of 0 means the operand does not carry that mode.
+struct ModeTab {
+  int n = 0;
+  int64_t dim[kMaxModes];
+  int64_t sa[kMaxModes];
+  int64_t sb[kMaxModes];
+};
+
+// out[o] = sum_l A[offA(o) + offA(l)] * B[offB(o) + offB(l)]   (FP64)
+// o runs over the `out` modes (dense output, last mode fastest), l over the
+// `loop` modes.  B may be null (single-operand reduction: B == 1).
+struct ContractArgs {
+  ModeTab out, loop;
+  int64_t n_out = 1, n_loop = 1;
+};
+
+enum DType { DT_F32 = 0, DT_F64 = 1 };
+
+cudaError_t launch_contract(const void* A, int dtA, const void* B, int dtB, double* out,
+                            const ContractArgs& a, int sm_count, cudaStream_t st);
+
+// Tensor-core operand preparation: gather an operand into [rows][Kp] (row =
+// flattened batch and M (or N) modes, K modes innermost) and split every
+// FP64 value into `pieces` low-precision pieces stored piece-major:
+// dst[p][row][k].  kind 0: BF16 pieces (3); kind 1: TF32 pieces (1 or 2).
+struct SplitArgs {
+  ModeTab row, k;  // sa = source strides
+  int64_t n_rows = 0, K = 0, Kp = 0;
+  int pieces = 3;
+  int kind = 0;
+};
+cudaError_t launch_split(const void* src, int dt, void* dst, const SplitArgs& a, int sm_count,
+                         cudaStream_t st);
+
+// prec: 1 = TF32 (1 piece, 1 product), 2 = 3xTF32 (2 pieces, 3 products),
+//       3 = BF16x3 (3 pieces, 6 products)
+struct GemmArgs {
+  CUtensorMap tmA, tmB;  // 4-D maps over [pieces][batch][rows][Kp]
+  double* C = nullptr;   // [batch][M][N] FP64, dense
+  int batch = 0, M = 0, N = 0, K = 0;
+  int kc_blocks = 0;     // k-blocks per TMEM accumulation chunk (0 = all)
+  int prec = 3;
+  uint32_t* status = nullptr;
+  uint64_t limit_ns = 2000000000ull;
+};
+cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st);
+
+// Build the 4-D TMA map of a split operand buffer (returns false on failure).
+bool make_operand_map(CUtensorMap* map, void* base, int prec, int64_t batch, int64_t rows, int64_t K,
+                      int64_t Kp, int box_rows);
+
+int gemm_block_n();        // N tile of the GEMM kernel
+int gemm_k_block(int prec);  // K elements per pipeline stage
+
+}  // namespace qtpu

@@ -1,0 +1,309 @@
+// Batched GEMM on the 5th-generation tensor cores (tcgen05 + TMEM + TMA).
+//
+// Pairwise contraction of two h-TN tensors (section 4.2: the post-processing
+// is a sequence of pairwise contractions) is, after regrouping indices, a
+// batched GEMM  C[b, m, n] = sum_k A[b, m, k] * B[b, n, k]  (both operands
+// K-major).  FP64 operands are split into low-precision pieces by the split
+// kernel (x = x0 + x1 + x2, BF16 or TF32 pieces); the products of the pieces
+// whose combined weight is at or above 2^-16 (BF16x3: 6 products) or 2^-22
+// (3xTF32: 3 products) accumulate in FP32 in TMEM, and the epilogue adds each
+// accumulation chunk into FP64 in the output, so the FP32 accumulation error
+// is bounded by the chunk length rather than by K.
+//
+// One CTA per SM, persistent over (batch, m-tile, n-tile) tiles:
+//   warp 0      TMA producer (one lane): pieces of A and B for one k-block
+//               per pipeline stage, completion counted on an mbarrier;
+//   warp 1      TMEM owner and MMA issuer (one lane): per k-block, 4 UMMA
+//               K-steps x the product list, into one of two TMEM
+//               accumulators (double-buffered so the epilogue of one chunk
+//               overlaps the MMAs of the next);
+//   warps 2..5  epilogue: tcgen05.ld 32 lanes x 16 columns, FP64 add/store.
+// Every wait is bounded (global timer); on give-up the kernel sets a status
+// bit, lets in-flight copies and MMAs land, frees TMEM and returns.
+#include <cstdio>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace qtpu {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BN = 128;
+constexpr int kThreads = 192;
+constexpr int kRowBytes = 128;  // one swizzle row: 64 BF16 or 32 TF32
+
+template <int PREC>
+struct Cfg;
+template <>
+struct Cfg<3> {  // BF16x3
+  static constexpr int NP = 3, NPROD = 6, ES = 2, KB = 64, UK = 16, FMT = 1, STAGES = 2;
+  __device__ static int pa(int i) { const int t[6] = {0, 0, 1, 0, 1, 2}; return t[i]; }
+  __device__ static int pb(int i) { const int t[6] = {0, 1, 0, 2, 1, 0}; return t[i]; }
+};
+template <>
+struct Cfg<2> {  // 3xTF32
+  static constexpr int NP = 2, NPROD = 3, ES = 4, KB = 32, UK = 8, FMT = 2, STAGES = 3;
+  __device__ static int pa(int i) { const int t[3] = {0, 0, 1}; return t[i]; }
+  __device__ static int pb(int i) { const int t[3] = {0, 1, 0}; return t[i]; }
+};
+template <>
+struct Cfg<1> {  // TF32
+  static constexpr int NP = 1, NPROD = 1, ES = 4, KB = 32, UK = 8, FMT = 2, STAGES = 4;
+  __device__ static int pa(int) { return 0; }
+  __device__ static int pb(int) { return 0; }
+};
+
+template <int PREC>
+struct Layout {
+  using C = Cfg<PREC>;
+  static constexpr int A_PIECE = BM * kRowBytes;
+  static constexpr int B_PIECE = BN * kRowBytes;
+  static constexpr int STAGE = C::NP * (A_PIECE + B_PIECE);
+  static constexpr int BAR_OFF = C::STAGES * STAGE;
+  // full[S], empty[S], accfull[2], accempty[2], mma_done
+  static constexpr int N_BARS = 2 * C::STAGES + 5;
+  static constexpr int SMEM = BAR_OFF + N_BARS * 8 + 16 + 1024;
+};
+
+__device__ __forceinline__ void set_abort(volatile int* abort, uint32_t* status, uint32_t bit) {
+  *abort = 1;
+  if (status) atomicOr(status, bit);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, double* __restrict__ Cout,
+              int batch, int M, int N, int K, int kc_blocks, uint32_t* status, uint64_t limit_ns) {
+  using C = Cfg<PREC>;
+  using L = Layout<PREC>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + L::BAR_OFF);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + C::STAGES;
+  uint64_t* accfull = bars + 2 * C::STAGES;
+  uint64_t* accempty = accfull + 2;
+  uint64_t* mma_done = accempty + 2;
+  uint32_t* tmem_holder = (uint32_t*)(bars + L::N_BARS);
+  volatile int* abort = (volatile int*)(tmem_holder + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
+  const long long n_tiles = (long long)batch * mt * nt;
+  const int nkb = (K + C::KB - 1) / C::KB;
+  const int kc = (kc_blocks > 0 && kc_blocks < nkb) ? kc_blocks : nkb;
+  const int nchunks = (nkb + kc - 1) / kc;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&accfull[a], 1);
+      mbar_init(&accempty[a], 4);
+    }
+    mbar_init(mma_done, 1);
+    *abort = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_holder, 2 * BN);
+    tmem_relinquish();
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ producer
+      int stage = 0;
+      uint32_t phase = 0;
+      int issued[C::STAGES];
+      uint32_t issued_phase[C::STAGES];
+      for (int s = 0; s < C::STAGES; ++s) issued[s] = 0, issued_phase[s] = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const int ntile = (int)(t % nt);
+        const long long r = t / nt;
+        const int mtile = (int)(r % mt);
+        const int b = (int)(r / mt);
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (!mbar_wait_bounded(&empty[stage], phase ^ 1, limit_ns, abort)) {
+            set_abort(abort, status, ST_TIMEOUT_TMA);
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&full[stage], L::STAGE);
+          uint8_t* sA = smem + stage * L::STAGE;
+          uint8_t* sB = sA + C::NP * L::A_PIECE;
+#pragma unroll
+          for (int p = 0; p < C::NP; ++p) {
+            tma_load_4d(sA + p * L::A_PIECE, &tmA, &full[stage], kb * C::KB, mtile * BM, b, p);
+            tma_load_4d(sB + p * L::B_PIECE, &tmB, &full[stage], kb * C::KB, ntile * BN, b, p);
+          }
+          issued[stage] = 1;
+          issued_phase[stage] = phase;
+          if (++stage == C::STAGES) stage = 0, phase ^= 1;
+        }
+      }
+      if (!ok) {  // let copies already in flight land before the CTA exits
+        for (int s = 0; s < C::STAGES; ++s)
+          if (issued[s]) {
+            volatile int no_abort = 0;
+            mbar_wait_bounded(&full[s], issued_phase[s], limit_ns, &no_abort);
+          }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------------------ MMA issuer
+      const uint32_t idesc = make_idesc(C::FMT, BM, BN);
+      int stage = 0;
+      uint32_t phase = 0;
+      long long item = 0;
+      bool ok = true, any = false;
+      for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        for (int ch = 0; ch < nchunks && ok; ++ch, ++item) {
+          const int acc = (int)(item & 1);
+          const uint32_t aph = (uint32_t)((item >> 1) & 1);
+          if (!mbar_wait_bounded(&accempty[acc], aph ^ 1, limit_ns, abort)) {
+            set_abort(abort, status, ST_TIMEOUT_MMA);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t dt = tmem + (uint32_t)(acc * BN);
+          const int kb0 = ch * kc, kb1 = min(nkb, kb0 + kc);
+          for (int kb = kb0; kb < kb1; ++kb) {
+            if (!mbar_wait_bounded(&full[stage], phase, limit_ns, abort)) {
+              set_abort(abort, status, ST_TIMEOUT_MMA);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sA = smem_u32(smem + stage * L::STAGE);
+            const uint32_t sB = sA + C::NP * L::A_PIECE;
+#pragma unroll
+            for (int kk = 0; kk < C::KB / C::UK; ++kk) {
+#pragma unroll
+              for (int pr = 0; pr < C::NPROD; ++pr) {
+                const uint64_t ad = smem_desc_sw128(sA + C::pa(pr) * L::A_PIECE + kk * C::UK * C::ES);
+                const uint64_t bd = smem_desc_sw128(sB + C::pb(pr) * L::B_PIECE + kk * C::UK * C::ES);
+                const uint32_t accum = (kb > kb0 || kk > 0 || pr > 0) ? 1u : 0u;
+                if (C::FMT == 1)
+                  umma_f16(dt, ad, bd, idesc, accum);
+                else
+                  umma_tf32(dt, ad, bd, idesc, accum);
+              }
+            }
+            umma_commit(&empty[stage]);
+            any = true;
+            if (++stage == C::STAGES) stage = 0, phase ^= 1;
+          }
+          if (ok) umma_commit(&accfull[acc]);
+        }
+      }
+      if (!ok && any) {  // let issued MMAs finish before TMEM is freed
+        umma_commit(mma_done);
+        volatile int no_abort = 0;
+        mbar_wait_bounded(mma_done, 0, limit_ns, &no_abort);
+      }
+    }
+  } else {
+    // -------------------------------------------------------------- epilogue
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    long long item = 0;
+    bool ok = true;
+    for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+      const int ntile = (int)(t % nt);
+      const long long r = t / nt;
+      const int mtile = (int)(r % mt);
+      const int b = (int)(r / mt);
+      const int row = mtile * BM + q * 32 + lane;
+      double* crow = Cout + ((long long)b * M + row) * (long long)N;
+      for (int ch = 0; ch < nchunks; ++ch, ++item) {
+        const int acc = (int)(item & 1);
+        const uint32_t aph = (uint32_t)((item >> 1) & 1);
+        // every lane waits, then the warp agrees (tcgen05.ld is warp-collective)
+        const bool got = mbar_wait_bounded(&accfull[acc], aph, limit_ns, abort);
+        if (!__all_sync(0xffffffffu, got)) {
+          if (lane == 0) set_abort(abort, status, ST_TIMEOUT_EPI);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+#pragma unroll 1
+        for (int c = 0; c < BN / 16; ++c) {
+          float v[16];
+          tmem_ld16(ta + c * 16, v);
+          const int n0 = ntile * BN + c * 16;
+          if (row < M) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int n = n0 + j;
+              if (n < N) {
+                const double prev = ch ? crow[n] : 0.0;
+                crow[n] = prev + (double)v[j];
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&accempty[acc]);
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    tmem_dealloc(tmem, 2 * BN);
+  }
+}
+
+template <int PREC>
+cudaError_t launch_t(const GemmArgs& a, int sm_count, cudaStream_t st) {
+  using L = Layout<PREC>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const long long tiles = (long long)a.batch * ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
+  if (tiles <= 0) return cudaSuccess;
+  const int grid = (int)(tiles < sm_count ? tiles : sm_count);
+  k_gemm_tc<PREC><<<grid, kThreads, L::SMEM, st>>>(a.tmA, a.tmB, a.C, a.batch, a.M, a.N, a.K, a.kc_blocks,
+                                                     a.status, a.limit_ns);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int gemm_block_n() { return BN; }
+int gemm_k_block(int prec) { return prec == 3 ? Cfg<3>::KB : Cfg<1>::KB; }
+
+cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st) {
+  switch (a.prec) {
+    case 1: return launch_t<1>(a, sm_count, st);
+    case 2: return launch_t<2>(a, sm_count, st);
+    case 3: return launch_t<3>(a, sm_count, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace qtpu

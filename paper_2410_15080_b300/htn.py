@@ -1,0 +1,211 @@
+"""Python binding of the C ABI in ``include/qtpu_htn.h`` (argument marshalling only).
+
+Every step of the contraction runs in ``libqtpu_htn.so``: this module passes
+device pointers (``tensor.data_ptr()``), sizes and the current CUDA stream,
+and turns status codes into exceptions.  There is no fallback: if the
+library is missing, importing ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqtpu_htn.so")
+
+QTPU_OK, QTPU_EINVAL, QTPU_ENOMEM, QTPU_ECUDA, QTPU_ESTATE, QTPU_ETIMEOUT, QTPU_ENOTSUP, QTPU_ELIMIT = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ESTATE", "ETIMEOUT", "ENOTSUP", "ELIMIT"]
+QTPU_F32, QTPU_F64 = 0, 1
+PREC = {"fp64": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3}
+QTPU_QT, QTPU_CT = 0, 1
+
+SYMBOLS = ["qtpu_htn_create", "qtpu_htn_add_tensor", "qtpu_htn_set_output", "qtpu_htn_plan",
+           "qtpu_htn_plan_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats", "qtpu_htn_contract",
+           "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_sync", "qtpu_htn_destroy",
+           "qtpu_last_error"]
+
+
+class QtpuError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+
+
+class PlanOpts(C.Structure):
+    _fields_ = [("max_intermediate_bytes", C.c_uint64), ("n_slices", C.c_uint32),
+                ("slice_dim", C.c_uint32), ("prec", C.c_int), ("cost_model", C.c_int),
+                ("seed", C.c_uint64), ("autotune_table", C.c_char_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run python -m paper_2410_15080_b300.build")
+        L = C.CDLL(LIB_PATH)
+        vp, i64p = C.c_void_p, C.POINTER(C.c_int64)
+        L.qtpu_htn_create.argtypes = [C.POINTER(vp), C.c_int, vp]
+        L.qtpu_htn_add_tensor.argtypes = [vp, C.c_int, C.c_int, i64p, i64p, C.c_int, vp, i64p,
+                                          C.POINTER(C.c_int)]
+        L.qtpu_htn_set_output.argtypes = [vp, C.c_int, i64p]
+        L.qtpu_htn_plan.argtypes = [vp, C.POINTER(PlanOpts)]
+        L.qtpu_htn_plan_info.argtypes = [vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]
+        L.qtpu_htn_output_size.argtypes = [vp, i64p]
+        L.qtpu_htn_plan_stats.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int),
+                                          C.POINTER(C.c_int), C.POINTER(C.c_uint64)]
+        L.qtpu_htn_contract.argtypes = [vp, vp]
+        L.qtpu_htn_contract_host.argtypes = [vp, C.POINTER(vp), vp]
+        L.qtpu_htn_contract_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), vp]
+        L.qtpu_htn_sync.argtypes = [vp]
+        L.qtpu_htn_destroy.argtypes = [vp]
+        L.qtpu_last_error.argtypes = [vp]
+        L.qtpu_last_error.restype = C.c_char_p
+        for s in SYMBOLS:
+            if s != "qtpu_last_error":
+                getattr(L, s).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _arr(vals, t=C.c_int64):
+    vals = list(vals)
+    return (t * max(1, len(vals)))(*vals)
+
+
+class HTN:
+    """One h-TN bound to a device and stream (device=-1: plan only)."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        self._L = lib()
+        self._h = C.c_void_p()
+        if stream is None and device >= 0:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self._check(self._L.qtpu_htn_create(C.byref(self._h), device, C.c_void_p(stream or 0)), create=True)
+        self.device = device
+        self._keep = []  # tensors whose memory the library borrows
+        self.n_tensors = 0
+
+    def _check(self, st, create=False):
+        if st != QTPU_OK:
+            msg = self._L.qtpu_last_error(None if create else self._h).decode()
+            raise QtpuError(st, msg)
+
+    def add_tensor(self, inds: Sequence[int], dims: Sequence[int] = None, data=None, kind: int = QTPU_QT,
+                   dtype: str | None = None, strides: Sequence[int] | None = None) -> int:
+        """Register a tensor: ``data`` is a CUDA torch tensor (its shape and
+        strides are used unless given) or None on a plan-only handle."""
+        ptr = 0
+        if data is not None:
+            import torch
+            assert data.device.type == "cuda", "tensors must be on the device"
+            dims = list(data.shape) if dims is None else dims
+            strides = list(data.stride()) if strides is None else strides
+            dtype = {torch.float64: "f64", torch.float32: "f32"}[data.dtype]
+            ptr = data.data_ptr()
+            self._keep.append(data)
+        dt = QTPU_F64 if (dtype or "f64") == "f64" else QTPU_F32
+        tid = C.c_int(-1)
+        self._check(self._L.qtpu_htn_add_tensor(
+            self._h, kind, len(inds), _arr(inds), _arr(dims), dt, C.c_void_p(ptr),
+            _arr(strides) if strides is not None else None, C.byref(tid)))
+        self.n_tensors += 1
+        return tid.value
+
+    def set_output(self, inds: Sequence[int]):
+        self._check(self._L.qtpu_htn_set_output(self._h, len(inds), _arr(inds)))
+
+    def plan(self, prec: str = "bf16x3", max_intermediate_bytes: int = 0, n_slices: int = 0,
+             slice_dim: int = 0):
+        o = PlanOpts(max_intermediate_bytes, n_slices, slice_dim, PREC[prec], 0, 0, None)
+        self._check(self._L.qtpu_htn_plan(self._h, C.byref(o)))
+
+    def plan_info(self) -> str:
+        need = C.c_size_t(0)
+        self._check(self._L.qtpu_htn_plan_info(self._h, None, 0, C.byref(need)))
+        buf = C.create_string_buffer(need.value)
+        self._check(self._L.qtpu_htn_plan_info(self._h, buf, need.value, None))
+        return buf.value.decode()
+
+    def output_size(self) -> int:
+        n = C.c_int64()
+        self._check(self._L.qtpu_htn_output_size(self._h, C.byref(n)))
+        return n.value
+
+    def plan_stats(self) -> dict:
+        f, ns, nt, ws = C.c_double(), C.c_int(), C.c_int(), C.c_uint64()
+        self._check(self._L.qtpu_htn_plan_stats(self._h, C.byref(f), C.byref(ns), C.byref(nt), C.byref(ws)))
+        return {"flops_total": f.value, "n_steps": ns.value, "n_tensor_core_steps": nt.value,
+                "workspace_bytes": ws.value}
+
+    def contract(self, out=None):
+        """Enqueue the contraction; returns the FP64 output (device tensor)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.output_size(), dtype=torch.float64, device=f"cuda:{self.device}")
+        self._check(self._L.qtpu_htn_contract(self._h, C.c_void_p(out.data_ptr())))
+        return out
+
+    def contract_host(self, host_arrays, out=None):
+        """End-to-end form: host arrays in (one per tensor, in add order),
+        host FP64 result out; copies happen inside the library call."""
+        import numpy as np
+        if out is None:
+            out = np.empty(self.output_size(), dtype=np.float64)
+        ptrs = (C.c_void_p * len(host_arrays))(*[a.ctypes.data if hasattr(a, "ctypes") else a.data_ptr()
+                                                for a in host_arrays])
+        self._check(self._L.qtpu_htn_contract_host(self._h, ptrs, C.c_void_p(out.ctypes.data)))
+        return out
+
+    def sync(self):
+        self._check(self._L.qtpu_htn_sync(self._h))
+
+    def close(self):
+        if self._h:
+            self._L.qtpu_htn_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def contract_batch(htns: Sequence[HTN], outs, stream: int | None = None):
+    L = lib()
+    hs = (C.c_void_p * len(htns))(*[h._h.value for h in htns])
+    ps = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+    st = L.qtpu_htn_contract_batch(hs, len(htns), ps, C.c_void_p(stream or 0))
+    if st != QTPU_OK:
+        raise QtpuError(st, "contract_batch failed")
+
+
+def plan_text(tensor_inds, dims: dict, output, max_intermediate_bytes=0, n_slices=0, slice_dim=0) -> str:
+    """Plan on a host-only handle and return the canonical plan text."""
+    h = HTN(device=-1)
+    for inds in tensor_inds:
+        h.add_tensor(inds, [dims[i] for i in inds])
+    h.set_output(output)
+    h.plan("fp64", max_intermediate_bytes, n_slices, slice_dim)
+    t = h.plan_info()
+    h.close()
+    return t
+
+
+def from_network(tensors, output, device: int = 0, prec: str = "bf16x3", stream: int | None = None,
+                 **plan_kw) -> HTN:
+    """Build and plan an HTN from (inds, device tensor, kind) triples."""
+    h = HTN(device, stream)
+    for t in tensors:
+        inds, data = t[0], t[1]
+        kind = t[2] if len(t) > 2 else QTPU_QT
+        h.add_tensor(inds, data=data, kind=kind)
+    h.set_output(output)
+    h.plan(prec, **plan_kw)
+    return h

@@ -67,12 +67,14 @@ class _Ids:
         return self.n - 1
 
 
-def _qt(rng, inds, dims, dtype):
+def _qt(rng, inds, dims, dtype, materialize=True):
     shape = tuple(dims[i] for i in inds)
+    if not materialize:  # structure only: a zero-stride view, no memory
+        return Tensor("QT", tuple(inds), np.broadcast_to(np.zeros((), dtype=dtype), shape))
     return Tensor("QT", tuple(inds), rng.uniform(-1.0, 1.0, size=shape).astype(dtype))
 
 
-def _edge_network(n_sub, edges, k, seed, dtype, name):
+def _edge_network(n_sub, edges, k, seed, dtype, name, materialize=True):
     """QTs joined by ``edges`` = list of (u, v, n_gate, n_wire); the wire
     index ``a`` sits on u (upstream), ``b`` on v (downstream)."""
     ids = _Ids()
@@ -99,7 +101,7 @@ def _edge_network(n_sub, edges, k, seed, dtype, name):
     tensors = []
     for j in range(n_sub):
         rng = np.random.default_rng([seed, j])
-        tensors.append(_qt(rng, qt_inds[j], dims, dtype))
+        tensors.append(_qt(rng, qt_inds[j], dims, dtype, materialize))
     tensors.extend(cts)
     out = (kid,) if kid is not None else ()
     return HTN(tensors, out, name=name,
@@ -125,14 +127,14 @@ def ring_htn(n_sub=8, gates_per_edge=2, wires_per_edge=1, k=64, seed=0,
 
 
 def ring_chords_htn(k=64, seed=0, dtype=np.float64, n_sub=12, n_chords=8,
-                    chord_step=3) -> HTN:
+                    chord_step=3, materialize=True) -> HTN:
     """The 100-qubit workload: 12 QTs on a ring (1 gate + 1 wire cut per ring
     edge) plus chords (i, i+3 mod 12) for i < 8 with 2 gate cuts each, i.e.
     28 gate cuts and 12 wire cuts; five QTs carry 47.8 M entries."""
     edges = [(j, (j + 1) % n_sub, 1, 1) for j in range(n_sub)]
     edges += [(i, (i + chord_step) % n_sub, 2, 0) for i in range(n_chords)]
     return _edge_network(n_sub, edges, k, seed, dtype,
-                         f"ring{n_sub}_chords{n_chords}_k{k}")
+                         f"ring{n_sub}_chords{n_chords}_k{k}", materialize)
 
 
 def random_htn(seed: int, n_sub_range=(2, 12), n_cuts_range=(2, 20),

@@ -1,0 +1,125 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry
+point the header declares, plans bit-exactly like the reference planner,
+and reports argument and state errors as status codes."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import planner
+from paper_2410_15080_b300 import build, htn
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+
+
+def test_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "qtpu_htn.h")).read()
+    declared = set(re.findall(r"\b(qtpu_\w+)\s*\(", hdr))
+    assert declared, "no declarations found"
+    L = htn.lib()
+    for name in declared:
+        assert hasattr(L, name), name
+    assert declared == set(htn.SYMBOLS)
+
+
+def _ref_text(net_inds, dims, output, **kw):
+    p = planner.make_plan(net_inds, dims, output, kw.get("max_intermediate_bytes", 0),
+                          kw.get("n_slices", 0), kw.get("slice_dim", 0))
+    return planner.plan_text(p, net_inds)
+
+
+CASES = [
+    ("ring8", lambda: synth.ring_htn(), {}),
+    ("ring4_sliced", lambda: synth.ring_htn(n_sub=4, gates_per_edge=1, wires_per_edge=1, k=8),
+     {"n_slices": 16, "slice_dim": 4}),
+    ("ring5_limit", lambda: synth.ring_htn(n_sub=5, gates_per_edge=1, wires_per_edge=2, k=3),
+     {"max_intermediate_bytes": 20000}),
+    ("chords100q", lambda: synth.ring_chords_htn(materialize=False), {}),
+    ("chords100q_sliced", lambda: synth.ring_chords_htn(materialize=False),
+     {"max_intermediate_bytes": 8 << 30, "n_slices": 1024, "slice_dim": 4}),
+]
+
+
+@pytest.mark.parametrize("name,make,kw", CASES, ids=[c[0] for c in CASES])
+def test_planner_bit_exact(name, make, kw):
+    net = make()
+    got = htn.plan_text(net.inds(), net.dims(), net.output, **kw)
+    assert got == _ref_text(net.inds(), net.dims(), net.output, **kw)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_planner_bit_exact_random(seed):
+    if seed < 20:
+        net = synth.tiny_random_htn(seed, n_tensors=3 + seed % 5, n_indices=4 + seed % 6,
+                                    n_output=seed % 3)
+    else:
+        net = synth.random_htn(seed)
+    got = htn.plan_text(net.inds(), net.dims(), net.output)
+    assert got == _ref_text(net.inds(), net.dims(), net.output)
+
+
+def test_status_codes():
+    h = htn.HTN(device=-1)
+    with pytest.raises(htn.QtpuError) as e:
+        h.plan()
+    assert e.value.status == htn.QTPU_ESTATE
+    h.add_tensor([0, 1], [2, 3])
+    with pytest.raises(htn.QtpuError) as e:
+        h.add_tensor([1], [4])  # dim mismatch for index 1
+    assert e.value.status == htn.QTPU_EINVAL
+    with pytest.raises(htn.QtpuError) as e:
+        h.add_tensor([2, 2], [2, 2])  # repeated id
+    assert e.value.status == htn.QTPU_EINVAL
+    with pytest.raises(htn.QtpuError) as e:
+        h.add_tensor([3], [0])
+    assert e.value.status == htn.QTPU_EINVAL
+    h.add_tensor([1, 2], [3, 5])
+    h.set_output([7])
+    with pytest.raises(htn.QtpuError) as e:
+        h.plan()  # output index on no tensor
+    assert e.value.status == htn.QTPU_EINVAL
+    h.close()
+
+    h = htn.HTN(device=-1)
+    h.add_tensor([0, 1], [2, 3])
+    h.add_tensor([1, 2], [3, 5])
+    h.set_output([0])
+    with pytest.raises(htn.QtpuError) as e:
+        h.plan(max_intermediate_bytes=8)  # cannot slice below one entry per step
+    assert e.value.status == htn.QTPU_ELIMIT
+    h.close()
+
+    h = htn.HTN(device=-1)
+    h.add_tensor([0, 1], [2, 3])
+    h.add_tensor([1, 2], [3, 5])
+    h.set_output([0, 2])
+    h.plan()
+    assert h.output_size() == 10
+    with pytest.raises(htn.QtpuError) as e:
+        h.add_tensor([4], [2])
+    assert e.value.status == htn.QTPU_ESTATE
+    L = htn.lib()
+    import ctypes as C
+    st = L.qtpu_htn_contract(h._h, C.c_void_p(1))
+    assert st == htn.QTPU_ENOTSUP
+    h.close()
+
+
+def test_overflow_is_enotsup():
+    # four tensors of 15 open indices of dim 60000 each, all kept: the
+    # result has 60000^60 entries, far beyond 2^255
+    h = htn.HTN(device=-1)
+    ids = list(range(60))
+    for t in range(4):
+        h.add_tensor(ids[15 * t:15 * t + 15] + [100], [60000] * 15 + [2])
+    h.set_output(ids)
+    with pytest.raises(htn.QtpuError) as e:
+        h.plan()
+    assert e.value.status == htn.QTPU_ENOTSUP

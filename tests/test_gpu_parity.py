@@ -1,0 +1,153 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances: the all-FP64 path matches to 1e-12 (summation order only);
+BF16x3 tensor-core steps to a normwise relative error of 1e-6; plain TF32
+is reported, not required to meet 1e-6 (10-bit mantissa)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import knit, qpd, tn
+from tests.gpu_util import FP64_TOL, REL_TOL, contract_gpu, oracle_value, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_15080_b300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_tiny_knitting_equals_uncut_statevector(seed, prec):
+    ang = np.random.default_rng(seed).uniform(0, 2 * np.pi, size=48)
+    exact = knit.uncut_expectation(ang)
+    TA, TB = knit.subcircuit_tensors(ang)
+    net = synth.HTN([synth.Tensor("QT", (0, 1), TA), synth.Tensor("QT", (0, 2), TB),
+                     synth.Tensor("CT", (0,), synth.GATE_CT.copy()),
+                     synth.Tensor("CT", (1, 2), synth.WIRE_CT.copy())], ())
+    got, _ = contract_gpu(net, prec=prec)
+    assert abs(got[0] - exact) <= 1e-12
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_tiny_random_hyper_networks(seed):
+    net = synth.tiny_random_htn(seed, n_tensors=3 + seed % 4, n_indices=5 + seed % 4, n_output=seed % 3)
+    ref = tn.brute_force(net.pairs(), net.output).ravel()
+    got, _ = contract_gpu(net, prec="bf16x3")
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-13)
+
+
+def test_single_tensor_and_disconnected():
+    rng = np.random.default_rng(1)
+    A = rng.uniform(-1, 1, (3, 4, 5))
+    net = synth.HTN([synth.Tensor("QT", (0, 1, 2), A)], (1,))
+    got, _ = contract_gpu(net)
+    np.testing.assert_allclose(got, A.sum(axis=(0, 2)), rtol=1e-13)
+    B = rng.uniform(-1, 1, (6,))
+    net = synth.HTN([synth.Tensor("QT", (0, 1, 2), A), synth.Tensor("QT", (3,), B)], (3, 1))
+    got, _ = contract_gpu(net)
+    np.testing.assert_allclose(got.reshape(6, 4), np.outer(B, A.sum(axis=(0, 2))), rtol=1e-13)
+
+
+GEMM_SHAPES = [(1, 128, 128, 128), (3, 300, 200, 333), (2, 64, 32, 32), (5, 144, 144, 144),
+               (1, 513, 257, 1000), (7, 96, 40, 72)]
+
+
+@pytest.mark.parametrize("shape", GEMM_SHAPES, ids=[str(s) for s in GEMM_SHAPES])
+@pytest.mark.parametrize("prec", ["bf16x3", "3xtf32", "tf32"])
+def test_pairwise_gemm_shapes(shape, prec):
+    """One pairwise step C[b,m,n] = sum_k A[b,m,k] B[b,k,n]: tiles, ragged
+    M/N/K tails, several batches."""
+    b, m, n, k = shape
+    rng = np.random.default_rng(sum(shape))
+    A = rng.uniform(-1, 1, (b, m, k))
+    B = rng.uniform(-1, 1, (b, k, n))
+    net = synth.HTN([synth.Tensor("QT", (0, 1, 3), A), synth.Tensor("QT", (0, 3, 2), B)], (0, 1, 2))
+    got, st = contract_gpu(net, prec=prec)
+    ref = np.matmul(A, B).ravel()
+    err = rel_err(got, ref)
+    tol = {"bf16x3": REL_TOL, "3xtf32": 1e-5, "tf32": 1e-2}[prec]
+    assert err <= tol, (err, st)
+    if m >= 64 and b * m * n * k >= 1 << 22:
+        assert st["n_tensor_core_steps"] == 1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_ring_small_with_tails(prec):
+    # bond 144 (two gate cuts and a wire cut per edge): M, N and K are 144,
+    # ragged against the 128-row tiles and 64-wide k-blocks
+    net = synth.ring_htn(n_sub=4, gates_per_edge=2, wires_per_edge=1, k=3, seed=5)
+    ref = oracle_value(net)
+    got, st = contract_gpu(net, prec=prec)
+    err = rel_err(got, ref)
+    assert err <= (FP64_TOL if prec == "fp64" else REL_TOL), err
+    if prec == "bf16x3":
+        assert st["n_tensor_core_steps"] >= 1
+
+
+def test_mid_ring_bf16x3():
+    """The mid-size workload (8 QTs of [64][144][144], 16 gate + 8 wire cuts)."""
+    net = synth.ring_htn()
+    ref = oracle_value(net)
+    got, st = contract_gpu(net, prec="bf16x3")
+    err = rel_err(got, ref)
+    print("mid ring bf16x3 rel err", err, st)
+    assert err <= REL_TOL
+    assert st["n_tensor_core_steps"] == 6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32", "3xtf32"])
+def test_mid_ring_other_precisions(prec):
+    net = synth.ring_htn()
+    ref = oracle_value(net)
+    got, _ = contract_gpu(net, prec=prec)
+    err = rel_err(got, ref)
+    print(f"mid ring {prec} rel err", err)
+    bound = {"fp64": FP64_TOL, "3xtf32": 1e-4, "tf32": 0.5}[prec]
+    assert err <= bound
+
+
+def test_sliced_equals_unsliced():
+    net = synth.ring_htn(n_sub=4, gates_per_edge=2, wires_per_edge=1, k=5, seed=2)
+    ref = oracle_value(net)
+    got, st = contract_gpu(net, prec="bf16x3", n_slices=16, slice_dim=4)
+    assert rel_err(got, ref) <= REL_TOL
+    got64, _ = contract_gpu(net, prec="fp64", n_slices=64, slice_dim=6)
+    assert rel_err(got64, ref) <= FP64_TOL
+
+
+def test_fp32_leaves():
+    net = synth.ring_htn(n_sub=4, gates_per_edge=2, wires_per_edge=1, k=3, seed=9, dtype=np.float32)
+    ref = oracle_value(net)
+    got, _ = contract_gpu(net, prec="bf16x3")
+    assert rel_err(got, ref) <= REL_TOL
+
+
+def test_contract_host_matches_device_path():
+    import torch
+    from paper_2410_15080_b300 import from_network
+    from tests.gpu_util import to_device
+    net = synth.ring_htn(n_sub=4, gates_per_edge=2, wires_per_edge=1, k=4, seed=11)
+    dev = to_device(net)
+    h = from_network(dev, net.output, prec="bf16x3")
+    d = h.contract().cpu().numpy()
+    host = [torch.from_numpy(np.ascontiguousarray(t.data)).pin_memory() for t in net.tensors]
+    for x in dev:  # clobber the device copies: contract_host must upload
+        x[1].zero_()
+    got = h.contract_host(host)
+    h.close()
+    np.testing.assert_array_equal(got, d)
+    assert rel_err(got, oracle_value(net)) <= REL_TOL
+
+
+def test_deterministic_repeat():
+    net = synth.ring_htn(n_sub=4, gates_per_edge=2, wires_per_edge=1, k=8, seed=4)
+    a, _ = contract_gpu(net)
+    b, _ = contract_gpu(net)
+    np.testing.assert_array_equal(a, b)
