@@ -5,10 +5,14 @@
 // batched GEMM  C[b, m, n] = sum_k A[b, m, k] * B[b, n, k]  (both operands
 // K-major).  FP64 operands are split into low-precision pieces by the split
 // kernel (x = x0 + x1 + x2, BF16 or TF32 pieces); the products of the pieces
-// whose combined weight is at or above 2^-16 (BF16x3: 6 products) or 2^-22
-// (3xTF32: 3 products) accumulate in FP32 in TMEM, and the epilogue adds each
-// accumulation chunk into FP64 in the output, so the FP32 accumulation error
-// is bounded by the chunk length rather than by K.
+// whose combined weight is at or above 2^-16 (BF16x3: 6 products) or 2^-11
+// (3xTF32: 3 products) accumulate in FP32 in TMEM.  The tensor cores'
+// FP32 accumulation loses precision with every MMA added into an accumulator
+// (measured: the error grows linearly with K), so (1) the leading product
+// x0*y0 has its own accumulator X and the smaller cross terms share Y, and
+// (2) both are drained every k-block (BF16x3: 64 K) and accumulated with
+// compensated (TwoSum) FP32 arithmetic in the epilogue's registers; FP64 math
+// is avoided in the drain (FP64 throughput on B300 is ~1/64 of FP32).
 //
 // One CTA per SM, persistent over (batch, m-tile, n-tile) tiles:
 //   warp 0      TMA producer (one lane): pieces of A and B for one k-block
@@ -17,7 +21,10 @@
 //               K-steps x the product list, into one of two TMEM
 //               accumulators (double-buffered so the epilogue of one chunk
 //               overlaps the MMAs of the next);
-//   warps 2..5  epilogue: tcgen05.ld 32 lanes x 16 columns, FP64 add/store.
+//   warps 2..17 epilogue: tcgen05.ld 32 lanes x 8 columns of both
+//               accumulators, chunk value X + Y accumulated with TwoSum into
+//               a float plus a BF16 error term per output in registers, FP64
+//               store at the end of the tile.
 // Every wait is bounded (global timer); on give-up the kernel sets a status
 // bit, lets in-flight copies and MMAs land, frees TMEM and returns.
 #include <cstdio>
@@ -31,26 +38,31 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BN = 128;
-constexpr int kThreads = 192;
-constexpr int kRowBytes = 128;  // one swizzle row: 64 BF16 or 32 TF32
+constexpr int kEpiWarps = 16;
+constexpr int kEpiCols = BN / (kEpiWarps / 4);  // columns per epilogue thread
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer, MMA, 16 epilogue warps
+constexpr int kRowBytes = 128;                 // one swizzle row: 64 BF16 or 32 TF32
+constexpr uint32_t kTmemCols = 512;            // 2 buffers x (X, Y) x BN columns
 
+// Product list: entry 0 is the leading product x0*y0 (accumulator X), the
+// rest are the cross terms (accumulator Y, a factor 2^-8 or 2^-11 smaller).
 template <int PREC>
 struct Cfg;
 template <>
-struct Cfg<3> {  // BF16x3
-  static constexpr int NP = 3, NPROD = 6, ES = 2, KB = 64, UK = 16, FMT = 1, STAGES = 2;
+struct Cfg<3> {  // BF16x3: pieces of 8 significant bits, products of weight >= 2^-16
+  static constexpr int NP = 3, NPROD = 6, ES = 2, KB = 64, UK = 16, FMT = 1, STAGES = 2, KC = 1;
   __device__ static int pa(int i) { const int t[6] = {0, 0, 1, 0, 1, 2}; return t[i]; }
   __device__ static int pb(int i) { const int t[6] = {0, 1, 0, 2, 1, 0}; return t[i]; }
 };
 template <>
-struct Cfg<2> {  // 3xTF32
-  static constexpr int NP = 2, NPROD = 3, ES = 4, KB = 32, UK = 8, FMT = 2, STAGES = 3;
+struct Cfg<2> {  // 3xTF32: pieces of 11 significant bits, products of weight >= 2^-11
+  static constexpr int NP = 2, NPROD = 3, ES = 4, KB = 32, UK = 8, FMT = 2, STAGES = 3, KC = 2;
   __device__ static int pa(int i) { const int t[3] = {0, 0, 1}; return t[i]; }
   __device__ static int pb(int i) { const int t[3] = {0, 1, 0}; return t[i]; }
 };
 template <>
-struct Cfg<1> {  // TF32
-  static constexpr int NP = 1, NPROD = 1, ES = 4, KB = 32, UK = 8, FMT = 2, STAGES = 4;
+struct Cfg<1> {  // TF32: one piece, one product
+  static constexpr int NP = 1, NPROD = 1, ES = 4, KB = 32, UK = 8, FMT = 2, STAGES = 4, KC = 8;
   __device__ static int pa(int) { return 0; }
   __device__ static int pb(int) { return 0; }
 };
@@ -72,10 +84,32 @@ __device__ __forceinline__ void set_abort(volatile int* abort, uint32_t* status,
   if (status) atomicOr(status, bit);
 }
 
+// hi + lo += v: TwoSum (Knuth) gives the exact rounding error e of hi + v;
+// e is added to lo.  lo is a running sum of such errors (|lo| << |hi|), so
+// it is kept as BF16 (8 significant bits are plenty) in packed pairs.
+__device__ __forceinline__ float two_sum_err(float& hi, float v) {
+  const float s = __fadd_rn(hi, v);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+  hi = s;
+  return e;
+}
+__device__ __forceinline__ uint32_t lo_add(uint32_t lo2, float e0, float e1) {
+  const float l0 = __uint_as_float(lo2 << 16) + e0;
+  const float l1 = __uint_as_float(lo2 & 0xffff0000u) + e1;
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(l1), "f"(l0));
+  return r;
+}
+__device__ __forceinline__ float lo_get(uint32_t lo2, int half) {
+  return half ? __uint_as_float(lo2 & 0xffff0000u) : __uint_as_float(lo2 << 16);
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, double* __restrict__ Cout,
-              int batch, int M, int N, int K, int kc_blocks, uint32_t* status, uint64_t limit_ns) {
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              double* __restrict__ Cout, int batch, int M, int N, int K, int kc_blocks, uint32_t* status,
+              uint64_t limit_ns) {
   using C = Cfg<PREC>;
   using L = Layout<PREC>;
   extern __shared__ uint8_t smem_raw[];
@@ -94,7 +128,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
   const long long n_tiles = (long long)batch * mt * nt;
   const int nkb = (K + C::KB - 1) / C::KB;
-  const int kc = (kc_blocks > 0 && kc_blocks < nkb) ? kc_blocks : nkb;
+  const int kc0 = kc_blocks > 0 ? kc_blocks : C::KC;
+  const int kc = kc0 < nkb ? kc0 : nkb;
   const int nchunks = (nkb + kc - 1) / kc;
 
   if (threadIdx.x == 0) {
@@ -104,14 +139,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&accfull[a], 1);
-      mbar_init(&accempty[a], 4);
+      mbar_init(&accempty[a], kEpiWarps);
     }
     mbar_init(mma_done, 1);
     *abort = 0;
     mbar_fence_init();
   }
   if (warp == 1) {
-    tmem_alloc(tmem_holder, 2 * BN);
+    tmem_alloc(tmem_holder, kTmemCols);
     tmem_relinquish();
   }
   if (warp == 0 && lane == 0) {
@@ -182,7 +217,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t dt = tmem + (uint32_t)(acc * BN);
+          const uint32_t dX = tmem + (uint32_t)(acc * 2 * BN);
+          const uint32_t dY = dX + BN;
           const int kb0 = ch * kc, kb1 = min(nkb, kb0 + kc);
           for (int kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait_bounded(&full[stage], phase, limit_ns, abort)) {
@@ -195,15 +231,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t sB = sA + C::NP * L::A_PIECE;
 #pragma unroll
             for (int kk = 0; kk < C::KB / C::UK; ++kk) {
+              const bool first = (kb == kb0 && kk == 0);
 #pragma unroll
               for (int pr = 0; pr < C::NPROD; ++pr) {
                 const uint64_t ad = smem_desc_sw128(sA + C::pa(pr) * L::A_PIECE + kk * C::UK * C::ES);
                 const uint64_t bd = smem_desc_sw128(sB + C::pb(pr) * L::B_PIECE + kk * C::UK * C::ES);
-                const uint32_t accum = (kb > kb0 || kk > 0 || pr > 0) ? 1u : 0u;
+                const uint32_t accum = (first && pr <= 1) ? 0u : 1u;
+                const uint32_t d = pr == 0 ? dX : dY;
                 if (C::FMT == 1)
-                  umma_f16(dt, ad, bd, idesc, accum);
+                  umma_f16(d, ad, bd, idesc, accum);
                 else
-                  umma_tf32(dt, ad, bd, idesc, accum);
+                  umma_tf32(d, ad, bd, idesc, accum);
               }
             }
             umma_commit(&empty[stage]);
@@ -221,16 +259,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // -------------------------------------------------------------- epilogue
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    // warp w owns TMEM lane quarter (w % 4) and column group h of the tile;
+    // each thread keeps one row's kEpiCols columns as float + BF16 errors
+    const int ew = warp - 2;
+    const int q = warp & 3;
+    const int h = ew >> 2;
     long long item = 0;
     bool ok = true;
+    float hi[kEpiCols];
+    uint32_t lo2[kEpiCols / 2];
     for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
       const int ntile = (int)(t % nt);
       const long long r = t / nt;
       const int mtile = (int)(r % mt);
       const int b = (int)(r / mt);
-      const int row = mtile * BM + q * 32 + lane;
-      double* crow = Cout + ((long long)b * M + row) * (long long)N;
+#pragma unroll
+      for (int j = 0; j < kEpiCols; ++j) hi[j] = 0.f;
+#pragma unroll
+      for (int j = 0; j < kEpiCols / 2; ++j) lo2[j] = 0u;
       for (int ch = 0; ch < nchunks; ++ch, ++item) {
         const int acc = (int)(item & 1);
         const uint32_t aph = (uint32_t)((item >> 1) & 1);
@@ -242,26 +288,37 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
-#pragma unroll 1
-        for (int c = 0; c < BN / 16; ++c) {
-          float v[16];
-          tmem_ld16(ta + c * 16, v);
-          const int n0 = ntile * BN + c * 16;
-          if (row < M) {
+        const uint32_t tX = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 2 * BN + h * kEpiCols);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int n = n0 + j;
-              if (n < N) {
-                const double prev = ch ? crow[n] : 0.0;
-                crow[n] = prev + (double)v[j];
-              }
-            }
+        for (int c = 0; c < kEpiCols / 8; ++c) {
+          float vx[8], vy[8];
+          tmem_ld8(tX + c * 8, vx);
+          if (C::NPROD > 1) {
+            tmem_ld8(tX + BN + c * 8, vy);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) vy[j] = 0.f;
+          }
+#pragma unroll
+          for (int j = 0; j < 8; j += 2) {
+            // X + Y of this chunk in one FP32 rounding, then exact accumulation
+            const float e0 = two_sum_err(hi[c * 8 + j], __fadd_rn(vx[j], vy[j]));
+            const float e1 = two_sum_err(hi[c * 8 + j + 1], __fadd_rn(vx[j + 1], vy[j + 1]));
+            lo2[(c * 8 + j) >> 1] = lo_add(lo2[(c * 8 + j) >> 1], e0, e1);
           }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&accempty[acc]);
+      }
+      if (!ok) break;
+      const int row = mtile * BM + q * 32 + lane;
+      if (row < M) {
+        double* crow = Cout + ((long long)b * M + row) * (long long)N;
+        const int n0 = ntile * BN + h * kEpiCols;
+#pragma unroll
+        for (int j = 0; j < kEpiCols; ++j)
+          if (n0 + j < N) crow[n0 + j] = (double)hi[j] + (double)lo_get(lo2[j >> 1], j & 1);
       }
     }
   }
@@ -271,19 +328,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   if (warp == 1) {
     __syncwarp();
-    tmem_dealloc(tmem, 2 * BN);
+    tmem_dealloc(tmem, kTmemCols);
   }
 }
 
 template <int PREC>
 cudaError_t launch_t(const GemmArgs& a, int sm_count, cudaStream_t st) {
   using L = Layout<PREC>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+  if (e != cudaSuccess) return e;
   const long long tiles = (long long)a.batch * ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
   if (tiles <= 0) return cudaSuccess;
   const int grid = (int)(tiles < sm_count ? tiles : sm_count);
