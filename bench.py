@@ -1,0 +1,396 @@
+"""Benchmark of the h-TN contraction hot path (one JSON line on stdout).
+
+Default workload: the mid-size 60-qubit ring h-TN (8 QTs of [64][144][144]
+FP64, 16 gate cuts + 8 wire cuts, 64 observables) contracted through the
+C ABI with BF16x3 tensor-core GEMMs.  Reported next to it:
+  * the same plan executed step by step with torch FP64 bmm (the plain FP64
+    GPU path), timed the same way;
+  * the FP64 CPU oracle on the host cores (``cpu_baseline``);
+  * the end-to-end form through ``qtpu_htn_contract_host`` (host buffers,
+    copies inside the timed region);
+  * the roofline of the dominant kernel class, from CUDA events recorded by
+    the library around every launch (a separate pass after the timed one);
+  * SM clocks sampled with nvidia-smi during the timed region.
+
+``--impl reference`` times the FP64 CPU oracle alone (the reference arm).
+Multi-GPU (torchrun): every rank contracts its own copy of the workload
+(independent replicas, weak scaling); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "h-TN contract TFLOP/s & %peak vs plain FP64 GPU path at rel err ≤1e-6"
+WORKLOADS = {
+    "mid": "mid-size 60-qubit ring h-TN: 8 QTs [k=64][6,6,4][6,6,4] FP64, 16 gate + 8 wire cuts, 32 tensors",
+    "100q": "100-qubit ring+chords h-TN: 12 QTs, 28 gate + 12 wire cuts, k=64, sliced over 4^5 wire-index values",
+}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]), "src": "measured"}
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "src": "fallback"}
+
+
+def make_network(workload: str):
+    import synth
+    if workload == "mid":
+        return synth.ring_htn(), {}
+    if workload == "100q":
+        return synth.ring_chords_htn(), {"max_intermediate_bytes": 8 << 30, "n_slices": 1024, "slice_dim": 4}
+    raise SystemExit(f"unknown workload {workload}")
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.dev = device_index
+
+    def __enter__(self):
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(self.dev)
+            bus = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", bus, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- plain FP64 GPU path
+def parse_plan(text: str):
+    steps, final_sum = [], []
+    for line in text.splitlines():
+        f = line.split()
+        if f[0] == "step":
+            kv = dict(x.split("=") for x in f[6:])
+            g = {k: ([] if v == "-" else [int(i) for i in v.split(",")]) for k, v in kv.items()
+                 if k in ("batch", "m", "n", "k", "sa", "sb")}
+            steps.append((int(f[2]), int(f[3]), g))
+        elif f[0] == "final":
+            v = f[2].split("=")[1]
+            final_sum = [] if v == "-" else [int(i) for i in v.split(",")]
+    return steps, final_sum
+
+
+def fp64_torch_path(tensors, output, steps, final_sum):
+    """The same pairwise plan with torch FP64 ops: permute + bmm per step."""
+    import torch
+    live = {t: (list(inds), x) for t, (inds, x) in enumerate(tensors)}
+    nxt = len(tensors)
+    for x, y, g in steps:
+        ia, a = live.pop(x)
+        ib, b = live.pop(y)
+        if g["sa"]:
+            a = a.sum(dim=[ia.index(i) for i in g["sa"]])
+            ia = [i for i in ia if i not in g["sa"]]
+        if g["sb"]:
+            b = b.sum(dim=[ib.index(i) for i in g["sb"]])
+            ib = [i for i in ib if i not in g["sb"]]
+        da = dict(zip(ia, a.shape))
+        db = dict(zip(ib, b.shape))
+        nb = int(np.prod([da[i] for i in g["batch"]], dtype=np.int64))
+        nm = int(np.prod([da[i] for i in g["m"]], dtype=np.int64))
+        nn = int(np.prod([db[i] for i in g["n"]], dtype=np.int64))
+        nk = int(np.prod([da[i] for i in g["k"]], dtype=np.int64))
+        A3 = a.permute([ia.index(i) for i in g["batch"] + g["m"] + g["k"]]).reshape(nb, nm, nk)
+        B3 = b.permute([ib.index(i) for i in g["batch"] + g["k"] + g["n"]]).reshape(nb, nk, nn)
+        c = torch.bmm(A3, B3)
+        shape = [da[i] for i in g["batch"] + g["m"]] + [db[i] for i in g["n"]]
+        live[nxt] = (g["batch"] + g["m"] + g["n"], c.reshape(shape))
+        nxt += 1
+    (inds, x), = live.values()
+    if final_sum:
+        x = x.sum(dim=[inds.index(i) for i in final_sum])
+        inds = [i for i in inds if i not in final_sum]
+    return x.permute([inds.index(i) for i in output]).reshape(-1) if output else x.reshape(1)
+
+
+# ----------------------------------------------------------------- timing helpers
+def timed_steps(fn, steps, flush):
+    """Per-step CUDA-event timing on the current stream; L2 flushed between
+    steps outside the timed events.  Returns the list of ms."""
+    import torch
+    ts = []
+    for _ in range(steps):
+        flush()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s.record()
+        fn()
+        e.record()
+        torch.cuda.synchronize()
+        ts.append(s.elapsed_time(e))
+    return ts
+
+
+def oracle_seconds(net, budget_s: float):
+    """Time the FP64 CPU oracle contracting the workload (full contractions
+    repeated until the budget is used).  Returns (seconds per contraction,
+    repetitions, threads)."""
+    from oracle import planner, tn
+    p = planner.make_plan(net.inds(), net.dims(), net.output)
+    order = planner.order_of(p)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        tn.contract_pairwise(net.pairs(), net.output, order)
+        reps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+    except Exception:
+        threads = os.cpu_count()
+    return dt, reps, threads
+
+
+def cpu_model():
+    try:
+        for l in open("/proc/cpuinfo"):
+            if l.startswith("model name"):
+                return l.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+# ----------------------------------------------------------------- arms
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 CPU oracle, timed on the host cores."""
+    if rank != 0:
+        return
+    net, _ = make_network(args.workload)
+    if args.workload != "mid":
+        print(json.dumps({"impl": "reference", "unavailable": "the FP64 CPU oracle needs >1e14 FLOP on this workload"}))
+        return
+    from oracle import planner
+    flops = int(planner.plan_text(planner.make_plan(net.inds(), net.dims(), net.output), net.inds())
+                .split("flops_total=")[1].split()[0])
+    for _ in range(args.warmup):
+        oracle_seconds(net, 0.0)
+    ts = [oracle_seconds(net, 0.0)[0] for _ in range(args.steps)]
+    _, _, threads = oracle_seconds(net, 0.0)
+    ms = 1e3 * statistics.mean(ts)
+    val = flops / (ms * 1e-3) / 1e12
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "flops_per_step": flops, "l2": "n/a (host)"},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} full contractions of the workload, numpy FP64 on {cpu_model()}"},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args, rank, world):
+    import torch
+    import torch.distributed as dist
+    from paper_2410_15080_b300 import from_network
+    from paper_2410_15080_b300.htn import QTPU_CT, QTPU_QT
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    net, plan_kw = make_network(args.workload)
+    tensors = [(t.inds, torch.from_numpy(np.ascontiguousarray(t.data)).to(dev), QTPU_CT if t.kind == "CT" else QTPU_QT)
+               for t in net.tensors]
+    h = from_network(tensors, net.output, prec=args.prec, **plan_kw)
+    st = h.plan_stats()
+    flops = st["flops_total"]
+    out = torch.empty(h.output_size(), dtype=torch.float64, device=dev)
+    flush_buf = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    flush = (lambda: flush_buf.zero_()) if net.nbytes() < (256 << 20) else (lambda: None)
+
+    for _ in range(args.warmup):
+        h.contract(out)
+    h.sync()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    with ClockSampler(dev.index) as clk:
+        ts = timed_steps(lambda: h.contract(out), args.steps, flush)
+        if world > 1:
+            dist.barrier()
+    h.sync()
+    tot = torch.tensor([sum(ts)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    ms = tot.item() / args.steps
+    value = world * flops / (ms * 1e-3) / 1e12
+
+    # per-kernel-class timing (separate pass, same launches)
+    h.profile(True)
+    for _ in range(args.steps):
+        flush()
+        h.contract(out)
+    prof = h.profile_read()
+    h.profile(False)
+
+    # parity of this run's output against the FP64 oracle (mid workload)
+    rel = None
+    if args.workload == "mid" and rank == 0:
+        from oracle import planner, tn
+        p = planner.make_plan(net.inds(), net.dims(), net.output)
+        ref = tn.contract_pairwise(net.pairs(), net.output, planner.order_of(p)).ravel()
+        got = out.cpu().numpy()
+        rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+    # plain FP64 GPU path: same plan, torch FP64 ops, one launch per step
+    fp64 = None
+    if args.workload == "mid":
+        steps, final_sum = parse_plan(h.plan_info())
+        t64 = [(list(i), x.double()) for i, x, _ in tensors]
+        for _ in range(2):
+            fp64_torch_path(t64, list(net.output), steps, final_sum)
+        ts64 = timed_steps(lambda: fp64_torch_path(t64, list(net.output), steps, final_sum),
+                           max(3, min(args.steps, 10)), flush)
+        ms64 = statistics.mean(ts64)
+        fp64 = {"value": flops / (ms64 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms64,
+                "impl": "torch FP64 permute+bmm per planned step", "speedup_of_ours": ms64 / ms}
+
+    # end to end through the C ABI with host buffers
+    host = [torch.from_numpy(np.ascontiguousarray(t.data)).pin_memory() for t in net.tensors]
+    hout = np.empty(h.output_size(), dtype=np.float64)
+    h.contract_host(host, hout)
+    te = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.contract_host(host, hout)
+        te.append(time.perf_counter() - t0)
+    e2e_ms = 1e3 * statistics.mean(te)
+    h2d = sum(x.numel() * x.element_size() for x in host)
+
+    peaks = load_peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    per_launch_ms = d["ms"] / max(d["launches"], 1)
+    if dom == "gemm":
+        ratio = {"bf16x3": 6, "3xtf32": 6, "tf32": 2}.get(args.prec, 6)  # bf16-MMA equivalents per useful FMA
+        peak = peaks["bf16_tflops"] / ratio
+        achieved = d["flops"] / d["launches"] / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_gemm_tc",
+                "peak_note": f"{peaks['src']} bf16 burst / {ratio} (useful FLOPs of {args.prec})"}
+    else:
+        achieved = d["bytes"] / d["launches"] / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": dom,
+                "peak_note": f"{peaks['src']} copy bandwidth"}
+    roof["per_launch_ms"] = per_launch_ms
+    roof["launches_per_step"] = d["launches"] / args.steps
+    roof["classes"] = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
+                       for k, v in prof.items()}
+
+    cpu = None
+    if rank == 0 and world == 1 and args.workload == "mid":
+        sec, reps, threads = oracle_seconds(net, args.cpu_budget)
+        cpu = {"value": flops / sec / 1e12, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+               "sample": f"{reps} full contractions of the workload in {reps * sec:.1f} s, numpy FP64 on "
+                         f"{cpu_model()} ({os.cpu_count()} host cores)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "flops_per_step": flops, "prec": args.prec,
+                   "l2": "flushed between timed steps (256 MiB write)" if net.nbytes() < (256 << 20)
+                   else "inputs larger than L2", "plan_steps": st["n_steps"],
+                   "tensor_core_steps": st["n_tensor_core_steps"], "parallelism": f"replicas x{world}"},
+        "rel_err_vs_oracle": rel,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "fp64_gpu_path": fp64,
+        "e2e": {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h.output_size() * 8},
+        "gpu_launches": st["launches_per_contract"] * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    h.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "3xtf32", "tf32", "fp64"])
+    ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle time for cpu_baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

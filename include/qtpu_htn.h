@@ -120,10 +120,34 @@ qtpu_status qtpu_htn_plan_info(const qtpu_htn* h, char* buf, size_t len,
 qtpu_status qtpu_htn_output_size(const qtpu_htn* h, int64_t* n);
 
 /* Useful FLOPs of the planned contraction (2 per multiply-add, all slices),
- * as a double, and the number of steps that run on the tensor cores. */
+ * as a double; the number of pairwise steps and of steps that run on the
+ * tensor cores; the device workspace the handle owns; and the number of
+ * kernel launches one contract call makes.  Any pointer may be NULL. */
 qtpu_status qtpu_htn_plan_stats(const qtpu_htn* h, double* flops_total,
                                 int* n_steps, int* n_tensor_core_steps,
-                                uint64_t* workspace_bytes);
+                                uint64_t* workspace_bytes,
+                                int64_t* launches_per_contract);
+
+/* Kernel classes reported by qtpu_htn_profile_read. */
+typedef enum {
+  QTPU_K_CONTRACT = 0, /* FP64 pairwise step on the CUDA cores            */
+  QTPU_K_SPLIT = 1,    /* operand gather + split into tensor-core pieces  */
+  QTPU_K_GEMM = 2,     /* tcgen05 batched GEMM                            */
+  QTPU_K_REDUCE = 3,   /* slice sum / final reduction                     */
+  QTPU_K_COUNT = 4
+} qtpu_kernel_class;
+
+/* Enable (1) or disable (0) timing of every launch with CUDA events recorded
+ * on the handle's stream around it.  Off by default. */
+qtpu_status qtpu_htn_profile(qtpu_htn* h, int enable);
+
+/* Wait for the stream, then return per kernel class (arrays of n entries,
+ * n <= QTPU_K_COUNT, indexed by qtpu_kernel_class) the summed device time in
+ * ms, the launch count, the useful FLOPs and the algorithmic bytes (each
+ * operand read once, each result written once) of the launches timed since
+ * the last read, and reset the counters.  Any array may be NULL. */
+qtpu_status qtpu_htn_profile_read(qtpu_htn* h, int n, double* ms, int64_t* launches,
+                                  double* flops, double* bytes);
 
 /* Contract: enqueue the whole contraction on the handle's stream and write
  * the FP64 result (output_size entries) to the device buffer dev_out.

@@ -179,9 +179,10 @@ qtpu_status qtpu_htn_output_size(const qtpu_htn* h, int64_t* n) {
 }
 
 qtpu_status qtpu_htn_plan_stats(const qtpu_htn* h, double* flops_total, int* n_steps, int* n_tc,
-                                uint64_t* ws) {
+                                uint64_t* ws, int64_t* launches) {
   if (!h) return QTPU_EINVAL;
   if (!h->planned) return QTPU_ESTATE;
+  if (launches) *launches = h->built ? h->ex.launches_per_contract : 0;
   if (flops_total) *flops_total = h->plan.flops_total.to_double();
   if (n_steps) *n_steps = (int)h->plan.steps.size();
   if (n_tc) *n_tc = h->built ? h->ex.n_tc_steps : 0;
@@ -257,6 +258,31 @@ qtpu_status qtpu_htn_contract_batch(qtpu_htn* const* hs, int n, double* const* d
     int code = QTPU_OK;
     std::string m = exec_run(&h->ex, h->leaves, dev_out[i], st, &code);
     if (code != QTPU_OK) return fail(h, (qtpu_status)code, m);
+  }
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_profile(qtpu_htn* h, int enable) {
+  if (!h) return QTPU_EINVAL;
+  h->ex.prof.on = enable != 0;
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_profile_read(qtpu_htn* h, int n, double* ms, int64_t* launches, double* flops,
+                                  double* bytes) {
+  if (!h || n < 0 || n > KC_COUNT) return QTPU_EINVAL;
+  if (h->host_only || !h->built) return fail(h, QTPU_ESTATE, "nothing to read");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
+  double m[KC_COUNT], f[KC_COUNT], b[KC_COUNT];
+  int64_t l[KC_COUNT];
+  std::string err = exec_profile_read(&h->ex, m, l, f, b);
+  if (!err.empty()) return fail(h, QTPU_ECUDA, err);
+  for (int k = 0; k < n; ++k) {
+    if (ms) ms[k] = m[k];
+    if (launches) launches[k] = l[k];
+    if (flops) flops[k] = f[k];
+    if (bytes) bytes[k] = b[k];
   }
   return QTPU_OK;
 }

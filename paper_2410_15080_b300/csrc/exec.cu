@@ -1,23 +1,35 @@
-// Executor: lowers a contraction plan to kernel launches.
+// Executor: lowers a contraction plan to a flat list of kernel launches.
 //
 // Section 6.1 step 4 contracts the evaluated classical TN on the available
-// accelerator.  Each planned pairwise step becomes either
-//   * a tensor-core step (large dense GEMM): two split kernels gather the
-//     operands into [batch][rows][K] piece planes, then the tcgen05 GEMM
-//     writes the FP64 result [batch][M][N]; or
-//   * a generic FP64 step (CT absorption, dot products, skinny shapes).
-// Intermediates live in one device arena laid out at build time (first-fit
-// over the steps' lifetimes).  Slices (fixed values of the sliced indices)
-// run one after another through the same launches with shifted leaf
-// pointers; each slice's final tensor lands in partial[slice], and one FP64
-// reduction sums the slices (and any leftover indices) in a fixed order into
-// the output.
+// accelerator.  With a tensor-core precision each planned pairwise step
+// becomes one of:
+//   * absorbed: a step that contracts a tensor with a small leaf (a QPD
+//     coefficient tensor, section 4.1; or any leaf of <= 256 entries) is not
+//     run on its own; the result stays a "virtual" tensor (base operands +
+//     small factors + internal summed indices) and the step that consumes it
+//     gathers the product on the fly (the h-TN simplification of section 4.3
+//     fuses the CTs between two QTs; here they are fused into the QT read);
+//   * tensor-core step (large dense GEMM): two gather-split launches lay the
+//     operands out as [batch][rows][K] piece planes, then the tcgen05 GEMM
+//     writes the result [batch][M][N] as (hi, lo) float pairs;
+//   * gather step: everything else (dot products, skinny or small steps),
+//     one multi-operand gather kernel with compensated FP32 arithmetic.
+// With QTPU_PREC_FP64 every step is an FP64 CUDA-core contraction and
+// intermediates are FP64.  Intermediates live in one device arena laid out at
+// build time (first-fit over the steps' lifetimes).  Slices (fixed values of
+// the sliced indices) run one after another through the same launches with
+// shifted leaf pointers; each slice's final tensor lands in partial[slice],
+// and one reduction sums the slices (and any leftover indices) in a fixed
+// order into the FP64 output.
 #include <algorithm>
+#include <climits>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <map>
 #include <set>
 #include <sstream>
+#include <unordered_map>
 
 #include "exec.h"
 #include "../../include/qtpu_htn.h"
@@ -148,157 +160,291 @@ bool make_operand_map(CUtensorMap* map, void* base, int prec, int64_t batch, int
   return r == CUDA_SUCCESS;
 }
 
+namespace {
+
+constexpr int64_t kSmallLeaf = 256;   // leaves up to this size are absorbed
+constexpr int kMaxVirtualOps = 4;     // operands of one virtual tensor
+constexpr int64_t kMaxVirtualLoop = 256;
+
+size_t dt_bytes(int dt) { return dt == DT_F32 ? 4 : 8; }
+
+// Add a mode to a gather table (dim-1 modes dropped), strides per operand.
+bool gpush(GModes& t, int64_t d, const int64_t* st, int nops) {
+  if (d == 1) return true;
+  if (t.n >= kMaxModes || d > 0xFFFFFFFFll) return false;
+  t.dim[t.n] = (uint32_t)d;
+  for (int j = 0; j < kMaxOps; ++j) t.stride[t.n][j] = j < nops ? st[j] : 0;
+  t.n++;
+  return true;
+}
+
+void gmerge(GModes& t, int nops) {
+  int w = 0;
+  for (int m = 0; m < t.n; ++m) {
+    bool can = w > 0;
+    for (int j = 0; j < nops && can; ++j) can = t.stride[w - 1][j] == t.stride[m][j] * (int64_t)t.dim[m];
+    if (can && (uint64_t)t.dim[w - 1] * t.dim[m] <= 0xFFFFFFFFull) {
+      t.dim[w - 1] *= t.dim[m];
+      for (int j = 0; j < kMaxOps; ++j) t.stride[w - 1][j] = t.stride[m][j];
+    } else {
+      t.dim[w] = t.dim[m];
+      for (int j = 0; j < kMaxOps; ++j) t.stride[w][j] = t.stride[m][j];
+      ++w;
+    }
+  }
+  t.n = w;
+  for (int m = 0; m < t.n; ++m) t.div[m] = make_fastdiv(t.dim[m]);
+}
+
+uint64_t gsize(const GModes& t) {
+  uint64_t s = 1;
+  for (int m = 0; m < t.n; ++m) s *= t.dim[m];
+  return s;
+}
+
+int64_t gmax(const GModes& t, int j) {
+  int64_t m = 0;
+  for (int k = 0; k < t.n; ++k) m += (int64_t)(t.dim[k] - 1) * t.stride[k][j];
+  return m;
+}
+
+// a tensor during lowering: either stored (one operand: itself) or virtual
+struct Repr {
+  std::vector<int> ops;  // stored tensor ids whose product forms the tensor
+  Inds L;                // indices summed inside a virtual tensor
+  bool virt = false;
+  double flops = 0;      // useful flops of absorbed steps not yet executed
+};
+
+}  // namespace
+
 std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& leaves, const DimMap& dims,
                        int prec, int* code) {
   *code = QTPU_OK;
   ex->prec = prec;
+  ex->n_leaves = plan.n_leaves;
+  ex->launches.clear();
+  ex->inter_off.clear();
+  ex->n_tc_steps = ex->n_fused_steps = 0;
   if (const char* e = std::getenv("QTPU_KC")) ex->kc_blocks = std::atoi(e);
+  const bool fp64 = prec == QTPU_PREC_FP64;
+  ex->inter_dt = fp64 ? DT_F64 : DT_F32X2;
   std::set<int64_t> sliced(plan.sliced.begin(), plan.sliced.end());
   const int nl = plan.n_leaves;
-  const size_t n_t = plan.tensor_inds.size();
+  const int n_plan = (int)plan.tensor_inds.size();
+  auto fail = [&](int c, const std::string& m) {
+    *code = c;
+    return m;
+  };
 
-  // slice bookkeeping
-  if (!plan.n_slices.fits_u64() || plan.n_slices.w[0] > (uint64_t)1 << 40) {
-    *code = QTPU_ENOTSUP;
-    return "slice count too large";
-  }
+  if (!plan.n_slices.fits_u64() || plan.n_slices.w[0] > ((uint64_t)1 << 40)) return fail(QTPU_ENOTSUP, "slice count too large");
   ex->n_slices = (int64_t)plan.n_slices.w[0];
   ex->slice_dims.clear();
   for (int64_t i : plan.sliced) ex->slice_dims.push_back(dims.get(i));
   ex->leaf_slice.assign(nl, {});
   for (int t = 0; t < nl; ++t)
-    for (size_t p = 0; p < plan.sliced.size(); ++p) {
-      const Leaf& L = leaves[t];
-      for (size_t a = 0; a < L.ids.size(); ++a)
-        if (L.ids[a] == plan.sliced[p]) ex->leaf_slice[t].push_back({(int)p, L.strides[a]});
-    }
+    for (size_t p = 0; p < plan.sliced.size(); ++p)
+      for (size_t a = 0; a < leaves[t].ids.size(); ++a)
+        if (leaves[t].ids[a] == plan.sliced[p]) ex->leaf_slice[t].push_back({(int)p, leaves[t].strides[a]});
 
-  // per-slice layout of every tensor: leaves keep their strides, step
-  // results are dense over their non-sliced indices
-  std::vector<Inds> live_inds(n_t);
-  std::vector<std::map<int64_t, int64_t>> stride(n_t);
-  for (int t = 0; t < nl; ++t)
-    for (size_t a = 0; a < leaves[t].ids.size(); ++a)
+  // per-slice layout of every stored tensor: leaves keep their strides, step
+  // results are dense over their non-sliced indices in [batch, M, N] order
+  std::unordered_map<int, std::map<int64_t, int64_t>> stride;
+  std::unordered_map<int, Inds> live_inds;
+  std::unordered_map<int, int64_t> extent, slice_max;
+  auto nsl = [&](const Inds& v) {
+    Inds r;
+    for (int64_t i : v)
+      if (!sliced.count(i)) r.push_back(i);
+    return r;
+  };
+  auto prod = [&](const Inds& v) {
+    double s = 1;
+    for (int64_t i : v) s *= (double)dims.get(i);
+    return s;
+  };
+  for (int t = 0; t < nl; ++t) {
+    int64_t e = 1;
+    for (size_t a = 0; a < leaves[t].ids.size(); ++a) {
+      e += (leaves[t].dims[a] - 1) * leaves[t].strides[a];
       if (!sliced.count(leaves[t].ids[a])) {
         live_inds[t].push_back(leaves[t].ids[a]);
         stride[t][leaves[t].ids[a]] = leaves[t].strides[a];
       }
-  for (size_t s = 0; s < plan.steps.size(); ++s) {
-    const int o = plan.steps[s].out;
-    for (int64_t i : plan.tensor_inds[o])
-      if (!sliced.count(i)) live_inds[o].push_back(i);
-    int64_t st = 1;
-    for (int j = (int)live_inds[o].size() - 1; j >= 0; --j) {
-      stride[o][live_inds[o][j]] = st;
-      st *= dims.get(live_inds[o][j]);
     }
+    extent[t] = e;
+    int64_t sm = 0;
+    for (auto& ps : ex->leaf_slice[t]) sm += (ex->slice_dims[ps.first] - 1) * ps.second;
+    slice_max[t] = sm;
   }
+  auto set_dense = [&](int t, const Inds& inds) {
+    live_inds[t] = inds;
+    int64_t st = 1;
+    for (int j = (int)inds.size() - 1; j >= 0; --j) {
+      stride[t][inds[j]] = st;
+      st *= dims.get(inds[j]);
+    }
+    extent[t] = st;
+    slice_max[t] = 0;
+  };
   auto sof = [&](int t, int64_t i) -> int64_t {
     auto it = stride[t].find(i);
     return it == stride[t].end() ? 0 : it->second;
   };
-  auto tsize = [&](int t) -> int64_t {
-    int64_t s = 1;
-    for (int64_t i : live_inds[t]) s *= dims.get(i);
-    return s;
-  };
-
-  // extent (elements) of every tensor's storage and the largest offset the
-  // slice loop adds to a leaf: every launch is checked to stay inside
-  std::vector<int64_t> extent(n_t, 0), slice_max(n_t, 0);
-  for (int t = 0; t < nl; ++t) {
-    int64_t e = 1;
-    for (size_t a = 0; a < leaves[t].ids.size(); ++a) e += (leaves[t].dims[a] - 1) * leaves[t].strides[a];
-    extent[t] = e;
-    for (auto& ps : ex->leaf_slice[t]) slice_max[t] += (ex->slice_dims[ps.first] - 1) * ps.second;
-  }
-  for (size_t s = 0; s < plan.steps.size(); ++s) extent[plan.steps[s].out] = tsize(plan.steps[s].out);
-  auto inside = [&](int t, int64_t off) { return off + slice_max[t] < extent[t]; };
+  auto dt_of = [&](int t) { return t < nl ? leaves[t].dt : ex->inter_dt; };
+  auto bytes_of = [&](int t) { return prod(live_inds[t]) * (double)dt_bytes(dt_of(t)); };
 
   Arena arena;
-  std::map<int, std::pair<size_t, size_t>> where;  // intermediate id -> (offset, bytes)
-  size_t split_need = 0;
-  ex->steps.clear();
-  ex->n_tc_steps = 0;
+  std::map<int, std::pair<size_t, size_t>> where;
+  std::map<int, size_t> offs;
+  auto place = [&](int t) {
+    const size_t b = (size_t)extent[t] * 8;
+    const size_t o = arena.alloc(b);
+    where[t] = {o, b};
+    offs[t] = o;
+  };
+  auto release = [&](int t) {
+    auto it = where.find(t);
+    if (t >= nl && it != where.end()) {
+      arena.release(it->second.first, it->second.second);
+      where.erase(it);
+    }
+  };
+  // every operand view must stay inside its tensor's storage
+  auto check = [&](const GatherArgs& g, const std::vector<int>& src) {
+    for (int j = 0; j < g.nops; ++j) {
+      const int64_t m = gmax(g.out, j) + gmax(g.loop, j) + gmax(g.kmodes, j) + slice_max[src[j]];
+      if (m >= extent[src[j]]) return false;
+    }
+    return true;
+  };
+
+  std::vector<Repr> repr(n_plan);
+  for (int t = 0; t < nl; ++t) repr[t].ops = {t};
+  size_t split_need_a = 0, split_need_b = 0;
   const int np = prec == 3 ? 3 : (prec == 2 ? 2 : 1);
   const int es = prec == 3 ? 2 : 4;
+  const int split_mode = prec == 3 ? GW_SPLIT_BF16X3 : (prec == 2 ? GW_SPLIT_TF32X2 : GW_SPLIT_TF32);
+  int next_tmp = n_plan;  // ids of materialised virtual tensors
+
+  // gather launch writing `inds` (dense) from the product of reprs
+  auto gather_launch = [&](const std::vector<const Repr*>& rs, const Inds& out_inds, const Inds& extra_loop,
+                           int mode, int dst, double flops, int kclass, Launch* L) -> bool {
+    GatherArgs g;
+    std::vector<int> src;
+    Inds loop;
+    for (auto* r : rs) {
+      for (int o : r->ops) src.push_back(o);
+      for (int64_t i : r->L) loop.push_back(i);
+    }
+    for (int64_t i : extra_loop) loop.push_back(i);
+    if ((int)src.size() > kMaxOps) return false;
+    g.nops = (int)src.size();
+    g.mode = mode;
+    for (int j = 0; j < g.nops; ++j) g.dt[j] = dt_of(src[j]);
+    int64_t st[kMaxOps];
+    bool ok = true;
+    for (int64_t i : out_inds) {
+      if (sliced.count(i)) continue;
+      for (int j = 0; j < g.nops; ++j) st[j] = sof(src[j], i);
+      ok &= gpush(g.out, dims.get(i), st, g.nops);
+    }
+    for (int64_t i : loop) {
+      if (sliced.count(i)) continue;
+      for (int j = 0; j < g.nops; ++j) st[j] = sof(src[j], i);
+      ok &= gpush(g.loop, dims.get(i), st, g.nops);
+    }
+    if (!ok) return false;
+    gmerge(g.out, g.nops);
+    gmerge(g.loop, g.nops);
+    if (gsize(g.out) > 0x7FFFFFFFull || gsize(g.loop) > 0x7FFFFFFFull) return false;
+    g.n_out = (uint32_t)gsize(g.out);
+    g.n_loop = (uint32_t)gsize(g.loop);
+    if (!check(g, src)) return false;
+    L->kind = LK_GATHER;
+    L->kclass = kclass;
+    L->nsrc = g.nops;
+    for (int j = 0; j < g.nops; ++j) L->src[j] = src[j];
+    L->dst = dst;
+    L->g = g;
+    L->flops = flops;
+    double by = (double)g.n_out * (mode == GW_DENSE_F64 ? 8 : 8);
+    for (int s : std::set<int>(src.begin(), src.end())) by += bytes_of(s);
+    L->bytes = by;
+    return true;
+  };
+  // split launch: rows = row_inds, K = k_inds, from one repr
+  auto split_launch = [&](const Repr& r, const Inds& row_inds, const Inds& k_inds, int dst, Launch* L,
+                          int64_t* rows_out, int64_t* K_out) -> bool {
+    GatherArgs g;
+    const std::vector<int>& src = r.ops;
+    if ((int)src.size() > kMaxOps) return false;
+    g.nops = (int)src.size();
+    g.mode = split_mode;
+    for (int j = 0; j < g.nops; ++j) g.dt[j] = dt_of(src[j]);
+    int64_t st[kMaxOps];
+    bool ok = true;
+    for (int64_t i : row_inds) {
+      for (int j = 0; j < g.nops; ++j) st[j] = sof(src[j], i);
+      ok &= gpush(g.out, dims.get(i), st, g.nops);
+    }
+    for (int64_t i : k_inds) {
+      for (int j = 0; j < g.nops; ++j) st[j] = sof(src[j], i);
+      ok &= gpush(g.kmodes, dims.get(i), st, g.nops);
+    }
+    for (int64_t i : r.L) {
+      if (sliced.count(i)) continue;
+      for (int j = 0; j < g.nops; ++j) st[j] = sof(src[j], i);
+      ok &= gpush(g.loop, dims.get(i), st, g.nops);
+    }
+    if (!ok) return false;
+    gmerge(g.out, g.nops);
+    gmerge(g.kmodes, g.nops);
+    gmerge(g.loop, g.nops);
+    // read rows fastest when the leading operand is contiguous along a row mode
+    int64_t min_row = INT64_MAX, min_k = INT64_MAX;
+    for (int q = 0; q < g.out.n; ++q)
+      if (g.out.stride[q][0] > 0) min_row = std::min(min_row, g.out.stride[q][0]);
+    for (int q = 0; q < g.kmodes.n; ++q)
+      if (g.kmodes.stride[q][0] > 0) min_k = std::min(min_k, g.kmodes.stride[q][0]);
+    g.row_fast = min_row < min_k ? 1 : 0;
+    const uint64_t rows = gsize(g.out), K = gsize(g.kmodes);
+    if (rows * ((K + 7) / 8) > 0x7FFFFFFFull || gsize(g.loop) > 0x7FFFFFFFull) return false;
+    g.n_rows = (uint32_t)rows;
+    g.K = (uint32_t)K;
+    g.Kp = (uint32_t)align_up(K, 8);
+    g.n_loop = (uint32_t)gsize(g.loop);
+    if (!check(g, src)) return false;
+    L->kind = LK_GATHER;
+    L->kclass = KC_SPLIT;
+    L->nsrc = g.nops;
+    for (int j = 0; j < g.nops; ++j) L->src[j] = src[j];
+    L->dst = dst;
+    L->g = g;
+    double by = (double)np * rows * g.Kp * es;
+    for (int s : std::set<int>(src.begin(), src.end())) by += bytes_of(s);
+    L->bytes = by;
+    *rows_out = (int64_t)rows;
+    *K_out = (int64_t)K;
+    return true;
+  };
+
   for (size_t s = 0; s < plan.steps.size(); ++s) {
     const PlanStep& ps = plan.steps[s];
-    StepExec e;
-    e.x = ps.x;
-    e.y = ps.y;
-    e.out = ps.out;
-    e.x_leaf = ps.x < nl;
-    e.y_leaf = ps.y < nl;
-    e.dtx = e.x_leaf ? leaves[ps.x].dt : DT_F64;
-    e.dty = e.y_leaf ? leaves[ps.y].dt : DT_F64;
-    e.last = (s + 1 == plan.steps.size());
-    auto nsl = [&](const Inds& v) {
-      Inds r;
-      for (int64_t i : v)
-        if (!sliced.count(i)) r.push_back(i);
-      return r;
-    };
+    const bool last = s + 1 == plan.steps.size();
     const Inds batch = nsl(ps.batch), m = nsl(ps.m), n = nsl(ps.n), k = nsl(ps.k), sa = nsl(ps.sa),
                sb = nsl(ps.sb);
-    double nb = 1, nm = 1, nn = 1, nk = 1;
-    for (int64_t i : batch) nb *= (double)dims.get(i);
-    for (int64_t i : m) nm *= (double)dims.get(i);
-    for (int64_t i : n) nn *= (double)dims.get(i);
-    for (int64_t i : k) nk *= (double)dims.get(i);
-    e.flops = 2.0 * nb * nm * nn * nk;
-    const double lim = 2147483647.0;
-    bool tc = prec != QTPU_PREC_FP64 && sa.empty() && sb.empty() && nm >= 64 && nn >= 32 && nk >= 32 &&
-              nb * nm * nn * nk >= (double)(1 << 22) && nb < lim && nm < lim && nn < lim && nk < lim;
-    if (tc) {
-      SplitArgs A, B;
-      memset(&A.row, 0, sizeof(ModeTab));
-      memset(&A.k, 0, sizeof(ModeTab));
-      memset(&B.row, 0, sizeof(ModeTab));
-      memset(&B.k, 0, sizeof(ModeTab));
-      bool ok = true;
-      for (int64_t i : batch) ok &= push_mode(A.row, dims.get(i), sof(ps.x, i), 0);
-      for (int64_t i : m) ok &= push_mode(A.row, dims.get(i), sof(ps.x, i), 0);
-      for (int64_t i : k) ok &= push_mode(A.k, dims.get(i), sof(ps.x, i), 0);
-      for (int64_t i : batch) ok &= push_mode(B.row, dims.get(i), sof(ps.y, i), 0);
-      for (int64_t i : n) ok &= push_mode(B.row, dims.get(i), sof(ps.y, i), 0);
-      for (int64_t i : k) ok &= push_mode(B.k, dims.get(i), sof(ps.y, i), 0);
-      if (ok) {
-        merge_modes(A.row);
-        merge_modes(A.k);
-        merge_modes(B.row);
-        merge_modes(B.k);
-        const int64_t K = (int64_t)nk, Kp = (int64_t)align_up((size_t)K, 8);
-        A.n_rows = (int64_t)(nb * nm);
-        B.n_rows = (int64_t)(nb * nn);
-        A.K = B.K = K;
-        A.Kp = B.Kp = Kp;
-        A.pieces = B.pieces = np;
-        A.kind = B.kind = prec == 3 ? 0 : 1;
-        if (!inside(ps.x, max_off(A.row, 0) + max_off(A.k, 0)) ||
-            !inside(ps.y, max_off(B.row, 0) + max_off(B.k, 0))) {
-          *code = QTPU_ENOTSUP;
-          return "internal: operand view out of bounds";
-        }
-        e.sa = A;
-        e.sb = B;
-        e.kind = SK_TC;
-        e.g.batch = (int)nb;
-        e.g.M = (int)nm;
-        e.g.N = (int)nn;
-        e.g.K = (int)K;
-        e.g.prec = prec;
-        e.g.kc_blocks = ex->kc_blocks;
-        const size_t abytes = align_up((size_t)np * A.n_rows * Kp * es, 1024);
-        const size_t bbytes = align_up((size_t)np * B.n_rows * Kp * es, 1024);
-        split_need = std::max(split_need, abytes + bbytes);
-        ex->n_tc_steps++;
-      } else {
-        tc = false;
-      }
-    }
-    if (!tc) {
-      e.kind = SK_GENERIC;
+    Inds out_inds = batch;
+    out_inds.insert(out_inds.end(), m.begin(), m.end());
+    out_inds.insert(out_inds.end(), n.begin(), n.end());
+    const double nb = prod(batch), nm = prod(m), nn = prod(n), nk = prod(k);
+    const double step_flops = 2.0 * nb * nm * nn * nk;
+    Repr& X = repr[ps.x];
+    Repr& Y = repr[ps.y];
+    const int dst = last ? DST_PARTIAL : ps.out;
+
+    if (fp64) {
+      // plain FP64 CUDA-core step
       ContractArgs c;
       memset(&c.out, 0, sizeof(ModeTab));
       memset(&c.loop, 0, sizeof(ModeTab));
@@ -309,89 +455,225 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       for (int64_t i : k) ok &= push_mode(c.loop, dims.get(i), sof(ps.x, i), sof(ps.y, i));
       for (int64_t i : sa) ok &= push_mode(c.loop, dims.get(i), sof(ps.x, i), 0);
       for (int64_t i : sb) ok &= push_mode(c.loop, dims.get(i), 0, sof(ps.y, i));
-      if (!ok) {
-        *code = QTPU_ENOTSUP;
-        return "a step has more than 12 modes in one group";
-      }
+      if (!ok) return fail(QTPU_ENOTSUP, "a step has more than 12 modes in one group");
       merge_modes(c.out);
       merge_modes(c.loop);
       c.n_out = tab_size(c.out);
       c.n_loop = tab_size(c.loop);
-      if (!inside(ps.x, max_off(c.out, 0) + max_off(c.loop, 0)) ||
-          !inside(ps.y, max_off(c.out, 1) + max_off(c.loop, 1)) || c.n_out != tsize(ps.out)) {
-        *code = QTPU_ENOTSUP;
-        return "internal: operand view out of bounds";
-      }
-      e.c = c;
+      if (max_off(c.out, 0) + max_off(c.loop, 0) + slice_max[ps.x] >= extent[ps.x] ||
+          max_off(c.out, 1) + max_off(c.loop, 1) + slice_max[ps.y] >= extent[ps.y])
+        return fail(QTPU_ENOTSUP, "internal: operand view out of bounds");
+      Launch L;
+      L.kind = LK_CONTRACT64;
+      L.kclass = KC_CONTRACT;
+      L.nsrc = 2;
+      L.src[0] = ps.x;
+      L.src[1] = ps.y;
+      L.dst = dst;
+      L.c64 = c;
+      L.flops = step_flops;
+      L.bytes = bytes_of(ps.x) + bytes_of(ps.y) + (double)c.n_out * 8;
+      set_dense(ps.out, out_inds);
+      if (!last) place(ps.out);
+      release(ps.x);
+      release(ps.y);
+      ex->launches.push_back(L);
+      continue;
     }
-    // output placement
-    const size_t obytes = (size_t)tsize(ps.out) * 8;
-    if (!e.last) {
-      e.out_off = arena.alloc(obytes);
-      where[ps.out] = {e.out_off, obytes};
+
+    // ---- absorption of a small leaf: keep the result virtual
+    auto small_leaf = [&](const Repr& r, int t) {
+      return !r.virt && t < nl && prod(live_inds[t]) <= (double)kSmallLeaf;
+    };
+    const bool sx = small_leaf(X, ps.x), sy = small_leaf(Y, ps.y);
+    const double big_size = sx ? prod(live_inds[ps.y]) : prod(live_inds[ps.x]);
+    Inds vL = X.L;
+    vL.insert(vL.end(), Y.L.begin(), Y.L.end());
+    for (const Inds* g : {&k, &sa, &sb}) vL.insert(vL.end(), g->begin(), g->end());
+    if (!last && (sx || sy) && !(sx && sy && nb * nm * nn > 4 * kSmallLeaf) &&
+        nb * nm * nn <= 4.0 * big_size && (int)(X.ops.size() + Y.ops.size()) <= kMaxVirtualOps &&
+        prod(vL) <= (double)kMaxVirtualLoop) {
+      Repr V;
+      V.ops = X.ops;
+      V.ops.insert(V.ops.end(), Y.ops.begin(), Y.ops.end());
+      V.L = vL;
+      V.virt = true;
+      V.flops = X.flops + Y.flops + step_flops;
+      live_inds[ps.out] = out_inds;
+      repr[ps.out] = V;
+      ex->n_fused_steps++;
+      continue;
     }
-    for (int t : {ps.x, ps.y})
-      if (t >= nl) {
-        arena.release(where[t].first, where[t].second);
-        where.erase(t);
+
+    // ---- tensor-core GEMM step
+    const double lim = 2147483647.0;
+    const bool tc = sa.empty() && sb.empty() && nm >= 64 && nn >= 32 && nk >= 32 &&
+                    nb * nm * nn * nk >= (double)(1 << 22) && nb < lim && nm < lim && nn < lim && nk < lim &&
+                    nb * std::ceil(nm / 128.0) * std::ceil(nn / (double)gemm_block_n()) < lim;
+    if (tc) {
+      Inds rowsA = batch, rowsB = batch;
+      rowsA.insert(rowsA.end(), m.begin(), m.end());
+      rowsB.insert(rowsB.end(), n.begin(), n.end());
+      Launch LA, LB, LG;
+      int64_t ra = 0, rb = 0, Ka = 0, Kb = 0;
+      if (split_launch(X, rowsA, k, DST_SPLIT_A, &LA, &ra, &Ka) &&
+          split_launch(Y, rowsB, k, DST_SPLIT_B, &LB, &rb, &Kb) && Ka == Kb) {
+        const size_t abytes = align_up((size_t)np * ra * align_up(Ka, 8) * es, 1024);
+        const size_t bbytes = align_up((size_t)np * rb * align_up(Kb, 8) * es, 1024);
+        split_need_a = std::max(split_need_a, abytes);
+        split_need_b = std::max(split_need_b, bbytes);
+        LG.kind = LK_GEMM;
+        LG.kclass = KC_GEMM;
+        LG.dst = dst;
+        LG.gemm.batch = (int)nb;
+        LG.gemm.M = (int)nm;
+        LG.gemm.N = (int)nn;
+        LG.gemm.K = (int)Ka;
+        LG.gemm.prec = prec;
+        LG.gemm.kc_blocks = ex->kc_blocks;
+        LG.flops = step_flops + X.flops + Y.flops;
+        LG.bytes = (double)np * (ra + rb) * align_up(Ka, 8) * es + nb * nm * nn * 8.0;
+        // the GEMM stores its result [batch][N][M]
+        Inds stored = batch;
+        stored.insert(stored.end(), n.begin(), n.end());
+        stored.insert(stored.end(), m.begin(), m.end());
+        set_dense(ps.out, stored);
+        if (!last) place(ps.out);
+        for (int o : X.ops) release(o);
+        for (int o : Y.ops) release(o);
+        ex->launches.push_back(LA);
+        ex->launches.push_back(LB);
+        ex->launches.push_back(LG);
+        ex->n_tc_steps++;
+        repr[ps.out] = Repr();
+        repr[ps.out].ops = {ps.out};
+        continue;
       }
-    ex->steps.push_back(e);
+    }
+
+    // ---- gather step (materialises the result)
+    Inds extra = k;
+    extra.insert(extra.end(), sa.begin(), sa.end());
+    extra.insert(extra.end(), sb.begin(), sb.end());
+    // a virtual operand with too many factors is materialised first
+    for (Repr* r : {&X, &Y}) {
+      if (r->virt && (int)(X.ops.size() + Y.ops.size()) > kMaxOps) {
+        const int tid = next_tmp++;
+        const Inds vin = live_inds[r == &X ? ps.x : ps.y];
+        Launch L;
+        if (!gather_launch({r}, vin, {}, GW_DENSE_PAIR, tid, r->flops, KC_CONTRACT, &L))
+          return fail(QTPU_ENOTSUP, "internal: cannot lower a fused tensor");
+        set_dense(tid, vin);
+        place(tid);
+        for (int o : r->ops) release(o);
+        ex->launches.push_back(L);
+        *r = Repr();
+        r->ops = {tid};
+      }
+    }
+    Launch L;
+    if (!gather_launch({&X, &Y}, out_inds, extra, last ? GW_DENSE_PAIR : GW_DENSE_PAIR, dst,
+                       step_flops + X.flops + Y.flops, KC_CONTRACT, &L))
+      return fail(QTPU_ENOTSUP, "internal: a step does not fit the gather kernel (modes or operand views)");
+    set_dense(ps.out, out_inds);
+    if (!last) place(ps.out);
+    for (int o : X.ops) release(o);
+    for (int o : Y.ops) release(o);
+    ex->launches.push_back(L);
+    repr[ps.out] = Repr();
+    repr[ps.out].ops = {ps.out};
   }
 
-  // final reduction: slices and leftover indices -> output order
-  ContractArgs r;
-  memset(&r.out, 0, sizeof(ModeTab));
-  memset(&r.loop, 0, sizeof(ModeTab));
-  bool ok = true;
+  // ---- final reduction: slices and leftover indices -> output order (FP64)
+  Launch R;
   if (plan.steps.empty()) {
-    ex->reduce_from_leaf = true;
-    ex->reduce_leaf = 0;
-    const Leaf& L = leaves[0];
-    for (int64_t i : plan.output) {
-      size_t a = std::find(L.ids.begin(), L.ids.end(), i) - L.ids.begin();
-      ok &= push_mode(r.out, L.dims[a], L.strides[a], 0);
-    }
-    for (size_t a = 0; a < L.ids.size(); ++a)
-      if (!contains(plan.output, L.ids[a])) ok &= push_mode(r.loop, L.dims[a], L.strides[a], 0);
+    const Leaf& Lf = leaves[0];
+    Inds loop;
+    for (size_t a = 0; a < Lf.ids.size(); ++a)
+      if (!contains(plan.output, Lf.ids[a])) loop.push_back(Lf.ids[a]);
+    // the leaf's sliced indices are summed here as well
+    stride[0].clear();
+    for (size_t a = 0; a < Lf.ids.size(); ++a) stride[0][Lf.ids[a]] = Lf.strides[a];
+    std::set<int64_t> saved = sliced;
+    sliced.clear();
+    slice_max[0] = 0;
+    Repr r0;
+    r0.ops = {0};
+    const bool ok = gather_launch({&r0}, plan.output, loop, GW_DENSE_F64, DST_OUT, 0, KC_REDUCE, &R);
+    sliced = saved;
+    if (!ok) return fail(QTPU_ENOTSUP, "the output does not fit the reduction kernel");
     ex->final_size = 0;
   } else {
-    ex->reduce_from_leaf = false;
     const int last = plan.steps.back().out;
-    ex->final_size = tsize(last);
-    for (int64_t i : plan.output) ok &= push_mode(r.out, dims.get(i), sof(last, i), 0);
-    ok &= push_mode(r.loop, ex->n_slices, ex->final_size, 0);
+    ex->final_size = extent[last];
+    // partial[slice][final] as a stored tensor with a slice index
+    const int pid = next_tmp++;
+    const int64_t slice_ix = -1;
+    live_inds[pid] = live_inds[last];
+    stride[pid] = stride[last];
+    stride[pid][slice_ix] = ex->final_size;
+    extent[pid] = ex->n_slices * ex->final_size;
+    slice_max[pid] = 0;
+    Inds loop;
+    if (ex->n_slices > 1) loop.push_back(slice_ix);
     for (int64_t i : plan.final_sum)
-      if (!sliced.count(i)) ok &= push_mode(r.loop, dims.get(i), sof(last, i), 0);
-  }
-  if (!ok) {
-    *code = QTPU_ENOTSUP;
-    return "the output has more than 12 modes";
-  }
-  merge_modes(r.out);
-  merge_modes(r.loop);
-  r.n_out = tab_size(r.out);
-  r.n_loop = tab_size(r.loop);
-  {
-    const int64_t src_extent = plan.steps.empty() ? extent[0] : ex->n_slices * ex->final_size;
-    if (max_off(r.out, 0) + max_off(r.loop, 0) >= src_extent) {
-      *code = QTPU_ENOTSUP;
-      return "internal: reduction view out of bounds";
+      if (!sliced.count(i)) loop.push_back(i);
+    GatherArgs g;
+    g.nops = 1;
+    g.mode = GW_DENSE_F64;
+    g.dt[0] = ex->inter_dt;
+    int64_t st[kMaxOps] = {};
+    bool ok = true;
+    for (int64_t i : plan.output) {
+      st[0] = sof(pid, i);
+      ok &= gpush(g.out, dims.get(i), st, 1);
     }
+    for (int64_t i : loop) {
+      st[0] = sof(pid, i);
+      ok &= gpush(g.loop, i == slice_ix ? ex->n_slices : dims.get(i), st, 1);
+    }
+    if (!ok) return fail(QTPU_ENOTSUP, "the output does not fit the reduction kernel");
+    gmerge(g.out, 1);
+    gmerge(g.loop, 1);
+    if (gsize(g.out) > 0x7FFFFFFFull || gsize(g.loop) > 0x7FFFFFFFull)
+      return fail(QTPU_ENOTSUP, "the output does not fit the reduction kernel");
+    g.n_out = (uint32_t)gsize(g.out);
+    g.n_loop = (uint32_t)gsize(g.loop);
+    if (gmax(g.out, 0) + gmax(g.loop, 0) >= extent[pid]) return fail(QTPU_ENOTSUP, "internal: reduction out of bounds");
+    R.kind = LK_GATHER;
+    R.kclass = KC_REDUCE;
+    R.nsrc = 1;
+    R.src[0] = pid;
+    R.dst = DST_OUT;
+    R.g = g;
+    R.bytes = (double)ex->n_slices * ex->final_size * 8 + (double)g.n_out * 8;
+    offs[pid] = 0;  // resolved to the partial buffer at run time
   }
-  ex->reduce = r;
+  if (fp64) {
+    // the FP64 path reduces with the FP64 kernel (same views)
+    ContractArgs c;
+    memset(&c.out, 0, sizeof(ModeTab));
+    memset(&c.loop, 0, sizeof(ModeTab));
+    for (int m = 0; m < R.g.out.n; ++m) push_mode(c.out, R.g.out.dim[m], R.g.out.stride[m][0], 0);
+    for (int m = 0; m < R.g.loop.n; ++m) push_mode(c.loop, R.g.loop.dim[m], R.g.loop.stride[m][0], 0);
+    c.n_out = tab_size(c.out);
+    c.n_loop = tab_size(c.loop);
+    R.kind = LK_CONTRACT64;
+    R.c64 = c;
+  }
+  ex->reduce = R;
+  ex->launches_per_contract = (plan.steps.empty() ? 0 : (int64_t)ex->launches.size() * ex->n_slices) + 1;
 
-  // device memory
+  // ---- device memory
   cudaError_t ce = cudaSetDevice(ex->device);
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&ex->sm_count, cudaDevAttrMultiProcessorCount, ex->device);
-  if (ce != cudaSuccess) {
-    *code = QTPU_ECUDA;
-    return std::string("cuda: ") + cudaGetErrorString(ce);
-  }
+  if (ce != cudaSuccess) return fail(QTPU_ECUDA, std::string("cuda: ") + cudaGetErrorString(ce));
   ex->arena_bytes = std::max<size_t>(arena.top, 256);
-  ex->split_bytes = split_need;
-  auto dalloc = [&](void** p, size_t n) -> bool {
-    if (!n) return true;
-    if (cudaMalloc(p, n) != cudaSuccess) {
+  ex->split_a_bytes = split_need_a;
+  ex->split_bytes = split_need_a + split_need_b;
+  auto dalloc = [&](void** p, size_t nbytes) -> bool {
+    if (!nbytes) return true;
+    if (cudaMalloc(p, nbytes) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }
@@ -399,80 +681,200 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
   };
   if (!dalloc((void**)&ex->arena, ex->arena_bytes) || !dalloc((void**)&ex->splitbuf, ex->split_bytes) ||
       !dalloc((void**)&ex->partial, (size_t)ex->n_slices * std::max<int64_t>(ex->final_size, 1) * 8) ||
-      !dalloc((void**)&ex->status, 16) || !dalloc((void**)&ex->out_stage, (size_t)r.n_out * 8)) {
+      !dalloc((void**)&ex->status, 16) || !dalloc((void**)&ex->out_stage, (size_t)R.g.n_out * 8 + 8)) {
     exec_free(ex);
-    *code = QTPU_ENOMEM;
-    return "device workspace allocation failed";
+    return fail(QTPU_ENOMEM, "device workspace allocation failed");
   }
   cudaMemset(ex->status, 0, 16);
-  // tensor maps of the split buffers (fixed addresses)
-  for (auto& e : ex->steps) {
-    if (e.kind != SK_TC) continue;
-    const size_t abytes = align_up((size_t)np * e.sa.n_rows * e.sa.Kp * es, 1024);
-    if (!make_operand_map(&e.g.tmA, ex->splitbuf, prec, e.g.batch, e.g.M, e.g.K, e.sa.Kp, 128) ||
-        !make_operand_map(&e.g.tmB, ex->splitbuf + abytes, prec, e.g.batch, e.g.N, e.g.K, e.sb.Kp,
-                          gemm_block_n())) {
+  if (ex->n_tc_steps) {
+    ce = gemm_prepare();
+    if (ce != cudaSuccess) {
       exec_free(ex);
-      *code = QTPU_ECUDA;
-      return "cuTensorMapEncodeTiled failed";
+      return fail(QTPU_ECUDA, std::string("GEMM setup: ") + cudaGetErrorString(ce));
     }
-    e.g.status = ex->status;
+  }
+  if (const char* e = std::getenv("QTPU_NO_GRAPH")) ex->use_graph = std::atoi(e) == 0;
+  if (ex->launches_per_contract > 20000) ex->use_graph = false;  // graph too large to be worth it
+  if (ex->use_graph) {
+    if (cudaStreamCreateWithFlags(&ex->own, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ex->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ex->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      ex->use_graph = false;
+    }
+  }
+  ex->inter_off.assign(next_tmp - nl + 1, 0);
+  for (auto& kv : offs)
+    if (kv.first >= nl) ex->inter_off[kv.first - nl] = kv.second;
+  // tensor maps of the split buffers (fixed addresses)
+  for (size_t i = 0; i < ex->launches.size(); ++i) {
+    Launch& L = ex->launches[i];
+    if (L.kind != LK_GEMM) continue;
+    const Launch& A = ex->launches[i - 2];
+    const Launch& B = ex->launches[i - 1];
+    if (!make_operand_map(&L.gemm.tmA, ex->splitbuf, prec, L.gemm.batch, L.gemm.M, L.gemm.K, A.g.Kp, 128) ||
+        !make_operand_map(&L.gemm.tmB, ex->splitbuf + ex->split_a_bytes, prec, L.gemm.batch, L.gemm.N, L.gemm.K,
+                          B.g.Kp, gemm_block_n())) {
+      exec_free(ex);
+      return fail(QTPU_ECUDA, "cuTensorMapEncodeTiled failed");
+    }
+    L.gemm.status = ex->status;
   }
   return "";
 }
 
-static size_t dt_size(int dt) { return dt == DT_F64 ? 8 : 4; }
+namespace {
+// event pair around one launch when profiling is on
+struct Timed {
+  Profiler& p;
+  cudaStream_t st;
+  size_t i = 0;
+  bool on;
+  Timed(Profiler& pr, cudaStream_t s, int kind, double fl, double by) : p(pr), st(s), on(pr.on) {
+    if (!on) return;
+    if (p.used * 2 + 2 > p.ev.size()) {
+      for (int k = 0; k < 2; ++k) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+          on = false;
+          return;
+        }
+        p.ev.push_back(e);
+      }
+      p.kind.push_back(0);
+      p.flops.push_back(0);
+      p.bytes.push_back(0);
+    }
+    i = p.used++;
+    p.kind[i] = kind;
+    p.flops[i] = fl;
+    p.bytes[i] = by;
+    cudaEventRecordWithFlags(p.ev[2 * i], st, cudaEventRecordExternal);
+  }
+  ~Timed() {
+    if (on) cudaEventRecordWithFlags(p.ev[2 * i + 1], st, cudaEventRecordExternal);
+  }
+};
+}  // namespace
 
-std::string exec_run(Executor* ex, const std::vector<Leaf>& leaves, double* dev_out, cudaStream_t st, int* code) {
-  *code = QTPU_OK;
+std::string exec_profile_read(Executor* ex, double* ms, int64_t* launches, double* flops, double* bytes) {
+  for (int k = 0; k < KC_COUNT; ++k) ms[k] = 0, launches[k] = 0, flops[k] = 0, bytes[k] = 0;
+  Profiler& p = ex->prof;
+  for (size_t i = 0; i < p.used; ++i) {
+    float t = 0;
+    cudaError_t e = cudaEventElapsedTime(&t, p.ev[2 * i], p.ev[2 * i + 1]);
+    if (e != cudaSuccess) {
+      p.used = 0;
+      return std::string("cudaEventElapsedTime: ") + cudaGetErrorString(e);
+    }
+    ms[p.kind[i]] += t;
+    launches[p.kind[i]] += 1;
+    flops[p.kind[i]] += p.flops[i];
+    bytes[p.kind[i]] += p.bytes[i];
+  }
+  p.used = 0;
+  return "";
+}
+
+namespace {
+// Enqueue every launch of one contraction on `st`; the result goes to `out`.
+cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* out, cudaStream_t st) {
   const int nl = (int)leaves.size();
   std::vector<int64_t> loff(nl, 0);
   std::vector<int64_t> digit(ex->slice_dims.size(), 0);
   cudaError_t ce = cudaSuccess;
-  if (!ex->reduce_from_leaf) {
-    for (int64_t s = 0; s < ex->n_slices && ce == cudaSuccess; ++s) {
-      int64_t r = s;
-      for (int j = (int)ex->slice_dims.size() - 1; j >= 0; --j) {
-        digit[j] = r % ex->slice_dims[j];
-        r /= ex->slice_dims[j];
-      }
-      for (int t = 0; t < nl; ++t) {
-        int64_t o = 0;
-        for (auto& ps : ex->leaf_slice[t]) o += digit[ps.first] * ps.second;
-        loff[t] = o;
-      }
-      for (auto& e : ex->steps) {
-        const void* A = e.x_leaf ? (const void*)((const uint8_t*)leaves[e.x].ptr + loff[e.x] * dt_size(e.dtx))
-                                 : nullptr;
-        const void* B = e.y_leaf ? (const void*)((const uint8_t*)leaves[e.y].ptr + loff[e.y] * dt_size(e.dty))
-                                 : nullptr;
-        if (!e.x_leaf) A = ex->arena + ex->steps[e.x - nl].out_off;
-        if (!e.y_leaf) B = ex->arena + ex->steps[e.y - nl].out_off;
-        double* out = e.last ? ex->partial + s * ex->final_size : (double*)(ex->arena + e.out_off);
-        if (e.kind == SK_GENERIC) {
-          ce = launch_contract(A, e.dtx, B, e.dty, out, e.c, ex->sm_count, st);
-        } else {
-          const int np = ex->prec == 3 ? 3 : (ex->prec == 2 ? 2 : 1);
-          const int es = ex->prec == 3 ? 2 : 4;
-          const size_t abytes = align_up((size_t)np * e.sa.n_rows * e.sa.Kp * es, 1024);
-          ce = launch_split(A, e.dtx, ex->splitbuf, e.sa, ex->sm_count, st);
-          if (ce == cudaSuccess) ce = launch_split(B, e.dty, ex->splitbuf + abytes, e.sb, ex->sm_count, st);
-          if (ce == cudaSuccess) {
-            GemmArgs g = e.g;
-            g.C = out;
-            ce = launch_gemm(g, ex->sm_count, st);
-          }
-        }
-        if (ce != cudaSuccess) break;
-      }
+  auto src_ptr = [&](int t) -> const void* {
+    if (t < nl) return (const uint8_t*)leaves[t].ptr + loff[t] * (int64_t)dt_bytes(leaves[t].dt);
+    return ex->arena + ex->inter_off[t - nl];
+  };
+  auto dst_ptr = [&](int d, int64_t s) -> void* {
+    switch (d) {
+      case DST_PARTIAL: return ex->partial + (size_t)s * ex->final_size * 8;
+      case DST_SPLIT_A: return ex->splitbuf;
+      case DST_SPLIT_B: return ex->splitbuf + ex->split_a_bytes;
+      case DST_OUT: return out;
+      default: return ex->arena + ex->inter_off[d - nl];
+    }
+  };
+  auto run_one = [&](const Launch& L, int64_t s, bool reduce) -> cudaError_t {
+    Timed t(ex->prof, st, L.kclass, L.flops, L.bytes);
+    const bool from_partial = reduce && !ex->launches.empty();
+    if (L.kind == LK_GATHER) {
+      GatherArgs g = L.g;
+      for (int j = 0; j < L.nsrc; ++j) g.ptr[j] = from_partial ? (const void*)ex->partial : src_ptr(L.src[j]);
+      return launch_gather(g, dst_ptr(L.dst, s), ex->sm_count, st);
+    }
+    if (L.kind == LK_GEMM) {
+      GemmArgs g = L.gemm;
+      g.C = dst_ptr(L.dst, s);
+      return launch_gemm(g, ex->sm_count, st);
+    }
+    const void* A = from_partial ? (const void*)ex->partial : src_ptr(L.src[0]);
+    const void* B = reduce ? nullptr : src_ptr(L.src[1]);
+    const int dta = L.src[0] < nl ? leaves[L.src[0]].dt : ex->inter_dt;
+    const int dtb = reduce ? DT_F64 : (L.src[1] < nl ? leaves[L.src[1]].dt : ex->inter_dt);
+    return launch_contract(A, dta, B, dtb, (double*)dst_ptr(L.dst, s), L.c64, ex->sm_count, st);
+  };
+  for (int64_t s = 0; s < ex->n_slices && ce == cudaSuccess && !ex->launches.empty(); ++s) {
+    int64_t r = s;
+    for (int j = (int)ex->slice_dims.size() - 1; j >= 0; --j) {
+      digit[j] = r % ex->slice_dims[j];
+      r /= ex->slice_dims[j];
+    }
+    for (int t = 0; t < nl; ++t) {
+      int64_t o = 0;
+      for (auto& ps : ex->leaf_slice[t]) o += digit[ps.first] * ps.second;
+      loff[t] = o;
+    }
+    for (auto& L : ex->launches) {
+      ce = run_one(L, s, false);
+      if (ce != cudaSuccess) break;
     }
   }
   if (ce == cudaSuccess) {
-    if (ex->reduce_from_leaf)
-      ce = launch_contract(leaves[ex->reduce_leaf].ptr, leaves[ex->reduce_leaf].dt, nullptr, DT_F64, dev_out,
-                           ex->reduce, ex->sm_count, st);
-    else
-      ce = launch_contract(ex->partial, DT_F64, nullptr, DT_F64, dev_out, ex->reduce, ex->sm_count, st);
+    std::fill(loff.begin(), loff.end(), 0);
+    ce = run_one(ex->reduce, 0, true);
+  }
+  return ce;
+}
+}  // namespace
+
+std::string exec_run(Executor* ex, const std::vector<Leaf>& leaves, double* dev_out, cudaStream_t st, int* code) {
+  *code = QTPU_OK;
+  cudaError_t ce = cudaSuccess;
+  if (!ex->use_graph) {
+    ce = enqueue_all(ex, leaves, dev_out, st);
+  } else {
+    // the graph writes the output to the staging buffer; one small copy
+    // moves it to the caller's buffer on the caller's stream
+    const int gi = ex->prof.on ? 1 : 0;
+    if (!ex->graph[gi]) {
+      if (ex->prof.on) ex->prof.used = 0;
+      cudaGraph_t g = nullptr;
+      ce = cudaStreamBeginCapture(ex->own, cudaStreamCaptureModeThreadLocal);
+      if (ce == cudaSuccess) {
+        cudaError_t e1 = enqueue_all(ex, leaves, ex->out_stage, ex->own);
+        ce = cudaStreamEndCapture(ex->own, &g);
+        if (e1 != cudaSuccess) ce = e1;
+      }
+      if (ce == cudaSuccess) ce = cudaGraphInstantiate(&ex->graph[gi], g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (ce != cudaSuccess) {
+        *code = QTPU_ECUDA;
+        return std::string("graph capture failed: ") + cudaGetErrorString(ce);
+      }
+      if (ex->prof.on) ex->prof.graph_events = ex->prof.used;
+    }
+    // each replay records the captured events again: a profile read sees the
+    // launches of the most recent contraction
+    if (ex->prof.on) ex->prof.used = ex->prof.graph_events;
+    ce = cudaEventRecord(ex->ev_in, st);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(ex->own, ex->ev_in, 0);
+    if (ce == cudaSuccess) ce = cudaGraphLaunch(ex->graph[gi], ex->own);
+    if (ce == cudaSuccess) ce = cudaEventRecord(ex->ev_out, ex->own);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(st, ex->ev_out, 0);
+    if (ce == cudaSuccess && dev_out != ex->out_stage)
+      ce = cudaMemcpyAsync(dev_out, ex->out_stage, (size_t)ex->reduce.g.n_out * 8, cudaMemcpyDeviceToDevice, st);
   }
   if (ce != cudaSuccess) {
     *code = QTPU_ECUDA;
@@ -482,15 +884,22 @@ std::string exec_run(Executor* ex, const std::vector<Leaf>& leaves, double* dev_
 }
 
 void exec_free(Executor* ex) {
+  for (int i = 0; i < 2; ++i)
+    if (ex->graph[i]) cudaGraphExecDestroy(ex->graph[i]), ex->graph[i] = nullptr;
+  if (ex->own) cudaStreamDestroy(ex->own), ex->own = nullptr;
+  if (ex->ev_in) cudaEventDestroy(ex->ev_in), ex->ev_in = nullptr;
+  if (ex->ev_out) cudaEventDestroy(ex->ev_out), ex->ev_out = nullptr;
+  for (auto e : ex->prof.ev) cudaEventDestroy(e);
+  ex->prof.ev.clear();
+  ex->prof.used = 0;
   if (ex->arena) cudaFree(ex->arena);
   if (ex->splitbuf) cudaFree(ex->splitbuf);
   if (ex->partial) cudaFree(ex->partial);
   if (ex->status) cudaFree(ex->status);
   if (ex->out_stage) cudaFree(ex->out_stage);
-  ex->out_stage = nullptr;
-  ex->arena = ex->splitbuf = nullptr;
-  ex->partial = nullptr;
+  ex->arena = ex->splitbuf = ex->partial = nullptr;
   ex->status = nullptr;
+  ex->out_stage = nullptr;
 }
 
 }  // namespace qtpu

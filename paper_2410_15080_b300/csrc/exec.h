@@ -1,4 +1,4 @@
-// Executor: turns a Plan into kernel launches on one device and stream.
+// Executor: turns a Plan into a list of kernel launches on one device/stream.
 #pragma once
 #include <cstdint>
 #include <string>
@@ -19,19 +19,32 @@ struct Leaf {
   const void* ptr = nullptr;
 };
 
-enum StepKind { SK_GENERIC = 0, SK_TC = 1 };
+enum KernelClass { KC_CONTRACT = 0, KC_SPLIT = 1, KC_GEMM = 2, KC_REDUCE = 3, KC_COUNT = 4 };
 
-struct StepExec {
-  int kind = SK_GENERIC;
-  int x = 0, y = 0, out = 0;
-  int dtx = DT_F64, dty = DT_F64;
-  bool x_leaf = false, y_leaf = false;
-  ContractArgs c;            // generic
-  SplitArgs sa, sb;          // tensor-core path
-  GemmArgs g;
-  size_t out_off = 0;        // arena byte offset (unused for the last step)
-  bool last = false;
-  double flops = 0;          // useful flops per slice
+enum LaunchKind { LK_GATHER = 0, LK_GEMM = 1, LK_CONTRACT64 = 2 };
+
+// Destinations of a launch's output
+enum : int { DST_PARTIAL = -1, DST_SPLIT_A = -2, DST_SPLIT_B = -3, DST_OUT = -4 };
+
+struct Launch {
+  int kind = LK_GATHER;
+  int kclass = KC_CONTRACT;
+  int nsrc = 0;
+  int src[kMaxOps] = {};  // operand tensor ids: leaf (< n_leaves) or intermediate
+  int dst = DST_PARTIAL;  // intermediate id (>= n_leaves) or a DST_* code
+  GatherArgs g;           // LK_GATHER (operand pointers patched per slice)
+  GemmArgs gemm;          // LK_GEMM (split buffers fixed; C patched)
+  ContractArgs c64;       // LK_CONTRACT64 (FP64 path)
+  double flops = 0, bytes = 0;
+};
+
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;  // pairs
+  std::vector<int> kind;
+  std::vector<double> flops, bytes;
+  size_t used = 0;
+  size_t graph_events = 0;  // event pairs inside the profiling graph
 };
 
 struct Executor {
@@ -40,25 +53,38 @@ struct Executor {
   cudaStream_t stream = nullptr;
   int prec = 3;
   int kc_blocks = 0;
-  std::vector<StepExec> steps;
-  // per leaf: (stride, dim) of each sliced index it carries, in slice order
-  std::vector<std::vector<std::pair<int, int64_t>>> leaf_slice;  // (slice position, stride)
-  std::vector<int64_t> slice_dims;  // dims of the sliced indices, plan order
+  int n_leaves = 0;
+  std::vector<Launch> launches;  // one slice, in order
+  Launch reduce;                 // slice sum + final reduction -> dev_out
+  std::vector<size_t> inter_off; // arena byte offset per intermediate (id - n_leaves)
+  // per leaf: (slice position, stride) of each sliced index it carries
+  std::vector<std::vector<std::pair<int, int64_t>>> leaf_slice;
+  std::vector<int64_t> slice_dims;
   int64_t n_slices = 1;
-  int64_t final_size = 1;           // entries of the last step's output per slice
-  ContractArgs reduce;              // partial[slices][final] -> out
-  bool reduce_from_leaf = false;    // single-tensor network: reduce the leaf
-  int reduce_leaf = 0;
+  int64_t final_size = 1;        // entries of the last step's result per slice
+  int inter_dt = DT_F32X2;       // storage of intermediates
+  size_t split_a_bytes = 0;      // offset of the B operand region
   // device memory (owned)
   uint8_t* arena = nullptr;
   size_t arena_bytes = 0;
   uint8_t* splitbuf = nullptr;
   size_t split_bytes = 0;
-  double* partial = nullptr;
+  uint8_t* partial = nullptr;
   uint32_t* status = nullptr;
-  double* out_stage = nullptr;     // staging buffer of the host-buffer entry point
+  double* out_stage = nullptr;   // staging buffer of the host-buffer entry point
   int n_tc_steps = 0;
-  size_t workspace_bytes() const { return arena_bytes + split_bytes + (size_t)n_slices * final_size * 8; }
+  int n_fused_steps = 0;         // absorption steps folded into a consumer
+  int64_t launches_per_contract = 0;
+  Profiler prof;
+  // CUDA graph of one whole contraction, replayed on a private stream
+  // (index 0: plain, 1: with profiling events)
+  bool use_graph = true;
+  cudaStream_t own = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  size_t workspace_bytes() const {
+    return arena_bytes + split_bytes + (size_t)n_slices * final_size * 8;
+  }
 };
 
 // Build launch descriptors and allocate the workspace.  Returns an empty
@@ -68,5 +94,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
 // Enqueue the whole contraction; writes output_size FP64 entries to dev_out.
 std::string exec_run(Executor* ex, const std::vector<Leaf>& leaves, double* dev_out, cudaStream_t st, int* code);
 void exec_free(Executor* ex);
+// Sum the timed launches per class (after a stream sync) and reset.
+std::string exec_profile_read(Executor* ex, double* ms, int64_t* launches, double* flops, double* bytes);
 
 }  // namespace qtpu

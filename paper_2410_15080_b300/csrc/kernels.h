@@ -34,7 +34,46 @@ struct ContractArgs {
   int64_t n_out = 1, n_loop = 1;
 };
 
-enum DType { DT_F32 = 0, DT_F64 = 1 };
+enum DType { DT_F32 = 0, DT_F64 = 1, DT_F32X2 = 2 /* (hi, lo) float pair per entry */ };
+
+// ---------------------------------------------------------------- gather
+constexpr int kMaxOps = 6;
+
+// n / d for 32-bit n via a multiply-high and a shift (d fixed per launch)
+struct FastDiv {
+  uint32_t magic = 0, shift = 0;
+};
+FastDiv make_fastdiv(uint32_t d);
+
+// modes (outermost first) with their element strides in every operand
+struct GModes {
+  int n = 0;
+  uint32_t dim[kMaxModes];
+  FastDiv div[kMaxModes];
+  int64_t stride[kMaxModes][kMaxOps];
+};
+
+enum GatherMode {
+  GW_DENSE_PAIR = 0,   // write (hi, lo) float pairs, dense in out-mode order
+  GW_DENSE_F64 = 1,    // write FP64, dense
+  GW_SPLIT_BF16X3 = 2, // write 3 BF16 piece planes [rows][Kp]
+  GW_SPLIT_TF32X2 = 3, // write 2 TF32 piece planes
+  GW_SPLIT_TF32 = 4    // write 1 TF32 plane
+};
+
+// value(o) = sum over loop modes of prod_j X_j[...]; for the split modes the
+// entry index is (row over `out`, k over `kmodes`).
+struct GatherArgs {
+  int nops = 1;
+  int mode = GW_DENSE_PAIR;
+  const void* ptr[kMaxOps] = {};
+  int dt[kMaxOps] = {};
+  GModes out, loop, kmodes;
+  uint32_t n_out = 1, n_loop = 1;        // dense modes
+  uint32_t n_rows = 0, K = 0, Kp = 0;   // split modes
+  int row_fast = 0;  // split: operand 0 is contiguous along rows (read rows fastest)
+};
+cudaError_t launch_gather(const GatherArgs& a, void* out, int sm_count, cudaStream_t st);
 
 cudaError_t launch_contract(const void* A, int dtA, const void* B, int dtB, double* out,
                             const ContractArgs& a, int sm_count, cudaStream_t st);
@@ -56,7 +95,7 @@ cudaError_t launch_split(const void* src, int dt, void* dst, const SplitArgs& a,
 //       3 = BF16x3 (3 pieces, 6 products)
 struct GemmArgs {
   CUtensorMap tmA, tmB;  // 4-D maps over [pieces][batch][rows][Kp]
-  double* C = nullptr;   // [batch][M][N] FP64, dense
+  void* C = nullptr;     // [batch][N][M] (hi, lo) float pairs, dense (M fastest)
   int batch = 0, M = 0, N = 0, K = 0;
   int kc_blocks = 0;     // k-blocks per TMEM accumulation chunk (0 = all)
   int prec = 3;
@@ -64,6 +103,8 @@ struct GemmArgs {
   uint64_t limit_ns = 2000000000ull;
 };
 cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st);
+// one-time per-device setup of the GEMM kernels (shared-memory attribute)
+cudaError_t gemm_prepare();
 
 // Build the 4-D TMA map of a split operand buffer (returns false on failure).
 bool make_operand_map(CUtensorMap* map, void* base, int prec, int64_t batch, int64_t rows, int64_t K,

@@ -1,0 +1,376 @@
+// Multi-operand gather-contract kernel with compensated FP32 arithmetic.
+//
+//   value(o) = sum_{l} prod_{j < nops} X_j[off_j(o) + off_j(l)]
+//
+// over strided operand views, written either as an FP32 pair (hi, lo) per
+// entry (an intermediate tensor), as FP64 (the final output), or split into
+// tensor-core pieces laid out [rows][Kp] (a GEMM operand).  One kernel covers
+// every non-GEMM piece of the contraction: absorbing the QPD coefficient
+// tensors into a QT (section 4.1: a gate CT scales along its hyper-index, the
+// wire CT of Eq. wire-tensor mixes one index; the executor folds chains of
+// such absorptions into the operand gather of the step that consumes them),
+// dot products over the last shared indices, small pairwise steps, and the
+// gather + split of each GEMM operand.
+//
+// Why FP32 pairs: FP64 throughput on B300 is ~1/64 of FP32, so FP64 values
+// are decoded into (hi, lo) floats with integer operations only, products and
+// sums use error-free transformations (TwoProd via FMA, TwoSum), and
+// intermediates are stored as pairs (value = hi + lo, ~44 significant bits).
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace qtpu {
+
+namespace {
+
+// ------------------------------------------------------------ FP64 decode
+// x = hi + lo with hi = x truncated to 24 significant bits and lo the next
+// bits truncated to 24 (|x - hi - lo| < 2^-47 |x|), using integer operations
+// only.  Zeros and subnormals decode to 0; exponents outside the FP32 range
+// fall back to conversions.
+__device__ __forceinline__ float2 decode_f64(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const uint32_t uh = (uint32_t)(u >> 32), ul = (uint32_t)u;
+  const uint32_t sign = uh & 0x80000000u;
+  const int e = (int)((uh >> 20) & 0x7FF) - 1023;
+  if (e < -126 || e > 127) {
+    if (e == -1023) return make_float2(0.f, 0.f);
+    const float h = (float)x;  // out of FP32 range: inf / denormal path
+    return make_float2(h, (float)(x - (double)h));
+  }
+  const uint32_t mhi = ((uh & 0xFFFFFu) << 3) | (ul >> 29);  // top 23 mantissa bits
+  const float hi = __uint_as_float(sign | ((uint32_t)(e + 127) << 23) | mhi);
+  uint32_t rem = ul & 0x1FFFFFFFu;  // remaining 29 mantissa bits, weight 2^(e-52)
+  float lo = 0.f;
+  if (rem) {
+    const int p = 31 - __clz(rem);  // leading one, 0..28
+    const int el = e - 52 + p;
+    if (el >= -126) {
+      const uint32_t m = p >= 23 ? (rem >> (p - 23)) : (rem << (23 - p));
+      lo = __uint_as_float(sign | ((uint32_t)(el + 127) << 23) | (m & 0x7FFFFFu));
+    }
+  }
+  return make_float2(hi, lo);
+}
+
+template <int DT>
+__device__ __forceinline__ float2 load_pair(const void* p, int64_t i) {
+  if (DT == DT_F32) return make_float2(__ldg((const float*)p + i), 0.f);
+  if (DT == DT_F64) return decode_f64(__ldg((const double*)p + i));
+  return __ldg((const float2*)p + i);
+}
+
+__device__ __forceinline__ float2 load_any(const void* p, int dt, int64_t i) {
+  if (dt == DT_F64) return load_pair<DT_F64>(p, i);
+  if (dt == DT_F32X2) return load_pair<DT_F32X2>(p, i);
+  return load_pair<DT_F32>(p, i);
+}
+
+// (a_hi + a_lo) * (b_hi + b_lo) as an unnormalised pair
+__device__ __forceinline__ float2 mul_pair(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  const float e = fmaf(a.x, b.x, -p);
+  return make_float2(p, e + fmaf(a.x, b.y, a.y * b.x));
+}
+
+struct Acc {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float2 v) {
+    const float s = __fadd_rn(hi, v.x);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v.x, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, v.y));
+  }
+  __device__ __forceinline__ float2 get() const {  // renormalised (Fast2Sum)
+    const float s = __fadd_rn(hi, lo);
+    return make_float2(s, __fsub_rn(lo, __fsub_rn(s, hi)));
+  }
+};
+
+// ------------------------------------------------------------ indexing
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& d) {
+  return (uint32_t)(((uint64_t)__umulhi(n, d.magic) + n) >> d.shift);
+}
+
+template <int NOPS>
+__device__ __forceinline__ void offsets(uint32_t o, const GModes& t, int64_t* off) {
+#pragma unroll
+  for (int j = 0; j < NOPS; ++j) off[j] = 0;
+  for (int m = t.n - 1; m >= 0; --m) {
+    const uint32_t q = fdiv(o, t.div[m]);
+    const uint32_t i = o - q * t.dim[m];
+    o = q;
+#pragma unroll
+    for (int j = 0; j < NOPS; ++j) off[j] += (int64_t)i * t.stride[m][j];
+  }
+}
+
+template <int NOPS>
+__device__ __forceinline__ float2 term(const GatherArgs& a, const int64_t* off) {
+  float2 v = load_any(a.ptr[0], a.dt[0], off[0]);
+#pragma unroll
+  for (int j = 1; j < NOPS; ++j) v = mul_pair(v, load_any(a.ptr[j], a.dt[j], off[j]));
+  return v;
+}
+
+// value of one output entry: base offsets + sum over the loop modes
+template <int NOPS>
+__device__ __forceinline__ float2 entry(const GatherArgs& a, const int64_t* base) {
+  if (a.loop.n == 0) return term<NOPS>(a, base);
+  Acc acc;
+  if (a.loop.n == 1) {
+    int64_t off[NOPS];
+#pragma unroll
+    for (int j = 0; j < NOPS; ++j) off[j] = base[j];
+    for (uint32_t i = 0; i < a.loop.dim[0]; ++i) {
+      acc.add(term<NOPS>(a, off));
+#pragma unroll
+      for (int j = 0; j < NOPS; ++j) off[j] += a.loop.stride[0][j];
+    }
+    return acc.get();
+  }
+  uint32_t idx[kMaxModes];
+  int64_t off[NOPS];
+  for (int m = 0; m < a.loop.n; ++m) idx[m] = 0;
+#pragma unroll
+  for (int j = 0; j < NOPS; ++j) off[j] = base[j];
+  for (uint32_t l = 0; l < a.n_loop; ++l) {
+    acc.add(term<NOPS>(a, off));
+    int m = a.loop.n - 1;
+    ++idx[m];
+#pragma unroll
+    for (int j = 0; j < NOPS; ++j) off[j] += a.loop.stride[m][j];
+    while (m > 0 && idx[m] == a.loop.dim[m]) {
+#pragma unroll
+      for (int j = 0; j < NOPS; ++j) off[j] -= (int64_t)a.loop.dim[m] * a.loop.stride[m][j];
+      idx[m] = 0;
+      --m;
+      ++idx[m];
+#pragma unroll
+      for (int j = 0; j < NOPS; ++j) off[j] += a.loop.stride[m][j];
+    }
+  }
+  return acc.get();
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// ------------------------------------------------------------ dense writers
+// out[o] for o < n_out, one thread per entry (FP32 pair or FP64 output)
+template <int NOPS, bool F64OUT>
+__global__ void __launch_bounds__(256) k_gather_dense(const GatherArgs a, void* __restrict__ out) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < a.n_out; o += stride) {
+    int64_t base[NOPS];
+    offsets<NOPS>(o, a.out, base);
+    const float2 v = entry<NOPS>(a, base);
+    if (F64OUT)
+      ((double*)out)[o] = (double)v.x + (double)v.y;
+    else
+      ((float2*)out)[o] = v;
+  }
+}
+
+// one block per output entry for long sums (deterministic fixed-shape tree)
+template <int NOPS, bool F64OUT>
+__global__ void __launch_bounds__(256) k_gather_block(const GatherArgs a, void* __restrict__ out) {
+  __shared__ float2 red[8];
+  for (uint32_t o = blockIdx.x; o < a.n_out; o += gridDim.x) {
+    int64_t base[NOPS];
+    offsets<NOPS>(o, a.out, base);
+    Acc acc;
+    for (uint32_t l = threadIdx.x; l < a.n_loop; l += blockDim.x) {
+      int64_t lo[NOPS];
+      offsets<NOPS>(l, a.loop, lo);
+#pragma unroll
+      for (int j = 0; j < NOPS; ++j) lo[j] += base[j];
+      acc.add(term<NOPS>(a, lo));
+    }
+    float2 v = acc.get();
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+      Acc t;
+      t.hi = v.x;
+      t.lo = v.y;
+      t.add(make_float2(__shfl_xor_sync(0xffffffffu, v.x, s), __shfl_xor_sync(0xffffffffu, v.y, s)));
+      v = t.get();
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Acc t;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t.add(red[w]);
+      const float2 r = t.get();
+      if (F64OUT)
+        ((double*)out)[o] = (double)r.x + (double)r.y;
+      else
+        ((float2*)out)[o] = r;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ split writer
+// GEMM operand [rows][Kp]: out modes = row modes (a.out) x K modes (a.kmodes).
+// A block takes a tile of kTR rows x kTK k: (1) the per-operand offsets of
+// the tile's rows and ks go to shared memory (the offset of an entry is
+// row part + k part), (2) the entries are computed in the order in which the
+// leading operand is contiguous (rows or k fastest) and staged in shared
+// memory, (3) every thread splits 8 consecutive k of one row into pieces and
+// writes each piece plane with 16-byte stores.
+constexpr int kTR = 32, kTK = 64;
+
+template <int NOPS, int KIND, int NP>
+__global__ void __launch_bounds__(256) k_gather_split(const GatherArgs a, void* __restrict__ dst) {
+  __shared__ int64_t rowoff[kTR][NOPS];
+  __shared__ int64_t koff[kTK][NOPS];
+  __shared__ float2 tile[kTR][kTK + 1];
+  const uint32_t n_rt = (a.n_rows + kTR - 1) / kTR;
+  const uint32_t n_kt = (a.Kp + kTK - 1) / kTK;
+  const int64_t piece = (int64_t)a.n_rows * a.Kp;
+  const int tid = threadIdx.x;
+  for (uint32_t t = blockIdx.x; t < n_rt * n_kt; t += gridDim.x) {
+    const uint32_t rt = t / n_kt, kt = t - rt * n_kt;
+    const uint32_t r0 = rt * kTR, k0 = kt * kTK;
+    if (tid < kTR) {
+      int64_t o[NOPS];
+      offsets<NOPS>(min(r0 + tid, a.n_rows - 1), a.out, o);
+#pragma unroll
+      for (int j = 0; j < NOPS; ++j) rowoff[tid][j] = o[j];
+    } else if (tid < kTR + kTK) {
+      int64_t o[NOPS];
+      offsets<NOPS>(min(k0 + (tid - kTR), a.K - 1), a.kmodes, o);
+#pragma unroll
+      for (int j = 0; j < NOPS; ++j) koff[tid - kTR][j] = o[j];
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int e = tid; e < kTR * kTK; e += 256) {
+      int r, k;
+      if (a.row_fast) {
+        r = e % kTR;
+        k = e / kTR;
+      } else {
+        k = e % kTK;
+        r = e / kTK;
+      }
+      float2 v = make_float2(0.f, 0.f);
+      if (r0 + r < a.n_rows && k0 + k < a.K) {
+        int64_t b[NOPS];
+#pragma unroll
+        for (int j = 0; j < NOPS; ++j) b[j] = rowoff[r][j] + koff[k][j];
+        v = entry<NOPS>(a, b);
+      }
+      tile[r][k] = v;
+    }
+    __syncthreads();
+    {
+      const int r = tid >> 3, kk = (tid & 7) * 8;
+      const uint32_t row = r0 + r, kb = k0 + kk;
+      if (row < a.n_rows && kb < a.Kp) {
+        const int64_t base = (int64_t)row * a.Kp + kb;
+        if (KIND == 0) {
+          // BF16 pieces of hi + lo: p0 = bf16(hi), p1 = bf16((hi - p0) + lo),
+          // p2 = bf16(remainder); |x - p0 - p1 - p2| <~ 2^-26 |x|
+          __nv_bfloat16 h[3][8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const float2 v = tile[r][kk + e];
+            const __nv_bfloat16 p0 = __float2bfloat16_rn(v.x);
+            const float r1 = __fadd_rn(__fsub_rn(v.x, __bfloat162float(p0)), v.y);
+            const __nv_bfloat16 p1 = __float2bfloat16_rn(r1);
+            h[0][e] = p0;
+            h[1][e] = p1;
+            h[2][e] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(p1)));
+          }
+          __nv_bfloat16* d = (__nv_bfloat16*)dst;
+#pragma unroll
+          for (int p = 0; p < 3; ++p) *(uint4*)(d + p * piece + base) = *(const uint4*)h[p];
+        } else {
+          float f[NP][8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const float2 v = tile[r][kk + e];
+            const float t0 = tf32_rna(v.x);
+            f[0][e] = t0;
+            if (NP > 1) f[NP - 1][e] = tf32_rna(__fadd_rn(__fsub_rn(v.x, t0), v.y));
+          }
+          float* d = (float*)dst;
+#pragma unroll
+          for (int p = 0; p < NP; ++p) {
+            *(float4*)(d + p * piece + base) = *(const float4*)&f[p][0];
+            *(float4*)(d + p * piece + base + 4) = *(const float4*)&f[p][4];
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int NOPS>
+cudaError_t launch_n(const GatherArgs& a, void* out, int sm, cudaStream_t st) {
+  if (a.mode == GW_SPLIT_BF16X3 || a.mode == GW_SPLIT_TF32X2 || a.mode == GW_SPLIT_TF32) {
+    const int64_t tiles = (int64_t)((a.n_rows + kTR - 1) / kTR) * ((a.Kp + kTK - 1) / kTK);
+    if (tiles <= 0) return cudaSuccess;
+    int64_t g = tiles < (int64_t)sm * 8 ? tiles : (int64_t)sm * 8;
+    if (a.mode == GW_SPLIT_BF16X3)
+      k_gather_split<NOPS, 0, 3><<<(int)g, 256, 0, st>>>(a, out);
+    else if (a.mode == GW_SPLIT_TF32X2)
+      k_gather_split<NOPS, 1, 2><<<(int)g, 256, 0, st>>>(a, out);
+    else
+      k_gather_split<NOPS, 1, 1><<<(int)g, 256, 0, st>>>(a, out);
+    return cudaGetLastError();
+  }
+  if (a.n_out == 0) return cudaSuccess;
+  const bool f64 = a.mode == GW_DENSE_F64;
+  const bool block_mode = a.n_loop >= 1024 && a.n_out <= (uint32_t)sm * 16;
+  if (block_mode) {
+    const uint32_t g = a.n_out < (uint32_t)sm * 16 ? a.n_out : (uint32_t)sm * 16;
+    if (f64)
+      k_gather_block<NOPS, true><<<g, 256, 0, st>>>(a, out);
+    else
+      k_gather_block<NOPS, false><<<g, 256, 0, st>>>(a, out);
+  } else {
+    int64_t g = ((int64_t)a.n_out + 255) / 256;
+    if (g > (int64_t)sm * 32) g = (int64_t)sm * 32;
+    if (f64)
+      k_gather_dense<NOPS, true><<<(int)g, 256, 0, st>>>(a, out);
+    else
+      k_gather_dense<NOPS, false><<<(int)g, 256, 0, st>>>(a, out);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  uint32_t l = 0;
+  while (l < 32 && (1ull << l) < d) ++l;
+  f.shift = l;
+  f.magic = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+  if (d == 1) f.magic = 0, f.shift = 0;
+  return f;
+}
+
+cudaError_t launch_gather(const GatherArgs& a, void* out, int sm, cudaStream_t st) {
+  switch (a.nops) {
+    case 1: return launch_n<1>(a, out, sm, st);
+    case 2: return launch_n<2>(a, out, sm, st);
+    case 3: return launch_n<3>(a, out, sm, st);
+    case 4: return launch_n<4>(a, out, sm, st);
+    case 5: return launch_n<5>(a, out, sm, st);
+    case 6: return launch_n<6>(a, out, sm, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace qtpu

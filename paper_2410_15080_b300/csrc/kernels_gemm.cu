@@ -3,7 +3,8 @@
 // Pairwise contraction of two h-TN tensors (section 4.2: the post-processing
 // is a sequence of pairwise contractions) is, after regrouping indices, a
 // batched GEMM  C[b, m, n] = sum_k A[b, m, k] * B[b, n, k]  (both operands
-// K-major).  FP64 operands are split into low-precision pieces by the split
+// K-major; C stored [b][n][m], the layout in which the epilogue's stores are
+// contiguous).  FP64 operands are split into low-precision pieces by the split
 // kernel (x = x0 + x1 + x2, BF16 or TF32 pieces); the products of the pieces
 // whose combined weight is at or above 2^-16 (BF16x3: 6 products) or 2^-11
 // (3xTF32: 3 products) accumulate in FP32 in TMEM.  The tensor cores'
@@ -23,8 +24,8 @@
 //               overlaps the MMAs of the next);
 //   warps 2..17 epilogue: tcgen05.ld 32 lanes x 8 columns of both
 //               accumulators, chunk value X + Y accumulated with TwoSum into
-//               a float plus a BF16 error term per output in registers, FP64
-//               store at the end of the tile.
+//               a float plus a BF16 error term per output in registers; the
+//               tile is stored as (hi, lo) float pairs (no FP64 arithmetic).
 // Every wait is bounded (global timer); on give-up the kernel sets a status
 // bit, lets in-flight copies and MMAs land, frees TMEM and returns.
 #include <cstdio>
@@ -108,7 +109,7 @@ __device__ __forceinline__ float lo_get(uint32_t lo2, int half) {
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              double* __restrict__ Cout, int batch, int M, int N, int K, int kc_blocks, uint32_t* status,
+              float2* __restrict__ Cout, int batch, int M, int N, int K, int kc_blocks, uint32_t* status,
               uint64_t limit_ns) {
   using C = Cfg<PREC>;
   using L = Layout<PREC>;
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
-  const long long n_tiles = (long long)batch * mt * nt;
+  const int n_tiles = batch * mt * nt;  // host checks n_tiles < 2^31
   const int nkb = (K + C::KB - 1) / C::KB;
   const int kc0 = kc_blocks > 0 ? kc_blocks : C::KC;
   const int kc = kc0 < nkb ? kc0 : nkb;
@@ -167,9 +168,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t issued_phase[C::STAGES];
       for (int s = 0; s < C::STAGES; ++s) issued[s] = 0, issued_phase[s] = 0;
       bool ok = true;
-      for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         const int ntile = (int)(t % nt);
-        const long long r = t / nt;
+        const int r = t / nt;
         const int mtile = (int)(r % mt);
         const int b = (int)(r / mt);
         for (int kb = 0; kb < nkb; ++kb) {
@@ -205,9 +206,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t idesc = make_idesc(C::FMT, BM, BN);
       int stage = 0;
       uint32_t phase = 0;
-      long long item = 0;
+      int item = 0;
       bool ok = true, any = false;
-      for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         for (int ch = 0; ch < nchunks && ok; ++ch, ++item) {
           const int acc = (int)(item & 1);
           const uint32_t aph = (uint32_t)((item >> 1) & 1);
@@ -264,13 +265,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int ew = warp - 2;
     const int q = warp & 3;
     const int h = ew >> 2;
-    long long item = 0;
+    int item = 0;
     bool ok = true;
     float hi[kEpiCols];
     uint32_t lo2[kEpiCols / 2];
-    for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+    for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
       const int ntile = (int)(t % nt);
-      const long long r = t / nt;
+      const int r = t / nt;
       const int mtile = (int)(r % mt);
       const int b = (int)(r / mt);
 #pragma unroll
@@ -312,13 +313,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(&accempty[acc]);
       }
       if (!ok) break;
+      // C is stored [batch][N][M] (M fastest): for a fixed column the 32
+      // lanes of a warp write 32 consecutive rows, 256 contiguous bytes
       const int row = mtile * BM + q * 32 + lane;
       if (row < M) {
-        double* crow = Cout + ((long long)b * M + row) * (long long)N;
+        float2* cb = Cout + (long long)b * M * N + row;
         const int n0 = ntile * BN + h * kEpiCols;
 #pragma unroll
         for (int j = 0; j < kEpiCols; ++j)
-          if (n0 + j < N) crow[n0 + j] = (double)hi[j] + (double)lo_get(lo2[j >> 1], j & 1);
+          if (n0 + j < N) cb[(long long)(n0 + j) * M] = make_float2(hi[j], lo_get(lo2[j >> 1], j & 1));
       }
     }
   }
@@ -335,12 +338,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 template <int PREC>
 cudaError_t launch_t(const GemmArgs& a, int sm_count, cudaStream_t st) {
   using L = Layout<PREC>;
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
-  if (e != cudaSuccess) return e;
   const long long tiles = (long long)a.batch * ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
   if (tiles <= 0) return cudaSuccess;
   const int grid = (int)(tiles < sm_count ? tiles : sm_count);
-  k_gemm_tc<PREC><<<grid, kThreads, L::SMEM, st>>>(a.tmA, a.tmB, a.C, a.batch, a.M, a.N, a.K, a.kc_blocks,
+  k_gemm_tc<PREC><<<grid, kThreads, L::SMEM, st>>>(a.tmA, a.tmB, (float2*)a.C, a.batch, a.M, a.N, a.K, a.kc_blocks,
                                                      a.status, a.limit_ns);
   return cudaGetLastError();
 }
@@ -348,6 +349,15 @@ cudaError_t launch_t(const GemmArgs& a, int sm_count, cudaStream_t st) {
 }  // namespace
 
 int gemm_block_n() { return BN; }
+
+cudaError_t gemm_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, Layout<1>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Layout<2>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gemm_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Layout<3>::SMEM);
+  return e;
+}
 int gemm_k_block(int prec) { return prec == 3 ? Cfg<3>::KB : Cfg<1>::KB; }
 
 cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st) {

@@ -23,7 +23,8 @@ QTPU_QT, QTPU_CT = 0, 1
 SYMBOLS = ["qtpu_htn_create", "qtpu_htn_add_tensor", "qtpu_htn_set_output", "qtpu_htn_plan",
            "qtpu_htn_plan_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats", "qtpu_htn_contract",
            "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_sync", "qtpu_htn_destroy",
-           "qtpu_last_error"]
+           "qtpu_htn_profile", "qtpu_htn_profile_read", "qtpu_last_error"]
+KERNEL_CLASSES = ["contract", "split", "gemm", "reduce"]
 
 
 class QtpuError(RuntimeError):
@@ -57,7 +58,10 @@ def lib():
         L.qtpu_htn_plan_info.argtypes = [vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]
         L.qtpu_htn_output_size.argtypes = [vp, i64p]
         L.qtpu_htn_plan_stats.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int),
-                                          C.POINTER(C.c_int), C.POINTER(C.c_uint64)]
+                                          C.POINTER(C.c_int), C.POINTER(C.c_uint64), i64p]
+        L.qtpu_htn_profile.argtypes = [vp, C.c_int]
+        dp = C.POINTER(C.c_double)
+        L.qtpu_htn_profile_read.argtypes = [vp, C.c_int, dp, i64p, dp, dp]
         L.qtpu_htn_contract.argtypes = [vp, vp]
         L.qtpu_htn_contract_host.argtypes = [vp, C.POINTER(vp), vp]
         L.qtpu_htn_contract_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), vp]
@@ -138,10 +142,23 @@ class HTN:
         return n.value
 
     def plan_stats(self) -> dict:
-        f, ns, nt, ws = C.c_double(), C.c_int(), C.c_int(), C.c_uint64()
-        self._check(self._L.qtpu_htn_plan_stats(self._h, C.byref(f), C.byref(ns), C.byref(nt), C.byref(ws)))
+        f, ns, nt, ws, nl = C.c_double(), C.c_int(), C.c_int(), C.c_uint64(), C.c_int64()
+        self._check(self._L.qtpu_htn_plan_stats(self._h, C.byref(f), C.byref(ns), C.byref(nt), C.byref(ws),
+                                                C.byref(nl)))
         return {"flops_total": f.value, "n_steps": ns.value, "n_tensor_core_steps": nt.value,
-                "workspace_bytes": ws.value}
+                "workspace_bytes": ws.value, "launches_per_contract": nl.value}
+
+    def profile(self, enable: bool = True):
+        self._check(self._L.qtpu_htn_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """Per kernel class: summed ms, launches, useful FLOPs, algorithmic bytes."""
+        n = len(KERNEL_CLASSES)
+        ms, fl, by = (C.c_double * n)(), (C.c_double * n)(), (C.c_double * n)()
+        la = (C.c_int64 * n)()
+        self._check(self._L.qtpu_htn_profile_read(self._h, n, ms, la, fl, by))
+        return {k: {"ms": ms[i], "launches": la[i], "flops": fl[i], "bytes": by[i]}
+                for i, k in enumerate(KERNEL_CLASSES)}
 
     def contract(self, out=None):
         """Enqueue the contraction; returns the FP64 output (device tensor)."""
