@@ -326,6 +326,81 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
   const int es = prec == 3 ? 2 : 4;
   const int split_mode = prec == 3 ? GW_SPLIT_BF16X3 : (prec == 2 ? GW_SPLIT_TF32X2 : GW_SPLIT_TF32);
   int next_tmp = n_plan;  // ids of materialised virtual tensors
+  bool fast_off = false;
+  if (const char* e = std::getenv("QTPU_NO_FAST")) fast_off = std::atoi(e) != 0;
+
+  // Typed fast-path arguments: large operands first, small leaves folded
+  // into a table W (dense over their joint non-sliced indices).  `groups`
+  // are the index lists of the out / k / loop tables.
+  auto fast_args = [&](const std::vector<int>& src, const Inds& outg, const Inds& kg, const Inds& loopg,
+                       GatherArgs g, Launch* L) -> bool {
+    std::vector<int> big, small;
+    for (int t : src) {
+      const bool is_small = t < nl && prod(live_inds[t]) <= (double)kSmallLeaf;
+      (is_small ? small : big).push_back(t);
+    }
+    if (big.empty() || big.size() > 2) return false;
+    for (int t : big)
+      if (dt_of(t) != DT_F64 && dt_of(t) != DT_F32X2) return false;
+    Inds U;
+    for (int t : small)
+      for (int64_t i : live_inds[t])
+        if (!contains(U, i)) U.push_back(i);
+    std::map<int64_t, int64_t> wst;
+    int64_t wsz = 1;
+    for (int j = (int)U.size() - 1; j >= 0; --j) {
+      wst[U[j]] = wsz;
+      wsz *= dims.get(U[j]);
+    }
+    if (small.empty()) wsz = 0;
+    if (wsz > (int64_t)kMaxW) return false;
+    const int nb = (int)big.size();
+    const int ne = nb + (wsz ? 1 : 0);
+    g.nops = nb + (int)small.size();
+    g.nbig = nb;
+    g.w_size = (uint32_t)wsz;
+    std::vector<int> order = big;
+    order.insert(order.end(), small.begin(), small.end());
+    for (int j = 0; j < g.nops; ++j) {
+      g.dt[j] = dt_of(order[j]);
+      L->gf_src[j] = order[j];
+    }
+    g.out = GModes();
+    g.kmodes = GModes();
+    g.loop = GModes();
+    g.wmodes = GModes();
+    int64_t st[kMaxOps];
+    bool ok = true;
+    auto fill = [&](GModes& t, const Inds& grp, bool is_loop) {
+      for (int64_t i : grp) {
+        if (sliced.count(i)) continue;
+        for (int j = 0; j < nb; ++j) st[j] = sof(big[j], i);
+        if (wsz) st[nb] = wst.count(i) ? wst[i] : 0;
+        ok &= gpush(t, is_loop ? dims.get(i) : dims.get(i), st, ne);
+      }
+      gmerge(t, ne);
+    };
+    fill(g.out, outg, false);
+    fill(g.kmodes, kg, false);
+    fill(g.loop, loopg, true);
+    for (int64_t i : U) {
+      for (int j = 0; j < (int)small.size(); ++j) st[j] = sof(small[j], i);
+      ok &= gpush(g.wmodes, dims.get(i), st, (int)small.size());
+    }
+    if (!ok) return false;
+    // keep W's modes unmerged but set up their divisions
+    for (int m = 0; m < g.wmodes.n; ++m) g.wmodes.div[m] = make_fastdiv(g.wmodes.dim[m]);
+    for (int j = 0; j < nb; ++j) {
+      const int64_t mx = gmax(g.out, j) + gmax(g.loop, j) + gmax(g.kmodes, j) + slice_max[big[j]];
+      if (mx >= extent[big[j]]) return false;
+    }
+    for (int j = 0; j < (int)small.size(); ++j)
+      if (gmax(g.wmodes, j) + slice_max[small[j]] >= extent[small[j]]) return false;
+    if (wsz && gmax(g.out, nb) + gmax(g.loop, nb) + gmax(g.kmodes, nb) >= wsz) return false;
+    L->gf = g;
+    L->has_fast = true;
+    return true;
+  };
 
   // gather launch writing `inds` (dense) from the product of reprs
   auto gather_launch = [&](const std::vector<const Repr*>& rs, const Inds& out_inds, const Inds& extra_loop,
@@ -368,6 +443,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     L->dst = dst;
     L->g = g;
     L->flops = flops;
+    if (!fast_off) fast_args(src, out_inds, {}, loop, g, L);
     double by = (double)g.n_out * (mode == GW_DENSE_F64 ? 8 : 8);
     for (int s : std::set<int>(src.begin(), src.end())) by += bytes_of(s);
     L->bytes = by;
@@ -421,6 +497,39 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     for (int j = 0; j < g.nops; ++j) L->src[j] = src[j];
     L->dst = dst;
     L->g = g;
+    if (!fast_off) {
+      Inds rl, kl;
+      for (int64_t i : row_inds) rl.push_back(i);
+      for (int64_t i : k_inds) kl.push_back(i);
+      if (fast_args(src, rl, kl, r.L, g, L)) {
+        // same read order as the generic table: decided by the leading operand
+        int64_t mr = INT64_MAX, mk = INT64_MAX;
+        for (int q = 0; q < L->gf.out.n; ++q)
+          if (L->gf.out.stride[q][0] > 0) mr = std::min(mr, L->gf.out.stride[q][0]);
+        for (int q = 0; q < L->gf.kmodes.n; ++q)
+          if (L->gf.kmodes.stride[q][0] > 0) mk = std::min(mk, L->gf.kmodes.stride[q][0]);
+        L->gf.row_fast = mr < mk ? 1 : 0;
+        // fan-out: innermost k (or row) mode carried by W alone, dim 2 or 4
+        GatherArgs& f = L->gf;
+        f.fan = 0;
+        f.fan_f = 1;
+        if (f.w_size && f.nbig == 1) {
+          auto fan_ok = [&](const GModes& t) {
+            if (t.n == 0) return 0;
+            const int m = t.n - 1;
+            const uint32_t d = t.dim[m];
+            return (t.stride[m][0] == 0 && t.stride[m][1] != 0 && (d == 2 || d == 4)) ? (int)d : 0;
+          };
+          if (int d = fan_ok(f.kmodes)) {
+            f.fan = 1;
+            f.fan_f = d;
+          } else if (int d2 = fan_ok(f.out)) {
+            f.fan = 2;
+            f.fan_f = d2;
+          }
+        }
+      }
+    }
     double by = (double)np * rows * g.Kp * es;
     for (int s : std::set<int>(src.begin(), src.end())) by += bytes_of(s);
     L->bytes = by;
@@ -800,6 +909,13 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
     Timed t(ex->prof, st, L.kclass, L.flops, L.bytes);
     const bool from_partial = reduce && !ex->launches.empty();
     if (L.kind == LK_GATHER) {
+      if (L.has_fast && !from_partial) {
+        GatherArgs g = L.gf;
+        for (int j = 0; j < g.nops; ++j) g.ptr[j] = src_ptr(L.gf_src[j]);
+        cudaError_t e = launch_gather_fast(g, dst_ptr(L.dst, s), ex->sm_count, st);
+        if (e != cudaErrorNotSupported) return e;
+        cudaGetLastError();
+      }
       GatherArgs g = L.g;
       for (int j = 0; j < L.nsrc; ++j) g.ptr[j] = from_partial ? (const void*)ex->partial : src_ptr(L.src[j]);
       return launch_gather(g, dst_ptr(L.dst, s), ex->sm_count, st);

@@ -33,6 +33,9 @@ struct Launch {
   int src[kMaxOps] = {};  // operand tensor ids: leaf (< n_leaves) or intermediate
   int dst = DST_PARTIAL;  // intermediate id (>= n_leaves) or a DST_* code
   GatherArgs g;           // LK_GATHER (operand pointers patched per slice)
+  bool has_fast = false;  // typed fast path available (gf, operands gf_src)
+  GatherArgs gf;
+  int gf_src[kMaxOps] = {};
   GemmArgs gemm;          // LK_GEMM (split buffers fixed; C patched)
   ContractArgs c64;       // LK_CONTRACT64 (FP64 path)
   double flops = 0, bytes = 0;

@@ -72,8 +72,23 @@ struct GatherArgs {
   uint32_t n_out = 1, n_loop = 1;        // dense modes
   uint32_t n_rows = 0, K = 0, Kp = 0;   // split modes
   int row_fast = 0;  // split: operand 0 is contiguous along rows (read rows fastest)
+  // fast path: operands [0, nbig) are large stored tensors; the small leaves
+  // that follow are pre-multiplied into a table W held in shared memory, W
+  // dense over `wmodes` (per small operand j: stride[m][nbig + j]); in the
+  // out/loop/k tables the W operand occupies slot nbig with W's own strides
+  int nbig = 0;          // 0 = fast path not set up
+  int fan = 0;           // split fast path: 1 = innermost k mode, 2 = innermost row
+                         // mode is carried by W alone (dim fan_f): one thread
+                         // computes the fan_f entries from one operand load
+  int fan_f = 1;
+  uint32_t w_size = 0;   // entries of W (0 = no small operands)
+  GModes wmodes;
 };
 cudaError_t launch_gather(const GatherArgs& a, void* out, int sm_count, cudaStream_t st);
+// The same computation through the typed fast kernels (shared-memory table of
+// the small factors); cudaErrorNotSupported when no instantiation fits.
+constexpr uint32_t kMaxW = 1024;
+cudaError_t launch_gather_fast(const GatherArgs& a, void* out, int sm_count, cudaStream_t st);
 
 cudaError_t launch_contract(const void* A, int dtA, const void* B, int dtB, double* out,
                             const ContractArgs& a, int sm_count, cudaStream_t st);

@@ -1,0 +1,363 @@
+// Typed fast path of the gather kernels.
+//
+// Same computation as kernels_gather.cu,
+//   value(o) = sum_l prod_j X_j[...],
+// specialised for the shapes the h-TN contraction produces: at most two
+// large operands (a QT or an intermediate, typed at compile time as FP64 or
+// FP32 pair), and any number of small leaves -- the QPD coefficient tensors
+// absorbed into the step (section 4.1) -- whose product over their joint
+// index space is computed once per block into a table W in shared memory.
+// Each term then costs one typed load per large operand, one shared-memory
+// load and one compensated multiply-add.
+#include <cuda_bf16.h>
+
+#include "arith.cuh"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace qtpu {
+
+namespace {
+using namespace arith;
+
+// W[u] = prod over the small operands of their entry at u (u dense over a.wmodes)
+__device__ void build_w(const GatherArgs& a, float2* W) {
+  const int nsmall = a.nops - a.nbig;
+  for (uint32_t u = threadIdx.x; u < a.w_size; u += blockDim.x) {
+    int64_t off[kMaxOps];
+    for (int j = 0; j < nsmall; ++j) off[j] = 0;
+    uint32_t o = u;
+    for (int m = a.wmodes.n - 1; m >= 0; --m) {
+      const uint32_t q = fdiv(o, a.wmodes.div[m]);
+      const uint32_t i = o - q * a.wmodes.dim[m];
+      o = q;
+      for (int j = 0; j < nsmall; ++j) off[j] += (int64_t)i * a.wmodes.stride[m][j];
+    }
+    float2 v = load_any(a.ptr[a.nbig], a.dt[a.nbig], off[0]);
+    for (int j = 1; j < nsmall; ++j) v = mul_pair(v, load_any(a.ptr[a.nbig + j], a.dt[a.nbig + j], off[j]));
+    W[u] = v;
+  }
+}
+
+template <int NB, int DT0, int DT1, bool HW>
+struct Op {
+  static constexpr int NOPS = NB + (HW ? 1 : 0);
+  __device__ static __forceinline__ float2 term(const GatherArgs& a, const float2* W, const int64_t* off) {
+    float2 v = load_pair<DT0>(a.ptr[0], off[0]);
+    if (NB == 2) v = mul_pair(v, load_pair<DT1>(a.ptr[1], off[1]));
+    if (HW) v = mul_pair(v, W[off[NB]]);
+    return v;
+  }
+  __device__ static __forceinline__ float2 entry(const GatherArgs& a, const float2* W, const int64_t* base) {
+    if (a.loop.n == 0) return term(a, W, base);
+    Acc acc;
+    int64_t off[NOPS];
+#pragma unroll
+    for (int j = 0; j < NOPS; ++j) off[j] = base[j];
+    if (a.loop.n == 1) {
+      const uint32_t d = a.loop.dim[0];
+      for (uint32_t i = 0; i < d; ++i) {
+        acc.add(term(a, W, off));
+#pragma unroll
+        for (int j = 0; j < NOPS; ++j) off[j] += a.loop.stride[0][j];
+      }
+      return acc.get();
+    }
+    uint32_t idx[kMaxModes];
+    for (int m = 0; m < a.loop.n; ++m) idx[m] = 0;
+    for (uint32_t l = 0; l < a.n_loop; ++l) {
+      acc.add(term(a, W, off));
+      int m = a.loop.n - 1;
+      ++idx[m];
+#pragma unroll
+      for (int j = 0; j < NOPS; ++j) off[j] += a.loop.stride[m][j];
+      while (m > 0 && idx[m] == a.loop.dim[m]) {
+#pragma unroll
+        for (int j = 0; j < NOPS; ++j) off[j] -= (int64_t)a.loop.dim[m] * a.loop.stride[m][j];
+        idx[m] = 0;
+        --m;
+        ++idx[m];
+#pragma unroll
+        for (int j = 0; j < NOPS; ++j) off[j] += a.loop.stride[m][j];
+      }
+    }
+    return acc.get();
+  }
+};
+
+// F entries that share every large-operand offset (they differ only along a
+// mode that W alone carries): W offsets per entry in wof[F]
+template <int DT0, int F>
+__device__ __forceinline__ void entry_fan(const GatherArgs& a, const float2* W, int64_t xo, const int* wof,
+                                          float2* v) {
+  Acc acc[F];
+  if (a.loop.n == 0) {
+    const float2 x = load_pair<DT0>(a.ptr[0], xo);
+#pragma unroll
+    for (int f = 0; f < F; ++f) v[f] = mul_pair(x, W[wof[f]]);
+    return;
+  }
+  if (a.loop.n == 1) {
+    const uint32_t d = a.loop.dim[0];
+    const int64_t sx = a.loop.stride[0][0];
+    const int sw = (int)a.loop.stride[0][1];
+    for (uint32_t i = 0; i < d; ++i) {
+      const float2 x = load_pair<DT0>(a.ptr[0], xo + (int64_t)i * sx);
+#pragma unroll
+      for (int f = 0; f < F; ++f) acc[f].add(mul_pair(x, W[wof[f] + (int)i * sw]));
+    }
+  } else {
+    uint32_t idx[kMaxModes];
+    for (int m = 0; m < a.loop.n; ++m) idx[m] = 0;
+    int64_t ox = xo;
+    int ow = 0;
+    for (uint32_t l = 0; l < a.n_loop; ++l) {
+      const float2 x = load_pair<DT0>(a.ptr[0], ox);
+#pragma unroll
+      for (int f = 0; f < F; ++f) acc[f].add(mul_pair(x, W[wof[f] + ow]));
+      int m = a.loop.n - 1;
+      ++idx[m];
+      ox += a.loop.stride[m][0];
+      ow += (int)a.loop.stride[m][1];
+      while (m > 0 && idx[m] == a.loop.dim[m]) {
+        ox -= (int64_t)a.loop.dim[m] * a.loop.stride[m][0];
+        ow -= (int)(a.loop.dim[m] * a.loop.stride[m][1]);
+        idx[m] = 0;
+        --m;
+        ++idx[m];
+        ox += a.loop.stride[m][0];
+        ow += (int)a.loop.stride[m][1];
+      }
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < F; ++f) v[f] = acc[f].get();
+}
+
+// ------------------------------------------------------------ dense output
+template <int NB, int DT0, int DT1, bool HW, bool F64OUT>
+__global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __restrict__ out) {
+  using O = Op<NB, DT0, DT1, HW>;
+  __shared__ float2 W[HW ? kMaxW : 1];
+  if (HW) {
+    build_w(a, W);
+    __syncthreads();
+  }
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < a.n_out; o += stride) {
+    int64_t base[O::NOPS];
+    offsets<O::NOPS>(o, a.out, base);
+    const float2 v = O::entry(a, W, base);
+    if (F64OUT)
+      ((double*)out)[o] = (double)v.x + (double)v.y;
+    else
+      ((float2*)out)[o] = v;
+  }
+}
+
+// ------------------------------------------------------------ split output
+constexpr int kTR = 32, kTK = 64;
+
+template <int DT0, bool HW, int KIND, int NP, int F>
+__global__ void __launch_bounds__(256) k_split_fast(const GatherArgs a, void* __restrict__ dst) {
+  using O = Op<1, DT0, DT0, HW>;
+  constexpr int NOPS = O::NOPS;
+  __shared__ float2 W[HW ? kMaxW : 1];
+  __shared__ int64_t rowoff[kTR][NOPS];
+  __shared__ int64_t koff[kTK][NOPS];
+  __shared__ float2 tile[kTR][kTK + 1];
+  if (HW) {
+    build_w(a, W);
+    __syncthreads();
+  }
+  const uint32_t n_rt = (a.n_rows + kTR - 1) / kTR;
+  const uint32_t n_kt = (a.Kp + kTK - 1) / kTK;
+  const int64_t piece = (int64_t)a.n_rows * a.Kp;
+  const int tid = threadIdx.x;
+  for (uint32_t t = blockIdx.x; t < n_rt * n_kt; t += gridDim.x) {
+    const uint32_t rt = t / n_kt, kt = t - rt * n_kt;
+    const uint32_t r0 = rt * kTR, k0 = kt * kTK;
+    if (tid < kTR) {
+      int64_t o[NOPS];
+      offsets<NOPS>(min(r0 + tid, a.n_rows - 1), a.out, o);
+#pragma unroll
+      for (int j = 0; j < NOPS; ++j) rowoff[tid][j] = o[j];
+    } else if (tid < kTR + kTK) {
+      int64_t o[NOPS];
+      offsets<NOPS>(min(k0 + (tid - kTR), a.K - 1), a.kmodes, o);
+#pragma unroll
+      for (int j = 0; j < NOPS; ++j) koff[tid - kTR][j] = o[j];
+    }
+    __syncthreads();
+    if (F > 1) {
+      // work item = F entries along the fan mode (rows or ks), one operand load each
+      constexpr int NI = kTR * kTK / F;
+      for (int e = tid; e < NI; e += 256) {
+        int r, k;
+        if (a.fan == 2) {  // F consecutive rows
+          const int ng = kTR / F;
+          if (a.row_fast) {
+            r = (e % ng) * F;
+            k = e / ng;
+          } else {
+            k = e % kTK;
+            r = (e / kTK) * F;
+          }
+        } else {  // F consecutive ks
+          const int ng = kTK / F;
+          if (a.row_fast) {
+            r = e % kTR;
+            k = (e / kTR) * F;
+          } else {
+            k = (e % ng) * F;
+            r = e / ng;
+          }
+        }
+        float2 v[F];
+        if (r0 + r < a.n_rows && k0 + k < a.K) {
+          int wof[F];
+#pragma unroll
+          for (int f = 0; f < F; ++f)
+            wof[f] = (int)(a.fan == 2 ? rowoff[r + f][1] + koff[k][1] : rowoff[r][1] + koff[k + f][1]);
+          entry_fan<DT0, F>(a, W, rowoff[r][0] + koff[k][0], wof, v);
+        } else {
+#pragma unroll
+          for (int f = 0; f < F; ++f) v[f] = make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+          const int rr = a.fan == 2 ? r + f : r, kk = a.fan == 2 ? k : k + f;
+          const bool in = r0 + rr < a.n_rows && k0 + kk < a.K;
+          tile[rr][kk] = in ? v[f] : make_float2(0.f, 0.f);
+        }
+      }
+    } else {
+#pragma unroll 2
+    for (int e = tid; e < kTR * kTK; e += 256) {
+      int r, k;
+      if (a.row_fast) {
+        r = e % kTR;
+        k = e / kTR;
+      } else {
+        k = e % kTK;
+        r = e / kTK;
+      }
+      float2 v = make_float2(0.f, 0.f);
+      if (r0 + r < a.n_rows && k0 + k < a.K) {
+        int64_t b[NOPS];
+#pragma unroll
+        for (int j = 0; j < NOPS; ++j) b[j] = rowoff[r][j] + koff[k][j];
+        v = O::entry(a, W, b);
+      }
+      tile[r][k] = v;
+    }
+    }
+    __syncthreads();
+    {
+      const int r = tid >> 3, kk = (tid & 7) * 8;
+      const uint32_t row = r0 + r, kb = k0 + kk;
+      if (row < a.n_rows && kb < a.Kp) {
+        const int64_t base = (int64_t)row * a.Kp + kb;
+        if (KIND == 0) {
+          __nv_bfloat16 h[3][8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const float2 v = tile[r][kk + e];
+            const __nv_bfloat16 p0 = __float2bfloat16_rn(v.x);
+            const float r1 = __fadd_rn(__fsub_rn(v.x, __bfloat162float(p0)), v.y);
+            const __nv_bfloat16 p1 = __float2bfloat16_rn(r1);
+            h[0][e] = p0;
+            h[1][e] = p1;
+            h[2][e] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(p1)));
+          }
+          __nv_bfloat16* d = (__nv_bfloat16*)dst;
+#pragma unroll
+          for (int p = 0; p < 3; ++p) *(uint4*)(d + p * piece + base) = *(const uint4*)h[p];
+        } else {
+          float f[NP][8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const float2 v = tile[r][kk + e];
+            const float t0 = tf32_rna(v.x);
+            f[0][e] = t0;
+            if (NP > 1) f[NP - 1][e] = tf32_rna(__fadd_rn(__fsub_rn(v.x, t0), v.y));
+          }
+          float* d = (float*)dst;
+#pragma unroll
+          for (int p = 0; p < NP; ++p) {
+            *(float4*)(d + p * piece + base) = *(const float4*)&f[p][0];
+            *(float4*)(d + p * piece + base + 4) = *(const float4*)&f[p][4];
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int DT0, bool HW, int F>
+cudaError_t split_f(const GatherArgs& a, void* out, int g, cudaStream_t st) {
+  if (a.mode == GW_SPLIT_BF16X3)
+    k_split_fast<DT0, HW, 0, 3, F><<<g, 256, 0, st>>>(a, out);
+  else if (a.mode == GW_SPLIT_TF32X2)
+    k_split_fast<DT0, HW, 1, 2, F><<<g, 256, 0, st>>>(a, out);
+  else
+    k_split_fast<DT0, HW, 1, 1, F><<<g, 256, 0, st>>>(a, out);
+  return cudaGetLastError();
+}
+
+template <int DT0, bool HW>
+cudaError_t split_dt(const GatherArgs& a, void* out, int sm, cudaStream_t st) {
+  const int64_t tiles = (int64_t)((a.n_rows + kTR - 1) / kTR) * ((a.Kp + kTK - 1) / kTK);
+  if (tiles <= 0) return cudaSuccess;
+  // several tiles per block when a W table is built; otherwise one per block
+  const int64_t cap = HW ? (int64_t)sm * 4 : (int64_t)sm * 8;
+  const int g = (int)(tiles < cap ? tiles : cap);
+  if (HW && a.fan && a.fan_f == 4) return split_f<DT0, HW, 4>(a, out, g, st);
+  if (HW && a.fan && a.fan_f == 2) return split_f<DT0, HW, 2>(a, out, g, st);
+  return split_f<DT0, HW, 1>(a, out, g, st);
+}
+
+template <int NB, int DT0, int DT1, bool HW>
+cudaError_t dense_dt(const GatherArgs& a, void* out, int sm, cudaStream_t st) {
+  if (a.n_out == 0) return cudaSuccess;
+  int64_t g = ((int64_t)a.n_out + 255) / 256;
+  if (g > (int64_t)sm * 8) g = (int64_t)sm * 8;
+  if (a.mode == GW_DENSE_F64)
+    k_dense_fast<NB, DT0, DT1, HW, true><<<(int)g, 256, 0, st>>>(a, out);
+  else
+    k_dense_fast<NB, DT0, DT1, HW, false><<<(int)g, 256, 0, st>>>(a, out);
+  return cudaGetLastError();
+}
+
+template <int NB, int DT0, int DT1>
+cudaError_t dense_w(const GatherArgs& a, void* out, int sm, cudaStream_t st) {
+  return a.w_size ? dense_dt<NB, DT0, DT1, true>(a, out, sm, st) : dense_dt<NB, DT0, DT1, false>(a, out, sm, st);
+}
+
+bool typed(int dt) { return dt == DT_F64 || dt == DT_F32X2; }
+
+}  // namespace
+
+cudaError_t launch_gather_fast(const GatherArgs& a, void* out, int sm, cudaStream_t st) {
+  if (a.nbig < 1 || a.nbig > 2 || a.w_size > kMaxW) return cudaErrorNotSupported;
+  for (int j = 0; j < a.nbig; ++j)
+    if (!typed(a.dt[j])) return cudaErrorNotSupported;
+  const bool split = a.mode == GW_SPLIT_BF16X3 || a.mode == GW_SPLIT_TF32X2 || a.mode == GW_SPLIT_TF32;
+  if (split) {
+    if (a.nbig != 1) return cudaErrorNotSupported;
+    if (a.dt[0] == DT_F64)
+      return a.w_size ? split_dt<DT_F64, true>(a, out, sm, st) : split_dt<DT_F64, false>(a, out, sm, st);
+    return a.w_size ? split_dt<DT_F32X2, true>(a, out, sm, st) : split_dt<DT_F32X2, false>(a, out, sm, st);
+  }
+  // long sums over few outputs go to the block-reduction kernel of the generic path
+  if (a.n_loop >= 1024 && a.n_out <= (uint32_t)sm * 16) return cudaErrorNotSupported;
+  if (a.nbig == 1)
+    return a.dt[0] == DT_F64 ? dense_w<1, DT_F64, DT_F64>(a, out, sm, st) : dense_w<1, DT_F32X2, DT_F64>(a, out, sm, st);
+  if (a.dt[0] == DT_F64)
+    return a.dt[1] == DT_F64 ? dense_w<2, DT_F64, DT_F64>(a, out, sm, st) : dense_w<2, DT_F64, DT_F32X2>(a, out, sm, st);
+  return a.dt[1] == DT_F64 ? dense_w<2, DT_F32X2, DT_F64>(a, out, sm, st)
+                           : dense_w<2, DT_F32X2, DT_F32X2>(a, out, sm, st);
+}
+
+}  // namespace qtpu

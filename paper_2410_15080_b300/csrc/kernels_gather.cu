@@ -18,95 +18,14 @@
 // intermediates are stored as pairs (value = hi + lo, ~44 significant bits).
 #include <cuda_bf16.h>
 
+#include "arith.cuh"
 #include "common.cuh"
 #include "kernels.h"
 
 namespace qtpu {
 
 namespace {
-
-// ------------------------------------------------------------ FP64 decode
-// x = hi + lo with hi = x truncated to 24 significant bits and lo the next
-// bits truncated to 24 (|x - hi - lo| < 2^-47 |x|), using integer operations
-// only.  Zeros and subnormals decode to 0; exponents outside the FP32 range
-// fall back to conversions.
-__device__ __forceinline__ float2 decode_f64(double x) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const uint32_t uh = (uint32_t)(u >> 32), ul = (uint32_t)u;
-  const uint32_t sign = uh & 0x80000000u;
-  const int e = (int)((uh >> 20) & 0x7FF) - 1023;
-  if (e < -126 || e > 127) {
-    if (e == -1023) return make_float2(0.f, 0.f);
-    const float h = (float)x;  // out of FP32 range: inf / denormal path
-    return make_float2(h, (float)(x - (double)h));
-  }
-  const uint32_t mhi = ((uh & 0xFFFFFu) << 3) | (ul >> 29);  // top 23 mantissa bits
-  const float hi = __uint_as_float(sign | ((uint32_t)(e + 127) << 23) | mhi);
-  uint32_t rem = ul & 0x1FFFFFFFu;  // remaining 29 mantissa bits, weight 2^(e-52)
-  float lo = 0.f;
-  if (rem) {
-    const int p = 31 - __clz(rem);  // leading one, 0..28
-    const int el = e - 52 + p;
-    if (el >= -126) {
-      const uint32_t m = p >= 23 ? (rem >> (p - 23)) : (rem << (23 - p));
-      lo = __uint_as_float(sign | ((uint32_t)(el + 127) << 23) | (m & 0x7FFFFFu));
-    }
-  }
-  return make_float2(hi, lo);
-}
-
-template <int DT>
-__device__ __forceinline__ float2 load_pair(const void* p, int64_t i) {
-  if (DT == DT_F32) return make_float2(__ldg((const float*)p + i), 0.f);
-  if (DT == DT_F64) return decode_f64(__ldg((const double*)p + i));
-  return __ldg((const float2*)p + i);
-}
-
-__device__ __forceinline__ float2 load_any(const void* p, int dt, int64_t i) {
-  if (dt == DT_F64) return load_pair<DT_F64>(p, i);
-  if (dt == DT_F32X2) return load_pair<DT_F32X2>(p, i);
-  return load_pair<DT_F32>(p, i);
-}
-
-// (a_hi + a_lo) * (b_hi + b_lo) as an unnormalised pair
-__device__ __forceinline__ float2 mul_pair(float2 a, float2 b) {
-  const float p = a.x * b.x;
-  const float e = fmaf(a.x, b.x, -p);
-  return make_float2(p, e + fmaf(a.x, b.y, a.y * b.x));
-}
-
-struct Acc {
-  float hi = 0.f, lo = 0.f;
-  __device__ __forceinline__ void add(float2 v) {
-    const float s = __fadd_rn(hi, v.x);
-    const float bb = __fsub_rn(s, hi);
-    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v.x, bb));
-    hi = s;
-    lo = __fadd_rn(lo, __fadd_rn(e, v.y));
-  }
-  __device__ __forceinline__ float2 get() const {  // renormalised (Fast2Sum)
-    const float s = __fadd_rn(hi, lo);
-    return make_float2(s, __fsub_rn(lo, __fsub_rn(s, hi)));
-  }
-};
-
-// ------------------------------------------------------------ indexing
-__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& d) {
-  return (uint32_t)(((uint64_t)__umulhi(n, d.magic) + n) >> d.shift);
-}
-
-template <int NOPS>
-__device__ __forceinline__ void offsets(uint32_t o, const GModes& t, int64_t* off) {
-#pragma unroll
-  for (int j = 0; j < NOPS; ++j) off[j] = 0;
-  for (int m = t.n - 1; m >= 0; --m) {
-    const uint32_t q = fdiv(o, t.div[m]);
-    const uint32_t i = o - q * t.dim[m];
-    o = q;
-#pragma unroll
-    for (int j = 0; j < NOPS; ++j) off[j] += (int64_t)i * t.stride[m][j];
-  }
-}
+using namespace arith;
 
 template <int NOPS>
 __device__ __forceinline__ float2 term(const GatherArgs& a, const int64_t* off) {
@@ -154,12 +73,6 @@ __device__ __forceinline__ float2 entry(const GatherArgs& a, const int64_t* base
     }
   }
   return acc.get();
-}
-
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
 }
 
 // ------------------------------------------------------------ dense writers

@@ -151,3 +151,18 @@ def test_deterministic_repeat():
     a, _ = contract_gpu(net)
     b, _ = contract_gpu(net)
     np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("fast", ["0", "1"])
+@pytest.mark.parametrize("graph", ["0", "1"])
+def test_generic_and_fast_gather_paths_agree(fast, graph, monkeypatch):
+    """The typed fast gather kernels and the generic ones (and direct launches
+    vs CUDA-graph replay) compute the same contraction."""
+    monkeypatch.setenv("QTPU_NO_FAST", "0" if fast == "1" else "1")
+    monkeypatch.setenv("QTPU_NO_GRAPH", "0" if graph == "1" else "1")
+    net = synth.ring_htn(n_sub=5, gates_per_edge=2, wires_per_edge=1, k=3, seed=21)
+    ref = oracle_value(net)
+    got, _ = contract_gpu(net, prec="bf16x3")
+    assert rel_err(got, ref) <= REL_TOL
+    got64, _ = contract_gpu(net, prec="fp64")
+    assert rel_err(got64, ref) <= FP64_TOL
