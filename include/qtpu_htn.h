@@ -179,6 +179,42 @@ qtpu_status qtpu_htn_destroy(qtpu_htn* h);
  * NULL).  Never NULL. */
 const char* qtpu_last_error(const qtpu_htn* h);
 
+/* Bytes of the fixed device scratch array used by
+ * qtpu_pairwise_contract_noalloc (held by every GPU that loads the library,
+ * from first use until the process exits). */
+#define QTPU_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* Allocation-free pairwise contraction.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory at call
+ * time -- code running inside a memory pool or arena that another component
+ * sized in advance, latency-critical loops where cudaMalloc / cudaFree would
+ * synchronise the device or stall, and plain C callers that only hold device
+ * pointers and no allocator.  It performs the computation of one
+ * tensor-core step of qtpu_htn_contract, with every scratch buffer taken from
+ * a fixed file-scope device array of QTPU_NOALLOC_SCRATCH_BYTES.
+ *
+ *   C[b][m][n] = sum_k A[b][m][k] * B[b][k][n]   for b < batch, m < M, n < N
+ *
+ *   A, B, C    device pointers, FP64, dense row-major ([batch][M][K],
+ *              [batch][K][N], [batch][M][N]); A and B are read, C written;
+ *              all owned by the caller
+ *   cuda_stream  the stream the work is enqueued on (NULL = legacy default);
+ *              the call is asynchronous, runs on the calling thread's current
+ *              device, and uses BF16x3 tensor-core arithmetic (error about
+ *              6e-8 relative, as the regular entry points)
+ *
+ * Scratch needed: 2048 + 6*batch*(M+N)*round_up(K,8) + 8*batch*M*N bytes; a
+ * call that needs more returns QTPU_ELIMIT and does nothing.  QTPU_EINVAL on
+ * NULL pointers or sizes < 1, QTPU_ECUDA if a CUDA call fails.  The first call
+ * on a device resolves the scratch array's device address
+ * (cudaGetSymbolAddress) for that device; make that first call before any
+ * stream capture.  Every call shares the one array and leaves its contents
+ * behind; calls whose GPU work overlaps in time race on it and must be
+ * serialised by the caller. */
+qtpu_status qtpu_pairwise_contract_noalloc(const double* A, const double* B, double* C,
+                                           int batch, int M, int N, int K,
+                                           void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,7 @@ QTPU_QT, QTPU_CT = 0, 1
 SYMBOLS = ["qtpu_htn_create", "qtpu_htn_add_tensor", "qtpu_htn_set_output", "qtpu_htn_plan",
            "qtpu_htn_plan_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats", "qtpu_htn_contract",
            "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_sync", "qtpu_htn_destroy",
-           "qtpu_htn_profile", "qtpu_htn_profile_read", "qtpu_last_error"]
+           "qtpu_htn_profile", "qtpu_htn_profile_read", "qtpu_pairwise_contract_noalloc", "qtpu_last_error"]
 KERNEL_CLASSES = ["contract", "split", "gemm", "reduce"]
 
 
@@ -66,6 +66,7 @@ def lib():
         L.qtpu_htn_contract_host.argtypes = [vp, C.POINTER(vp), vp]
         L.qtpu_htn_contract_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), vp]
         L.qtpu_htn_sync.argtypes = [vp]
+        L.qtpu_pairwise_contract_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]
         L.qtpu_htn_destroy.argtypes = [vp]
         L.qtpu_last_error.argtypes = [vp]
         L.qtpu_last_error.restype = C.c_char_p
@@ -201,6 +202,27 @@ def contract_batch(htns: Sequence[HTN], outs, stream: int | None = None):
     st = L.qtpu_htn_contract_batch(hs, len(htns), ps, C.c_void_p(stream or 0))
     if st != QTPU_OK:
         raise QtpuError(st, "contract_batch failed")
+
+
+def pairwise_contract_noalloc(A, B, C_out, stream: int | None = None):
+    """C_out[b] = A[b] @ B[b] through the allocation-free entry point (for
+    callers that cannot allocate device memory at call time; see the C
+    header).  A: [batch, M, K], B: [batch, K, N], C_out: [batch, M, N], all
+    contiguous FP64 CUDA tensors owned by the caller."""
+    import torch
+    L = lib()
+    b, m, k = A.shape
+    n = B.shape[2]
+    assert B.shape == (b, k, n) and C_out.shape == (b, m, n)
+    for t in (A, B, C_out):
+        assert t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()
+    if stream is None:
+        stream = torch.cuda.current_stream(A.device).cuda_stream
+    st = L.qtpu_pairwise_contract_noalloc(C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()),
+                                          C.c_void_p(C_out.data_ptr()), b, m, n, k, C.c_void_p(stream or 0))
+    if st != QTPU_OK:
+        raise QtpuError(st, "qtpu_pairwise_contract_noalloc failed")
+    return C_out
 
 
 def plan_text(tensor_inds, dims: dict, output, max_intermediate_bytes=0, n_slices=0, slice_dim=0) -> str:
