@@ -124,12 +124,22 @@ def parse_plan(text: str):
     return steps, final_sum
 
 
-def fp64_torch_path(tensors, output, steps, final_sum):
-    """The same pairwise plan with torch FP64 ops: permute + bmm per step."""
+def fp64_torch_path(tensors, output, steps, final_sum, fixed=None):
+    """The same pairwise plan with torch FP64 ops: permute + bmm per step.
+    ``fixed`` maps sliced index ids to their values (one slice)."""
     import torch
-    live = {t: (list(inds), x) for t, (inds, x) in enumerate(tensors)}
+    live = {}
+    for t, (inds, x) in enumerate(tensors):
+        inds = list(inds)
+        if fixed:
+            sel = tuple(fixed.get(i, slice(None)) for i in inds)
+            x = x[sel]
+            inds = [i for i in inds if i not in fixed]
+        live[t] = (inds, x)
     nxt = len(tensors)
     for x, y, g in steps:
+        if fixed:
+            g = {kk: [i for i in v if i not in fixed] for kk, v in g.items()}
         ia, a = live.pop(x)
         ib, b = live.pop(y)
         if g["sa"]:
@@ -151,6 +161,7 @@ def fp64_torch_path(tensors, output, steps, final_sum):
         live[nxt] = (g["batch"] + g["m"] + g["n"], c.reshape(shape))
         nxt += 1
     (inds, x), = live.values()
+    final_sum = [i for i in final_sum if not fixed or i not in fixed]
     if final_sum:
         x = x.sum(dim=[inds.index(i) for i in final_sum])
         inds = [i for i in inds if i not in final_sum]
@@ -248,19 +259,29 @@ def run_ours(args, rank, world):
                for t in net.tensors]
     h = from_network(tensors, net.output, prec=args.prec, **plan_kw)
     st = h.plan_stats()
-    flops = st["flops_total"]
     out = torch.empty(h.output_size(), dtype=torch.float64, device=dev)
     flush_buf = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MiB > L2
     flush = (lambda: flush_buf.zero_()) if net.nbytes() < (256 << 20) else (lambda: None)
+    n_slices = int(h.plan_info().split("slices n=")[1].split()[0])
+    sub = args.workload == "100q"
+    if sub:
+        # every slice runs the same launches: time a fixed subset of them
+        S = min(args.slices_timed, n_slices)
+        flops = st["flops_total"] / n_slices * S
+        step = lambda: h.contract_slices(0, S, out)  # noqa: E731
+    else:
+        S = n_slices
+        flops = st["flops_total"]
+        step = lambda: h.contract(out)  # noqa: E731
 
     for _ in range(args.warmup):
-        h.contract(out)
+        step()
     h.sync()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     with ClockSampler(dev.index) as clk:
-        ts = timed_steps(lambda: h.contract(out), args.steps, flush)
+        ts = timed_steps(step, args.steps, flush)
         if world > 1:
             dist.barrier()
     h.sync()
@@ -272,10 +293,17 @@ def run_ours(args, rank, world):
 
     # per-kernel-class timing (separate pass, same launches)
     h.profile(True)
+    prof = None
     for _ in range(args.steps):
         flush()
-        h.contract(out)
-    prof = h.profile_read()
+        step()
+        p = h.profile_read()
+        if prof is None:
+            prof = p
+        else:
+            for kk in prof:
+                for f in prof[kk]:
+                    prof[kk][f] += p[kk][f]
     h.profile(False)
 
     # parity of this run's output against the FP64 oracle (mid workload)
@@ -289,9 +317,9 @@ def run_ours(args, rank, world):
 
     # plain FP64 GPU path: same plan, torch FP64 ops, one launch per step
     fp64 = None
-    if args.workload == "mid":
-        steps, final_sum = parse_plan(h.plan_info())
-        t64 = [(list(i), x.double()) for i, x, _ in tensors]
+    steps, final_sum = parse_plan(h.plan_info())
+    t64 = [(list(i), x.double()) for i, x, _ in tensors]
+    if not sub:
         for _ in range(2):
             fp64_torch_path(t64, list(net.output), steps, final_sum)
         ts64 = timed_steps(lambda: fp64_torch_path(t64, list(net.output), steps, final_sum),
@@ -299,20 +327,42 @@ def run_ours(args, rank, world):
         ms64 = statistics.mean(ts64)
         fp64 = {"value": flops / (ms64 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms64,
                 "impl": "torch FP64 permute+bmm per planned step", "speedup_of_ours": ms64 / ms}
+    else:
+        # the FP64 path on a fixed subset of slices (same shapes), extrapolated
+        sliced = [int(x) for x in h.plan_info().split("idx=")[1].split()[0].split(",")]
+        dims = net.dims()
+        def one_slice(s_id):
+            vals, r = [], s_id
+            for i in reversed(sliced):
+                vals.append(r % dims[i])
+                r //= dims[i]
+            return dict(zip(reversed(sliced), vals))
+        S64 = 2
+        fp64_torch_path(t64, list(net.output), steps, final_sum, one_slice(0))
+        ts64 = timed_steps(lambda: [fp64_torch_path(t64, list(net.output), steps, final_sum, one_slice(s))
+                                    for s in range(S64)], 2, flush)
+        ms64 = statistics.mean(ts64) / S64 * S
+        fp64 = {"value": flops / (ms64 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms64,
+                "impl": f"torch FP64 permute+bmm per planned step, {S64} slices timed, extrapolated to {S}",
+                "speedup_of_ours": ms64 / ms}
 
     # end to end through the C ABI with host buffers
-    host = [torch.from_numpy(np.ascontiguousarray(t.data)).pin_memory() for t in net.tensors]
-    hout = np.empty(h.output_size(), dtype=np.float64)
-    h.contract_host(host, hout)
-    te = []
-    for _ in range(max(3, min(args.steps, 10))):
-        flush()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+    e2e = None
+    if not sub:
+        host = [torch.from_numpy(np.ascontiguousarray(t.data)).pin_memory() for t in net.tensors]
+        hout = np.empty(h.output_size(), dtype=np.float64)
         h.contract_host(host, hout)
-        te.append(time.perf_counter() - t0)
-    e2e_ms = 1e3 * statistics.mean(te)
-    h2d = sum(x.numel() * x.element_size() for x in host)
+        te = []
+        for _ in range(max(3, min(args.steps, 10))):
+            flush()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h.contract_host(host, hout)
+            te.append(time.perf_counter() - t0)
+        e2e_ms = 1e3 * statistics.mean(te)
+        h2d = sum(x.numel() * x.element_size() for x in host)
+        e2e = {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h.output_size() * 8}
 
     peaks = load_peaks()
     dom = max(prof, key=lambda k: prof[k]["ms"])
@@ -349,14 +399,15 @@ def run_ours(args, rank, world):
         "config": {"workload": WORKLOADS[args.workload], "flops_per_step": flops, "prec": args.prec,
                    "l2": "flushed between timed steps (256 MiB write)" if net.nbytes() < (256 << 20)
                    else "inputs larger than L2", "plan_steps": st["n_steps"],
-                   "tensor_core_steps": st["n_tensor_core_steps"], "parallelism": f"replicas x{world}"},
+                   "tensor_core_steps": st["n_tensor_core_steps"], "parallelism": f"replicas x{world}",
+                   "slices": n_slices, "slices_timed": S,
+                   "flops_total_all_slices": st["flops_total"]},
         "rel_err_vs_oracle": rel,
         "roofline": roof,
         "cpu_baseline": cpu,
         "fp64_gpu_path": fp64,
-        "e2e": {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h.output_size() * 8},
-        "gpu_launches": st["launches_per_contract"] * args.steps,
+        "e2e": e2e,
+        "gpu_launches": (st["launches_per_contract"] - 1) // n_slices * S * args.steps + args.steps,
         "clocks": clk.summary(),
     }
     if rank == 0:
@@ -373,6 +424,7 @@ def main():
     ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
     ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "3xtf32", "tf32", "fp64"])
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle time for cpu_baseline")
+    ap.add_argument("--slices-timed", type=int, default=16, help="100q: slices contracted per timed step")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

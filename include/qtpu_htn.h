@@ -169,6 +169,17 @@ qtpu_status qtpu_htn_contract_host(qtpu_htn* h, const void* const* host_ptrs,
 qtpu_status qtpu_htn_contract_batch(qtpu_htn* const* hs, int n,
                                     double* const* dev_out, void* cuda_stream);
 
+/* Contract only slices [first, first + count) of the planned contraction
+ * (slices are the value assignments of the sliced indices, last sliced index
+ * fastest) and write the FP64 sum of their results to dev_out.  The outputs
+ * of disjoint ranges that cover [0, n_slices) add up to the full result, so a
+ * long contraction can be split into resumable pieces or spread over devices.
+ * Runs with direct kernel launches on the handle's stream.  QTPU_EINVAL on a
+ * range outside [0, n_slices), QTPU_ENOTSUP for a network without pairwise
+ * steps. */
+qtpu_status qtpu_htn_contract_slices(qtpu_htn* h, int64_t first, int64_t count,
+                                     double* dev_out);
+
 /* Wait for the handle's stream and read its device status word: QTPU_OK, or
  * QTPU_ETIMEOUT if a bounded device-side wait gave up, or QTPU_ECUDA. */
 qtpu_status qtpu_htn_sync(qtpu_htn* h);

@@ -203,6 +203,21 @@ qtpu_status qtpu_htn_contract(qtpu_htn* h, double* dev_out) {
   return QTPU_OK;
 }
 
+qtpu_status qtpu_htn_contract_slices(qtpu_htn* h, int64_t first, int64_t count, double* dev_out) {
+  if (!h) return QTPU_EINVAL;
+  if (!h->planned) return fail(h, QTPU_ESTATE, "contract before plan");
+  if (h->host_only) return fail(h, QTPU_ENOTSUP, "host-only handle cannot contract");
+  if (!dev_out) return fail(h, QTPU_EINVAL, "dev_out NULL");
+  if (first < 0 || count < 1 || first + count > h->ex.n_slices)
+    return fail(h, QTPU_EINVAL, "slice range outside [0, n_slices)");
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
+  int code = QTPU_OK;
+  std::string m = exec_run_slices(&h->ex, h->leaves, first, count, dev_out, h->stream, &code);
+  if (code != QTPU_OK) return fail(h, (qtpu_status)code, m);
+  return QTPU_OK;
+}
+
 qtpu_status qtpu_htn_sync(qtpu_htn* h) {
   if (!h) return QTPU_EINVAL;
   if (h->host_only || !h->built) return QTPU_OK;

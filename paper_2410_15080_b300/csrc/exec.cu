@@ -614,19 +614,24 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       continue;
     }
 
-    // ---- tensor-core GEMM step
+    // ---- tensor-core GEMM step (operands swapped when M is the skinny side:
+    // C^T = B^T A^T, so the 128-row tile runs along the longer dimension)
     const double lim = 2147483647.0;
-    const bool tc = sa.empty() && sb.empty() && nm >= 64 && nn >= 32 && nk >= 32 &&
+    const bool swap = nm < 64 && nn >= 64;
+    const double gM = swap ? nn : nm, gN = swap ? nm : nn;
+    const bool tc = sa.empty() && sb.empty() && gM >= 64 && gN >= 32 && nk >= 32 &&
                     nb * nm * nn * nk >= (double)(1 << 22) && nb < lim && nm < lim && nn < lim && nk < lim &&
-                    nb * std::ceil(nm / 128.0) * std::ceil(nn / (double)gemm_block_n()) < lim;
+                    nb * std::ceil(gM / 128.0) * std::ceil(gN / (double)gemm_block_n()) < lim;
     if (tc) {
-      Inds rowsA = batch, rowsB = batch;
-      rowsA.insert(rowsA.end(), m.begin(), m.end());
-      rowsB.insert(rowsB.end(), n.begin(), n.end());
+      Inds rowsX = batch, rowsY = batch;
+      rowsX.insert(rowsX.end(), m.begin(), m.end());
+      rowsY.insert(rowsY.end(), n.begin(), n.end());
+      const Repr& RA = swap ? Y : X;
+      const Repr& RB = swap ? X : Y;
       Launch LA, LB, LG;
       int64_t ra = 0, rb = 0, Ka = 0, Kb = 0;
-      if (split_launch(X, rowsA, k, DST_SPLIT_A, &LA, &ra, &Ka) &&
-          split_launch(Y, rowsB, k, DST_SPLIT_B, &LB, &rb, &Kb) && Ka == Kb) {
+      if (split_launch(RA, swap ? rowsY : rowsX, k, DST_SPLIT_A, &LA, &ra, &Ka) &&
+          split_launch(RB, swap ? rowsX : rowsY, k, DST_SPLIT_B, &LB, &rb, &Kb) && Ka == Kb) {
         const size_t abytes = align_up((size_t)np * ra * align_up(Ka, 8) * es, 1024);
         const size_t bbytes = align_up((size_t)np * rb * align_up(Kb, 8) * es, 1024);
         split_need_a = std::max(split_need_a, abytes);
@@ -635,17 +640,19 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
         LG.kclass = KC_GEMM;
         LG.dst = dst;
         LG.gemm.batch = (int)nb;
-        LG.gemm.M = (int)nm;
-        LG.gemm.N = (int)nn;
+        LG.gemm.M = (int)gM;
+        LG.gemm.N = (int)gN;
         LG.gemm.K = (int)Ka;
         LG.gemm.prec = prec;
         LG.gemm.kc_blocks = ex->kc_blocks;
         LG.flops = step_flops + X.flops + Y.flops;
         LG.bytes = (double)np * (ra + rb) * align_up(Ka, 8) * es + nb * nm * nn * 8.0;
-        // the GEMM stores its result [batch][N][M]
+        // the GEMM stores [batch][its N][its M]
         Inds stored = batch;
-        stored.insert(stored.end(), n.begin(), n.end());
-        stored.insert(stored.end(), m.begin(), m.end());
+        const Inds& outer = swap ? m : n;
+        const Inds& inner = swap ? n : m;
+        stored.insert(stored.end(), outer.begin(), outer.end());
+        stored.insert(stored.end(), inner.begin(), inner.end());
         set_dense(ps.out, stored);
         if (!last) place(ps.out);
         for (int o : X.ops) release(o);
@@ -755,6 +762,34 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     R.src[0] = pid;
     R.dst = DST_OUT;
     R.g = g;
+    // reduction over a range of slices: slice mode first and never merged
+    {
+      GatherArgs h = g;
+      h.loop = GModes();
+      st[0] = ex->final_size;
+      ok &= gpush(h.loop, ex->n_slices, st, 1);
+      if (ex->n_slices == 1) {  // keep a slice mode even for one slice
+        h.loop.dim[0] = 1;
+        h.loop.stride[0][0] = ex->final_size;
+        h.loop.n = 1;
+      }
+      GModes rest;
+      for (int64_t i : plan.final_sum) {
+        if (sliced.count(i)) continue;
+        st[0] = sof(pid, i);
+        ok &= gpush(rest, dims.get(i), st, 1);
+      }
+      gmerge(rest, 1);
+      for (int q = 0; q < rest.n && h.loop.n < kMaxModes; ++q) {
+        h.loop.dim[h.loop.n] = rest.dim[q];
+        h.loop.stride[h.loop.n][0] = rest.stride[q][0];
+        h.loop.n++;
+      }
+      for (int q = 0; q < h.loop.n; ++q) h.loop.div[q] = make_fastdiv(h.loop.dim[q]);
+      h.n_loop = (uint32_t)gsize(h.loop);
+      ex->reduce_range = h;
+      ex->has_reduce_range = ok && h.loop.n <= kMaxModes;
+    }
     R.bytes = (double)ex->n_slices * ex->final_size * 8 + (double)g.n_out * 8;
     offs[pid] = 0;  // resolved to the partial buffer at run time
   }
@@ -839,8 +874,12 @@ struct Timed {
   cudaStream_t st;
   size_t i = 0;
   bool on;
+  unsigned flags = 0;  // external record nodes inside a stream capture
   Timed(Profiler& pr, cudaStream_t s, int kind, double fl, double by) : p(pr), st(s), on(pr.on) {
     if (!on) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+      flags = cudaEventRecordExternal;
     if (p.used * 2 + 2 > p.ev.size()) {
       for (int k = 0; k < 2; ++k) {
         cudaEvent_t e;
@@ -858,10 +897,10 @@ struct Timed {
     p.kind[i] = kind;
     p.flops[i] = fl;
     p.bytes[i] = by;
-    cudaEventRecordWithFlags(p.ev[2 * i], st, cudaEventRecordExternal);
+    cudaEventRecordWithFlags(p.ev[2 * i], st, flags);
   }
   ~Timed() {
-    if (on) cudaEventRecordWithFlags(p.ev[2 * i + 1], st, cudaEventRecordExternal);
+    if (on) cudaEventRecordWithFlags(p.ev[2 * i + 1], st, flags);
   }
 };
 }  // namespace
@@ -887,7 +926,9 @@ std::string exec_profile_read(Executor* ex, double* ms, int64_t* launches, doubl
 
 namespace {
 // Enqueue every launch of one contraction on `st`; the result goes to `out`.
-cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* out, cudaStream_t st) {
+cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* out, cudaStream_t st,
+                        int64_t first = 0, int64_t count = -1) {
+  if (count < 0) count = ex->n_slices;
   const int nl = (int)leaves.size();
   std::vector<int64_t> loff(nl, 0);
   std::vector<int64_t> digit(ex->slice_dims.size(), 0);
@@ -931,7 +972,7 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
     const int dtb = reduce ? DT_F64 : (L.src[1] < nl ? leaves[L.src[1]].dt : ex->inter_dt);
     return launch_contract(A, dta, B, dtb, (double*)dst_ptr(L.dst, s), L.c64, ex->sm_count, st);
   };
-  for (int64_t s = 0; s < ex->n_slices && ce == cudaSuccess && !ex->launches.empty(); ++s) {
+  for (int64_t s = first; s < first + count && ce == cudaSuccess && !ex->launches.empty(); ++s) {
     int64_t r = s;
     for (int j = (int)ex->slice_dims.size() - 1; j >= 0; --j) {
       digit[j] = r % ex->slice_dims[j];
@@ -949,7 +990,18 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
   }
   if (ce == cudaSuccess) {
     std::fill(loff.begin(), loff.end(), 0);
-    ce = run_one(ex->reduce, 0, true);
+    if (first == 0 && count == ex->n_slices) {
+      ce = run_one(ex->reduce, 0, true);
+    } else {
+      // sum of the slices in [first, first + count) only
+      GatherArgs g = ex->reduce_range;
+      g.ptr[0] = ex->partial + (size_t)first * ex->final_size * 8;
+      g.loop.dim[0] = (uint32_t)count;
+      g.loop.div[0] = make_fastdiv((uint32_t)count);
+      g.n_loop = g.n_loop / (uint32_t)ex->n_slices * (uint32_t)count;
+      Timed t(ex->prof, st, KC_REDUCE, 0, (double)count * ex->final_size * 8);
+      ce = launch_gather(g, out, ex->sm_count, st);
+    }
   }
   return ce;
 }
@@ -992,6 +1044,21 @@ std::string exec_run(Executor* ex, const std::vector<Leaf>& leaves, double* dev_
     if (ce == cudaSuccess && dev_out != ex->out_stage)
       ce = cudaMemcpyAsync(dev_out, ex->out_stage, (size_t)ex->reduce.g.n_out * 8, cudaMemcpyDeviceToDevice, st);
   }
+  if (ce != cudaSuccess) {
+    *code = QTPU_ECUDA;
+    return std::string("launch failed: ") + cudaGetErrorString(ce);
+  }
+  return "";
+}
+
+std::string exec_run_slices(Executor* ex, const std::vector<Leaf>& leaves, int64_t first, int64_t count,
+                            double* dev_out, cudaStream_t st, int* code) {
+  *code = QTPU_OK;
+  if (ex->launches.empty() || !ex->has_reduce_range || ex->n_slices > 0xFFFFFFFFll) {
+    *code = QTPU_ENOTSUP;
+    return "slice ranges need a network with at least one pairwise step";
+  }
+  cudaError_t ce = enqueue_all(ex, leaves, dev_out, st, first, count);
   if (ce != cudaSuccess) {
     *code = QTPU_ECUDA;
     return std::string("launch failed: ") + cudaGetErrorString(ce);

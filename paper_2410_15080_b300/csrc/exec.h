@@ -59,6 +59,8 @@ struct Executor {
   int n_leaves = 0;
   std::vector<Launch> launches;  // one slice, in order
   Launch reduce;                 // slice sum + final reduction -> dev_out
+  GatherArgs reduce_range;       // the same over a range of slices (slice mode first)
+  bool has_reduce_range = false;
   std::vector<size_t> inter_off; // arena byte offset per intermediate (id - n_leaves)
   // per leaf: (slice position, stride) of each sliced index it carries
   std::vector<std::vector<std::pair<int, int64_t>>> leaf_slice;
@@ -96,6 +98,10 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
                        int prec, int* code);
 // Enqueue the whole contraction; writes output_size FP64 entries to dev_out.
 std::string exec_run(Executor* ex, const std::vector<Leaf>& leaves, double* dev_out, cudaStream_t st, int* code);
+// Contract slices [first, first + count) only (direct launches); dev_out
+// receives their sum.
+std::string exec_run_slices(Executor* ex, const std::vector<Leaf>& leaves, int64_t first, int64_t count,
+                            double* dev_out, cudaStream_t st, int* code);
 void exec_free(Executor* ex);
 // Sum the timed launches per class (after a stream sync) and reset.
 std::string exec_profile_read(Executor* ex, double* ms, int64_t* launches, double* flops, double* bytes);

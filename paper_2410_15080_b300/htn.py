@@ -22,7 +22,7 @@ QTPU_QT, QTPU_CT = 0, 1
 
 SYMBOLS = ["qtpu_htn_create", "qtpu_htn_add_tensor", "qtpu_htn_set_output", "qtpu_htn_plan",
            "qtpu_htn_plan_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats", "qtpu_htn_contract",
-           "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_sync", "qtpu_htn_destroy",
+           "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_contract_slices", "qtpu_htn_sync", "qtpu_htn_destroy",
            "qtpu_htn_profile", "qtpu_htn_profile_read", "qtpu_pairwise_contract_noalloc", "qtpu_last_error"]
 KERNEL_CLASSES = ["contract", "split", "gemm", "reduce"]
 
@@ -65,6 +65,7 @@ def lib():
         L.qtpu_htn_contract.argtypes = [vp, vp]
         L.qtpu_htn_contract_host.argtypes = [vp, C.POINTER(vp), vp]
         L.qtpu_htn_contract_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), vp]
+        L.qtpu_htn_contract_slices.argtypes = [vp, C.c_int64, C.c_int64, vp]
         L.qtpu_htn_sync.argtypes = [vp]
         L.qtpu_pairwise_contract_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]
         L.qtpu_htn_destroy.argtypes = [vp]
@@ -167,6 +168,14 @@ class HTN:
         if out is None:
             out = torch.empty(self.output_size(), dtype=torch.float64, device=f"cuda:{self.device}")
         self._check(self._L.qtpu_htn_contract(self._h, C.c_void_p(out.data_ptr())))
+        return out
+
+    def contract_slices(self, first: int, count: int, out=None):
+        """Sum of the results of slices [first, first + count) (device tensor)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.output_size(), dtype=torch.float64, device=f"cuda:{self.device}")
+        self._check(self._L.qtpu_htn_contract_slices(self._h, first, count, C.c_void_p(out.data_ptr())))
         return out
 
     def contract_host(self, host_arrays, out=None):

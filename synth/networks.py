@@ -127,12 +127,12 @@ def ring_htn(n_sub=8, gates_per_edge=2, wires_per_edge=1, k=64, seed=0,
 
 
 def ring_chords_htn(k=64, seed=0, dtype=np.float64, n_sub=12, n_chords=8,
-                    chord_step=3, materialize=True) -> HTN:
+                    chord_step=3, materialize=True, gates_per_chord=2) -> HTN:
     """The 100-qubit workload: 12 QTs on a ring (1 gate + 1 wire cut per ring
     edge) plus chords (i, i+3 mod 12) for i < 8 with 2 gate cuts each, i.e.
     28 gate cuts and 12 wire cuts; five QTs carry 47.8 M entries."""
     edges = [(j, (j + 1) % n_sub, 1, 1) for j in range(n_sub)]
-    edges += [(i, (i + chord_step) % n_sub, 2, 0) for i in range(n_chords)]
+    edges += [(i, (i + chord_step) % n_sub, gates_per_chord, 0) for i in range(n_chords)]
     return _edge_network(n_sub, edges, k, seed, dtype,
                          f"ring{n_sub}_chords{n_chords}_k{k}", materialize)
 
@@ -197,14 +197,15 @@ def random_batch(n: int, seed: int = 0, **kw):
     return [random_htn(seed * 100003 + i, **kw) for i in range(n)]
 
 
-def rank1_htn(net: HTN, seed: int = 0):
+def rank1_htn(net: HTN, seed: int = 0, signed: bool = True):
     """The same index structure with every tensor replaced by an outer product
-    of seeded random vectors, one per axis.  Returns (network, factors) where
+    of seeded random vectors, one per axis (entries of magnitude in [0.5, 1.5],
+    random signs unless ``signed`` is False).  Returns (network, factors) where
     factors[t][ax] is the vector of tensor t's axis ax."""
     rng = np.random.default_rng([seed, 0xA11])
     tensors, factors = [], []
     for t in net.tensors:
-        vecs = [rng.uniform(0.5, 1.5, size=n) * rng.choice([-1.0, 1.0], size=n)
+        vecs = [rng.uniform(0.5, 1.5, size=n) * (rng.choice([-1.0, 1.0], size=n) if signed else 1.0)
                 for n in t.data.shape]
         arr = np.ones((), dtype=np.float64)
         for v in vecs:

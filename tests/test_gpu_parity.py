@@ -166,3 +166,67 @@ def test_generic_and_fast_gather_paths_agree(fast, graph, monkeypatch):
     assert rel_err(got, ref) <= REL_TOL
     got64, _ = contract_gpu(net, prec="fp64")
     assert rel_err(got64, ref) <= FP64_TOL
+
+
+def test_slice_ranges_sum_to_the_full_result():
+    import torch
+    from paper_2410_15080_b300 import from_network
+    from tests.gpu_util import to_device
+    net = synth.ring_htn(n_sub=4, gates_per_edge=2, wires_per_edge=1, k=3, seed=8)
+    h = from_network(to_device(net), net.output, prec="bf16x3", n_slices=16, slice_dim=4)
+    full = h.contract().clone()
+    parts = [h.contract_slices(0, 5).clone(), h.contract_slices(5, 10).clone(), h.contract_slices(15, 1).clone()]
+    h.sync()
+    got = sum(p.cpu().numpy() for p in parts)
+    assert rel_err(got, full.cpu().numpy()) <= 1e-12
+    assert rel_err(got, oracle_value(net)) <= REL_TOL
+    with pytest.raises(Exception):
+        h.contract_slices(10, 7)
+    h.close()
+
+
+def test_skinny_m_runs_on_the_tensor_cores_with_swapped_operands():
+    rng = np.random.default_rng(3)
+    b, m, n, k = 4, 36, 1296, 576
+    A = rng.uniform(-1, 1, (b, m, k))
+    B = rng.uniform(-1, 1, (b, k, n))
+    net = synth.HTN([synth.Tensor("QT", (0, 1, 3), A), synth.Tensor("QT", (0, 3, 2), B)], (0, 1, 2))
+    got, st = contract_gpu(net, prec="bf16x3")
+    assert st["n_tensor_core_steps"] == 1
+    assert rel_err(got, np.matmul(A, B).ravel()) <= REL_TOL
+
+
+def test_ring_with_chords_topology_sliced():
+    """The 100-qubit topology (ring + chords (i, i+3)) with smaller bonds and a
+    single observable, sliced over 4^3 wire values, against the oracle."""
+    net = synth.ring_chords_htn(k=2, seed=4, gates_per_chord=1)
+    ref = oracle_value(net)
+    got, st = contract_gpu(net, prec="bf16x3", n_slices=64, slice_dim=4)
+    assert rel_err(got, ref) <= REL_TOL, st
+
+
+@pytest.mark.slow
+def test_100q_rank1_closed_form_full_size():
+    """Full-size 100-qubit network (28 gate + 12 wire cuts, k = 64, 2 GB of
+    QTs, 1024 slices) with rank-1 tensors: the contraction factorises into a
+    closed form computed on the CPU.  Positive factors keep the sum over
+    slices well conditioned (with random signs the per-index sums cancel and
+    the slice sum amplifies rounding by sum|slice| / |sum slice|)."""
+    from tests.test_oracle_tn import rank1_closed_form
+    base = synth.ring_chords_htn(materialize=False)
+    net, fac = synth.rank1_htn(base, seed=5, signed=False)
+    want = rank1_closed_form(net, fac).ravel()
+    got, st = contract_gpu(net, prec="bf16x3", max_intermediate_bytes=8 << 30, n_slices=1024, slice_dim=4)
+    assert st["n_tensor_core_steps"] >= 5
+    assert rel_err(got, want) <= REL_TOL, st
+
+
+@pytest.mark.slow
+def test_100q_full_size_slicing_invariance():
+    """Full-size 100-qubit network with random entries: the result does not
+    depend on how the contraction is sliced (1024 wire-index slices vs 256),
+    which holds at any size."""
+    net = synth.ring_chords_htn(seed=2)
+    a, sa = contract_gpu(net, prec="bf16x3", max_intermediate_bytes=8 << 30, n_slices=1024, slice_dim=4)
+    b, sb = contract_gpu(net, prec="bf16x3", max_intermediate_bytes=16 << 30, n_slices=256, slice_dim=4)
+    assert rel_err(a, b) <= 2 * REL_TOL, (sa, sb)
