@@ -163,9 +163,14 @@ qtpu_status qtpu_htn_contract(qtpu_htn* h, double* dev_out);
 qtpu_status qtpu_htn_contract_host(qtpu_htn* h, const void* const* host_ptrs,
                                    double* host_out);
 
-/* Contract n planned networks (possibly of different shapes) and write
- * dev_out[i] for each, all enqueued on cuda_stream (NULL = each handle's own
- * stream).  Handles must share one device. */
+/* Contract n planned networks (of any shapes) and write dev_out[i] for each.
+ * All n contractions run as ONE CUDA graph: each network's launches form one
+ * branch, spread over 16 parallel branches (networks own disjoint
+ * workspaces), so small latency-bound networks overlap.  The graph is built
+ * on the first call for a given (handles, outputs) list and replayed by later
+ * calls with the same list; it is ordered after the work already enqueued on
+ * cuda_stream (NULL = the first handle's stream), which waits for it.
+ * Handles must be distinct and share one device. */
 qtpu_status qtpu_htn_contract_batch(qtpu_htn* const* hs, int n,
                                     double* const* dev_out, void* cuda_stream);
 

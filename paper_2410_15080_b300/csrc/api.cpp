@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <set>
 #include <string>
@@ -258,22 +259,131 @@ qtpu_status qtpu_htn_contract_host(qtpu_htn* h, const void* const* host_ptrs, do
   return qtpu_htn_sync(h);
 }
 
+// ---------------------------------------------------------------- batches
+// Many networks in one CUDA graph: every network's launch sequence is
+// captured on one of kBranches parallel streams (networks own disjoint
+// workspaces, so they may run concurrently), followed by the copy of its
+// output; the graph is cached per (handles, outputs) and replayed with one
+// graph launch.
+namespace {
+constexpr int kBranches = 16;
+struct BatchGraph {
+  std::vector<qtpu_htn*> hs;
+  std::vector<double*> outs;
+  int device = 0;
+  cudaGraphExec_t exec = nullptr;
+};
+struct BatchState {
+  std::mutex mu;
+  std::vector<BatchGraph*> cache;  // most recent last, at most 4
+  cudaStream_t cap[64] = {};
+  cudaStream_t br[64][kBranches] = {};
+  cudaEvent_t fork[64] = {}, join[64][kBranches] = {}, in[64] = {}, out[64] = {};
+};
+BatchState g_batch;
+
+void batch_free(BatchGraph* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  delete b;
+}
+
+bool batch_streams(int dev) {
+  if (g_batch.cap[dev]) return true;
+  if (cudaStreamCreateWithFlags(&g_batch.cap[dev], cudaStreamNonBlocking) != cudaSuccess) return false;
+  for (int i = 0; i < kBranches; ++i) {
+    if (cudaStreamCreateWithFlags(&g_batch.br[dev][i], cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (cudaEventCreateWithFlags(&g_batch.join[dev][i], cudaEventDisableTiming) != cudaSuccess) return false;
+  }
+  return cudaEventCreateWithFlags(&g_batch.fork[dev], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&g_batch.in[dev], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&g_batch.out[dev], cudaEventDisableTiming) == cudaSuccess;
+}
+
+void batch_forget(qtpu_htn* h) {
+  std::lock_guard<std::mutex> g(g_batch.mu);
+  for (size_t i = 0; i < g_batch.cache.size();) {
+    BatchGraph* b = g_batch.cache[i];
+    if (std::find(b->hs.begin(), b->hs.end(), h) != b->hs.end()) {
+      batch_free(b);
+      g_batch.cache.erase(g_batch.cache.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+}  // namespace
+
 qtpu_status qtpu_htn_contract_batch(qtpu_htn* const* hs, int n, double* const* dev_out, void* cuda_stream) {
   if (n < 0 || (n > 0 && (!hs || !dev_out))) return QTPU_EINVAL;
+  if (n == 0) return QTPU_OK;
   for (int i = 0; i < n; ++i) {
     qtpu_htn* h = hs[i];
     if (!h) return QTPU_EINVAL;
     if (!h->planned) return fail(h, QTPU_ESTATE, "contract before plan");
     if (h->host_only) return fail(h, QTPU_ENOTSUP, "host-only handle cannot contract");
     if (h->device != hs[0]->device) return fail(h, QTPU_EINVAL, "handles on different devices");
+    if (!dev_out[i]) return fail(h, QTPU_EINVAL, "dev_out NULL");
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == h) return fail(h, QTPU_EINVAL, "a handle appears twice in the batch");
   }
-  for (int i = 0; i < n; ++i) {
-    qtpu_htn* h = hs[i];
-    cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : h->stream;
-    int code = QTPU_OK;
-    std::string m = exec_run(&h->ex, h->leaves, dev_out[i], st, &code);
-    if (code != QTPU_OK) return fail(h, (qtpu_status)code, m);
+  const int dev = hs[0]->device;
+  if (dev >= 64) return fail(hs[0], QTPU_ENOTSUP, "device index >= 64");
+  cudaError_t e = cudaSetDevice(dev);
+  if (e != cudaSuccess) return fail(hs[0], QTPU_ECUDA, cudaGetErrorString(e));
+  cudaStream_t user = cuda_stream ? (cudaStream_t)cuda_stream : hs[0]->stream;
+  std::lock_guard<std::mutex> g(g_batch.mu);
+  if (!batch_streams(dev)) return fail(hs[0], QTPU_ECUDA, "batch streams");
+  BatchGraph* b = nullptr;
+  for (BatchGraph* c : g_batch.cache)
+    if (c->device == dev && (int)c->hs.size() == n && std::equal(c->hs.begin(), c->hs.end(), hs) &&
+        std::equal(c->outs.begin(), c->outs.end(), dev_out))
+      b = c;
+  if (!b) {
+    cudaStream_t cs = g_batch.cap[dev];
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = cudaEventRecord(g_batch.fork[dev], cs);
+      for (int i = 0; i < kBranches && e1 == cudaSuccess; ++i)
+        e1 = cudaStreamWaitEvent(g_batch.br[dev][i], g_batch.fork[dev], 0);
+      for (int i = 0; i < n && e1 == cudaSuccess; ++i) {
+        qtpu_htn* h = hs[i];
+        cudaStream_t bs = g_batch.br[dev][i % kBranches];
+        int64_t no = 1;
+        qtpu_htn_output_size(h, &no);
+        e1 = exec_enqueue(&h->ex, h->leaves, h->ex.out_stage, bs);
+        if (e1 == cudaSuccess)
+          e1 = cudaMemcpyAsync(dev_out[i], h->ex.out_stage, (size_t)no * 8, cudaMemcpyDeviceToDevice, bs);
+      }
+      for (int i = 0; i < kBranches && e1 == cudaSuccess; ++i) {
+        e1 = cudaEventRecord(g_batch.join[dev][i], g_batch.br[dev][i]);
+        if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(cs, g_batch.join[dev][i], 0);
+      }
+      e = cudaStreamEndCapture(cs, &graph);
+      if (e1 != cudaSuccess) e = e1;
+    }
+    cudaGraphExec_t ge = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(hs[0], QTPU_ECUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    b = new BatchGraph();
+    b->hs.assign(hs, hs + n);
+    b->outs.assign(dev_out, dev_out + n);
+    b->device = dev;
+    b->exec = ge;
+    g_batch.cache.push_back(b);
+    if (g_batch.cache.size() > 4) {
+      batch_free(g_batch.cache.front());
+      g_batch.cache.erase(g_batch.cache.begin());
+    }
   }
+  cudaStream_t cs = g_batch.cap[dev];
+  e = cudaEventRecord(g_batch.in[dev], user);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, g_batch.in[dev], 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(g_batch.out[dev], cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(user, g_batch.out[dev], 0);
+  if (e != cudaSuccess) return fail(hs[0], QTPU_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
   return QTPU_OK;
 }
 
@@ -288,6 +398,7 @@ qtpu_status qtpu_htn_profile_read(qtpu_htn* h, int n, double* ms, int64_t* launc
   if (!h || n < 0 || n > KC_COUNT) return QTPU_EINVAL;
   if (h->host_only || !h->built) return fail(h, QTPU_ESTATE, "nothing to read");
   cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess && h->ex.own) e = cudaStreamSynchronize(h->ex.own);
   if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
   double m[KC_COUNT], f[KC_COUNT], b[KC_COUNT];
   int64_t l[KC_COUNT];
@@ -304,6 +415,7 @@ qtpu_status qtpu_htn_profile_read(qtpu_htn* h, int n, double* ms, int64_t* launc
 
 qtpu_status qtpu_htn_destroy(qtpu_htn* h) {
   if (!h) return QTPU_EINVAL;
+  batch_forget(h);
   if (h->built) {
     cudaSetDevice(h->device);
     exec_free(&h->ex);

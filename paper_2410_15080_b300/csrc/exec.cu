@@ -1051,6 +1051,10 @@ std::string exec_run(Executor* ex, const std::vector<Leaf>& leaves, double* dev_
   return "";
 }
 
+cudaError_t exec_enqueue(Executor* ex, const std::vector<Leaf>& leaves, double* out, cudaStream_t st) {
+  return enqueue_all(ex, leaves, out, st);
+}
+
 std::string exec_run_slices(Executor* ex, const std::vector<Leaf>& leaves, int64_t first, int64_t count,
                             double* dev_out, cudaStream_t st, int* code) {
   *code = QTPU_OK;

@@ -98,6 +98,9 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
                        int prec, int* code);
 // Enqueue the whole contraction; writes output_size FP64 entries to dev_out.
 std::string exec_run(Executor* ex, const std::vector<Leaf>& leaves, double* dev_out, cudaStream_t st, int* code);
+// Enqueue one whole contraction on `st` with direct launches, result to out
+// (used to capture several networks into one graph).
+cudaError_t exec_enqueue(Executor* ex, const std::vector<Leaf>& leaves, double* out, cudaStream_t st);
 // Contract slices [first, first + count) only (direct launches); dev_out
 // receives their sum.
 std::string exec_run_slices(Executor* ex, const std::vector<Leaf>& leaves, int64_t first, int64_t count,
