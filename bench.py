@@ -49,6 +49,23 @@ def load_peaks():
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "src": "fallback"}
 
 
+def measured_traffic(kclass: str):
+    """DRAM bytes per launch of a kernel class from the committed ncu summary,
+    or None if the kernel source changed since the capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kclass)
+    if not e:
+        return None
+    src = os.path.join(ROOT, e["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != e["sha256_16"]:
+        return None
+    return e["bytes_per_launch"]
+
+
 def make_network(workload: str):
     import synth
     if workload == "mid":
@@ -458,6 +475,7 @@ def run_ours(args, rank, world):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": dom,
                 "peak_note": f"{peaks['src']} copy bandwidth"}
+    roof["traffic"] = measured_traffic(dom)
     roof["per_launch_ms"] = per_launch_ms
     roof["launches_per_step"] = d["launches"] / args.steps
     roof["classes"] = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
