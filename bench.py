@@ -35,6 +35,7 @@ METRIC = "h-TN contract TFLOP/s & %peak vs plain FP64 GPU path at rel err ≤1e-
 WORKLOADS = {
     "mid": "mid-size 60-qubit ring h-TN: 8 QTs [k=64][6,6,4][6,6,4] FP64, 16 gate + 8 wire cuts, 32 tensors",
     "100q": "100-qubit ring+chords h-TN: 12 QTs, 28 gate + 12 wire cuts, k=64, sliced over 4^5 wire-index values",
+    "gemm": "one pairwise step C[b,m,n] = sum_k A[b,m,k] B[b,k,n] of the given --shape (FP64 leaves)",
     "batch": "512 independent random h-TNs (ring / 2-D grid, 2-12 subcircuits, 2-20 cuts, k 1-64, FP32/FP64) "
              "in one CUDA graph",
 }
@@ -66,8 +67,15 @@ def measured_traffic(kclass: str):
     return e["bytes_per_launch"]
 
 
-def make_network(workload: str):
+def make_network(workload: str, shape: str = "8x1024x1024x1024"):
     import synth
+    if workload == "gemm":
+        b, m, n, k = (int(x) for x in shape.split("x"))
+        rng = np.random.default_rng(b + m + n + k)
+        A = rng.uniform(-1, 1, (b, m, k))
+        B = rng.uniform(-1, 1, (b, k, n))
+        return synth.HTN([synth.Tensor("QT", (0, 1, 3), A), synth.Tensor("QT", (0, 3, 2), B)], (0, 1, 2),
+                         name=f"gemm{shape}"), {}
     if workload == "mid":
         return synth.ring_htn(), {}
     if workload == "100q":
@@ -349,7 +357,7 @@ def run_ours(args, rank, world):
     from paper_2410_15080_b300.htn import QTPU_CT, QTPU_QT
 
     dev = torch.device("cuda", torch.cuda.current_device())
-    net, plan_kw = make_network(args.workload)
+    net, plan_kw = make_network(args.workload, args.shape)
     tensors = [(t.inds, torch.from_numpy(np.ascontiguousarray(t.data)).to(dev), QTPU_CT if t.kind == "CT" else QTPU_QT)
                for t in net.tensors]
     h = from_network(tensors, net.output, prec=args.prec, **plan_kw)
@@ -403,7 +411,7 @@ def run_ours(args, rank, world):
 
     # parity of this run's output against the FP64 oracle (mid workload)
     rel = None
-    if args.workload == "mid" and rank == 0:
+    if args.workload in ("mid", "gemm") and rank == 0:
         from oracle import planner, tn
         p = planner.make_plan(net.inds(), net.dims(), net.output)
         ref = tn.contract_pairwise(net.pairs(), net.output, planner.order_of(p)).ravel()
@@ -492,7 +500,8 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "flops_per_step": flops, "prec": args.prec,
+        "config": {"workload": WORKLOADS[args.workload] + (f" ({args.shape})" if args.workload == "gemm" else ""),
+                   "flops_per_step": flops, "prec": args.prec,
                    "l2": "flushed between timed steps (256 MiB write)" if net.nbytes() < (256 << 20)
                    else "inputs larger than L2", "plan_steps": st["n_steps"],
                    "tensor_core_steps": st["n_tensor_core_steps"], "parallelism": f"replicas x{world}",
@@ -521,6 +530,7 @@ def main():
     ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "3xtf32", "tf32", "fp64"])
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--slices-timed", type=int, default=16, help="100q: slices contracted per timed step")
+    ap.add_argument("--shape", default="8x1024x1024x1024", help="gemm workload: batch x M x N x K")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

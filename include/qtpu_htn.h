@@ -69,7 +69,9 @@ typedef struct {
   uint32_t slice_dim;              /* only slice indices of this dim; 0 = any */
   qtpu_prec prec;
   int cost_model;                  /* 0 = exact FLOP cost (greedy)            */
-  uint64_t seed;                   /* reserved for randomised planners        */
+  uint64_t seed;                   /* 0: greedy; else randomised greedy (the
+                                      pair drawn among the 3 best keys by
+                                      SplitMix64(seed)), for plan candidates */
   const char* autotune_table;      /* reserved; may be NULL                   */
 } qtpu_plan_opts;
 
@@ -105,7 +107,7 @@ qtpu_status qtpu_htn_set_output(qtpu_htn* h, int n, const int64_t* index_ids);
 /* Plan the contraction (host only): greedy pairwise order on exact 256-bit
  * integer costs, then slicing until the peak intermediate fits
  * max_intermediate_bytes and the slice count reaches n_slices.  opts may be
- * NULL (defaults: no limit, no slicing, BF16X3).  QTPU_ESTATE with no
+ * NULL (defaults: no limit, no slicing, BF16X3, greedy).  QTPU_ESTATE with no
  * tensors, QTPU_EINVAL on an unknown output id, QTPU_ELIMIT if the limit
  * cannot be met, QTPU_ENOTSUP on a size of 2^255 or more. */
 qtpu_status qtpu_htn_plan(qtpu_htn* h, const qtpu_plan_opts* opts);
@@ -194,6 +196,35 @@ qtpu_status qtpu_htn_destroy(qtpu_htn* h);
 /* Message of the last failure on h (or of the last failed create when h is
  * NULL).  Never NULL. */
 const char* qtpu_last_error(const qtpu_htn* h);
+
+/* ------------------------------------------------------------------------
+ * Learned cost model (ranks candidate plans; never changes a computed value).
+ * A 3-layer perceptron  h1 = relu(x W1 + b1), h2 = relu(h1 W2 + b2),
+ * y = h2 W3 + b3  on plan features x (FP32), predicting log contraction time.
+ * Weights are used in BF16, rounded from FP32 master copies; products are
+ * accumulated in FP32; loss = mean squared error; optimiser = Adam.
+ * Parameter layout (FP32): W1[in][hidden] b1[hidden] W2[hidden][hidden]
+ * b2[hidden] W3[hidden] b3. */
+typedef struct qtpu_mlp qtpu_mlp;
+
+/* Create a model on `device`, enqueueing on `cuda_stream`; weights drawn
+ * uniformly in +-sqrt(6 / fan_in) from SplitMix64(seed), biases 0. */
+qtpu_status qtpu_mlp_create(qtpu_mlp** out, int device, void* cuda_stream,
+                            int in_dim, int hidden, uint64_t seed);
+qtpu_status qtpu_mlp_num_params(const qtpu_mlp* m, int64_t* n);
+/* Copy the FP32 master parameters out (host_out) and/or in (host_in). */
+qtpu_status qtpu_mlp_params(qtpu_mlp* m, float* host_out, const float* host_in);
+/* dev_y[b] = model(dev_x[b]) for b < batch; dev_x is [batch][in] FP32. */
+qtpu_status qtpu_mlp_forward(qtpu_mlp* m, const float* dev_x, int batch, float* dev_y);
+/* Gradients of the MSE loss against targets dev_t (FP32, parameter layout)
+ * copied to host_grads, and the loss to host_loss (either may be NULL). */
+qtpu_status qtpu_mlp_gradients(qtpu_mlp* m, const float* dev_x, const float* dev_t,
+                               int batch, float* host_grads, float* host_loss);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) with learning rate lr; the
+ * batch loss before the step goes to host_loss (may be NULL). */
+qtpu_status qtpu_mlp_train_step(qtpu_mlp* m, const float* dev_x, const float* dev_t,
+                                int batch, float lr, float* host_loss);
+qtpu_status qtpu_mlp_destroy(qtpu_mlp* m);
 
 /* Bytes of the fixed device scratch array used by
  * qtpu_pairwise_contract_noalloc (held by every GPU that loads the library,

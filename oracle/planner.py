@@ -24,6 +24,11 @@ Slicing (fixed tree): while the peak intermediate exceeds the byte limit
   the non-output index (of dim ``slice_dim`` if nonzero) minimising
   (peak entries per slice, total flops over all slices, index id).
 
+Randomised variant (seed != 0, the candidates a cost model ranks): at each
+step the pair is drawn uniformly among the 3 smallest keys with the
+SplitMix64 generator (Steele, Lea and Flood 2014; Vigna's reference
+constants) seeded with ``seed`` and advanced once per step.
+
 ``plan_text`` is the canonical text the C++ planner must reproduce byte for
 byte.  Sizes above 2**255 raise ``OverflowError`` (the C++ side returns
 QTPU_ENOTSUP at the same point).
@@ -94,8 +99,21 @@ def step_flops(dims, ia, ib, batch, m, n, k, sa, sb, sliced=()):
     return f
 
 
-def greedy(tensors_inds, dims, output) -> Plan:
-    """Greedy pairwise order (see module header)."""
+M64 = (1 << 64) - 1
+RAND_TOP = 3
+
+
+def splitmix64(state):
+    """One SplitMix64 step: returns (new state, 64-bit output)."""
+    state = (state + 0x9E3779B97F4A7C15) & M64
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+    return state, z ^ (z >> 31)
+
+
+def greedy(tensors_inds, dims, output, seed: int = 0) -> Plan:
+    """Greedy pairwise order (see module header); seed != 0 randomises it."""
     n = len(tensors_inds)
     live = {t: tuple(inds) for t, inds in enumerate(tensors_inds)}
     count = {}
@@ -106,6 +124,7 @@ def greedy(tensors_inds, dims, output) -> Plan:
         count[i] = count.get(i, 0) + 1
     plan = Plan(n_leaves=n, output=tuple(output), dims=dict(dims))
     nxt = n
+    rng = seed & M64
     while len(live) > 1:
         ids = sorted(live)
         pairs = [(x, y) for a, x in enumerate(ids) for y in ids[a + 1:]
@@ -113,6 +132,7 @@ def greedy(tensors_inds, dims, output) -> Plan:
         if not pairs:
             pairs = [(x, y) for a, x in enumerate(ids) for y in ids[a + 1:]]
         best = None
+        cands = []
         for x, y in pairs:
             ia, ib = live[x], live[y]
             sx, sy = set(ia), set(ib)
@@ -121,9 +141,15 @@ def greedy(tensors_inds, dims, output) -> Plan:
             size_out = _p([dims[i] for i in batch + m + nn])
             key = (size_out - _p([dims[i] for i in ia]) - _p([dims[i] for i in ib]),
                    step_flops(dims, ia, ib, batch, m, nn, k, sa, sb), x, y)
+            cand = (key, Step(x, y, nxt, batch, m, nn, k, sa, sb))
+            cands.append(cand)
             if best is None or key < best[0]:
-                best = (key, Step(x, y, nxt, batch, m, nn, k, sa, sb))
+                best = cand
         st = best[1]
+        if seed:
+            top = sorted(cands, key=lambda c: c[0])[:RAND_TOP]
+            rng, r = splitmix64(rng)
+            st = top[r % len(top)][1]
         for i in set(live[st.x]):
             count[i] -= 1
         for i in set(live[st.y]):
@@ -215,8 +241,8 @@ def plan_text(plan, tensors_inds) -> str:
     return "\n".join(lines) + "\n"
 
 
-def make_plan(tensors_inds, dims, output, max_bytes=0, n_slices=0, slice_dim=0):
-    p = greedy(tensors_inds, dims, output)
+def make_plan(tensors_inds, dims, output, max_bytes=0, n_slices=0, slice_dim=0, seed=0):
+    p = greedy(tensors_inds, dims, output, seed)
     return slice_plan(p, tensors_inds, max_bytes, n_slices, slice_dim)
 
 

@@ -12,6 +12,9 @@
 //    flops = 2 * batch * M * N * K (+ size(x) if sa, + size(y) if sb);
 //  * the result's axes are [batch, M, N], groups ordered as in x (batch, M)
 //    and y (N), and it takes the next id;
+//  * randomised variant (seed != 0): the pair is drawn uniformly among the
+//    kRandTop smallest keys, with SplitMix64 (Steele, Lea and Flood 2014;
+//    the constants of Vigna's reference version) advanced once per step;
 //  * slicing keeps the tree fixed and repeatedly slices the non-output index
 //    (of dim slice_dim if nonzero) minimising (peak entries per slice, total
 //    flops over all slices, index id) until 8 * peak <= max_bytes and the
@@ -133,8 +136,18 @@ void stats(const Plan& p, Ctx& c, U256* peak, U256* fl) {
 
 }  // namespace
 
+namespace {
+uint64_t splitmix64(uint64_t* state) {
+  uint64_t z = (*state += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+}  // namespace
+
 int make_plan(const std::vector<Inds>& leaves, const DimMap& dims, const Inds& output,
-              uint64_t max_bytes, uint64_t n_slices, int64_t slice_dim, Plan* plan) {
+              uint64_t max_bytes, uint64_t n_slices, int64_t slice_dim, Plan* plan, uint64_t seed) {
+  uint64_t rng = seed;
   Ctx c{&dims};
   Plan& p = *plan;
   p = Plan();
@@ -168,6 +181,7 @@ int make_plan(const std::vector<Inds>& leaves, const DimMap& dims, const Inds& o
     bool have = false;
     Key best{};
     PlanStep best_step;
+    std::vector<std::pair<Key, PlanStep>> top;  // randomised: the kRandTop best
     for (auto& pr : pairs) {
       const Inds& ia = live[pr.first];
       const Inds& ib = live[pr.second];
@@ -185,7 +199,15 @@ int make_plan(const std::vector<Inds>& leaves, const DimMap& dims, const Inds& o
       k.x = pr.first; k.y = pr.second;
       if (c.ovf) return PLAN_OVERFLOW;
       if (!have || key_less(k, best)) { best = k; best_step = st; have = true; }
+      if (seed) {
+        top.push_back({k, st});
+        std::sort(top.begin(), top.end(), [](const std::pair<Key, PlanStep>& a, const std::pair<Key, PlanStep>& b) {
+          return key_less(a.first, b.first);
+        });
+        if ((int)top.size() > kRandTop) top.pop_back();
+      }
     }
+    if (seed) best_step = top[splitmix64(&rng) % top.size()].second;
     for (int64_t i : std::set<int64_t>(live[best_step.x].begin(), live[best_step.x].end())) count[i]--;
     for (int64_t i : std::set<int64_t>(live[best_step.y].begin(), live[best_step.y].end())) count[i]--;
     live.erase(best_step.x);

@@ -53,8 +53,12 @@ enum PlanErr { PLAN_OK = 0, PLAN_OVERFLOW = 1, PLAN_LIMIT = 2 };
 
 // Greedy order then slicing.  Returns PLAN_OK, PLAN_OVERFLOW (a size >= 2^255)
 // or PLAN_LIMIT (peak limit unreachable).
+// seed != 0: randomised greedy (candidate plans for the cost model): at each
+// step the pair is drawn uniformly among the kRandTop best keys with the
+// SplitMix64 generator seeded by `seed`.
+constexpr int kRandTop = 3;
 int make_plan(const std::vector<Inds>& leaves, const DimMap& dims, const Inds& output,
-              uint64_t max_bytes, uint64_t n_slices, int64_t slice_dim, Plan* plan);
+              uint64_t max_bytes, uint64_t n_slices, int64_t slice_dim, Plan* plan, uint64_t seed = 0);
 
 std::string plan_text(const Plan& plan);
 

@@ -23,7 +23,9 @@ QTPU_QT, QTPU_CT = 0, 1
 SYMBOLS = ["qtpu_htn_create", "qtpu_htn_add_tensor", "qtpu_htn_set_output", "qtpu_htn_plan",
            "qtpu_htn_plan_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats", "qtpu_htn_contract",
            "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_contract_slices", "qtpu_htn_sync", "qtpu_htn_destroy",
-           "qtpu_htn_profile", "qtpu_htn_profile_read", "qtpu_pairwise_contract_noalloc", "qtpu_last_error"]
+           "qtpu_htn_profile", "qtpu_htn_profile_read", "qtpu_pairwise_contract_noalloc", "qtpu_last_error",
+           "qtpu_mlp_create", "qtpu_mlp_num_params", "qtpu_mlp_params", "qtpu_mlp_forward",
+           "qtpu_mlp_gradients", "qtpu_mlp_train_step", "qtpu_mlp_destroy"]
 KERNEL_CLASSES = ["contract", "split", "gemm", "reduce"]
 
 
@@ -69,6 +71,14 @@ def lib():
         L.qtpu_htn_sync.argtypes = [vp]
         L.qtpu_pairwise_contract_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]
         L.qtpu_htn_destroy.argtypes = [vp]
+        fp = C.POINTER(C.c_float)
+        L.qtpu_mlp_create.argtypes = [C.POINTER(vp), C.c_int, vp, C.c_int, C.c_int, C.c_uint64]
+        L.qtpu_mlp_num_params.argtypes = [vp, i64p]
+        L.qtpu_mlp_params.argtypes = [vp, vp, vp]
+        L.qtpu_mlp_forward.argtypes = [vp, vp, C.c_int, vp]
+        L.qtpu_mlp_gradients.argtypes = [vp, vp, vp, C.c_int, vp, fp]
+        L.qtpu_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_float, fp]
+        L.qtpu_mlp_destroy.argtypes = [vp]
         L.qtpu_last_error.argtypes = [vp]
         L.qtpu_last_error.restype = C.c_char_p
         for s in SYMBOLS:
@@ -127,8 +137,8 @@ class HTN:
         self._check(self._L.qtpu_htn_set_output(self._h, len(inds), _arr(inds)))
 
     def plan(self, prec: str = "bf16x3", max_intermediate_bytes: int = 0, n_slices: int = 0,
-             slice_dim: int = 0):
-        o = PlanOpts(max_intermediate_bytes, n_slices, slice_dim, PREC[prec], 0, 0, None)
+             slice_dim: int = 0, seed: int = 0):
+        o = PlanOpts(max_intermediate_bytes, n_slices, slice_dim, PREC[prec], 0, seed, None)
         self._check(self._L.qtpu_htn_plan(self._h, C.byref(o)))
 
     def plan_info(self) -> str:
@@ -213,6 +223,73 @@ def contract_batch(htns: Sequence[HTN], outs, stream: int | None = None):
         raise QtpuError(st, "contract_batch failed")
 
 
+class MLP:
+    """The cost model's perceptron through the C ABI (all arithmetic in the
+    library's CUDA kernels; this class only marshals tensors)."""
+
+    def __init__(self, in_dim: int, hidden: int = 256, seed: int = 1, device: int = 0, stream: int | None = None):
+        import torch
+        self._L = lib()
+        self._m = C.c_void_p()
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        st = self._L.qtpu_mlp_create(C.byref(self._m), device, C.c_void_p(stream or 0), in_dim, hidden, seed)
+        if st != QTPU_OK:
+            raise QtpuError(st, "qtpu_mlp_create failed")
+        n = C.c_int64()
+        self._L.qtpu_mlp_num_params(self._m, C.byref(n))
+        self.n_params = n.value
+        self.in_dim, self.hidden, self.device = in_dim, hidden, device
+
+    def _ok(self, st, what):
+        if st != QTPU_OK:
+            raise QtpuError(st, what)
+
+    def params(self, new=None):
+        """FP32 master parameters as a numpy array (optionally set them first)."""
+        import numpy as np
+        out = np.empty(self.n_params, dtype=np.float32)
+        src = None
+        if new is not None:
+            new = np.ascontiguousarray(new, dtype=np.float32)
+            src = C.c_void_p(new.ctypes.data)
+        self._ok(self._L.qtpu_mlp_params(self._m, C.c_void_p(out.ctypes.data), src), "qtpu_mlp_params")
+        return out
+
+    def forward(self, x, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        self._ok(self._L.qtpu_mlp_forward(self._m, C.c_void_p(x.data_ptr()), x.shape[0], C.c_void_p(out.data_ptr())),
+                 "qtpu_mlp_forward")
+        return out
+
+    def gradients(self, x, t):
+        import numpy as np
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = C.c_float()
+        self._ok(self._L.qtpu_mlp_gradients(self._m, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()), x.shape[0],
+                                            C.c_void_p(g.ctypes.data), C.byref(loss)), "qtpu_mlp_gradients")
+        return g, loss.value
+
+    def train_step(self, x, t, lr: float = 1e-3) -> float:
+        loss = C.c_float()
+        self._ok(self._L.qtpu_mlp_train_step(self._m, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()), x.shape[0],
+                                             lr, C.byref(loss)), "qtpu_mlp_train_step")
+        return loss.value
+
+    def close(self):
+        if self._m:
+            self._L.qtpu_mlp_destroy(self._m)
+            self._m = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def pairwise_contract_noalloc(A, B, C_out, stream: int | None = None):
     """C_out[b] = A[b] @ B[b] through the allocation-free entry point (for
     callers that cannot allocate device memory at call time; see the C
@@ -234,13 +311,14 @@ def pairwise_contract_noalloc(A, B, C_out, stream: int | None = None):
     return C_out
 
 
-def plan_text(tensor_inds, dims: dict, output, max_intermediate_bytes=0, n_slices=0, slice_dim=0) -> str:
+def plan_text(tensor_inds, dims: dict, output, max_intermediate_bytes=0, n_slices=0, slice_dim=0,
+              seed=0) -> str:
     """Plan on a host-only handle and return the canonical plan text."""
     h = HTN(device=-1)
     for inds in tensor_inds:
         h.add_tensor(inds, [dims[i] for i in inds])
     h.set_output(output)
-    h.plan("fp64", max_intermediate_bytes, n_slices, slice_dim)
+    h.plan("fp64", max_intermediate_bytes, n_slices, slice_dim, seed)
     t = h.plan_info()
     h.close()
     return t

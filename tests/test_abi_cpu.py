@@ -31,7 +31,7 @@ def test_exports_every_declared_symbol():
 
 def _ref_text(net_inds, dims, output, **kw):
     p = planner.make_plan(net_inds, dims, output, kw.get("max_intermediate_bytes", 0),
-                          kw.get("n_slices", 0), kw.get("slice_dim", 0))
+                          kw.get("n_slices", 0), kw.get("slice_dim", 0), kw.get("seed", 0))
     return planner.plan_text(p, net_inds)
 
 
@@ -123,3 +123,23 @@ def test_overflow_is_enotsup():
     with pytest.raises(htn.QtpuError) as e:
         h.plan()
     assert e.value.status == htn.QTPU_ENOTSUP
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 12345, 2 ** 63 + 5])
+@pytest.mark.parametrize("net_id", ["ring8", "rand7", "chords"])
+def test_randomised_planner_bit_exact(seed, net_id):
+    net = {"ring8": lambda: synth.ring_htn(), "rand7": lambda: synth.random_htn(7),
+           "chords": lambda: synth.ring_chords_htn(materialize=False)}[net_id]()
+    kw = {"seed": seed, "n_slices": 16, "slice_dim": 4} if net_id == "chords" else {"seed": seed}
+    got = htn.plan_text(net.inds(), net.dims(), net.output, **kw)
+    assert got == _ref_text(net.inds(), net.dims(), net.output, **kw)
+
+
+def test_splitmix64_reference_values():
+    # the first outputs of the published SplitMix64 reference implementation
+    # seeded with 1234567
+    s, outs = 1234567, []
+    for _ in range(3):
+        s, r = planner.splitmix64(s)
+        outs.append(r)
+    assert outs == [6457827717110365317, 3203168211198807973, 9817491932198370423]
