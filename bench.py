@@ -368,10 +368,17 @@ def run_ours(args, rank, world):
     n_slices = int(h.plan_info().split("slices n=")[1].split()[0])
     sub = args.workload == "100q"
     if sub:
-        # every slice runs the same launches: time a fixed subset of them
-        S = min(args.slices_timed, n_slices)
+        # every slice runs the same launches: time a fixed subset of them; with
+        # several ranks each contracts its own S slices and the outputs are
+        # summed over ranks (the slice sum is the path's one exchange step)
+        S = min(args.slices_timed, n_slices // world)
         flops = st["flops_total"] / n_slices * S
-        step = lambda: h.contract_slices(0, S, out)  # noqa: E731
+        first = rank * S
+
+        def step():
+            h.contract_slices(first, S, out)
+            if world > 1:
+                dist.all_reduce(out, op=dist.ReduceOp.SUM)
     else:
         S = n_slices
         flops = st["flops_total"]
@@ -501,6 +508,8 @@ def run_ours(args, rank, world):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload] + (f" ({args.shape})" if args.workload == "gemm" else ""),
+                   "sharding": ("slices split over ranks, one all-reduce of the output per step" if sub
+                                else "independent replicas") if world > 1 else "single GPU",
                    "flops_per_step": flops, "prec": args.prec,
                    "l2": "flushed between timed steps (256 MiB write)" if net.nbytes() < (256 << 20)
                    else "inputs larger than L2", "plan_steps": st["n_steps"],

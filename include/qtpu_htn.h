@@ -187,9 +187,18 @@ qtpu_status qtpu_htn_contract_batch(qtpu_htn* const* hs, int n,
 qtpu_status qtpu_htn_contract_slices(qtpu_htn* h, int64_t first, int64_t count,
                                      double* dev_out);
 
-/* Wait for the handle's stream and read its device status word: QTPU_OK, or
- * QTPU_ETIMEOUT if a bounded device-side wait gave up, or QTPU_ECUDA. */
+/* Wait for the handle's streams and read its device status word: QTPU_OK, or
+ * QTPU_ETIMEOUT if a bounded device-side wait gave up, or QTPU_ECUDA.  A
+ * nonzero status is reported once (reading clears it). */
 qtpu_status qtpu_htn_sync(qtpu_htn* h);
+
+/* Failure-path self-test: enqueue on the handle's stream one warp whose
+ * bounded device-side wait (the same bounded mbarrier wait the GEMM pipeline
+ * uses) is on a barrier that nothing completes.  After limit_ns (at most 10
+ * s) it gives up and sets the timeout bit of the status word, so the next
+ * qtpu_htn_sync returns QTPU_ETIMEOUT.  Nothing faults, traps or hangs, and
+ * the handle stays usable. */
+qtpu_status qtpu_htn_selftest_timeout(qtpu_htn* h, uint64_t limit_ns);
 
 qtpu_status qtpu_htn_destroy(qtpu_htn* h);
 

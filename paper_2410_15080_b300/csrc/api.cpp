@@ -224,9 +224,14 @@ qtpu_status qtpu_htn_sync(qtpu_htn* h) {
   if (h->host_only || !h->built) return QTPU_OK;
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
+  if (h->ex.own) {
+    e = cudaStreamSynchronize(h->ex.own);
+    if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
+  }
   uint32_t st = 0;
   e = cudaMemcpy(&st, h->ex.status, 4, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
+  if (st) cudaMemset(h->ex.status, 0, 4);  // reported once
   if (st & (ST_TIMEOUT_TMA | ST_TIMEOUT_MMA | ST_TIMEOUT_EPI | ST_TIMEOUT_DEP))
     return fail(h, QTPU_ETIMEOUT, "a bounded device-side wait gave up (status 0x" + std::to_string(st) + ")");
   if (st) return fail(h, QTPU_ECUDA, "device status word " + std::to_string(st));
@@ -410,6 +415,16 @@ qtpu_status qtpu_htn_profile_read(qtpu_htn* h, int n, double* ms, int64_t* launc
     if (flops) flops[k] = f[k];
     if (bytes) bytes[k] = b[k];
   }
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_selftest_timeout(qtpu_htn* h, uint64_t limit_ns) {
+  if (!h) return QTPU_EINVAL;
+  if (h->host_only || !h->built) return fail(h, QTPU_ESTATE, "needs a planned device handle");
+  if (limit_ns == 0 || limit_ns > 10000000000ull) return fail(h, QTPU_EINVAL, "limit must be in (0, 10 s]");
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e == cudaSuccess) e = launch_bounded_wait_probe(h->ex.status, limit_ns, h->stream);
+  if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
   return QTPU_OK;
 }
 

@@ -815,7 +815,12 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
   ex->arena_bytes = std::max<size_t>(arena.top, 256);
   ex->split_a_bytes = split_need_a;
   ex->split_bytes = split_need_a + split_need_b;
+  // QTPU_TEST_FAIL_ALLOC=1 makes the workspace allocation fail (a host-side
+  // injection point for the out-of-memory path)
+  const char* fa = std::getenv("QTPU_TEST_FAIL_ALLOC");
+  const bool force_fail = fa && std::atoi(fa) != 0;
   auto dalloc = [&](void** p, size_t nbytes) -> bool {
+    if (force_fail) return false;
     if (!nbytes) return true;
     if (cudaMalloc(p, nbytes) != cudaSuccess) {
       cudaGetLastError();

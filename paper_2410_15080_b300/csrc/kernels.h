@@ -118,6 +118,8 @@ struct GemmArgs {
   uint64_t limit_ns = 2000000000ull;
 };
 cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st);
+// one warp waiting (bounded) on a barrier nothing completes: sets ST_TIMEOUT_DEP
+cudaError_t launch_bounded_wait_probe(uint32_t* status, uint64_t limit_ns, cudaStream_t st);
 // one-time per-device setup of the GEMM kernels (shared-memory attribute)
 cudaError_t gemm_prepare();
 

@@ -346,7 +346,29 @@ cudaError_t launch_t(const GemmArgs& a, int sm_count, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// A single warp waits on an mbarrier that nothing completes, with the same
+// bounded wait the GEMM pipeline uses; after limit_ns it gives up and sets
+// the dependency-timeout bit of the status word.  Exercises the device-side
+// failure path without faulting or hanging the GPU.
+__global__ void k_bounded_wait_probe(uint32_t* status, uint64_t limit_ns) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(&bar, 0, limit_ns, &abort_flag);
+  if (!__all_sync(0xffffffffu, ok) && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT_DEP);
+}
+
 }  // namespace
+
+cudaError_t launch_bounded_wait_probe(uint32_t* status, uint64_t limit_ns, cudaStream_t st) {
+  k_bounded_wait_probe<<<1, 32, 0, st>>>(status, limit_ns);
+  return cudaGetLastError();
+}
 
 int gemm_block_n() { return BN; }
 

@@ -22,7 +22,7 @@ QTPU_QT, QTPU_CT = 0, 1
 
 SYMBOLS = ["qtpu_htn_create", "qtpu_htn_add_tensor", "qtpu_htn_set_output", "qtpu_htn_plan",
            "qtpu_htn_plan_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats", "qtpu_htn_contract",
-           "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_contract_slices", "qtpu_htn_sync", "qtpu_htn_destroy",
+           "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_contract_slices", "qtpu_htn_sync", "qtpu_htn_selftest_timeout", "qtpu_htn_destroy",
            "qtpu_htn_profile", "qtpu_htn_profile_read", "qtpu_pairwise_contract_noalloc", "qtpu_last_error",
            "qtpu_mlp_create", "qtpu_mlp_num_params", "qtpu_mlp_params", "qtpu_mlp_forward",
            "qtpu_mlp_gradients", "qtpu_mlp_train_step", "qtpu_mlp_destroy"]
@@ -69,6 +69,7 @@ def lib():
         L.qtpu_htn_contract_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), vp]
         L.qtpu_htn_contract_slices.argtypes = [vp, C.c_int64, C.c_int64, vp]
         L.qtpu_htn_sync.argtypes = [vp]
+        L.qtpu_htn_selftest_timeout.argtypes = [vp, C.c_uint64]
         L.qtpu_pairwise_contract_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]
         L.qtpu_htn_destroy.argtypes = [vp]
         fp = C.POINTER(C.c_float)
@@ -198,6 +199,10 @@ class HTN:
                                                 for a in host_arrays])
         self._check(self._L.qtpu_htn_contract_host(self._h, ptrs, C.c_void_p(out.ctypes.data)))
         return out
+
+    def selftest_timeout(self, limit_ns: int):
+        """Enqueue a bounded device wait that is bound to time out (see header)."""
+        self._check(self._L.qtpu_htn_selftest_timeout(self._h, limit_ns))
 
     def sync(self):
         self._check(self._L.qtpu_htn_sync(self._h))

@@ -58,13 +58,14 @@ def test_cost_model_pipeline_picks_a_plan_that_contracts_exactly():
     """Train on measured candidate plans of a few networks, choose for a new
     one: the chosen plan's result equals the oracle (the model only chooses)."""
     from paper_2410_15080_b300 import costmodel as cm
-    X, y, _ = cm.gen_dataset(cm.train_networks(3), per_net=8)
+    X, y, groups, flops = cm.gen_dataset(cm.train_networks(3), per_net=8)
     assert np.isfinite(y).all()
     model = cm.CostModel(hidden=64)
     losses = model.train(X, y, epochs=40, batch=8)
     assert losses[-1] < losses[0]
     net = cm.eval_networks(1)[0]
-    cands, im, ie, pred = cm.choose(model, net)
+    f = cm.select_factor(model.predict(X), y, flops, groups)
+    cands, im, ie, pred = cm.choose(model, net, f)
     assert len(cands) == 64 and np.isfinite(pred).all()
     _, out = cm.measure(cm.to_device(net), net.output, cands[im][0], reps=1)
     assert rel_err(out.cpu().numpy(), oracle_value(net)) <= REL_TOL
