@@ -493,7 +493,9 @@ def run_ours(args, rank, world):
     roof["traffic"] = measured_traffic(dom)
     roof["per_launch_ms"] = per_launch_ms
     roof["launches_per_step"] = d["launches"] / args.steps
-    roof["classes"] = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
+    roof["classes"] = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                           "algorithmic_GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] else None,
+                           "useful_TFLOPs": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] else None}
                        for k, v in prof.items()}
 
     cpu = None

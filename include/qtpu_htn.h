@@ -118,6 +118,15 @@ qtpu_status qtpu_htn_plan(qtpu_htn* h, const qtpu_plan_opts* opts);
 qtpu_status qtpu_htn_plan_info(const qtpu_htn* h, char* buf, size_t len,
                                size_t* needed);
 
+/* The lowered launch list, one line per kernel launch of one slice (kind,
+ * fast or generic gather, operand count, shape, operands, destination, useful
+ * FLOPs, algorithmic bytes), then the reduction and a summary line
+ * (launches per slice, tensor-core steps, fused absorption steps, ...).
+ * Available after plan, also on a host-only handle (lowering needs no GPU).
+ * Same buffer convention as qtpu_htn_plan_info. */
+qtpu_status qtpu_htn_lowering_info(const qtpu_htn* h, char* buf, size_t len,
+                                   size_t* needed);
+
 /* Number of FP64 entries of the output (product of output dims). */
 qtpu_status qtpu_htn_output_size(const qtpu_htn* h, int64_t* n);
 

@@ -148,11 +148,14 @@ qtpu_status qtpu_htn_plan(qtpu_htn* h, const qtpu_plan_opts* opts) {
   if (r == PLAN_OVERFLOW) return fail(h, QTPU_ENOTSUP, "a contraction size reaches 2^255");
   if (r == PLAN_LIMIT) return fail(h, QTPU_ELIMIT, "the peak-intermediate limit cannot be met by slicing");
   h->opts = o;
-  if (!h->host_only) {
+  {
+    // a host-only handle lowers the plan too (no device work), so its
+    // launch list can be inspected
     int code = QTPU_OK;
-    std::string m = exec_build(&h->ex, h->plan, h->leaves, h->dims, (int)o.prec, &code);
-    if (code != QTPU_OK) return fail(h, (qtpu_status)code, m);
-    h->built = true;
+    std::string m = exec_build(&h->ex, h->plan, h->leaves, h->dims, (int)o.prec, &code, h->host_only);
+    if (code != QTPU_OK && !h->host_only) return fail(h, (qtpu_status)code, m);
+    if (code != QTPU_OK) h->ex.lowered = false;  // planning still succeeded
+    h->built = !h->host_only;
   }
   h->planned = true;
   return QTPU_OK;
@@ -162,6 +165,19 @@ qtpu_status qtpu_htn_plan_info(const qtpu_htn* h, char* buf, size_t len, size_t*
   if (!h) return QTPU_EINVAL;
   if (!h->planned) return QTPU_ESTATE;
   std::string t = plan_text(h->plan);
+  if (needed) *needed = t.size() + 1;
+  if (buf && len) {
+    size_t n = std::min(len - 1, t.size());
+    memcpy(buf, t.data(), n);
+    buf[n] = 0;
+  }
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_lowering_info(const qtpu_htn* h, char* buf, size_t len, size_t* needed) {
+  if (!h) return QTPU_EINVAL;
+  if (!h->planned || !h->ex.lowered) return QTPU_ESTATE;
+  std::string t = exec_describe(&h->ex);
   if (needed) *needed = t.size() + 1;
   if (buf && len) {
     size_t n = std::min(len - 1, t.size());

@@ -219,7 +219,7 @@ struct Repr {
 }  // namespace
 
 std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& leaves, const DimMap& dims,
-                       int prec, int* code) {
+                       int prec, int* code, bool dry_run) {
   *code = QTPU_OK;
   ex->prec = prec;
   ex->n_leaves = plan.n_leaves;
@@ -808,6 +808,43 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
   ex->reduce = R;
   ex->launches_per_contract = (plan.steps.empty() ? 0 : (int64_t)ex->launches.size() * ex->n_slices) + 1;
 
+  // ---- concurrent leaf splits: in an unsliced plan, a GEMM operand gathered
+  // from leaves only does not depend on the chain; give it its own buffer
+  // and run it on a second stream
+  if (const char* e = std::getenv("QTPU_NO_GRAPH")) ex->use_graph = std::atoi(e) == 0;
+  bool side_ok = !fp64 && ex->n_slices == 1 && ex->use_graph;
+  if (const char* e = std::getenv("QTPU_NO_SIDE")) side_ok = side_ok && std::atoi(e) == 0;
+  size_t side_total = 0;
+  ex->n_side = 0;
+  if (side_ok) {
+    for (size_t i = 0; i < ex->launches.size(); ++i) {
+      Launch& L = ex->launches[i];
+      if (L.kind != LK_GATHER || (L.dst != DST_SPLIT_A && L.dst != DST_SPLIT_B)) continue;
+      bool leaves_only = true;
+      for (int j = 0; j < L.nsrc; ++j) leaves_only = leaves_only && L.src[j] < nl;
+      if (!leaves_only) continue;
+      const GatherArgs& g = L.has_fast ? L.gf : L.g;
+      const size_t bytes = align_up((size_t)np * g.n_rows * g.Kp * es, 1024);
+      if (side_total + bytes > ((size_t)4 << 30)) continue;
+      L.side = ex->n_side++;
+      L.side_off = side_total;
+      side_total += bytes;
+      // the GEMM right after its two splits waits for this one
+      for (size_t q = i + 1; q < ex->launches.size() && q <= i + 2; ++q)
+        if (ex->launches[q].kind == LK_GEMM) {
+          ex->launches[q].wait_side[L.dst == DST_SPLIT_A ? 0 : 1] = L.side;
+          break;
+        }
+      L.dst = DST_SIDE;
+    }
+  }
+  ex->side_bytes = side_total;
+  ex->arena_bytes = std::max<size_t>(arena.top, 256);
+  ex->split_a_bytes = split_need_a;
+  ex->split_bytes = split_need_a + split_need_b;
+  ex->lowered = true;
+  if (dry_run) return "";
+
   // ---- device memory
   cudaError_t ce = cudaSetDevice(ex->device);
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&ex->sm_count, cudaDevAttrMultiProcessorCount, ex->device);
@@ -833,6 +870,20 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       !dalloc((void**)&ex->status, 16) || !dalloc((void**)&ex->out_stage, (size_t)R.g.n_out * 8 + 8)) {
     exec_free(ex);
     return fail(QTPU_ENOMEM, "device workspace allocation failed");
+  }
+  if (ex->n_side) {
+    bool ok = dalloc((void**)&ex->sidebuf, ex->side_bytes) &&
+              cudaStreamCreateWithFlags(&ex->side_stream, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; ok && k < ex->n_side + 2; ++k) {
+      cudaEvent_t e;
+      ok = cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+      if (ok) ex->side_ev.push_back(e);
+    }
+    if (!ok) {
+      cudaGetLastError();
+      exec_free(ex);
+      return fail(QTPU_ENOMEM, "side buffers");
+    }
   }
   cudaMemset(ex->status, 0, 16);
   if (ex->n_tc_steps) {
@@ -861,9 +912,10 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     if (L.kind != LK_GEMM) continue;
     const Launch& A = ex->launches[i - 2];
     const Launch& B = ex->launches[i - 1];
-    if (!make_operand_map(&L.gemm.tmA, ex->splitbuf, prec, L.gemm.batch, L.gemm.M, L.gemm.K, A.g.Kp, 128) ||
-        !make_operand_map(&L.gemm.tmB, ex->splitbuf + ex->split_a_bytes, prec, L.gemm.batch, L.gemm.N, L.gemm.K,
-                          B.g.Kp, gemm_block_n())) {
+    uint8_t* pa = A.side >= 0 ? ex->sidebuf + A.side_off : ex->splitbuf;
+    uint8_t* pb = B.side >= 0 ? ex->sidebuf + B.side_off : ex->splitbuf + ex->split_a_bytes;
+    if (!make_operand_map(&L.gemm.tmA, pa, prec, L.gemm.batch, L.gemm.M, L.gemm.K, A.g.Kp, 128) ||
+        !make_operand_map(&L.gemm.tmB, pb, prec, L.gemm.batch, L.gemm.N, L.gemm.K, B.g.Kp, gemm_block_n())) {
       exec_free(ex);
       return fail(QTPU_ECUDA, "cuTensorMapEncodeTiled failed");
     }
@@ -910,6 +962,39 @@ struct Timed {
 };
 }  // namespace
 
+std::string exec_describe(const Executor* ex) {
+  std::ostringstream o;
+  const char* cls[] = {"contract", "split", "gemm", "reduce"};
+  auto one = [&](const Launch& L, size_t i) {
+    o << "launch " << i << " " << cls[L.kclass] << " ";
+    if (L.kind == LK_GEMM) {
+      o << "gemm batch=" << L.gemm.batch << " M=" << L.gemm.M << " N=" << L.gemm.N << " K=" << L.gemm.K;
+    } else if (L.kind == LK_CONTRACT64) {
+      o << "fp64 out=" << L.c64.n_out << " loop=" << L.c64.n_loop;
+    } else {
+      const GatherArgs& g = L.has_fast ? L.gf : L.g;
+      o << (L.has_fast ? "fast" : "generic") << " ops=" << g.nops;
+      if (L.has_fast) o << " big=" << g.nbig << " w=" << g.w_size << " fan=" << g.fan_f;
+      if (g.mode >= GW_SPLIT_BF16X3)
+        o << " rows=" << g.n_rows << " K=" << g.K;
+      else
+        o << " out=" << g.n_out;
+      o << " loop=" << g.n_loop;
+    }
+    o << " src=";
+    for (int j = 0; j < L.nsrc; ++j) o << (j ? "," : "") << L.src[j];
+    if (L.kind == LK_GEMM) o << "-";
+    o << " dst=" << L.dst << (L.side >= 0 ? " side" : "") << " flops=" << (long long)L.flops
+      << " bytes=" << (long long)L.bytes << "\n";
+  };
+  for (size_t i = 0; i < ex->launches.size(); ++i) one(ex->launches[i], i);
+  o << "reduce slices=" << ex->n_slices << " out=" << ex->reduce.g.n_out << " loop=" << ex->reduce.g.n_loop << "\n";
+  o << "summary launches_per_slice=" << ex->launches.size() << " tensor_core_steps=" << ex->n_tc_steps
+    << " fused_steps=" << ex->n_fused_steps << " side_splits=" << ex->n_side << " arena_bytes=" << ex->arena_bytes
+    << " split_bytes=" << ex->split_bytes << "\n";
+  return o.str();
+}
+
 std::string exec_profile_read(Executor* ex, double* ms, int64_t* launches, double* flops, double* bytes) {
   for (int k = 0; k < KC_COUNT; ++k) ms[k] = 0, launches[k] = 0, flops[k] = 0, bytes[k] = 0;
   Profiler& p = ex->prof;
@@ -942,8 +1027,11 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
     if (t < nl) return (const uint8_t*)leaves[t].ptr + loff[t] * (int64_t)dt_bytes(leaves[t].dt);
     return ex->arena + ex->inter_off[t - nl];
   };
+  const bool sided = ex->n_side > 0 && count == ex->n_slices && ex->n_slices == 1;
+  const Launch* cur = nullptr;
   auto dst_ptr = [&](int d, int64_t s) -> void* {
     switch (d) {
+      case DST_SIDE: return ex->sidebuf + cur->side_off;
       case DST_PARTIAL: return ex->partial + (size_t)s * ex->final_size * 8;
       case DST_SPLIT_A: return ex->splitbuf;
       case DST_SPLIT_B: return ex->splitbuf + ex->split_a_bytes;
@@ -951,7 +1039,8 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
       default: return ex->arena + ex->inter_off[d - nl];
     }
   };
-  auto run_one = [&](const Launch& L, int64_t s, bool reduce) -> cudaError_t {
+  auto run_one_on = [&](const Launch& L, int64_t s, bool reduce, cudaStream_t st) -> cudaError_t {
+    cur = &L;
     Timed t(ex->prof, st, L.kclass, L.flops, L.bytes);
     const bool from_partial = reduce && !ex->launches.empty();
     if (L.kind == LK_GATHER) {
@@ -977,6 +1066,31 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
     const int dtb = reduce ? DT_F64 : (L.src[1] < nl ? leaves[L.src[1]].dt : ex->inter_dt);
     return launch_contract(A, dta, B, dtb, (double*)dst_ptr(L.dst, s), L.c64, ex->sm_count, st);
   };
+  auto run_one = [&](const Launch& L, int64_t s, bool reduce) { return run_one_on(L, s, reduce, st); };
+  if (sided) {
+    // fork: every leaf-only split on the side stream first, one event each
+    cudaStream_t ss = ex->side_stream;
+    cudaEvent_t fork = ex->side_ev[ex->n_side], join = ex->side_ev[ex->n_side + 1];
+    ce = cudaEventRecord(fork, st);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(ss, fork, 0);
+    for (auto& L : ex->launches) {
+      if (ce != cudaSuccess) break;
+      if (L.side < 0) continue;
+      ce = run_one_on(L, 0, false, ss);
+      if (ce == cudaSuccess) ce = cudaEventRecord(ex->side_ev[L.side], ss);
+    }
+    for (auto& L : ex->launches) {
+      if (ce != cudaSuccess) break;
+      if (L.side >= 0) continue;
+      for (int w : L.wait_side)
+        if (w >= 0 && ce == cudaSuccess) ce = cudaStreamWaitEvent(st, ex->side_ev[w], 0);
+      if (ce == cudaSuccess) ce = run_one(L, 0, false);
+    }
+    if (ce == cudaSuccess) ce = cudaEventRecord(join, ss);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(st, join, 0);
+    if (ce == cudaSuccess) ce = run_one(ex->reduce, 0, true);
+    return ce;
+  }
   for (int64_t s = first; s < first + count && ce == cudaSuccess && !ex->launches.empty(); ++s) {
     int64_t r = s;
     for (int j = (int)ex->slice_dims.size() - 1; j >= 0; --j) {

@@ -24,7 +24,7 @@ enum KernelClass { KC_CONTRACT = 0, KC_SPLIT = 1, KC_GEMM = 2, KC_REDUCE = 3, KC
 enum LaunchKind { LK_GATHER = 0, LK_GEMM = 1, LK_CONTRACT64 = 2 };
 
 // Destinations of a launch's output
-enum : int { DST_PARTIAL = -1, DST_SPLIT_A = -2, DST_SPLIT_B = -3, DST_OUT = -4 };
+enum : int { DST_PARTIAL = -1, DST_SPLIT_A = -2, DST_SPLIT_B = -3, DST_OUT = -4, DST_SIDE = -5 };
 
 struct Launch {
   int kind = LK_GATHER;
@@ -39,6 +39,12 @@ struct Launch {
   GemmArgs gemm;          // LK_GEMM (split buffers fixed; C patched)
   ContractArgs c64;       // LK_CONTRACT64 (FP64 path)
   double flops = 0, bytes = 0;
+  // side stream: a split whose operands are all leaves runs on a second
+  // stream into its own buffer (side_off) ahead of the chain; the GEMM that
+  // consumes it waits for its event (wait_side: indices into side events)
+  int side = -1;
+  size_t side_off = 0;
+  int wait_side[2] = {-1, -1};
 };
 
 struct Profiler {
@@ -80,6 +86,7 @@ struct Executor {
   int n_tc_steps = 0;
   int n_fused_steps = 0;         // absorption steps folded into a consumer
   int64_t launches_per_contract = 0;
+  bool lowered = false;
   Profiler prof;
   // CUDA graph of one whole contraction, replayed on a private stream
   // (index 0: plain, 1: with profiling events)
@@ -87,15 +94,26 @@ struct Executor {
   cudaStream_t own = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // concurrent leaf splits (graph mode, unsliced plans only)
+  int n_side = 0;
+  uint8_t* sidebuf = nullptr;
+  size_t side_bytes = 0;
+  cudaStream_t side_stream = nullptr;
+  std::vector<cudaEvent_t> side_ev;  // one per side launch, plus fork and join
+  double planned_side_bytes = 0;
   size_t workspace_bytes() const {
-    return arena_bytes + split_bytes + (size_t)n_slices * final_size * 8;
+    return arena_bytes + split_bytes + side_bytes + (size_t)n_slices * final_size * 8;
   }
 };
 
 // Build launch descriptors and allocate the workspace.  Returns an empty
 // string on success, else an error message (*code receives a qtpu_status).
 std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& leaves, const DimMap& dims,
-                       int prec, int* code);
+                       int prec, int* code, bool dry_run = false);
+// One line per launch of the lowered contraction (kind, operands, shape,
+// useful FLOPs, algorithmic bytes) -- available after exec_build, also on a
+// dry run.
+std::string exec_describe(const Executor* ex);
 // Enqueue the whole contraction; writes output_size FP64 entries to dev_out.
 std::string exec_run(Executor* ex, const std::vector<Leaf>& leaves, double* dev_out, cudaStream_t st, int* code);
 // Enqueue one whole contraction on `st` with direct launches, result to out

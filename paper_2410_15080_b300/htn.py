@@ -21,7 +21,7 @@ PREC = {"fp64": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3}
 QTPU_QT, QTPU_CT = 0, 1
 
 SYMBOLS = ["qtpu_htn_create", "qtpu_htn_add_tensor", "qtpu_htn_set_output", "qtpu_htn_plan",
-           "qtpu_htn_plan_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats", "qtpu_htn_contract",
+           "qtpu_htn_plan_info", "qtpu_htn_lowering_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats", "qtpu_htn_contract",
            "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_contract_slices", "qtpu_htn_sync", "qtpu_htn_selftest_timeout", "qtpu_htn_destroy",
            "qtpu_htn_profile", "qtpu_htn_profile_read", "qtpu_pairwise_contract_noalloc", "qtpu_last_error",
            "qtpu_mlp_create", "qtpu_mlp_num_params", "qtpu_mlp_params", "qtpu_mlp_forward",
@@ -58,6 +58,7 @@ def lib():
         L.qtpu_htn_set_output.argtypes = [vp, C.c_int, i64p]
         L.qtpu_htn_plan.argtypes = [vp, C.POINTER(PlanOpts)]
         L.qtpu_htn_plan_info.argtypes = [vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]
+        L.qtpu_htn_lowering_info.argtypes = [vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]
         L.qtpu_htn_output_size.argtypes = [vp, i64p]
         L.qtpu_htn_plan_stats.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int),
                                           C.POINTER(C.c_int), C.POINTER(C.c_uint64), i64p]
@@ -147,6 +148,13 @@ class HTN:
         self._check(self._L.qtpu_htn_plan_info(self._h, None, 0, C.byref(need)))
         buf = C.create_string_buffer(need.value)
         self._check(self._L.qtpu_htn_plan_info(self._h, buf, need.value, None))
+        return buf.value.decode()
+
+    def lowering_info(self) -> str:
+        need = C.c_size_t(0)
+        self._check(self._L.qtpu_htn_lowering_info(self._h, None, 0, C.byref(need)))
+        buf = C.create_string_buffer(need.value)
+        self._check(self._L.qtpu_htn_lowering_info(self._h, buf, need.value, None))
         return buf.value.decode()
 
     def output_size(self) -> int:
@@ -314,6 +322,18 @@ def pairwise_contract_noalloc(A, B, C_out, stream: int | None = None):
     if st != QTPU_OK:
         raise QtpuError(st, "qtpu_pairwise_contract_noalloc failed")
     return C_out
+
+
+def lowering_text(tensor_inds, dims: dict, output, prec="bf16x3", dtypes=None, **plan_kw) -> str:
+    """Lower a plan on a host-only handle and return the launch list text."""
+    h = HTN(device=-1)
+    for t, inds in enumerate(tensor_inds):
+        h.add_tensor(inds, [dims[i] for i in inds], dtype=(dtypes[t] if dtypes else "f64"))
+    h.set_output(output)
+    h.plan(prec, **plan_kw)
+    t = h.lowering_info()
+    h.close()
+    return t
 
 
 def plan_text(tensor_inds, dims: dict, output, max_intermediate_bytes=0, n_slices=0, slice_dim=0,
