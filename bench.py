@@ -34,7 +34,10 @@ sys.path.insert(0, ROOT)
 METRIC = "h-TN contract TFLOP/s & %peak vs plain FP64 GPU path at rel err ≤1e-6"
 WORKLOADS = {
     "mid": "mid-size 60-qubit ring h-TN: 8 QTs [k=64][6,6,4][6,6,4] FP64, 16 gate + 8 wire cuts, 32 tensors",
-    "100q": "100-qubit ring+chords h-TN: 12 QTs, 28 gate + 12 wire cuts, k=64, sliced over 4^5 wire-index values",
+    "100q": "100-qubit ring+chords h-TN: 12 QTs, 28 gate + 12 wire cuts, k=64, sliced over 4^5 wire-index values, "
+            "order: best of 256 planner candidates by exact FLOPs",
+    "100q-free": "100-qubit ring+chords h-TN: 12 QTs, 28 gate + 12 wire cuts, k=64, peak intermediate <= 8 GB, "
+                 "slices chosen by the planner, order: best of 256 planner candidates by exact FLOPs",
     "gemm": "one pairwise step C[b,m,n] = sum_k A[b,m,k] B[b,k,n] of the given --shape (FP64 leaves)",
     "batch": "512 independent random h-TNs (ring / 2-D grid, 2-12 subcircuits, 2-20 cuts, k 1-64, FP32/FP64) "
              "in one CUDA graph",
@@ -79,7 +82,10 @@ def make_network(workload: str, shape: str = "8x1024x1024x1024"):
     if workload == "mid":
         return synth.ring_htn(), {}
     if workload == "100q":
-        return synth.ring_chords_htn(), {"max_intermediate_bytes": 8 << 30, "n_slices": 1024, "slice_dim": 4}
+        return synth.ring_chords_htn(), {"max_intermediate_bytes": 8 << 30, "n_slices": 1024, "slice_dim": 4,
+                                         "n_candidates": 256}
+    if workload == "100q-free":
+        return synth.ring_chords_htn(), {"max_intermediate_bytes": 8 << 30, "n_candidates": 256}
     raise SystemExit(f"unknown workload {workload}")
 
 
@@ -366,7 +372,7 @@ def run_ours(args, rank, world):
     flush_buf = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MiB > L2
     flush = (lambda: flush_buf.zero_()) if net.nbytes() < (256 << 20) else (lambda: None)
     n_slices = int(h.plan_info().split("slices n=")[1].split()[0])
-    sub = args.workload == "100q"
+    sub = args.workload in ("100q", "100q-free")
     if sub:
         # every slice runs the same launches: time a fixed subset of them; with
         # several ranks each contracts its own S slices and the outputs are

@@ -73,6 +73,12 @@ typedef struct {
                                       pair drawn among the 3 best keys by
                                       SplitMix64(seed)), for plan candidates */
   const char* autotune_table;      /* reserved; may be NULL                   */
+  uint32_t n_candidates;           /* > 1: plan with seeds seed, seed+1, ...,
+                                      seed+n-1 (seed 0 = greedy) under the same
+                                      slicing options and keep the plan with
+                                      the fewest total FLOPs (ties: the lower
+                                      seed); candidates that cannot meet the
+                                      limit are skipped                      */
 } qtpu_plan_opts;
 
 /* Create an empty network bound to CUDA device `device` and the CUDA stream

@@ -238,10 +238,29 @@ def plan_text(plan, tensors_inds) -> str:
     lines.append(f"slices n={plan.n_slices} idx={_l(plan.sliced)}")
     lines.append(f"cost flops_per_slice={total} flops_total={total * plan.n_slices} "
                  f"peak={peak}")
+    if getattr(plan, "search", None):
+        lines.append(f"search candidates={plan.search[0]} seed={plan.search[1]}")
     return "\n".join(lines) + "\n"
 
 
-def make_plan(tensors_inds, dims, output, max_bytes=0, n_slices=0, slice_dim=0, seed=0):
+def make_plan(tensors_inds, dims, output, max_bytes=0, n_slices=0, slice_dim=0, seed=0, n_candidates=0):
+    """One plan, or with n_candidates > 1 the plan with the fewest total flops
+    among seeds seed .. seed+n-1 (ties: the lower seed; candidates that cannot
+    meet the limit are skipped)."""
+    if n_candidates > 1:
+        best = None
+        for s in range(seed, seed + n_candidates):
+            try:
+                p = make_plan(tensors_inds, dims, output, max_bytes, n_slices, slice_dim, s)
+            except ValueError:
+                continue
+            tot = slice_stats(p, tensors_inds, p.sliced)[1] * p.n_slices
+            if best is None or tot < best[0]:
+                best = (tot, s, p)
+        if best is None:
+            raise ValueError("peak limit cannot be met")
+        best[2].search = (n_candidates, best[1])
+        return best[2]
     p = greedy(tensors_inds, dims, output, seed)
     return slice_plan(p, tensors_inds, max_bytes, n_slices, slice_dim)
 

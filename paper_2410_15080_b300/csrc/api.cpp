@@ -144,7 +144,14 @@ qtpu_status qtpu_htn_plan(qtpu_htn* h, const qtpu_plan_opts* opts) {
     if (!h->dims.has(i)) return fail(h, QTPU_EINVAL, "output index " + std::to_string(i) + " is on no tensor");
   std::vector<Inds> li;
   for (auto& L : h->leaves) li.push_back(L.ids);
-  int r = make_plan(li, h->dims, h->output, o.max_intermediate_bytes, o.n_slices, o.slice_dim, &h->plan, o.seed);
+  int r;
+  if (o.n_candidates > 1) {
+    uint64_t chosen = 0;
+    r = make_plan_best(li, h->dims, h->output, o.max_intermediate_bytes, o.n_slices, o.slice_dim, o.seed,
+                       o.n_candidates, &h->plan, &chosen);
+  } else {
+    r = make_plan(li, h->dims, h->output, o.max_intermediate_bytes, o.n_slices, o.slice_dim, &h->plan, o.seed);
+  }
   if (r == PLAN_OVERFLOW) return fail(h, QTPU_ENOTSUP, "a contraction size reaches 2^255");
   if (r == PLAN_LIMIT) return fail(h, QTPU_ELIMIT, "the peak-intermediate limit cannot be met by slicing");
   h->opts = o;

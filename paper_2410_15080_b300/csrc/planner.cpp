@@ -281,6 +281,30 @@ int make_plan(const std::vector<Inds>& leaves, const DimMap& dims, const Inds& o
   return PLAN_OK;
 }
 
+int make_plan_best(const std::vector<Inds>& leaves, const DimMap& dims, const Inds& output, uint64_t max_bytes,
+                   uint64_t n_slices, int64_t slice_dim, uint64_t seed, uint32_t n, Plan* plan, uint64_t* chosen) {
+  int last_err = PLAN_LIMIT;
+  bool have = false;
+  Plan cand;
+  for (uint32_t i = 0; i < n; ++i) {
+    const uint64_t s = seed + i;
+    const int r = make_plan(leaves, dims, output, max_bytes, n_slices, slice_dim, &cand, s);
+    if (r != PLAN_OK) {
+      last_err = r;
+      continue;
+    }
+    if (!have || cand.flops_total < plan->flops_total) {
+      *plan = cand;
+      *chosen = s;
+      have = true;
+    }
+  }
+  if (!have) return last_err;
+  plan->search = n;
+  plan->search_seed = *chosen;
+  return PLAN_OK;
+}
+
 static std::string lst(const Inds& v) {
   if (v.empty()) return "-";
   std::ostringstream o;
@@ -305,6 +329,7 @@ std::string plan_text(const Plan& p) {
   o << "slices n=" << p.n_slices.str() << " idx=" << lst(p.sliced) << "\n";
   o << "cost flops_per_slice=" << p.flops_per_slice.str() << " flops_total=" << p.flops_total.str()
     << " peak=" << p.peak.str() << "\n";
+  if (p.search) o << "search candidates=" << p.search << " seed=" << p.search_seed << "\n";
   return o.str();
 }
 

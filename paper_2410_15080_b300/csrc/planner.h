@@ -38,6 +38,8 @@ struct Plan {
   // per-slice accounting (sliced indices count as dim 1)
   std::vector<U256> step_size, step_flops;
   U256 flops_per_slice, flops_total, peak;
+  uint32_t search = 0;     // candidates searched (0: a single plan)
+  uint64_t search_seed = 0;
 };
 
 // index id -> dim lookup
@@ -59,6 +61,11 @@ enum PlanErr { PLAN_OK = 0, PLAN_OVERFLOW = 1, PLAN_LIMIT = 2 };
 constexpr int kRandTop = 3;
 int make_plan(const std::vector<Inds>& leaves, const DimMap& dims, const Inds& output,
               uint64_t max_bytes, uint64_t n_slices, int64_t slice_dim, Plan* plan, uint64_t seed = 0);
+
+// Best of n candidates (seeds seed .. seed+n-1) by total FLOPs; ties keep the
+// lower seed.  *chosen receives the winning seed.
+int make_plan_best(const std::vector<Inds>& leaves, const DimMap& dims, const Inds& output, uint64_t max_bytes,
+                   uint64_t n_slices, int64_t slice_dim, uint64_t seed, uint32_t n, Plan* plan, uint64_t* chosen);
 
 std::string plan_text(const Plan& plan);
 

@@ -38,7 +38,7 @@ class QtpuError(RuntimeError):
 class PlanOpts(C.Structure):
     _fields_ = [("max_intermediate_bytes", C.c_uint64), ("n_slices", C.c_uint32),
                 ("slice_dim", C.c_uint32), ("prec", C.c_int), ("cost_model", C.c_int),
-                ("seed", C.c_uint64), ("autotune_table", C.c_char_p)]
+                ("seed", C.c_uint64), ("autotune_table", C.c_char_p), ("n_candidates", C.c_uint32)]
 
 
 _lib = None
@@ -139,8 +139,8 @@ class HTN:
         self._check(self._L.qtpu_htn_set_output(self._h, len(inds), _arr(inds)))
 
     def plan(self, prec: str = "bf16x3", max_intermediate_bytes: int = 0, n_slices: int = 0,
-             slice_dim: int = 0, seed: int = 0):
-        o = PlanOpts(max_intermediate_bytes, n_slices, slice_dim, PREC[prec], 0, seed, None)
+             slice_dim: int = 0, seed: int = 0, n_candidates: int = 0):
+        o = PlanOpts(max_intermediate_bytes, n_slices, slice_dim, PREC[prec], 0, seed, None, n_candidates)
         self._check(self._L.qtpu_htn_plan(self._h, C.byref(o)))
 
     def plan_info(self) -> str:
@@ -337,13 +337,13 @@ def lowering_text(tensor_inds, dims: dict, output, prec="bf16x3", dtypes=None, *
 
 
 def plan_text(tensor_inds, dims: dict, output, max_intermediate_bytes=0, n_slices=0, slice_dim=0,
-              seed=0) -> str:
+              seed=0, n_candidates=0) -> str:
     """Plan on a host-only handle and return the canonical plan text."""
     h = HTN(device=-1)
     for inds in tensor_inds:
         h.add_tensor(inds, [dims[i] for i in inds])
     h.set_output(output)
-    h.plan("fp64", max_intermediate_bytes, n_slices, slice_dim, seed)
+    h.plan("fp64", max_intermediate_bytes, n_slices, slice_dim, seed, n_candidates)
     t = h.plan_info()
     h.close()
     return t

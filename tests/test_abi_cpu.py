@@ -31,7 +31,8 @@ def test_exports_every_declared_symbol():
 
 def _ref_text(net_inds, dims, output, **kw):
     p = planner.make_plan(net_inds, dims, output, kw.get("max_intermediate_bytes", 0),
-                          kw.get("n_slices", 0), kw.get("slice_dim", 0), kw.get("seed", 0))
+                          kw.get("n_slices", 0), kw.get("slice_dim", 0), kw.get("seed", 0),
+                          kw.get("n_candidates", 0))
     return planner.plan_text(p, net_inds)
 
 
@@ -143,3 +144,20 @@ def test_splitmix64_reference_values():
         s, r = planner.splitmix64(s)
         outs.append(r)
     assert outs == [6457827717110365317, 3203168211198807973, 9817491932198370423]
+
+
+@pytest.mark.parametrize("net_id", ["ring8", "rand5", "chords"])
+def test_best_of_candidates_planner_bit_exact(net_id):
+    net = {"ring8": lambda: synth.ring_htn(), "rand5": lambda: synth.random_htn(5),
+           "chords": lambda: synth.ring_chords_htn(materialize=False)}[net_id]()
+    kw = {"n_candidates": 12, "seed": 0}
+    if net_id == "chords":
+        kw.update(max_intermediate_bytes=8 << 30)
+    got = htn.plan_text(net.inds(), net.dims(), net.output, **kw)
+    assert got == _ref_text(net.inds(), net.dims(), net.output, **kw)
+    assert "search candidates=12" in got
+    # never worse than the greedy plan under the same options
+    kw0 = {k: v for k, v in kw.items() if k != "n_candidates"}
+    g = htn.plan_text(net.inds(), net.dims(), net.output, **kw0)
+    tot = lambda t: int(t.split("flops_total=")[1].split()[0])  # noqa: E731
+    assert tot(got) <= tot(g)
