@@ -208,6 +208,108 @@ int64_t gmax(const GModes& t, int j) {
   return m;
 }
 
+// Dot layout of a fast two-operand gather with a long loop (see GatherArgs):
+// the tile takes, for each operand, its loop modes in rising stride order
+// while they stay contiguous and until its run reaches 32 entries; a
+// unit-stride mode too long for the tile is split at a divisor first.
+bool dot_setup(GatherArgs& g, int sm) {
+  GModes L = g.loop;
+  for (int j = 0; j < 2; ++j)
+    for (int m = 0; m < L.n; ++m) {
+      if (L.stride[m][j] != 1 || L.dim[m] <= 256 || L.n >= kMaxModes) continue;
+      uint32_t d2 = 0;
+      for (uint32_t d = 256; d >= 16 && !d2; --d)
+        if (L.dim[m] % d == 0) d2 = d;
+      if (!d2) continue;
+      for (int k = L.n; k > m + 1; --k) {
+        L.dim[k] = L.dim[k - 1];
+        for (int q = 0; q < kMaxOps; ++q) L.stride[k][q] = L.stride[k - 1][q];
+      }
+      L.n++;
+      L.dim[m + 1] = d2;
+      for (int q = 0; q < kMaxOps; ++q) L.stride[m + 1][q] = L.stride[m][q];
+      L.dim[m] /= d2;
+      for (int q = 0; q < kMaxOps; ++q) L.stride[m][q] *= d2;
+    }
+  std::vector<int> in_tile(L.n, 0);
+  uint64_t T = 1;
+  for (int j = 0; j < 2; ++j) {
+    std::vector<int> ord;
+    for (int m = 0; m < L.n; ++m)
+      if (L.stride[m][j] > 0) ord.push_back(m);
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return L.stride[a][j] < L.stride[b][j]; });
+    int64_t run = 1;
+    for (int m : ord) {
+      if (L.stride[m][j] != run || run >= 32) break;
+      if (!in_tile[m]) {
+        if (T * L.dim[m] > kDotMaxTile) break;
+        T *= L.dim[m];
+        in_tile[m] = 1;
+      }
+      run *= L.dim[m];
+    }
+  }
+  // widen the tile (fewer block barriers per entry): the remaining modes in
+  // rising operand-1 stride order while the tile stays within bounds
+  {
+    std::vector<int> ord;
+    for (int m = 0; m < L.n; ++m)
+      if (!in_tile[m]) ord.push_back(m);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return L.stride[a][1] < L.stride[b][1]; });
+    for (int m : ord) {
+      if (T >= 1024) break;
+      if (T * L.dim[m] > kDotMaxTile) continue;
+      T *= L.dim[m];
+      in_tile[m] = 1;
+    }
+  }
+  if (T < 32) return false;
+  std::vector<int> tile;
+  for (int m = 0; m < L.n; ++m)
+    if (in_tile[m]) tile.push_back(m);
+  // slot order: operand 1's strides, outermost first
+  std::vector<int> so = tile;
+  std::stable_sort(so.begin(), so.end(), [&](int a, int b) { return L.stride[a][1] > L.stride[b][1]; });
+  std::map<int, int64_t> slot;
+  int64_t acc = 1;
+  for (int k = (int)so.size() - 1; k >= 0; --k) {
+    slot[so[k]] = acc;
+    acc *= L.dim[so[k]];
+  }
+  GModes tx, ty, outer;
+  for (int m : so) {
+    ty.dim[ty.n] = L.dim[m];
+    for (int q = 0; q < kMaxOps; ++q) ty.stride[ty.n][q] = q == 0 ? L.stride[m][1] : 0;
+    ty.div[ty.n] = make_fastdiv(L.dim[m]);
+    ty.n++;
+  }
+  std::vector<int> xo = tile;
+  std::stable_sort(xo.begin(), xo.end(), [&](int a, int b) { return L.stride[a][0] > L.stride[b][0]; });
+  for (int m : xo) {
+    tx.dim[tx.n] = L.dim[m];
+    for (int q = 0; q < kMaxOps; ++q) tx.stride[tx.n][q] = q == 0 ? L.stride[m][0] : (q == 1 ? slot[m] : 0);
+    tx.div[tx.n] = make_fastdiv(L.dim[m]);
+    tx.n++;
+  }
+  for (int m = 0; m < L.n; ++m) {
+    if (in_tile[m]) continue;
+    outer.dim[outer.n] = L.dim[m];
+    for (int q = 0; q < kMaxOps; ++q) outer.stride[outer.n][q] = L.stride[m][q];
+    outer.n++;
+  }
+  gmerge(outer, 2);
+  if (gmax(tx, 0) >= 0x7FFFFFFF || gmax(ty, 0) >= 0x7FFFFFFF || gsize(outer) > 0xFFFFFFFFull) return false;
+  g.n_outer = (uint32_t)gsize(outer);
+  g.loop = outer;
+  g.kmodes = tx;
+  g.wmodes = ty;
+  g.tile_n = (uint32_t)T;
+  uint32_t c = (uint32_t)((sm * 8 + g.n_out - 1) / g.n_out);
+  g.chunks = std::max<uint32_t>(1, std::min<uint32_t>(c, g.n_outer));
+  g.dot = 1;
+  return true;
+}
+
 // a tensor during lowering: either stored (one operand: itself) or virtual
 struct Repr {
   std::vector<int> ops;  // stored tensor ids whose product forms the tensor
@@ -397,6 +499,16 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     for (int j = 0; j < (int)small.size(); ++j)
       if (gmax(g.wmodes, j) + slice_max[small[j]] >= extent[small[j]]) return false;
     if (wsz && gmax(g.out, nb) + gmax(g.loop, nb) + gmax(g.kmodes, nb) >= wsz) return false;
+    // a long sum over few outputs: the tiled dot kernel, else the generic
+    // path's block reduction
+    if (g.mode == GW_DENSE_PAIR || g.mode == GW_DENSE_F64) {
+      const int64_t nl_ = (int64_t)gsize(g.loop), no_ = (int64_t)gsize(g.out);
+      if (nl_ >= 1024 && no_ <= (int64_t)ex->sm_count * 16) {
+        g.n_out = (uint32_t)no_;
+        g.n_loop = (uint32_t)nl_;
+        if (nb != 2 || wsz || !dot_setup(g, ex->sm_count)) return false;
+      }
+    }
     L->gf = g;
     L->has_fast = true;
     return true;
@@ -543,6 +655,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     const bool last = s + 1 == plan.steps.size();
     const Inds batch = nsl(ps.batch), m = nsl(ps.m), n = nsl(ps.n), k = nsl(ps.k), sa = nsl(ps.sa),
                sb = nsl(ps.sb);
+    const Inds &m_plan = m, &n_plan = n, &k_plan = k;
     Inds out_inds = batch;
     out_inds.insert(out_inds.end(), m.begin(), m.end());
     out_inds.insert(out_inds.end(), n.begin(), n.end());
@@ -619,10 +732,30 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     const double lim = 2147483647.0;
     const bool swap = nm < 64 && nn >= 64;
     const double gM = swap ? nn : nm, gN = swap ? nm : nn;
-    const bool tc = sa.empty() && sb.empty() && gM >= 64 && gN >= 32 && nk >= 32 &&
+    const bool tc = sa.empty() && sb.empty() && gM >= 64 && gN >= 16 && nk >= 8 &&
                     nb * nm * nn * nk >= (double)(1 << 22) && nb < lim && nm < lim && nn < lim && nk < lim &&
                     nb * std::ceil(gM / 128.0) * std::ceil(gN / (double)gemm_block_n()) < lim;
     if (tc) {
+      // Mode order inside each split operand is free (K only has to agree
+      // between the two): rows follow their operand's source strides, and K
+      // follows the larger operand's, so its split reads and writes run
+      // along the same unit-stride direction.
+      auto rep_stride = [&](const Repr& r, int64_t i) {
+        int64_t best = 0;
+        double bsz = -1;
+        for (int o : r.ops) {
+          const double sz = prod(live_inds[o]);
+          if (sz > bsz && sof(o, i)) best = sof(o, i), bsz = sz;
+        }
+        return best;
+      };
+      auto by_stride = [&](Inds v, const Repr& r) {
+        std::stable_sort(v.begin(), v.end(),
+                         [&](int64_t a, int64_t b) { return rep_stride(r, a) > rep_stride(r, b); });
+        return v;
+      };
+      const double szX = prod(live_inds[ps.x]), szY = prod(live_inds[ps.y]);
+      const Inds m = by_stride(m_plan, X), n = by_stride(n_plan, Y), k = by_stride(k_plan, szX >= szY ? X : Y);
       Inds rowsX = batch, rowsY = batch;
       rowsX.insert(rowsX.end(), m.begin(), m.end());
       rowsY.insert(rowsY.end(), n.begin(), n.end());
@@ -671,9 +804,13 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     Inds extra = k;
     extra.insert(extra.end(), sa.begin(), sa.end());
     extra.insert(extra.end(), sb.begin(), sb.end());
-    // a virtual operand with too many factors is materialised first
+    // a virtual operand is materialised first when it has too many factors
+    // for one gather, or when this step would recompute each of its entries
+    // many times (every output reads it over the whole loop)
     for (Repr* r : {&X, &Y}) {
-      if (r->virt && (int)(X.ops.size() + Y.ops.size()) > kMaxOps) {
+      const double vsize = r->virt ? prod(live_inds[r == &X ? ps.x : ps.y]) : 1.0;
+      const double reuse = r->virt ? (nb * nm * nn) * prod(extra) / vsize : 0.0;
+      if (r->virt && ((int)(X.ops.size() + Y.ops.size()) > kMaxOps || reuse > 4.0)) {
         const int tid = next_tmp++;
         const Inds vin = live_inds[r == &X ? ps.x : ps.y];
         Launch L;
@@ -867,7 +1004,8 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
   };
   if (!dalloc((void**)&ex->arena, ex->arena_bytes) || !dalloc((void**)&ex->splitbuf, ex->split_bytes) ||
       !dalloc((void**)&ex->partial, (size_t)ex->n_slices * std::max<int64_t>(ex->final_size, 1) * 8) ||
-      !dalloc((void**)&ex->status, 16) || !dalloc((void**)&ex->out_stage, (size_t)R.g.n_out * 8 + 8)) {
+      !dalloc((void**)&ex->status, 16) || !dalloc((void**)&ex->out_stage, (size_t)R.g.n_out * 8 + 8) ||
+      !dalloc((void**)&ex->dot_scratch, dot_scratch_entries(ex->sm_count) * sizeof(float2))) {
     exec_free(ex);
     return fail(QTPU_ENOMEM, "device workspace allocation failed");
   }
@@ -975,11 +1113,24 @@ std::string exec_describe(const Executor* ex) {
       const GatherArgs& g = L.has_fast ? L.gf : L.g;
       o << (L.has_fast ? "fast" : "generic") << " ops=" << g.nops;
       if (L.has_fast) o << " big=" << g.nbig << " w=" << g.w_size << " fan=" << g.fan_f;
+      if (L.has_fast && g.dot) o << " dot tile=" << g.tile_n << " outer=" << g.n_outer << " chunks=" << g.chunks;
       if (g.mode >= GW_SPLIT_BF16X3)
         o << " rows=" << g.n_rows << " K=" << g.K;
       else
         o << " out=" << g.n_out;
       o << " loop=" << g.n_loop;
+      // per mode: dim:stride of each operand (0 = operand does not carry it)
+      auto modes = [&](const char* name, const GModes& t) {
+        o << " " << name << "=";
+        for (int m = 0; m < t.n; ++m) {
+          o << (m ? "," : "") << t.dim[m];
+          for (int j = 0; j < g.nops && j < kMaxOps; ++j) o << (j ? "/" : ":") << t.stride[m][j];
+        }
+        if (!t.n) o << "-";
+      };
+      modes("om", g.out);
+      if (g.mode >= GW_SPLIT_BF16X3) modes("km", g.kmodes);
+      modes("lm", g.loop);
     }
     o << " src=";
     for (int j = 0; j < L.nsrc; ++j) o << (j ? "," : "") << L.src[j];
@@ -1047,6 +1198,7 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
       if (L.has_fast && !from_partial) {
         GatherArgs g = L.gf;
         for (int j = 0; j < g.nops; ++j) g.ptr[j] = src_ptr(L.gf_src[j]);
+        g.scratch = ex->dot_scratch;
         cudaError_t e = launch_gather_fast(g, dst_ptr(L.dst, s), ex->sm_count, st);
         if (e != cudaErrorNotSupported) return e;
         cudaGetLastError();
@@ -1203,6 +1355,8 @@ void exec_free(Executor* ex) {
   if (ex->partial) cudaFree(ex->partial);
   if (ex->status) cudaFree(ex->status);
   if (ex->out_stage) cudaFree(ex->out_stage);
+  if (ex->dot_scratch) cudaFree(ex->dot_scratch);
+  ex->dot_scratch = nullptr;
   ex->arena = ex->splitbuf = ex->partial = nullptr;
   ex->status = nullptr;
   ex->out_stage = nullptr;

@@ -83,6 +83,7 @@ struct Executor {
   uint8_t* partial = nullptr;
   uint32_t* status = nullptr;
   double* out_stage = nullptr;   // staging buffer of the host-buffer entry point
+  float2* dot_scratch = nullptr; // per-chunk sums of the dot-reduction kernel
   int n_tc_steps = 0;
   int n_fused_steps = 0;         // absorption steps folded into a consumer
   int64_t launches_per_contract = 0;

@@ -83,28 +83,28 @@ struct GatherArgs {
   int fan_f = 1;
   uint32_t w_size = 0;   // entries of W (0 = no small operands)
   GModes wmodes;
+  // fast dot path (two large operands, no W, a long sum over few outputs):
+  // the loop splits into a tile of `tile_n` entries over the modes nearest
+  // unit stride in either operand, and the outer modes left in `loop`.  The
+  // tile's modes sit in `kmodes` in operand-0 stride order (stride 0: operand
+  // 0, stride 1: slot in the tile) and in `wmodes` in slot order (stride 0:
+  // operand 1).  Each block adds `chunks`-th of one output's tiles into
+  // `scratch`, and a second kernel adds the chunks of every output.
+  int dot = 0;
+  uint32_t tile_n = 0, n_outer = 0, chunks = 0;
+  float2* scratch = nullptr;
 };
+constexpr uint32_t kDotMaxTile = 2048;
+// scratch entries a dot launch may use (float2)
+inline size_t dot_scratch_entries(int sm_count) { return (size_t)sm_count * 24; }
 cudaError_t launch_gather(const GatherArgs& a, void* out, int sm_count, cudaStream_t st);
 // The same computation through the typed fast kernels (shared-memory table of
 // the small factors); cudaErrorNotSupported when no instantiation fits.
-constexpr uint32_t kMaxW = 1024;
+constexpr uint32_t kMaxW = 4096;
 cudaError_t launch_gather_fast(const GatherArgs& a, void* out, int sm_count, cudaStream_t st);
 
 cudaError_t launch_contract(const void* A, int dtA, const void* B, int dtB, double* out,
                             const ContractArgs& a, int sm_count, cudaStream_t st);
-
-// Tensor-core operand preparation: gather an operand into [rows][Kp] (row =
-// flattened batch and M (or N) modes, K modes innermost) and split every
-// FP64 value into `pieces` low-precision pieces stored piece-major:
-// dst[p][row][k].  kind 0: BF16 pieces (3); kind 1: TF32 pieces (1 or 2).
-struct SplitArgs {
-  ModeTab row, k;  // sa = source strides
-  int64_t n_rows = 0, K = 0, Kp = 0;
-  int pieces = 3;
-  int kind = 0;
-};
-cudaError_t launch_split(const void* src, int dt, void* dst, const SplitArgs& a, int sm_count,
-                         cudaStream_t st);
 
 // prec: 1 = TF32 (1 piece, 1 product), 2 = 3xTF32 (2 pieces, 3 products),
 //       3 = BF16x3 (3 pieces, 6 products)

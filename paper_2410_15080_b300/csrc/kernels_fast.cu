@@ -138,7 +138,7 @@ __device__ __forceinline__ void entry_fan(const GatherArgs& a, const float2* W, 
 template <int NB, int DT0, int DT1, bool HW, bool F64OUT>
 __global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __restrict__ out) {
   using O = Op<NB, DT0, DT1, HW>;
-  __shared__ float2 W[HW ? kMaxW : 1];
+  extern __shared__ float2 W[];  // w_size entries (dynamic shared memory)
   if (HW) {
     build_w(a, W);
     __syncthreads();
@@ -155,6 +155,121 @@ __global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __
   }
 }
 
+// ------------------------------------------------------------ dot reduction
+// value(o) = sum over the loop of X0 * X1 for few outputs and a long loop.
+// Block (c, o) walks its range of outer tuples; per tuple it stages the
+// operand-0 tile in shared memory in operand 1's order (both global reads
+// run along each operand's own unit stride), then multiplies it with the
+// operand-1 tile read straight from global memory.
+__host__ __device__ __forceinline__ uint32_t dot_slot(uint32_t u) { return u + (u >> 4); }  // padded: fewer bank conflicts
+
+template <int DT0, int DT1>
+__global__ void __launch_bounds__(256) k_dot_fast(const GatherArgs a) {
+  constexpr int PER = kDotMaxTile / 256;
+  extern __shared__ float2 dsm[];
+  const uint32_t T = a.tile_n;
+  float2* sX = dsm;                                                   // T + T/16 slots
+  int2* tx = reinterpret_cast<int2*>(dsm + dot_slot(T) + 1);          // v -> (slot, op-0 offset)
+  int* ty = reinterpret_cast<int*>(tx + T);                           // slot -> op-1 offset
+  for (uint32_t v = threadIdx.x; v < T; v += blockDim.x) {
+    int64_t off[2];
+    offsets<2>(v, a.kmodes, off);
+    tx[v] = make_int2((int)dot_slot((uint32_t)off[1]), (int)off[0]);
+    int64_t yo[1];
+    offsets<1>(v, a.wmodes, yo);
+    ty[v] = (int)yo[0];
+  }
+  __syncthreads();
+  const uint32_t o = blockIdx.y;
+  int64_t base[2];
+  offsets<2>(o, a.out, base);
+  const uint32_t per = (a.n_outer + a.chunks - 1) / a.chunks;
+  const uint32_t t0 = blockIdx.x * per;
+  const uint32_t t1 = min(a.n_outer, t0 + per);
+  const void* X = a.ptr[0];
+  const void* Y = a.ptr[1];
+  Acc acc;
+  for (uint32_t t = t0; t < t1; ++t) {
+    int64_t ot[2];
+    offsets<2>(t, a.loop, ot);
+    const int64_t xb = base[0] + ot[0], yb = base[1] + ot[1];
+    float2 xv[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const uint32_t v = threadIdx.x + k * 256;
+      if (v < T) xv[k] = load_pair<DT0>(X, xb + tx[v].y);
+    }
+    __syncthreads();  // the previous tuple's tile is consumed
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const uint32_t v = threadIdx.x + k * 256;
+      if (v < T) sX[tx[v].x] = xv[k];
+    }
+    __syncthreads();
+    float2 yv[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const uint32_t u = threadIdx.x + k * 256;
+      if (u < T) yv[k] = load_pair<DT1>(Y, yb + ty[u]);
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const uint32_t u = threadIdx.x + k * 256;
+      if (u < T) acc.add(mul_pair(sX[dot_slot(u)], yv[k]));
+    }
+  }
+  // block sum (compensated) -> scratch[o][c]
+  __shared__ float2 red[8];
+  float2 v = acc.get();
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    Acc t;
+    t.hi = v.x;
+    t.lo = v.y;
+    t.add(make_float2(__shfl_xor_sync(0xffffffffu, v.x, s), __shfl_xor_sync(0xffffffffu, v.y, s)));
+    v = t.get();
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Acc t;
+    for (int w = 0; w < 8; ++w) t.add(red[w]);
+    a.scratch[(size_t)o * a.chunks + blockIdx.x] = t.get();
+  }
+}
+
+template <bool F64OUT>
+__global__ void __launch_bounds__(256) k_dot_finish(const float2* __restrict__ part, uint32_t n_out,
+                                                    uint32_t chunks, void* __restrict__ out) {
+  for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < n_out; o += gridDim.x * blockDim.x) {
+    Acc acc;
+    for (uint32_t c = 0; c < chunks; ++c) acc.add(part[(size_t)o * chunks + c]);
+    const float2 r = acc.get();
+    if (F64OUT)
+      ((double*)out)[o] = (double)r.x + (double)r.y;
+    else
+      ((float2*)out)[o] = r;
+  }
+}
+
+size_t dot_smem_bytes(uint32_t T) { return (dot_slot(T) + 1) * sizeof(float2) + T * (sizeof(int2) + sizeof(int)); }
+
+template <int DT0, int DT1>
+cudaError_t dot_launch(const GatherArgs& a, void* out, cudaStream_t st) {
+  const size_t sm_bytes = dot_smem_bytes(a.tile_n);
+  cudaError_t e = cudaSuccess;
+  if (sm_bytes > 40960)
+    e = cudaFuncSetAttribute(k_dot_fast<DT0, DT1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_bytes);
+  if (e != cudaSuccess) return e;
+  k_dot_fast<DT0, DT1><<<dim3(a.chunks, a.n_out), 256, sm_bytes, st>>>(a);
+  const uint32_t g = (a.n_out + 255) / 256;
+  if (a.mode == GW_DENSE_F64)
+    k_dot_finish<true><<<g, 256, 0, st>>>(a.scratch, a.n_out, a.chunks, out);
+  else
+    k_dot_finish<false><<<g, 256, 0, st>>>(a.scratch, a.n_out, a.chunks, out);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ split output
 constexpr int kTR = 32, kTK = 64;
 
@@ -162,7 +277,7 @@ template <int DT0, bool HW, int KIND, int NP, int F>
 __global__ void __launch_bounds__(256) k_split_fast(const GatherArgs a, void* __restrict__ dst) {
   using O = Op<1, DT0, DT0, HW>;
   constexpr int NOPS = O::NOPS;
-  __shared__ float2 W[HW ? kMaxW : 1];
+  extern __shared__ float2 W[];  // w_size entries (dynamic shared memory)
   __shared__ int64_t rowoff[kTR][NOPS];
   __shared__ int64_t koff[kTK][NOPS];
   __shared__ float2 tile[kTR][kTK + 1];
@@ -256,24 +371,34 @@ __global__ void __launch_bounds__(256) k_split_fast(const GatherArgs a, void* __
     {
       const int r = tid >> 3, kk = (tid & 7) * 8;
       const uint32_t row = r0 + r, kb = k0 + kk;
-      if (row < a.n_rows && kb < a.Kp) {
-        const int64_t base = (int64_t)row * a.Kp + kb;
-        if (KIND == 0) {
+      const bool in = row < a.n_rows && kb < a.Kp;
+      if (KIND == 0) {
+        // BF16 pieces on the grid of this row's 64-entry k-block (the 8
+        // threads of a row are 8 consecutive lanes)
+        float m = 0.f;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) m = fmaxf(m, fabsf(tile[r][kk + e].x));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+        const int E = grid_exp(m);
+        if (in) {
+          const int64_t base = (int64_t)row * a.Kp + kb;
           __nv_bfloat16 h[3][8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
-            const float2 v = tile[r][kk + e];
-            const __nv_bfloat16 p0 = __float2bfloat16_rn(v.x);
-            const float r1 = __fadd_rn(__fsub_rn(v.x, __bfloat162float(p0)), v.y);
-            const __nv_bfloat16 p1 = __float2bfloat16_rn(r1);
-            h[0][e] = p0;
-            h[1][e] = p1;
-            h[2][e] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(p1)));
+            float pc[3];
+            grid_pieces(tile[r][kk + e], E, pc);
+#pragma unroll
+            for (int p = 0; p < 3; ++p) h[p][e] = __float2bfloat16_rn(pc[p]);  // exact
           }
           __nv_bfloat16* d = (__nv_bfloat16*)dst;
 #pragma unroll
           for (int p = 0; p < 3; ++p) *(uint4*)(d + p * piece + base) = *(const uint4*)h[p];
-        } else {
+        }
+      } else if (in) {
+        const int64_t base = (int64_t)row * a.Kp + kb;
+        {
           float f[NP][8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
@@ -295,15 +420,27 @@ __global__ void __launch_bounds__(256) k_split_fast(const GatherArgs a, void* __
   }
 }
 
+// dynamic shared memory above the 48 KB default needs a one-time opt-in
+template <typename K>
+cudaError_t allow_smem(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kMaxW * sizeof(float2)));
+}
+
 template <int DT0, bool HW, int F>
 cudaError_t split_f(const GatherArgs& a, void* out, int g, cudaStream_t st) {
-  if (a.mode == GW_SPLIT_BF16X3)
-    k_split_fast<DT0, HW, 0, 3, F><<<g, 256, 0, st>>>(a, out);
-  else if (a.mode == GW_SPLIT_TF32X2)
-    k_split_fast<DT0, HW, 1, 2, F><<<g, 256, 0, st>>>(a, out);
-  else
-    k_split_fast<DT0, HW, 1, 1, F><<<g, 256, 0, st>>>(a, out);
-  return cudaGetLastError();
+  const size_t sm_bytes = HW ? a.w_size * sizeof(float2) : 0;
+  cudaError_t e = cudaSuccess;
+  if (a.mode == GW_SPLIT_BF16X3) {
+    if (sm_bytes > 16384) e = allow_smem(k_split_fast<DT0, HW, 0, 3, F>);
+    if (e == cudaSuccess) k_split_fast<DT0, HW, 0, 3, F><<<g, 256, sm_bytes, st>>>(a, out);
+  } else if (a.mode == GW_SPLIT_TF32X2) {
+    if (sm_bytes > 16384) e = allow_smem(k_split_fast<DT0, HW, 1, 2, F>);
+    if (e == cudaSuccess) k_split_fast<DT0, HW, 1, 2, F><<<g, 256, sm_bytes, st>>>(a, out);
+  } else {
+    if (sm_bytes > 16384) e = allow_smem(k_split_fast<DT0, HW, 1, 1, F>);
+    if (e == cudaSuccess) k_split_fast<DT0, HW, 1, 1, F><<<g, 256, sm_bytes, st>>>(a, out);
+  }
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 template <int DT0, bool HW>
@@ -323,11 +460,16 @@ cudaError_t dense_dt(const GatherArgs& a, void* out, int sm, cudaStream_t st) {
   if (a.n_out == 0) return cudaSuccess;
   int64_t g = ((int64_t)a.n_out + 255) / 256;
   if (g > (int64_t)sm * 8) g = (int64_t)sm * 8;
-  if (a.mode == GW_DENSE_F64)
-    k_dense_fast<NB, DT0, DT1, HW, true><<<(int)g, 256, 0, st>>>(a, out);
-  else
-    k_dense_fast<NB, DT0, DT1, HW, false><<<(int)g, 256, 0, st>>>(a, out);
-  return cudaGetLastError();
+  const size_t sm_bytes = HW ? a.w_size * sizeof(float2) : 0;
+  cudaError_t e = cudaSuccess;
+  if (a.mode == GW_DENSE_F64) {
+    if (sm_bytes > 40960) e = allow_smem(k_dense_fast<NB, DT0, DT1, HW, true>);
+    if (e == cudaSuccess) k_dense_fast<NB, DT0, DT1, HW, true><<<(int)g, 256, sm_bytes, st>>>(a, out);
+  } else {
+    if (sm_bytes > 40960) e = allow_smem(k_dense_fast<NB, DT0, DT1, HW, false>);
+    if (e == cudaSuccess) k_dense_fast<NB, DT0, DT1, HW, false><<<(int)g, 256, sm_bytes, st>>>(a, out);
+  }
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 template <int NB, int DT0, int DT1>
@@ -349,6 +491,14 @@ cudaError_t launch_gather_fast(const GatherArgs& a, void* out, int sm, cudaStrea
     if (a.dt[0] == DT_F64)
       return a.w_size ? split_dt<DT_F64, true>(a, out, sm, st) : split_dt<DT_F64, false>(a, out, sm, st);
     return a.w_size ? split_dt<DT_F32X2, true>(a, out, sm, st) : split_dt<DT_F32X2, false>(a, out, sm, st);
+  }
+  if (a.dot) {
+    if (a.nbig != 2 || a.w_size || a.tile_n == 0 || a.tile_n > kDotMaxTile || a.chunks == 0 || a.n_out > 65535 ||
+        (size_t)a.n_out * a.chunks > dot_scratch_entries(sm) || !a.scratch)
+      return cudaErrorNotSupported;
+    if (a.dt[0] == DT_F64)
+      return a.dt[1] == DT_F64 ? dot_launch<DT_F64, DT_F64>(a, out, st) : dot_launch<DT_F64, DT_F32X2>(a, out, st);
+    return a.dt[1] == DT_F64 ? dot_launch<DT_F32X2, DT_F64>(a, out, st) : dot_launch<DT_F32X2, DT_F32X2>(a, out, st);
   }
   // long sums over few outputs go to the block-reduction kernel of the generic path
   if (a.n_loop >= 1024 && a.n_out <= (uint32_t)sm * 16) return cudaErrorNotSupported;

@@ -187,26 +187,34 @@ __global__ void __launch_bounds__(256) k_gather_split(const GatherArgs a, void* 
     {
       const int r = tid >> 3, kk = (tid & 7) * 8;
       const uint32_t row = r0 + r, kb = k0 + kk;
-      if (row < a.n_rows && kb < a.Kp) {
-        const int64_t base = (int64_t)row * a.Kp + kb;
-        if (KIND == 0) {
-          // BF16 pieces of hi + lo: p0 = bf16(hi), p1 = bf16((hi - p0) + lo),
-          // p2 = bf16(remainder); |x - p0 - p1 - p2| <~ 2^-26 |x|
+      const bool in = row < a.n_rows && kb < a.Kp;
+      if (KIND == 0) {
+        // BF16 pieces on the grid of this row's 64-entry k-block (the 8
+        // threads of a row are 8 consecutive lanes)
+        float m = 0.f;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) m = fmaxf(m, fabsf(tile[r][kk + e].x));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+        const int E = grid_exp(m);
+        if (in) {
+          const int64_t base = (int64_t)row * a.Kp + kb;
           __nv_bfloat16 h[3][8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
-            const float2 v = tile[r][kk + e];
-            const __nv_bfloat16 p0 = __float2bfloat16_rn(v.x);
-            const float r1 = __fadd_rn(__fsub_rn(v.x, __bfloat162float(p0)), v.y);
-            const __nv_bfloat16 p1 = __float2bfloat16_rn(r1);
-            h[0][e] = p0;
-            h[1][e] = p1;
-            h[2][e] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(p1)));
+            float pc[3];
+            grid_pieces(tile[r][kk + e], E, pc);
+#pragma unroll
+            for (int p = 0; p < 3; ++p) h[p][e] = __float2bfloat16_rn(pc[p]);  // exact
           }
           __nv_bfloat16* d = (__nv_bfloat16*)dst;
 #pragma unroll
           for (int p = 0; p < 3; ++p) *(uint4*)(d + p * piece + base) = *(const uint4*)h[p];
-        } else {
+        }
+      } else if (in) {
+        const int64_t base = (int64_t)row * a.Kp + kb;
+        {
           float f[NP][8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) {

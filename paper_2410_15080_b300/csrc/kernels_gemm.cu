@@ -11,9 +11,13 @@
 // FP32 accumulation loses precision with every MMA added into an accumulator
 // (measured: the error grows linearly with K), so (1) the leading product
 // x0*y0 has its own accumulator X and the smaller cross terms share Y, and
-// (2) both are drained every k-block (BF16x3: 64 K) and accumulated with
-// compensated (TwoSum) FP32 arithmetic in the epilogue's registers; FP64 math
-// is avoided in the drain (FP64 throughput on B300 is ~1/64 of FP32).
+// (2) both are drained every few k-blocks and accumulated with compensated
+// (TwoSum) FP32 arithmetic in the epilogue's registers; FP64 math is avoided
+// in the drain (FP64 throughput on B300 is ~1/64 of FP32).  BF16x3 pieces
+// are cut on a grid shared by each operand row's 64-entry k-block (see
+// grid_pieces), which makes every k-block's sum of leading products exact in
+// X; between drains (4 k-blocks) X rounds only where neighbouring blocks'
+// grids differ.
 //
 // One CTA per SM, persistent over (batch, m-tile, n-tile) tiles:
 //   warp 0      TMA producer (one lane): pieces of A and B for one k-block

@@ -10,9 +10,6 @@
 //    final reduction to the output indices.  Everything accumulates in FP64
 //    in a fixed order, so results are deterministic.  HBM-bound: each output
 //    is written once and operand runs are read along the innermost mode.
-//  * k_split: gathers one GEMM operand into [rows][Kp] (K innermost) and
-//    splits each FP64 value into BF16 or TF32 pieces for the tensor cores.
-#include <cuda_bf16.h>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -139,114 +136,6 @@ cudaError_t launch3(const void* A, const void* B, double* out, const ContractArg
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ split
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-template <typename T, int KIND, int NP>
-__global__ void __launch_bounds__(256) k_split(const T* __restrict__ src, void* __restrict__ dst,
-                                               const SplitArgs a) {
-  const int64_t kv = a.Kp / 8;  // 8-element vectors per row
-  const int64_t total = a.n_rows * kv;
-  const int64_t piece = a.n_rows * a.Kp;  // elements per piece plane
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += stride) {
-    const int64_t row = w / kv;
-    const int64_t k0 = (w - row * kv) * 8;
-    int64_t ro, unused;
-    decompose(row, a.row, ro, unused);
-    double x[8];
-    // k offsets: decompose k0 once, then step an odometer
-    int64_t idx[kMaxModes];
-    int64_t off = 0;
-    {
-      int64_t r = k0 < a.K ? k0 : 0;
-      for (int j = a.k.n - 1; j >= 0; --j) {
-        const int64_t q = r / a.k.dim[j];
-        idx[j] = r - q * a.k.dim[j];
-        r = q;
-        off += idx[j] * a.k.sa[j];
-      }
-    }
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int64_t k = k0 + e;
-      if (k < a.K) {
-        x[e] = ld(src, ro + off);
-        int j = a.k.n - 1;
-        if (j >= 0) {
-          ++idx[j];
-          off += a.k.sa[j];
-          while (j > 0 && idx[j] == a.k.dim[j]) {
-            off -= a.k.dim[j] * a.k.sa[j];
-            idx[j] = 0;
-            --j;
-            ++idx[j];
-            off += a.k.sa[j];
-          }
-        }
-      } else {
-        x[e] = 0.0;
-      }
-    }
-    const int64_t base = row * a.Kp + k0;
-    if (KIND == 0) {
-      // BF16 pieces: x = h0 + h1 + h2 (+ a remainder below 2^-24 |x|)
-      __nv_bfloat16 h[NP][8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        double r = x[e];
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-          h[p][e] = __double2bfloat16(r);
-          r -= (double)__bfloat162float(h[p][e]);
-        }
-      }
-      __nv_bfloat16* d = (__nv_bfloat16*)dst;
-#pragma unroll
-      for (int p = 0; p < NP; ++p) *(uint4*)(d + p * piece + base) = *(const uint4*)h[p];
-    } else {
-      // TF32 pieces stored as FP32 words with the low 13 mantissa bits zero
-      float f[NP][8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        double r = x[e];
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-          f[p][e] = tf32_rna((float)r);
-          r -= (double)f[p][e];
-        }
-      }
-      float* d = (float*)dst;
-#pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        *(float4*)(d + p * piece + base) = *(const float4*)&f[p][0];
-        *(float4*)(d + p * piece + base + 4) = *(const float4*)&f[p][4];
-      }
-    }
-  }
-}
-
-template <typename T>
-cudaError_t launch_split_t(const void* src, void* dst, const SplitArgs& a, int sm, cudaStream_t st) {
-  const int64_t total = a.n_rows * (a.Kp / 8);
-  if (total <= 0) return cudaSuccess;
-  int64_t g = (total + 255) / 256;
-  if (g > (int64_t)sm * 32) g = (int64_t)sm * 32;
-  if (a.kind == 0 && a.pieces == 3)
-    k_split<T, 0, 3><<<(int)g, 256, 0, st>>>((const T*)src, dst, a);
-  else if (a.kind == 1 && a.pieces == 1)
-    k_split<T, 1, 1><<<(int)g, 256, 0, st>>>((const T*)src, dst, a);
-  else if (a.kind == 1 && a.pieces == 2)
-    k_split<T, 1, 2><<<(int)g, 256, 0, st>>>((const T*)src, dst, a);
-  else
-    return cudaErrorInvalidValue;
-  return cudaGetLastError();
-}
-
 }  // namespace
 
 cudaError_t launch_contract(const void* A, int dtA, const void* B, int dtB, double* out, const ContractArgs& a,
@@ -261,8 +150,5 @@ cudaError_t launch_contract(const void* A, int dtA, const void* B, int dtB, doub
   return launch3<float, float, true>(A, B, out, a, sm, st);
 }
 
-cudaError_t launch_split(const void* src, int dt, void* dst, const SplitArgs& a, int sm, cudaStream_t st) {
-  return dt == DT_F64 ? launch_split_t<double>(src, dst, a, sm, st) : launch_split_t<float>(src, dst, a, sm, st);
-}
 
 }  // namespace qtpu

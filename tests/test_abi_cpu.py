@@ -161,3 +161,17 @@ def test_best_of_candidates_planner_bit_exact(net_id):
     g = htn.plan_text(net.inds(), net.dims(), net.output, **kw0)
     tot = lambda t: int(t.split("flops_total=")[1].split()[0])  # noqa: E731
     assert tot(got) <= tot(g)
+
+
+def test_long_sum_over_few_outputs_lowers_to_the_tiled_dot():
+    """A batched dot whose operands run along different unit-stride indices is
+    tiled over both (36 x 40 entries here), one block range per output."""
+    import synth
+    from paper_2410_15080_b300.htn import lowering_text
+    rng = np.random.default_rng(0)
+    A = rng.uniform(-1, 1, (5, 36, 6, 40))
+    B = rng.uniform(-1, 1, (5, 40, 6, 36))
+    net = synth.HTN([synth.Tensor("QT", (0, 1, 2, 3), A), synth.Tensor("QT", (0, 3, 2, 1), B)], (0,))
+    t = lowering_text(net.inds(), net.dims(), net.output)
+    line = [l for l in t.splitlines() if l.startswith("launch 0")][0]
+    assert " dot tile=1440 outer=6 " in line

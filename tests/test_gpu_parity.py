@@ -56,7 +56,7 @@ def test_single_tensor_and_disconnected():
 
 
 GEMM_SHAPES = [(1, 128, 128, 128), (3, 300, 200, 333), (2, 64, 32, 32), (5, 144, 144, 144),
-               (1, 513, 257, 1000), (7, 96, 40, 72)]
+               (1, 513, 257, 1000), (7, 96, 40, 72), (4, 512, 512, 24), (2, 640, 384, 12), (9, 200, 20, 8)]
 
 
 @pytest.mark.parametrize("shape", GEMM_SHAPES, ids=[str(s) for s in GEMM_SHAPES])
@@ -230,3 +230,47 @@ def test_100q_full_size_slicing_invariance():
     a, sa = contract_gpu(net, prec="bf16x3", max_intermediate_bytes=8 << 30, n_slices=1024, slice_dim=4)
     b, sb = contract_gpu(net, prec="bf16x3", max_intermediate_bytes=16 << 30, n_slices=256, slice_dim=4)
     assert rel_err(a, b) <= 2 * REL_TOL, (sa, sb)
+
+
+def _dot_nets():
+    """Long sums over few outputs (the tiled dot kernel): operands transposed
+    against each other, a tile that is not a multiple of the block, and two
+    FP32-pair intermediates as operands."""
+    rng = np.random.default_rng(17)
+    A = rng.uniform(-1, 1, (5, 36, 6, 40))
+    B = rng.uniform(-1, 1, (5, 40, 6, 36))
+    yield synth.HTN([synth.Tensor("QT", (0, 1, 2, 3), A), synth.Tensor("QT", (0, 3, 2, 1), B)], (0,))
+    A = rng.uniform(-1, 1, (3, 7, 13, 50))
+    B = rng.uniform(-1, 1, (3, 50, 13, 7))
+    yield synth.HTN([synth.Tensor("QT", (0, 1, 2, 3), A), synth.Tensor("QT", (0, 3, 2, 1), B)], (0,))
+    A = rng.uniform(-1, 1, (2, 48, 32))
+    B = rng.uniform(-1, 1, (32, 8, 64))
+    C = rng.uniform(-1, 1, (2, 64, 8, 32))
+    D = rng.uniform(-1, 1, (32, 48))
+    yield synth.HTN([synth.Tensor("QT", (0, 1, 4), A), synth.Tensor("QT", (4, 2, 3), B),
+                     synth.Tensor("QT", (0, 3, 2, 5), C), synth.Tensor("QT", (5, 1), D)], (0,))
+
+
+@pytest.mark.parametrize("case", range(3))
+def test_long_dot_reductions(case):
+    net = list(_dot_nets())[case]
+    ref = tn.brute_force(net.pairs(), net.output).ravel() if case < 2 else oracle_value(net)
+    got, _ = contract_gpu(net, prec="bf16x3")
+    assert rel_err(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("kc", ["1", "4", "8"])
+def test_bf16x3_with_magnitudes_varying_along_k_and_rows(kc, monkeypatch):
+    """Entries whose magnitude changes by up to 2^24 along K and across rows,
+    so neighbouring k-blocks sit on different piece grids, at several drain
+    intervals (k-blocks per accumulator chunk)."""
+    monkeypatch.setenv("QTPU_KC", kc)
+    rng = np.random.default_rng(5)
+    b, m, n, k = 2, 200, 150, 640
+    sk = 2.0 ** rng.integers(-12, 13, k)
+    A = rng.uniform(-1, 1, (b, m, k)) * 2.0 ** rng.integers(-12, 13, (1, m, 1)) * sk[None, None, :]
+    B = rng.uniform(-1, 1, (b, k, n)) * 2.0 ** rng.integers(-12, 13, (1, 1, n)) * sk[None, ::-1, None]
+    net = synth.HTN([synth.Tensor("QT", (0, 1, 3), A), synth.Tensor("QT", (0, 3, 2), B)], (0, 1, 2))
+    got, st = contract_gpu(net, prec="bf16x3")
+    assert st["n_tensor_core_steps"] == 1
+    assert rel_err(got, np.matmul(A, B).ravel()) <= REL_TOL
