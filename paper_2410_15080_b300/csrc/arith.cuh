@@ -81,12 +81,13 @@ struct Acc {
 // ------------------------------------------------------------ BF16x3 pieces
 // The three BF16 pieces of the values of one operand row over one 64-entry
 // k-block share a grid: with 2^E above every |x| of the block, the pieces are
-// integer multiples of 2^(E-8), 2^(E-17) and 2^(E-26) of magnitude at most
-// 2^8 units (at most 8 significant bits, so exact in BF16), and
-// |x - x0 - x1 - x2| <= 2^(E-27).  A product of two leading pieces is an
-// integer multiple of 2^(Ea+Eb-16) of at most 2^16 units, so the sum of up to
-// 256 of them on one grid (4 k-blocks) stays within 2^24 units and is exact in
-// the tensor cores' FP32 accumulator whatever rounding it applies.
+// integer multiples of 2^(E-7), 2^(E-16) and 2^(E-25), the first of magnitude
+// at most 2^7 units and the others at most 2^8 (at most 8 significant bits,
+// so exact in BF16), and |x - x0 - x1 - x2| <= 2^(E-26).  A product of two
+// leading pieces is an integer multiple of 2^(Ea+Eb-14) of at most 2^14
+// units, so the sum of up to 1024 of them on one grid (16 k-blocks) stays
+// within 2^24 units and is exact in the tensor cores' FP32 accumulator
+// whatever rounding it applies.
 __device__ __forceinline__ int grid_exp(float m) {  // E with |m| < 2^E, clamped to [-123, 111]
   const int e = (int)((__float_as_uint(fabsf(m)) >> 23) & 0xffu) - 126;
   return e > 111 ? 111 : (e < -123 ? -123 : e);
@@ -100,13 +101,13 @@ __device__ __forceinline__ float grid_round(float x, int e) {
 }
 // pieces of v = v.x + v.y on the grid of exponent E
 __device__ __forceinline__ void grid_pieces(float2 v, int E, float* p) {
-  const float h0 = grid_round(v.x, E + 15);              // multiple of 2^(E-8)
+  const float h0 = grid_round(v.x, E + 16);              // multiple of 2^(E-7)
   const float r1 = __fadd_rn(__fsub_rn(v.x, h0), v.y);  // v.x - h0 is exact
-  const float h1 = grid_round(r1, E + 6);                // multiple of 2^(E-17)
+  const float h1 = grid_round(r1, E + 7);                // multiple of 2^(E-16)
   const float r2 = __fsub_rn(r1, h1);                    // exact
   p[0] = h0;
   p[1] = h1;
-  p[2] = grid_round(r2, E - 3);                          // multiple of 2^(E-26)
+  p[2] = grid_round(r2, E - 2);                          // multiple of 2^(E-25)
 }
 
 // ------------------------------------------------------------ indexing

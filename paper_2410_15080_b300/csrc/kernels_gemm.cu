@@ -11,13 +11,13 @@
 // FP32 accumulation loses precision with every MMA added into an accumulator
 // (measured: the error grows linearly with K), so (1) the leading product
 // x0*y0 has its own accumulator X and the smaller cross terms share Y, and
-// (2) both are drained every few k-blocks and accumulated with compensated
-// (TwoSum) FP32 arithmetic in the epilogue's registers; FP64 math is avoided
-// in the drain (FP64 throughput on B300 is ~1/64 of FP32).  BF16x3 pieces
-// are cut on a grid shared by each operand row's 64-entry k-block (see
-// grid_pieces), which makes every k-block's sum of leading products exact in
-// X; between drains (4 k-blocks) X rounds only where neighbouring blocks'
-// grids differ.
+// (2) BF16x3 pieces are cut on a grid shared by each operand row's 64-entry
+// k-block (see grid_pieces): every k-block's sum of leading products, and a
+// chunk of up to 16 k-blocks on one grid, is then exact in X, so one chunk
+// covers K <= 1024 and the accumulators are drained once per tile.  Longer
+// K (and the TF32 forms, 4 or 32 k-blocks per chunk) add each chunk's X + Y
+// to the stored result with compensated (TwoSum) FP32 arithmetic; FP64 math
+// is avoided (FP64 throughput on B300 is ~1/64 of FP32).
 //
 // One CTA per SM, persistent over (batch, m-tile, n-tile) tiles:
 //   warp 0      TMA producer (one lane): pieces of A and B for one k-block
@@ -26,10 +26,9 @@
 //               K-steps x the product list, into one of two TMEM
 //               accumulators (double-buffered so the epilogue of one chunk
 //               overlaps the MMAs of the next);
-//   warps 2..17 epilogue: tcgen05.ld 32 lanes x 8 columns of both
-//               accumulators, chunk value X + Y accumulated with TwoSum into
-//               a float plus a BF16 error term per output in registers; the
-//               tile is stored as (hi, lo) float pairs (no FP64 arithmetic).
+//   warps 2..17 epilogue: tcgen05.ld 32 lanes x 32 columns of both
+//               accumulators, X + Y as an exact (hi, lo) float pair (TwoSum)
+//               stored, or added to the stored pair for later chunks.
 // Every wait is bounded (global timer); on give-up the kernel sets a status
 // bit, lets in-flight copies and MMAs land, frees TMEM and returns.
 #include <cstdio>
@@ -55,19 +54,19 @@ template <int PREC>
 struct Cfg;
 template <>
 struct Cfg<3> {  // BF16x3: pieces of 8 significant bits, products of weight >= 2^-16
-  static constexpr int NP = 3, NPROD = 6, ES = 2, KB = 64, UK = 16, FMT = 1, STAGES = 2, KC = 1;
+  static constexpr int NP = 3, NPROD = 6, ES = 2, KB = 64, UK = 16, FMT = 1, STAGES = 2, KC = 16;
   __device__ static int pa(int i) { const int t[6] = {0, 0, 1, 0, 1, 2}; return t[i]; }
   __device__ static int pb(int i) { const int t[6] = {0, 1, 0, 2, 1, 0}; return t[i]; }
 };
 template <>
 struct Cfg<2> {  // 3xTF32: pieces of 11 significant bits, products of weight >= 2^-11
-  static constexpr int NP = 2, NPROD = 3, ES = 4, KB = 32, UK = 8, FMT = 2, STAGES = 3, KC = 2;
+  static constexpr int NP = 2, NPROD = 3, ES = 4, KB = 32, UK = 8, FMT = 2, STAGES = 3, KC = 4;
   __device__ static int pa(int i) { const int t[3] = {0, 0, 1}; return t[i]; }
   __device__ static int pb(int i) { const int t[3] = {0, 1, 0}; return t[i]; }
 };
 template <>
 struct Cfg<1> {  // TF32: one piece, one product
-  static constexpr int NP = 1, NPROD = 1, ES = 4, KB = 32, UK = 8, FMT = 2, STAGES = 4, KC = 8;
+  static constexpr int NP = 1, NPROD = 1, ES = 4, KB = 32, UK = 8, FMT = 2, STAGES = 4, KC = 32;
   __device__ static int pa(int) { return 0; }
   __device__ static int pb(int) { return 0; }
 };
@@ -89,25 +88,19 @@ __device__ __forceinline__ void set_abort(volatile int* abort, uint32_t* status,
   if (status) atomicOr(status, bit);
 }
 
-// hi + lo += v: TwoSum (Knuth) gives the exact rounding error e of hi + v;
-// e is added to lo.  lo is a running sum of such errors (|lo| << |hi|), so
-// it is kept as BF16 (8 significant bits are plenty) in packed pairs.
-__device__ __forceinline__ float two_sum_err(float& hi, float v) {
-  const float s = __fadd_rn(hi, v);
-  const float bb = __fsub_rn(s, hi);
-  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
-  hi = s;
-  return e;
+// s + e = a + b exactly (TwoSum, Knuth)
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return make_float2(s, e);
 }
-__device__ __forceinline__ uint32_t lo_add(uint32_t lo2, float e0, float e1) {
-  const float l0 = __uint_as_float(lo2 << 16) + e0;
-  const float l1 = __uint_as_float(lo2 & 0xffff0000u) + e1;
-  uint32_t r;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(l1), "f"(l0));
-  return r;
-}
-__device__ __forceinline__ float lo_get(uint32_t lo2, int half) {
-  return half ? __uint_as_float(lo2 & 0xffff0000u) : __uint_as_float(lo2 << 16);
+// (hi, lo) pair plus (hi, lo) pair, renormalised (Fast2Sum)
+__device__ __forceinline__ float2 pair_add(float2 p, float2 q) {
+  const float2 t = two_sum(p.x, q.x);
+  const float lo = __fadd_rn(t.y, __fadd_rn(p.y, q.y));
+  const float hi = __fadd_rn(t.x, lo);
+  return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, t.x)));
 }
 
 template <int PREC>
@@ -265,23 +258,25 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // -------------------------------------------------------------- epilogue
     // warp w owns TMEM lane quarter (w % 4) and column group h of the tile;
-    // each thread keeps one row's kEpiCols columns as float + BF16 errors
+    // per chunk each thread loads its row's kEpiCols columns of X and Y,
+    // hands the accumulator back to the MMA warp, and stores X + Y as an
+    // exact (hi, lo) pair -- added to the stored pair for chunks after the
+    // first (the same thread owns the same outputs in every chunk).
     const int ew = warp - 2;
     const int q = warp & 3;
     const int h = ew >> 2;
     int item = 0;
     bool ok = true;
-    float hi[kEpiCols];
-    uint32_t lo2[kEpiCols / 2];
     for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
       const int ntile = (int)(t % nt);
       const int r = t / nt;
       const int mtile = (int)(r % mt);
       const int b = (int)(r / mt);
-#pragma unroll
-      for (int j = 0; j < kEpiCols; ++j) hi[j] = 0.f;
-#pragma unroll
-      for (int j = 0; j < kEpiCols / 2; ++j) lo2[j] = 0u;
+      // C is stored [batch][N][M] (M fastest): for a fixed column the 32
+      // lanes of a warp write 32 consecutive rows, 256 contiguous bytes
+      const int row = mtile * BM + q * 32 + lane;
+      float2* cb = Cout + (long long)b * M * N + row;
+      const int n0 = ntile * BN + h * kEpiCols;
       for (int ch = 0; ch < nchunks; ++ch, ++item) {
         const int acc = (int)(item & 1);
         const uint32_t aph = (uint32_t)((item >> 1) & 1);
@@ -294,38 +289,32 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_after();
         const uint32_t tX = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 2 * BN + h * kEpiCols);
-#pragma unroll
-        for (int c = 0; c < kEpiCols / 8; ++c) {
-          float vx[8], vy[8];
-          tmem_ld8(tX + c * 8, vx);
-          if (C::NPROD > 1) {
-            tmem_ld8(tX + BN + c * 8, vy);
-          } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) vy[j] = 0.f;
+        // groups of 8 columns: X and Y of a group in 16 registers (all
+        // register indices compile-time constants)
+#pragma unroll 1
+        for (int g = 0; g < kEpiCols / 8; ++g) {
+          uint32_t rx[8], ry[8];
+          tmem_ld8_nowait(tX + g * 8, rx);
+          if (C::NPROD > 1) tmem_ld8_nowait(tX + BN + g * 8, ry);
+          tmem_wait_ld();
+          if (g == kEpiCols / 8 - 1) {  // the accumulator is free for the next chunk
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accempty[acc]);
           }
+          if (row < M) {
+            const int c0 = n0 + g * 8;
+            float2* dst = cb + (long long)c0 * M;
 #pragma unroll
-          for (int j = 0; j < 8; j += 2) {
-            // X + Y of this chunk in one FP32 rounding, then exact accumulation
-            const float e0 = two_sum_err(hi[c * 8 + j], __fadd_rn(vx[j], vy[j]));
-            const float e1 = two_sum_err(hi[c * 8 + j + 1], __fadd_rn(vx[j + 1], vy[j + 1]));
-            lo2[(c * 8 + j) >> 1] = lo_add(lo2[(c * 8 + j) >> 1], e0, e1);
+            for (int j = 0; j < 8; ++j) {
+              if (c0 + j < N) {
+                float2 v = two_sum(__uint_as_float(rx[j]), C::NPROD > 1 ? __uint_as_float(ry[j]) : 0.f);
+                if (ch > 0) v = pair_add(dst[(long long)j * M], v);
+                dst[(long long)j * M] = v;
+              }
+            }
           }
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&accempty[acc]);
-      }
-      if (!ok) break;
-      // C is stored [batch][N][M] (M fastest): for a fixed column the 32
-      // lanes of a warp write 32 consecutive rows, 256 contiguous bytes
-      const int row = mtile * BM + q * 32 + lane;
-      if (row < M) {
-        float2* cb = Cout + (long long)b * M * N + row;
-        const int n0 = ntile * BN + h * kEpiCols;
-#pragma unroll
-        for (int j = 0; j < kEpiCols; ++j)
-          if (n0 + j < N) cb[(long long)(n0 + j) * M] = make_float2(hi[j], lo_get(lo2[j >> 1], j & 1));
       }
     }
   }

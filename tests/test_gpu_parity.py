@@ -259,7 +259,7 @@ def test_long_dot_reductions(case):
     assert rel_err(got, ref) <= 1e-12
 
 
-@pytest.mark.parametrize("kc", ["1", "4", "8"])
+@pytest.mark.parametrize("kc", ["1", "4", "16", "64"])
 def test_bf16x3_with_magnitudes_varying_along_k_and_rows(kc, monkeypatch):
     """Entries whose magnitude changes by up to 2^24 along K and across rows,
     so neighbouring k-blocks sit on different piece grids, at several drain
