@@ -163,7 +163,7 @@ bool make_operand_map(CUtensorMap* map, void* base, int prec, int64_t batch, int
 namespace {
 
 constexpr int64_t kSmallLeaf = 256;   // leaves up to this size are absorbed
-constexpr int kMaxVirtualOps = 4;     // operands of one virtual tensor
+constexpr int kMaxVirtualOps = 5;     // operands of one virtual tensor
 constexpr int64_t kMaxVirtualLoop = 256;
 
 size_t dt_bytes(int dt) { return dt == DT_F32 ? 4 : 8; }
@@ -258,9 +258,29 @@ bool dot_setup(GatherArgs& g, int sm) {
     std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return L.stride[a][1] < L.stride[b][1]; });
     for (int m : ord) {
       if (T >= 1024) break;
-      if (T * L.dim[m] > kDotMaxTile) continue;
-      T *= L.dim[m];
-      in_tile[m] = 1;
+      if (T * L.dim[m] <= kDotMaxTile) {
+        T *= L.dim[m];
+        in_tile[m] = 1;
+        continue;
+      }
+      // the largest divisor of the mode that still fits: split it, the inner
+      // part joins the tile
+      uint32_t d2 = 0;
+      for (uint32_t d = (uint32_t)(kDotMaxTile / T); d >= 2 && !d2; --d)
+        if (L.dim[m] % d == 0) d2 = d;
+      if (!d2 || L.n >= kMaxModes) continue;
+      for (int k = L.n; k > m + 1; --k) {
+        L.dim[k] = L.dim[k - 1];
+        for (int q = 0; q < kMaxOps; ++q) L.stride[k][q] = L.stride[k - 1][q];
+      }
+      in_tile.insert(in_tile.begin() + m + 1, 1);
+      L.n++;
+      L.dim[m + 1] = d2;
+      for (int q = 0; q < kMaxOps; ++q) L.stride[m + 1][q] = L.stride[m][q];
+      L.dim[m] /= d2;
+      for (int q = 0; q < kMaxOps; ++q) L.stride[m][q] *= d2;
+      T *= d2;
+      break;
     }
   }
   if (T < 32) return false;
@@ -1290,6 +1310,7 @@ std::string exec_run(Executor* ex, const std::vector<Leaf>& leaves, double* dev_
     if (!ex->graph[gi]) {
       if (ex->prof.on) ex->prof.used = 0;
       cudaGraph_t g = nullptr;
+      cudaGetLastError();  // a launch error left by earlier work must not fail this capture
       ce = cudaStreamBeginCapture(ex->own, cudaStreamCaptureModeThreadLocal);
       if (ce == cudaSuccess) {
         cudaError_t e1 = enqueue_all(ex, leaves, ex->out_stage, ex->own);
@@ -1299,6 +1320,7 @@ std::string exec_run(Executor* ex, const std::vector<Leaf>& leaves, double* dev_
       if (ce == cudaSuccess) ce = cudaGraphInstantiate(&ex->graph[gi], g, 0);
       if (g) cudaGraphDestroy(g);
       if (ce != cudaSuccess) {
+        cudaGetLastError();
         *code = QTPU_ECUDA;
         return std::string("graph capture failed: ") + cudaGetErrorString(ce);
       }

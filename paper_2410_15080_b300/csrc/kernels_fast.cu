@@ -39,6 +39,17 @@ __device__ void build_w(const GatherArgs& a, float2* W) {
   }
 }
 
+// Offsets of every loop position (summed terms) per operand, built once per
+// block when the loop is short: the terms of an entry then issue independent
+// loads instead of walking the loop modes one dependent step at a time.
+constexpr uint32_t kLoopTab = 64;
+template <int NOPS>
+__device__ void build_loop_tab(const GatherArgs& a, int64_t (*lt)[NOPS]) {
+  if (a.n_loop > kLoopTab || a.loop.n == 0) return;
+  for (uint32_t l = threadIdx.x; l < a.n_loop; l += blockDim.x) offsets<NOPS>(l, a.loop, lt[l]);
+}
+__device__ __forceinline__ bool use_loop_tab(const GatherArgs& a) { return a.loop.n > 0 && a.n_loop <= kLoopTab; }
+
 template <int NB, int DT0, int DT1, bool HW>
 struct Op {
   static constexpr int NOPS = NB + (HW ? 1 : 0);
@@ -48,8 +59,20 @@ struct Op {
     if (HW) v = mul_pair(v, W[off[NB]]);
     return v;
   }
-  __device__ static __forceinline__ float2 entry(const GatherArgs& a, const float2* W, const int64_t* base) {
+  __device__ static __forceinline__ float2 entry(const GatherArgs& a, const float2* W, const int64_t* base,
+                                                 const int64_t (*lt)[NOPS]) {
     if (a.loop.n == 0) return term(a, W, base);
+    if (use_loop_tab(a)) {
+      Acc acc;
+#pragma unroll 4
+      for (uint32_t l = 0; l < a.n_loop; ++l) {
+        int64_t off[NOPS];
+#pragma unroll
+        for (int j = 0; j < NOPS; ++j) off[j] = base[j] + lt[l][j];
+        acc.add(term(a, W, off));
+      }
+      return acc.get();
+    }
     Acc acc;
     int64_t off[NOPS];
 #pragma unroll
@@ -89,7 +112,7 @@ struct Op {
 // mode that W alone carries): W offsets per entry in wof[F]
 template <int DT0, int F>
 __device__ __forceinline__ void entry_fan(const GatherArgs& a, const float2* W, int64_t xo, const int* wof,
-                                          float2* v) {
+                                          float2* v, const int64_t (*lt)[2]) {
   Acc acc[F];
   if (a.loop.n == 0) {
     const float2 x = load_pair<DT0>(a.ptr[0], xo);
@@ -97,7 +120,15 @@ __device__ __forceinline__ void entry_fan(const GatherArgs& a, const float2* W, 
     for (int f = 0; f < F; ++f) v[f] = mul_pair(x, W[wof[f]]);
     return;
   }
-  if (a.loop.n == 1) {
+  if (use_loop_tab(a)) {
+#pragma unroll 4
+    for (uint32_t l = 0; l < a.n_loop; ++l) {
+      const float2 x = load_pair<DT0>(a.ptr[0], xo + lt[l][0]);
+      const int ow = (int)lt[l][1];
+#pragma unroll
+      for (int f = 0; f < F; ++f) acc[f].add(mul_pair(x, W[wof[f] + ow]));
+    }
+  } else if (a.loop.n == 1) {
     const uint32_t d = a.loop.dim[0];
     const int64_t sx = a.loop.stride[0][0];
     const int sw = (int)a.loop.stride[0][1];
@@ -139,15 +170,15 @@ template <int NB, int DT0, int DT1, bool HW, bool F64OUT>
 __global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __restrict__ out) {
   using O = Op<NB, DT0, DT1, HW>;
   extern __shared__ float2 W[];  // w_size entries (dynamic shared memory)
-  if (HW) {
-    build_w(a, W);
-    __syncthreads();
-  }
+  __shared__ int64_t lt[kLoopTab][O::NOPS];
+  if (HW) build_w(a, W);
+  build_loop_tab<O::NOPS>(a, lt);
+  __syncthreads();
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < a.n_out; o += stride) {
     int64_t base[O::NOPS];
     offsets<O::NOPS>(o, a.out, base);
-    const float2 v = O::entry(a, W, base);
+    const float2 v = O::entry(a, W, base, lt);
     if (F64OUT)
       ((double*)out)[o] = (double)v.x + (double)v.y;
     else
@@ -189,33 +220,47 @@ __global__ void __launch_bounds__(256) k_dot_fast(const GatherArgs a) {
   const void* X = a.ptr[0];
   const void* Y = a.ptr[1];
   Acc acc;
-  for (uint32_t t = t0; t < t1; ++t) {
+  // register double buffer: the next tuple's loads are in flight while the
+  // current tuple is multiplied
+  float2 xv[PER], yv[PER];
+  if (t0 < t1) {
     int64_t ot[2];
-    offsets<2>(t, a.loop, ot);
-    const int64_t xb = base[0] + ot[0], yb = base[1] + ot[1];
-    float2 xv[PER];
+    offsets<2>(t0, a.loop, ot);
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const uint32_t v = threadIdx.x + k * 256;
-      if (v < T) xv[k] = load_pair<DT0>(X, xb + tx[v].y);
+      if (v < T) {
+        xv[k] = load_pair<DT0>(X, base[0] + ot[0] + tx[v].y);
+        yv[k] = load_pair<DT1>(Y, base[1] + ot[1] + ty[v]);
+      }
     }
+  }
+  for (uint32_t t = t0; t < t1; ++t) {
     __syncthreads();  // the previous tuple's tile is consumed
+    float2 yc[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const uint32_t v = threadIdx.x + k * 256;
       if (v < T) sX[tx[v].x] = xv[k];
+      yc[k] = yv[k];
     }
     __syncthreads();
-    float2 yv[PER];
+    if (t + 1 < t1) {
+      int64_t ot[2];
+      offsets<2>(t + 1, a.loop, ot);
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const uint32_t u = threadIdx.x + k * 256;
-      if (u < T) yv[k] = load_pair<DT1>(Y, yb + ty[u]);
+      for (int k = 0; k < PER; ++k) {
+        const uint32_t v = threadIdx.x + k * 256;
+        if (v < T) {
+          xv[k] = load_pair<DT0>(X, base[0] + ot[0] + tx[v].y);
+          yv[k] = load_pair<DT1>(Y, base[1] + ot[1] + ty[v]);
+        }
+      }
     }
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const uint32_t u = threadIdx.x + k * 256;
-      if (u < T) acc.add(mul_pair(sX[dot_slot(u)], yv[k]));
+      if (u < T) acc.add(mul_pair(sX[dot_slot(u)], yc[k]));
     }
   }
   // block sum (compensated) -> scratch[o][c]
@@ -281,10 +326,10 @@ __global__ void __launch_bounds__(256) k_split_fast(const GatherArgs a, void* __
   __shared__ int64_t rowoff[kTR][NOPS];
   __shared__ int64_t koff[kTK][NOPS];
   __shared__ float2 tile[kTR][kTK + 1];
-  if (HW) {
-    build_w(a, W);
-    __syncthreads();
-  }
+  __shared__ int64_t lt[kLoopTab][NOPS];
+  if (HW) build_w(a, W);
+  build_loop_tab<NOPS>(a, lt);
+  __syncthreads();
   const uint32_t n_rt = (a.n_rows + kTR - 1) / kTR;
   const uint32_t n_kt = (a.Kp + kTK - 1) / kTK;
   const int64_t piece = (int64_t)a.n_rows * a.Kp;
@@ -307,6 +352,7 @@ __global__ void __launch_bounds__(256) k_split_fast(const GatherArgs a, void* __
     if (F > 1) {
       // work item = F entries along the fan mode (rows or ks), one operand load each
       constexpr int NI = kTR * kTK / F;
+#pragma unroll
       for (int e = tid; e < NI; e += 256) {
         int r, k;
         if (a.fan == 2) {  // F consecutive rows
@@ -334,7 +380,7 @@ __global__ void __launch_bounds__(256) k_split_fast(const GatherArgs a, void* __
 #pragma unroll
           for (int f = 0; f < F; ++f)
             wof[f] = (int)(a.fan == 2 ? rowoff[r + f][1] + koff[k][1] : rowoff[r][1] + koff[k + f][1]);
-          entry_fan<DT0, F>(a, W, rowoff[r][0] + koff[k][0], wof, v);
+          entry_fan<DT0, F>(a, W, rowoff[r][0] + koff[k][0], wof, v, (const int64_t (*)[2])lt);
         } else {
 #pragma unroll
           for (int f = 0; f < F; ++f) v[f] = make_float2(0.f, 0.f);
@@ -345,6 +391,26 @@ __global__ void __launch_bounds__(256) k_split_fast(const GatherArgs a, void* __
           const bool in = r0 + rr < a.n_rows && k0 + kk < a.K;
           tile[rr][kk] = in ? v[f] : make_float2(0.f, 0.f);
         }
+      }
+    } else if (a.loop.n == 0) {
+      // one term per entry: every load of the tile issued before any use
+      constexpr int PER = kTR * kTK / 256;
+      float2 v[PER];
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int e = tid + u * 256;
+        const int r = a.row_fast ? e % kTR : e / kTK;
+        const int k = a.row_fast ? e / kTR : e % kTK;
+        v[u] = r0 + r < a.n_rows && k0 + k < a.K ? load_pair<DT0>(a.ptr[0], rowoff[r][0] + koff[k][0])
+                                                  : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int e = tid + u * 256;
+        const int r = a.row_fast ? e % kTR : e / kTK;
+        const int k = a.row_fast ? e / kTR : e % kTK;
+        if (HW) v[u] = mul_pair(v[u], W[rowoff[r][NOPS - 1] + koff[k][NOPS - 1]]);
+        tile[r][k] = v[u];
       }
     } else {
 #pragma unroll 2
@@ -362,7 +428,7 @@ __global__ void __launch_bounds__(256) k_split_fast(const GatherArgs a, void* __
         int64_t b[NOPS];
 #pragma unroll
         for (int j = 0; j < NOPS; ++j) b[j] = rowoff[r][j] + koff[k][j];
-        v = O::entry(a, W, b);
+        v = O::entry(a, W, b, lt);
       }
       tile[r][k] = v;
     }
@@ -447,8 +513,9 @@ template <int DT0, bool HW>
 cudaError_t split_dt(const GatherArgs& a, void* out, int sm, cudaStream_t st) {
   const int64_t tiles = (int64_t)((a.n_rows + kTR - 1) / kTR) * ((a.Kp + kTK - 1) / kTK);
   if (tiles <= 0) return cudaSuccess;
-  // several tiles per block when a W table is built; otherwise one per block
-  const int64_t cap = HW ? (int64_t)sm * 4 : (int64_t)sm * 8;
+  // blocks loop over tiles; with a large W table fewer blocks, each building
+  // the table once
+  const int64_t cap = HW && a.w_size > 1024 ? (int64_t)sm * 4 : (int64_t)sm * 8;
   const int g = (int)(tiles < cap ? tiles : cap);
   if (HW && a.fan && a.fan_f == 4) return split_f<DT0, HW, 4>(a, out, g, st);
   if (HW && a.fan && a.fan_f == 2) return split_f<DT0, HW, 2>(a, out, g, st);
