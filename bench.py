@@ -53,15 +53,15 @@ def load_peaks():
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "src": "fallback"}
 
 
-def measured_traffic(kclass: str):
-    """DRAM bytes per launch of a kernel class from the committed ncu summary,
-    or None if the kernel source changed since the capture."""
+def measured_traffic(workload: str, kclass: str):
+    """DRAM bytes per launch of a kernel class of a workload from the committed
+    ncu summary, or None if the kernel source changed since the capture."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    e = d.get(kclass)
+    e = (d.get(workload) or {}).get(kclass)
     if not e:
         return None
     src = os.path.join(ROOT, e["source"])
@@ -496,7 +496,7 @@ def run_ours(args, rank, world):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": dom,
                 "peak_note": f"{peaks['src']} copy bandwidth"}
-    roof["traffic"] = measured_traffic(dom)
+    roof["traffic"] = measured_traffic(args.workload, dom)
     roof["per_launch_ms"] = per_launch_ms
     roof["launches_per_step"] = d["launches"] / args.steps
     roof["classes"] = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
