@@ -3,6 +3,8 @@
 // All inline PTX targets sm_103a.
 #pragma once
 #include <cstdint>
+#include <cstdlib>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -161,6 +163,43 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
 // both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint32_t N) {
   return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// ------------------------------------------------------------ dependent launch
+// A kernel launched by launch_k may begin while the previous kernel of its
+// stream drains (programmatic dependent launch).  Before its first read of
+// anything an earlier kernel wrote, and before its first global write, it
+// calls pdl_wait(), which returns once that kernel has completed and its
+// writes are visible (at once when the kernel was launched plainly).  Work
+// before the wait is limited to shared memory, registers and the h-TN's leaf
+// tensors, which no kernel writes.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Off unless QTPU_PDL=1: on the measured workloads it did not shorten the
+// contraction (the kernels' prologues are short).
+inline bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("QTPU_PDL");
+    return e && std::atoi(e) != 0;
+  }();
+  return on;
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                            Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 }  // namespace qtpu

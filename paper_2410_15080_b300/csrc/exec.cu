@@ -442,6 +442,19 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
   };
 
   std::vector<Repr> repr(n_plan);
+  // GEMM results not yet consumed: producing launch, index groups of the
+  // stored [batch][N][M] layout, and K (for the fused operand split)
+  struct GemmOut {
+    size_t li;
+    Inds batch, inner, outer;
+    int64_t K;
+  };
+  std::map<int, GemmOut> gemm_out;
+  bool fuse_off = false, fuse_keep_layout = false;
+  if (const char* e = std::getenv("QTPU_NO_FUSE")) fuse_off = std::atoi(e) != 0;
+  // QTPU_FUSE_KEEP_LAYOUT=1: no operand swap in favour of the fused split
+  // (exercises the epilogue form with K along the tile's rows)
+  if (const char* e = std::getenv("QTPU_FUSE_KEEP_LAYOUT")) fuse_keep_layout = std::atoi(e) != 0;
   for (int t = 0; t < nl; ++t) repr[t].ops = {t};
   size_t split_need_a = 0, split_need_b = 0;
   const int np = prec == 3 ? 3 : (prec == 2 ? 2 : 1);
@@ -670,6 +683,119 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     return true;
   };
 
+  // The (non-sliced) indices the step consuming tensor t contracts, following
+  // t through absorptions of small leaves; empty if there is none.
+  auto consumer_k = [&](int t, size_t from) -> Inds {
+    for (size_t u = from + 1; u < plan.steps.size(); ++u) {
+      const PlanStep& q = plan.steps[u];
+      if (q.x != t && q.y != t) continue;
+      const int other = q.x == t ? q.y : q.x;
+      if (other < nl && prod(live_inds[other]) <= (double)kSmallLeaf && u + 1 < plan.steps.size()) {
+        t = q.out;  // folded into the consumer of the absorption's result
+        continue;
+      }
+      return nsl(q.k);
+    }
+    return Inds();
+  };
+
+  // Can operand R (rows, K in the consumer's order) be written in piece form
+  // by the epilogue of the GEMM that produced its one large factor?  It must
+  // be that GEMM result times small leaves, with no summed index, carry
+  // exactly the result's indices, have K equal to the result's M or N index
+  // group in stored order, and fit the result's arena slot.
+  auto fuse_check = [&](const Repr& R, const Inds& rows, const Inds& K, GemmFuse* F, std::vector<int>* small_ids,
+                        int* T_out) -> bool {
+    if (fuse_off || prec != 3 || !R.L.empty()) return false;
+    int T = -1;
+    std::vector<int> small;
+    for (int o : R.ops) {
+      if (o < nl && prod(live_inds[o]) <= (double)kSmallLeaf) {
+        small.push_back(o);
+      } else {
+        if (T >= 0) return false;
+        T = o;
+      }
+    }
+    auto it = gemm_out.find(T);
+    if (T < 0 || it == gemm_out.end()) return false;
+    const GemmOut& P = it->second;
+    const Launch& LP = ex->launches[P.li];
+    if (LP.kind != LK_GEMM || LP.gemm.fuse.on || LP.gemm.prec != 3 || (P.K + 63) / 64 > 16) return false;
+    int k_is_m;
+    if (K == P.inner)
+      k_is_m = 1;
+    else if (K == P.outer)
+      k_is_m = 0;
+    else
+      return false;
+    std::set<int64_t> mine(rows.begin(), rows.end()), theirs;
+    for (int64_t i : K) mine.insert(i);
+    for (const Inds* g : {&P.batch, &P.inner, &P.outer}) theirs.insert(g->begin(), g->end());
+    if (mine != theirs || mine.size() != rows.size() + K.size()) return false;
+    const double rows_total = prod(rows);
+    const uint64_t Kp = align_up((uint64_t)prod(K), 8);
+    if (rows_total * (double)Kp >= 2147483647.0 || 3.0 * rows_total * (double)Kp * 2.0 > (double)extent[T] * 8.0)
+      return false;
+    // W over the small leaves' non-sliced indices, dense in first-seen order
+    Inds U;
+    for (int t : small)
+      for (int64_t i : live_inds[t])
+        if (!sliced.count(i) && !contains(U, i)) U.push_back(i);
+    std::map<int64_t, int64_t> wst;
+    int64_t wsz = 1;
+    for (int j = (int)U.size() - 1; j >= 0; --j) {
+      wst[U[j]] = wsz;
+      wsz *= dims.get(U[j]);
+    }
+    if (small.empty()) wsz = 0;
+    if (wsz > (int64_t)kFuseMaxW || (int)small.size() > kMaxOps) return false;
+    for (int64_t i : U)
+      if (!mine.count(i)) return false;
+    std::map<int64_t, int64_t> rst;
+    int64_t acc = 1;
+    for (int j = (int)rows.size() - 1; j >= 0; --j) {
+      rst[rows[j]] = acc;
+      acc *= dims.get(rows[j]);
+    }
+    GemmFuse f;
+    f.on = 1;
+    f.k_is_m = k_is_m;
+    f.Kp = (uint32_t)Kp;
+    f.piece = (int64_t)rows_total * (int64_t)Kp;
+    auto add = [&](GModes& t, const Inds& g, bool to_rows) {
+      for (int64_t i : g) {
+        if (t.n >= kMaxModes) return false;
+        t.dim[t.n] = (uint32_t)dims.get(i);
+        t.div[t.n] = make_fastdiv(t.dim[t.n]);
+        for (int q = 0; q < kMaxOps; ++q) t.stride[t.n][q] = 0;
+        if (to_rows) t.stride[t.n][0] = rst.at(i);
+        t.stride[t.n][1] = wst.count(i) ? wst[i] : 0;
+        t.n++;
+      }
+      return true;
+    };
+    if (!add(f.bmodes, P.batch, true) || !add(f.mmodes, P.inner, !k_is_m) || !add(f.nmodes, P.outer, k_is_m))
+      return false;
+    for (int64_t i : P.batch)
+      if (!rst.count(i)) return false;
+    f.nsmall = (int)small.size();
+    f.w_size = (uint32_t)wsz;
+    for (int j = 0; j < f.nsmall; ++j) f.wdt[j] = dt_of(small[j]);
+    int64_t st[kMaxOps];
+    for (int64_t i : U) {
+      for (int j = 0; j < f.nsmall; ++j) st[j] = sof(small[j], i);
+      if (!gpush(f.wmodes, dims.get(i), st, f.nsmall)) return false;
+    }
+    for (int m = 0; m < f.wmodes.n; ++m) f.wmodes.div[m] = make_fastdiv(f.wmodes.dim[m]);
+    for (int j = 0; j < f.nsmall; ++j)
+      if (gmax(f.wmodes, j) + slice_max[small[j]] >= extent[small[j]]) return false;
+    *F = f;
+    *small_ids = small;
+    *T_out = T;
+    return true;
+  };
+
   for (size_t s = 0; s < plan.steps.size(); ++s) {
     const PlanStep& ps = plan.steps[s];
     const bool last = s + 1 == plan.steps.size();
@@ -750,7 +876,18 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     // ---- tensor-core GEMM step (operands swapped when M is the skinny side:
     // C^T = B^T A^T, so the 128-row tile runs along the longer dimension)
     const double lim = 2147483647.0;
-    const bool swap = nm < 64 && nn >= 64;
+    bool swap = nm < 64 && nn >= 64;
+    // when the next GEMM will contract this result over exactly the m (or n)
+    // indices, make that group the stored outer (N) one: the epilogue then
+    // writes the next operand's pieces along each thread's own columns
+    if (!fuse_off && !fuse_keep_layout && prec == 3 && !last) {
+      const Inds ck = consumer_k(ps.out, s);
+      const std::set<int64_t> cks(ck.begin(), ck.end());
+      int pref = -1;
+      if (!ck.empty() && cks == std::set<int64_t>(m.begin(), m.end())) pref = 1;
+      if (!ck.empty() && cks == std::set<int64_t>(n.begin(), n.end())) pref = 0;
+      if (pref >= 0 && (pref ? nn : nm) >= 64 && (pref ? nm : nn) >= 16) swap = pref == 1;
+    }
     const double gM = swap ? nn : nm, gN = swap ? nm : nn;
     const bool tc = sa.empty() && sb.empty() && gM >= 64 && gN >= 16 && nk >= 8 &&
                     nb * nm * nn * nk >= (double)(1 << 22) && nb < lim && nm < lim && nn < lim && nk < lim &&
@@ -781,14 +918,54 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       rowsY.insert(rowsY.end(), n.begin(), n.end());
       const Repr& RA = swap ? Y : X;
       const Repr& RB = swap ? X : Y;
+      const Inds& rowsA = swap ? rowsY : rowsX;
+      const Inds& rowsB = swap ? rowsX : rowsY;
+      // an operand that is a GEMM result is written in piece form by that
+      // GEMM's epilogue when K can follow the result's M or N index group
+      Inds kk = k;
+      for (const Repr* R : {&RA, &RB}) {
+        int T = -1;
+        for (int o : R->ops)
+          if (!(o < nl && prod(live_inds[o]) <= (double)kSmallLeaf)) T = o;
+        auto it = gemm_out.find(T);
+        if (it == gemm_out.end()) continue;
+        const std::set<int64_t> ks(k.begin(), k.end());
+        if (ks == std::set<int64_t>(it->second.inner.begin(), it->second.inner.end()) && k.size() == it->second.inner.size()) {
+          kk = it->second.inner;
+          break;
+        }
+        if (ks == std::set<int64_t>(it->second.outer.begin(), it->second.outer.end()) && k.size() == it->second.outer.size()) {
+          kk = it->second.outer;
+          break;
+        }
+      }
+      GemmFuse FA, FB;
+      std::vector<int> smA, smB;
+      int TA = -1, TB = -1;
+      const bool fa = fuse_check(RA, rowsA, kk, &FA, &smA, &TA);
+      const bool fb = fuse_check(RB, rowsB, kk, &FB, &smB, &TB) && TB != TA;
       Launch LA, LB, LG;
       int64_t ra = 0, rb = 0, Ka = 0, Kb = 0;
-      if (split_launch(RA, swap ? rowsY : rowsX, k, DST_SPLIT_A, &LA, &ra, &Ka) &&
-          split_launch(RB, swap ? rowsX : rowsY, k, DST_SPLIT_B, &LB, &rb, &Kb) && Ka == Kb) {
+      if (fa) ra = (int64_t)prod(rowsA), Ka = (int64_t)prod(kk);
+      if (fb) rb = (int64_t)prod(rowsB), Kb = (int64_t)prod(kk);
+      if ((fa || split_launch(RA, rowsA, kk, DST_SPLIT_A, &LA, &ra, &Ka)) &&
+          (fb || split_launch(RB, rowsB, kk, DST_SPLIT_B, &LB, &rb, &Kb)) && Ka == Kb) {
         const size_t abytes = align_up((size_t)np * ra * align_up(Ka, 8) * es, 1024);
         const size_t bbytes = align_up((size_t)np * rb * align_up(Kb, 8) * es, 1024);
-        split_need_a = std::max(split_need_a, abytes);
-        split_need_b = std::max(split_need_b, bbytes);
+        if (!fa) split_need_a = std::max(split_need_a, abytes);
+        if (!fb) split_need_b = std::max(split_need_b, bbytes);
+        for (int side = 0; side < 2; ++side) {
+          const bool f = side ? fb : fa;
+          if (!f) continue;
+          const int T = side ? TB : TA;
+          Launch& LP = ex->launches[gemm_out[T].li];
+          LP.gemm.fuse = side ? FB : FA;
+          const std::vector<int>& sm = side ? smB : smA;
+          for (size_t j = 0; j < sm.size(); ++j) LP.fuse_src[j] = sm[j];
+          LG.opnd_fused[side] = T;
+          LG.opnd_kp[side] = (uint32_t)align_up(Ka, 8);
+          ex->n_fused_splits++;
+        }
         LG.kind = LK_GEMM;
         LG.kclass = KC_GEMM;
         LG.dst = dst;
@@ -810,8 +987,17 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
         if (!last) place(ps.out);
         for (int o : X.ops) release(o);
         for (int o : Y.ops) release(o);
-        ex->launches.push_back(LA);
-        ex->launches.push_back(LB);
+        for (int t : {TA, TB})
+          if (t >= 0) gemm_out.erase(t);
+        if (!fa) {
+          LG.opnd_split[0] = (int)ex->launches.size();
+          ex->launches.push_back(LA);
+        }
+        if (!fb) {
+          LG.opnd_split[1] = (int)ex->launches.size();
+          ex->launches.push_back(LB);
+        }
+        if (!last) gemm_out[ps.out] = GemmOut{ex->launches.size(), batch, inner, outer, (int64_t)Ka};
         ex->launches.push_back(LG);
         ex->n_tc_steps++;
         repr[ps.out] = Repr();
@@ -1068,12 +1254,20 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
   for (size_t i = 0; i < ex->launches.size(); ++i) {
     Launch& L = ex->launches[i];
     if (L.kind != LK_GEMM) continue;
-    const Launch& A = ex->launches[i - 2];
-    const Launch& B = ex->launches[i - 1];
-    uint8_t* pa = A.side >= 0 ? ex->sidebuf + A.side_off : ex->splitbuf;
-    uint8_t* pb = B.side >= 0 ? ex->sidebuf + B.side_off : ex->splitbuf + ex->split_a_bytes;
-    if (!make_operand_map(&L.gemm.tmA, pa, prec, L.gemm.batch, L.gemm.M, L.gemm.K, A.g.Kp, 128) ||
-        !make_operand_map(&L.gemm.tmB, pb, prec, L.gemm.batch, L.gemm.N, L.gemm.K, B.g.Kp, gemm_block_n())) {
+    uint8_t* base[2];
+    int64_t kp[2];
+    for (int side = 0; side < 2; ++side) {
+      if (L.opnd_split[side] >= 0) {
+        const Launch& S = ex->launches[L.opnd_split[side]];
+        base[side] = S.side >= 0 ? ex->sidebuf + S.side_off : ex->splitbuf + (side ? ex->split_a_bytes : 0);
+        kp[side] = S.g.Kp;
+      } else {
+        base[side] = ex->arena + ex->inter_off[L.opnd_fused[side] - nl];
+        kp[side] = L.opnd_kp[side];
+      }
+    }
+    if (!make_operand_map(&L.gemm.tmA, base[0], prec, L.gemm.batch, L.gemm.M, L.gemm.K, kp[0], 128) ||
+        !make_operand_map(&L.gemm.tmB, base[1], prec, L.gemm.batch, L.gemm.N, L.gemm.K, kp[1], gemm_block_n())) {
       exec_free(ex);
       return fail(QTPU_ECUDA, "cuTensorMapEncodeTiled failed");
     }
@@ -1127,6 +1321,7 @@ std::string exec_describe(const Executor* ex) {
     o << "launch " << i << " " << cls[L.kclass] << " ";
     if (L.kind == LK_GEMM) {
       o << "gemm batch=" << L.gemm.batch << " M=" << L.gemm.M << " N=" << L.gemm.N << " K=" << L.gemm.K;
+      if (L.gemm.fuse.on) o << " writes-pieces k=" << (L.gemm.fuse.k_is_m ? "M" : "N") << " w=" << L.gemm.fuse.w_size;
     } else if (L.kind == LK_CONTRACT64) {
       o << "fp64 out=" << L.c64.n_out << " loop=" << L.c64.n_loop;
     } else {
@@ -1161,7 +1356,7 @@ std::string exec_describe(const Executor* ex) {
   for (size_t i = 0; i < ex->launches.size(); ++i) one(ex->launches[i], i);
   o << "reduce slices=" << ex->n_slices << " out=" << ex->reduce.g.n_out << " loop=" << ex->reduce.g.n_loop << "\n";
   o << "summary launches_per_slice=" << ex->launches.size() << " tensor_core_steps=" << ex->n_tc_steps
-    << " fused_steps=" << ex->n_fused_steps << " side_splits=" << ex->n_side << " arena_bytes=" << ex->arena_bytes
+    << " fused_steps=" << ex->n_fused_steps << " fused_splits=" << ex->n_fused_splits << " side_splits=" << ex->n_side << " arena_bytes=" << ex->arena_bytes
     << " split_bytes=" << ex->split_bytes << "\n";
   return o.str();
 }
@@ -1230,6 +1425,7 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
     if (L.kind == LK_GEMM) {
       GemmArgs g = L.gemm;
       g.C = dst_ptr(L.dst, s);
+      for (int j = 0; g.fuse.on && j < g.fuse.nsmall; ++j) g.fuse.wptr[j] = src_ptr(L.fuse_src[j]);
       return launch_gemm(g, ex->sm_count, st);
     }
     const void* A = from_partial ? (const void*)ex->partial : src_ptr(L.src[0]);

@@ -45,6 +45,14 @@ struct Launch {
   int side = -1;
   size_t side_off = 0;
   int wait_side[2] = {-1, -1};
+  // LK_GEMM operands: index of the split launch that writes each one, or the
+  // intermediate whose arena slot holds its pieces (written by the epilogue
+  // of the GEMM that produced it), with that layout's row length
+  int opnd_split[2] = {-1, -1};
+  int opnd_fused[2] = {-1, -1};
+  uint32_t opnd_kp[2] = {0, 0};
+  // LK_GEMM with gemm.fuse.on: the small leaves of the fused W (patched per slice)
+  int fuse_src[kMaxOps] = {};
 };
 
 struct Profiler {
@@ -86,6 +94,7 @@ struct Executor {
   float2* dot_scratch = nullptr; // per-chunk sums of the dot-reduction kernel
   int n_tc_steps = 0;
   int n_fused_steps = 0;         // absorption steps folded into a consumer
+  int n_fused_splits = 0;        // operand splits written by the producing GEMM's epilogue
   int64_t launches_per_contract = 0;
   bool lowered = false;
   Profiler prof;

@@ -106,6 +106,28 @@ cudaError_t launch_gather_fast(const GatherArgs& a, void* out, int sm_count, cud
 cudaError_t launch_contract(const void* A, int dtA, const void* B, int dtB, double* out,
                             const ContractArgs& a, int sm_count, cudaStream_t st);
 
+// Fused operand split (BF16x3, a single accumulator chunk): the GEMM's
+// epilogue writes the BF16x3 pieces of the next GEMM's operand, on the grid of
+// grid_pieces, straight from the accumulators instead of the (hi, lo) result.
+// The consumer's K is the tile's M rows (k_is_m) or its N columns, in the same
+// order; batch and the other tile coordinate map onto consumer rows through
+// per-digit row strides, and absorbed small factors multiply each entry
+// through a table W over their joint indices (per-digit W strides).
+constexpr uint32_t kFuseMaxW = 1024;
+struct GemmFuse {
+  int on = 0;
+  int k_is_m = 1;
+  uint32_t Kp = 0;                // consumer row length
+  int64_t piece = 0;              // entries per piece plane
+  GModes bmodes, mmodes, nmodes;  // digits of batch / m / n: stride 0 = consumer row
+                                  // contribution, stride 1 = W offset contribution
+  int nsmall = 0;                 // small factors in W
+  const void* wptr[kMaxOps] = {};
+  int wdt[kMaxOps] = {};
+  GModes wmodes;                  // W's modes, stride j = small factor j
+  uint32_t w_size = 0;
+};
+
 // prec: 1 = TF32 (1 piece, 1 product), 2 = 3xTF32 (2 pieces, 3 products),
 //       3 = BF16x3 (3 pieces, 6 products)
 struct GemmArgs {
@@ -116,6 +138,7 @@ struct GemmArgs {
   int prec = 3;
   uint32_t* status = nullptr;
   uint64_t limit_ns = 2000000000ull;
+  GemmFuse fuse;         // fuse.on: C receives the consumer's piece planes
 };
 cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st);
 // one warp waiting (bounded) on a barrier nothing completes: sets ST_TIMEOUT_DEP

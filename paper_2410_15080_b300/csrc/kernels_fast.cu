@@ -174,6 +174,8 @@ __global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __
   if (HW) build_w(a, W);
   build_loop_tab<O::NOPS>(a, lt);
   __syncthreads();
+  pdl_wait();
+  pdl_launch_dependents();
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < a.n_out; o += stride) {
     int64_t base[O::NOPS];
@@ -211,6 +213,8 @@ __global__ void __launch_bounds__(256) k_dot_fast(const GatherArgs a) {
     ty[v] = (int)yo[0];
   }
   __syncthreads();
+  pdl_wait();
+  pdl_launch_dependents();
   const uint32_t o = blockIdx.y;
   int64_t base[2];
   offsets<2>(o, a.out, base);
@@ -286,6 +290,8 @@ __global__ void __launch_bounds__(256) k_dot_fast(const GatherArgs a) {
 template <bool F64OUT>
 __global__ void __launch_bounds__(256) k_dot_finish(const float2* __restrict__ part, uint32_t n_out,
                                                     uint32_t chunks, void* __restrict__ out) {
+  pdl_wait();
+  pdl_launch_dependents();
   for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < n_out; o += gridDim.x * blockDim.x) {
     Acc acc;
     for (uint32_t c = 0; c < chunks; ++c) acc.add(part[(size_t)o * chunks + c]);
@@ -306,13 +312,12 @@ cudaError_t dot_launch(const GatherArgs& a, void* out, cudaStream_t st) {
   if (sm_bytes > 40960)
     e = cudaFuncSetAttribute(k_dot_fast<DT0, DT1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_bytes);
   if (e != cudaSuccess) return e;
-  k_dot_fast<DT0, DT1><<<dim3(a.chunks, a.n_out), 256, sm_bytes, st>>>(a);
+  e = launch_k(k_dot_fast<DT0, DT1>, dim3(a.chunks, a.n_out), dim3(256), sm_bytes, st, a);
+  if (e != cudaSuccess) return e;
   const uint32_t g = (a.n_out + 255) / 256;
-  if (a.mode == GW_DENSE_F64)
-    k_dot_finish<true><<<g, 256, 0, st>>>(a.scratch, a.n_out, a.chunks, out);
-  else
-    k_dot_finish<false><<<g, 256, 0, st>>>(a.scratch, a.n_out, a.chunks, out);
-  return cudaGetLastError();
+  const float2* part = a.scratch;
+  if (a.mode == GW_DENSE_F64) return launch_k(k_dot_finish<true>, dim3(g), dim3(256), 0, st, part, a.n_out, a.chunks, out);
+  return launch_k(k_dot_finish<false>, dim3(g), dim3(256), 0, st, part, a.n_out, a.chunks, out);
 }
 
 // ------------------------------------------------------------ split output
@@ -330,6 +335,8 @@ __global__ void __launch_bounds__(256) k_split_fast(const GatherArgs a, void* __
   if (HW) build_w(a, W);
   build_loop_tab<NOPS>(a, lt);
   __syncthreads();
+  pdl_wait();
+  pdl_launch_dependents();
   const uint32_t n_rt = (a.n_rows + kTR - 1) / kTR;
   const uint32_t n_kt = (a.Kp + kTK - 1) / kTK;
   const int64_t piece = (int64_t)a.n_rows * a.Kp;
@@ -498,15 +505,15 @@ cudaError_t split_f(const GatherArgs& a, void* out, int g, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   if (a.mode == GW_SPLIT_BF16X3) {
     if (sm_bytes > 16384) e = allow_smem(k_split_fast<DT0, HW, 0, 3, F>);
-    if (e == cudaSuccess) k_split_fast<DT0, HW, 0, 3, F><<<g, 256, sm_bytes, st>>>(a, out);
+    if (e == cudaSuccess) e = launch_k(k_split_fast<DT0, HW, 0, 3, F>, dim3(g), dim3(256), sm_bytes, st, a, out);
   } else if (a.mode == GW_SPLIT_TF32X2) {
     if (sm_bytes > 16384) e = allow_smem(k_split_fast<DT0, HW, 1, 2, F>);
-    if (e == cudaSuccess) k_split_fast<DT0, HW, 1, 2, F><<<g, 256, sm_bytes, st>>>(a, out);
+    if (e == cudaSuccess) e = launch_k(k_split_fast<DT0, HW, 1, 2, F>, dim3(g), dim3(256), sm_bytes, st, a, out);
   } else {
     if (sm_bytes > 16384) e = allow_smem(k_split_fast<DT0, HW, 1, 1, F>);
-    if (e == cudaSuccess) k_split_fast<DT0, HW, 1, 1, F><<<g, 256, sm_bytes, st>>>(a, out);
+    if (e == cudaSuccess) e = launch_k(k_split_fast<DT0, HW, 1, 1, F>, dim3(g), dim3(256), sm_bytes, st, a, out);
   }
-  return e == cudaSuccess ? cudaGetLastError() : e;
+  return e;
 }
 
 template <int DT0, bool HW>
@@ -531,12 +538,12 @@ cudaError_t dense_dt(const GatherArgs& a, void* out, int sm, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   if (a.mode == GW_DENSE_F64) {
     if (sm_bytes > 40960) e = allow_smem(k_dense_fast<NB, DT0, DT1, HW, true>);
-    if (e == cudaSuccess) k_dense_fast<NB, DT0, DT1, HW, true><<<(int)g, 256, sm_bytes, st>>>(a, out);
+    if (e == cudaSuccess) e = launch_k(k_dense_fast<NB, DT0, DT1, HW, true>, dim3((unsigned)g), dim3(256), sm_bytes, st, a, out);
   } else {
     if (sm_bytes > 40960) e = allow_smem(k_dense_fast<NB, DT0, DT1, HW, false>);
-    if (e == cudaSuccess) k_dense_fast<NB, DT0, DT1, HW, false><<<(int)g, 256, sm_bytes, st>>>(a, out);
+    if (e == cudaSuccess) e = launch_k(k_dense_fast<NB, DT0, DT1, HW, false>, dim3((unsigned)g), dim3(256), sm_bytes, st, a, out);
   }
-  return e == cudaSuccess ? cudaGetLastError() : e;
+  return e;
 }
 
 template <int NB, int DT0, int DT1>

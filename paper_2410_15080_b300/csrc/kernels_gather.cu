@@ -79,6 +79,8 @@ __device__ __forceinline__ float2 entry(const GatherArgs& a, const int64_t* base
 // out[o] for o < n_out, one thread per entry (FP32 pair or FP64 output)
 template <int NOPS, bool F64OUT>
 __global__ void __launch_bounds__(256) k_gather_dense(const GatherArgs a, void* __restrict__ out) {
+  pdl_wait();
+  pdl_launch_dependents();
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < a.n_out; o += stride) {
     int64_t base[NOPS];
@@ -95,6 +97,8 @@ __global__ void __launch_bounds__(256) k_gather_dense(const GatherArgs a, void* 
 template <int NOPS, bool F64OUT>
 __global__ void __launch_bounds__(256) k_gather_block(const GatherArgs a, void* __restrict__ out) {
   __shared__ float2 red[8];
+  pdl_wait();
+  pdl_launch_dependents();
   for (uint32_t o = blockIdx.x; o < a.n_out; o += gridDim.x) {
     int64_t base[NOPS];
     offsets<NOPS>(o, a.out, base);
@@ -145,6 +149,8 @@ __global__ void __launch_bounds__(256) k_gather_split(const GatherArgs a, void* 
   __shared__ int64_t rowoff[kTR][NOPS];
   __shared__ int64_t koff[kTK][NOPS];
   __shared__ float2 tile[kTR][kTK + 1];
+  pdl_wait();
+  pdl_launch_dependents();
   const uint32_t n_rt = (a.n_rows + kTR - 1) / kTR;
   const uint32_t n_kt = (a.Kp + kTK - 1) / kTK;
   const int64_t piece = (int64_t)a.n_rows * a.Kp;
@@ -242,32 +248,22 @@ cudaError_t launch_n(const GatherArgs& a, void* out, int sm, cudaStream_t st) {
     const int64_t tiles = (int64_t)((a.n_rows + kTR - 1) / kTR) * ((a.Kp + kTK - 1) / kTK);
     if (tiles <= 0) return cudaSuccess;
     int64_t g = tiles < (int64_t)sm * 8 ? tiles : (int64_t)sm * 8;
-    if (a.mode == GW_SPLIT_BF16X3)
-      k_gather_split<NOPS, 0, 3><<<(int)g, 256, 0, st>>>(a, out);
-    else if (a.mode == GW_SPLIT_TF32X2)
-      k_gather_split<NOPS, 1, 2><<<(int)g, 256, 0, st>>>(a, out);
-    else
-      k_gather_split<NOPS, 1, 1><<<(int)g, 256, 0, st>>>(a, out);
-    return cudaGetLastError();
+    if (a.mode == GW_SPLIT_BF16X3) return launch_k(k_gather_split<NOPS, 0, 3>, dim3((unsigned)g), dim3(256), 0, st, a, out);
+    if (a.mode == GW_SPLIT_TF32X2) return launch_k(k_gather_split<NOPS, 1, 2>, dim3((unsigned)g), dim3(256), 0, st, a, out);
+    return launch_k(k_gather_split<NOPS, 1, 1>, dim3((unsigned)g), dim3(256), 0, st, a, out);
   }
   if (a.n_out == 0) return cudaSuccess;
   const bool f64 = a.mode == GW_DENSE_F64;
   const bool block_mode = a.n_loop >= 1024 && a.n_out <= (uint32_t)sm * 16;
   if (block_mode) {
     const uint32_t g = a.n_out < (uint32_t)sm * 16 ? a.n_out : (uint32_t)sm * 16;
-    if (f64)
-      k_gather_block<NOPS, true><<<g, 256, 0, st>>>(a, out);
-    else
-      k_gather_block<NOPS, false><<<g, 256, 0, st>>>(a, out);
-  } else {
-    int64_t g = ((int64_t)a.n_out + 255) / 256;
-    if (g > (int64_t)sm * 32) g = (int64_t)sm * 32;
-    if (f64)
-      k_gather_dense<NOPS, true><<<(int)g, 256, 0, st>>>(a, out);
-    else
-      k_gather_dense<NOPS, false><<<(int)g, 256, 0, st>>>(a, out);
+    if (f64) return launch_k(k_gather_block<NOPS, true>, dim3(g), dim3(256), 0, st, a, out);
+    return launch_k(k_gather_block<NOPS, false>, dim3(g), dim3(256), 0, st, a, out);
   }
-  return cudaGetLastError();
+  int64_t g = ((int64_t)a.n_out + 255) / 256;
+  if (g > (int64_t)sm * 32) g = (int64_t)sm * 32;
+  if (f64) return launch_k(k_gather_dense<NOPS, true>, dim3((unsigned)g), dim3(256), 0, st, a, out);
+  return launch_k(k_gather_dense<NOPS, false>, dim3((unsigned)g), dim3(256), 0, st, a, out);
 }
 
 }  // namespace

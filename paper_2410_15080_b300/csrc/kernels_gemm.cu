@@ -33,6 +33,9 @@
 // bit, lets in-flight copies and MMAs land, frees TMEM and returns.
 #include <cstdio>
 
+#include <cuda_bf16.h>
+
+#include "arith.cuh"
 #include "common.cuh"
 #include "kernels.h"
 
@@ -80,7 +83,11 @@ struct Layout {
   static constexpr int BAR_OFF = C::STAGES * STAGE;
   // full[S], empty[S], accfull[2], accempty[2], mma_done
   static constexpr int N_BARS = 2 * C::STAGES + 5;
-  static constexpr int SMEM = BAR_OFF + N_BARS * 8 + 16 + 1024;
+  // fused split (BF16x3 only): W table, per-tile digit tables, maxima
+  static constexpr int FUSE_OFF = (BAR_OFF + N_BARS * 8 + 16 + 15) / 16 * 16;
+  static constexpr int FUSE_W = (int)kFuseMaxW * 8;
+  static constexpr int FUSE_BYTES = PREC == 3 ? FUSE_W + 4 * 128 * 4 + 4 * 128 * 4 + 16 : 0;
+  static constexpr int SMEM = FUSE_OFF + FUSE_BYTES + 1024;
 };
 
 __device__ __forceinline__ void set_abort(volatile int* abort, uint32_t* status, uint32_t bit) {
@@ -103,11 +110,173 @@ __device__ __forceinline__ float2 pair_add(float2 p, float2 q) {
   return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, t.x)));
 }
 
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory"); }
+
+// offsets of x over digit modes: stride 0 -> *r, stride 1 -> *w
+__device__ __forceinline__ void digits(uint32_t x, const GModes& t, int* r, int* w) {
+  int64_t a = 0, b = 0;
+  for (int m = t.n - 1; m >= 0; --m) {
+    const uint32_t q = arith::fdiv(x, t.div[m]);
+    const uint32_t i = x - q * t.dim[m];
+    x = q;
+    a += (int64_t)i * t.stride[m][0];
+    b += (int64_t)i * t.stride[m][1];
+  }
+  *r = (int)a;
+  *w = (int)b;
+}
+
+// Epilogue that writes the consumer operand's BF16x3 pieces (GemmFuse).  Per
+// tile: digit tables of the tile's rows and columns, then pass 1 (X + Y times
+// W, maxima per consumer row and 64-entry k-block, exchanged through shared
+// memory), then pass 2 (pieces on each block's grid, stored).  Both passes
+// read the accumulator, which is handed back after pass 2.  Every epilogue
+// warp reaches every named barrier of a tile; a timeout (abort) ends the tile
+// loop for all of them after the second barrier.
+template <int PREC>
+__device__ void fused_epilogue(const GemmFuse& fz, const float2* fW, uint8_t* smem, uint32_t tmem, uint64_t* accfull,
+                               uint64_t* accempty, volatile int* abort, uint32_t* status, uint64_t limit_ns, int batch,
+                               int M, int N, int mt, int nt, int n_tiles, __nv_bfloat16* out) {
+  using L = Layout<PREC>;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ew = warp - 2, q = warp & 3, h = ew >> 2;
+  const int et = threadIdx.x - 64;
+  int* rm = reinterpret_cast<int*>(smem + L::FUSE_OFF + L::FUSE_W);
+  int* wm = rm + 128;
+  int* rn = wm + 128;
+  int* wn = rn + 128;
+  float* xmax = reinterpret_cast<float*>(wn + 128);  // [4][128]
+  // set only by epilogue threads, and only before a tile's last barrier, so
+  // every epilogue warp reads the same value after it
+  volatile int* epi_abort = reinterpret_cast<volatile int*>(xmax + 4 * 128);
+  if (et == 0) *epi_abort = 0;
+  const bool hasW = fz.w_size != 0;
+  const uint32_t Kp = fz.Kp;
+  int item = 0;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++item) {
+    const int ntile = (int)(t % nt);
+    const int r = t / nt;
+    const int mtile = (int)(r % mt);
+    const int b = (int)(r / mt);
+    epi_bar();  // the previous tile's readers of the tables are done
+    if (et < 128) {  // entries outside the matrix get offset 0 (never stored)
+      const int m = mtile * BM + et;
+      rm[et] = wm[et] = 0;
+      if (m < M) digits((uint32_t)m, fz.mmodes, &rm[et], &wm[et]);
+    } else if (et < 256) {
+      const int n = ntile * BN + (et - 128);
+      rn[et - 128] = wn[et - 128] = 0;
+      if (n < N) digits((uint32_t)n, fz.nmodes, &rn[et - 128], &wn[et - 128]);
+    }
+    int rb, wb;
+    digits((uint32_t)b, fz.bmodes, &rb, &wb);
+    epi_bar();
+    const int acc = item & 1;
+    const uint32_t aph = (uint32_t)((item >> 1) & 1);
+    const bool got = mbar_wait_bounded(&accfull[acc], aph, limit_ns, abort);
+    const bool all = __all_sync(0xffffffffu, got);
+    if (!all && lane == 0) {
+      set_abort(abort, status, ST_TIMEOUT_EPI);
+      *epi_abort = 1;
+    }
+    if (all) tc_fence_after();
+    const uint32_t tX = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 2 * BN + h * kEpiCols);
+    const int ml = q * 32 + lane;
+    const int m = mtile * BM + ml;
+    // pass 1: maxima of |X + Y| * W
+    float tmax = 0.f;
+#pragma unroll 1
+    for (int g = 0; g < kEpiCols / 8 && all; ++g) {
+      uint32_t rx[8], ry[8];
+      tmem_ld8_nowait(tX + g * 8, rx);
+      tmem_ld8_nowait(tX + BN + g * 8, ry);
+      tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int cl = h * kEpiCols + g * 8 + j;
+        float2 v = two_sum(__uint_as_float(rx[j]), __uint_as_float(ry[j]));
+        if (hasW) v = arith::mul_pair(v, fW[wb + wm[ml] + wn[cl]]);
+        float a = (m < M && ntile * BN + cl < N) ? fabsf(v.x) : 0.f;
+        if (fz.k_is_m) {  // k runs over the lanes: maximum per column over the warp
+#pragma unroll
+          for (int s = 16; s > 0; s >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, s));
+          if (lane == 0) xmax[q * 128 + cl] = a;
+        } else {
+          tmax = fmaxf(tmax, a);
+        }
+      }
+    }
+    if (!fz.k_is_m) xmax[h * 128 + ml] = tmax;
+    epi_bar();
+    if (*epi_abort) break;
+    // pass 2: pieces
+    if (fz.k_is_m) {
+#pragma unroll 1
+      for (int g = 0; g < kEpiCols / 8; ++g) {
+        uint32_t rx[8], ry[8];
+        tmem_ld8_nowait(tX + g * 8, rx);
+        tmem_ld8_nowait(tX + BN + g * 8, ry);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int cl = h * kEpiCols + g * 8 + j;
+          const int n = ntile * BN + cl;
+          if (m >= M || n >= N) continue;
+          float2 v = two_sum(__uint_as_float(rx[j]), __uint_as_float(ry[j]));
+          if (hasW) v = arith::mul_pair(v, fW[wb + wm[ml] + wn[cl]]);
+          const int qb = q & 2;  // the two lane quarters of this 64-entry k-block
+          const int E = arith::grid_exp(fmaxf(xmax[qb * 128 + cl], xmax[(qb + 1) * 128 + cl]));
+          float pc[3];
+          arith::grid_pieces(v, E, pc);
+          const int64_t dst = (int64_t)(rb + rn[cl]) * Kp + m;
+#pragma unroll
+          for (int p = 0; p < 3; ++p) out[p * fz.piece + dst] = __float2bfloat16_rn(pc[p]);
+        }
+      }
+    } else {
+      const int hb = h & ~1;  // the two column groups of this 64-entry k-block
+      const int E = arith::grid_exp(fmaxf(xmax[hb * 128 + ml], xmax[(hb + 1) * 128 + ml]));
+#pragma unroll 1
+      for (int g = 0; g < kEpiCols / 8; ++g) {
+        uint32_t rx[8], ry[8];
+        tmem_ld8_nowait(tX + g * 8, rx);
+        tmem_ld8_nowait(tX + BN + g * 8, ry);
+        tmem_wait_ld();
+        const int c0 = h * kEpiCols + g * 8;
+        const int n0 = ntile * BN + c0;
+        if (m >= M || n0 >= N) continue;
+        __nv_bfloat16 hp[3][8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float2 v = two_sum(__uint_as_float(rx[j]), __uint_as_float(ry[j]));
+          if (hasW) v = arith::mul_pair(v, fW[wb + wm[ml] + wn[c0 + j]]);
+          float pc[3];
+          arith::grid_pieces(v, E, pc);
+#pragma unroll
+          for (int p = 0; p < 3; ++p) hp[p][j] = __float2bfloat16_rn(pc[p]);
+        }
+        const int64_t dst = (int64_t)(rb + rm[ml]) * Kp + n0;
+        if (n0 + 8 <= N) {
+#pragma unroll
+          for (int p = 0; p < 3; ++p) *reinterpret_cast<uint4*>(out + p * fz.piece + dst) = *reinterpret_cast<const uint4*>(hp[p]);
+        } else {
+          for (int j = 0; j < 8 && n0 + j < N; ++j)
+#pragma unroll
+            for (int p = 0; p < 3; ++p) out[p * fz.piece + dst + j] = hp[p][j];
+        }
+      }
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&accempty[acc]);
+  }
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               float2* __restrict__ Cout, int batch, int M, int N, int K, int kc_blocks, uint32_t* status,
-              uint64_t limit_ns) {
+              uint64_t limit_ns, const __grid_constant__ GemmFuse fz) {
   using C = Cfg<PREC>;
   using L = Layout<PREC>;
   extern __shared__ uint8_t smem_raw[];
@@ -126,7 +295,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
   const int n_tiles = batch * mt * nt;  // host checks n_tiles < 2^31
   const int nkb = (K + C::KB - 1) / C::KB;
-  const int kc0 = kc_blocks > 0 ? kc_blocks : C::KC;
+  // the fused split takes the whole K in one accumulator chunk (host: K <= 1024)
+  const int kc0 = (PREC == 3 && fz.on) ? nkb : (kc_blocks > 0 ? kc_blocks : C::KC);
   const int kc = kc0 < nkb ? kc0 : nkb;
   const int nchunks = (nkb + kc - 1) / kc;
 
@@ -155,6 +325,27 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
+  float2* fW = reinterpret_cast<float2*>(smem + L::FUSE_OFF);
+  if (PREC == 3 && fz.on && fz.w_size) {  // product of the absorbed small leaves
+    for (uint32_t u = threadIdx.x; u < fz.w_size; u += blockDim.x) {
+      int64_t off[kMaxOps];
+      for (int j = 0; j < fz.nsmall; ++j) off[j] = 0;
+      uint32_t o = u;
+      for (int m = fz.wmodes.n - 1; m >= 0; --m) {
+        const uint32_t qq = arith::fdiv(o, fz.wmodes.div[m]);
+        const uint32_t i = o - qq * fz.wmodes.dim[m];
+        o = qq;
+        for (int j = 0; j < fz.nsmall; ++j) off[j] += (int64_t)i * fz.wmodes.stride[m][j];
+      }
+      float2 v = arith::load_any(fz.wptr[0], fz.wdt[0], off[0]);
+      for (int j = 1; j < fz.nsmall; ++j) v = arith::mul_pair(v, arith::load_any(fz.wptr[j], fz.wdt[j], off[j]));
+      fW[u] = v;
+    }
+    __syncthreads();
+  }
+  // operands and the output buffer belong to earlier kernels of the stream
+  pdl_wait();
+  pdl_launch_dependents();
 
   if (warp == 0) {
     if (lane == 0) {
@@ -257,6 +448,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // -------------------------------------------------------------- epilogue
+    if (PREC == 3 && fz.on) {
+      fused_epilogue<PREC>(fz, fW, smem, tmem, accfull, accempty, abort, status, limit_ns, batch, M, N, mt, nt,
+                           n_tiles, reinterpret_cast<__nv_bfloat16*>(Cout));
+    } else {
     // warp w owns TMEM lane quarter (w % 4) and column group h of the tile;
     // per chunk each thread loads its row's kEpiCols columns of X and Y,
     // hands the accumulator back to the MMA warp, and stores X + Y as an
@@ -317,6 +512,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
+    }
   }
 
   tc_fence_before();
@@ -334,9 +530,9 @@ cudaError_t launch_t(const GemmArgs& a, int sm_count, cudaStream_t st) {
   const long long tiles = (long long)a.batch * ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
   if (tiles <= 0) return cudaSuccess;
   const int grid = (int)(tiles < sm_count ? tiles : sm_count);
-  k_gemm_tc<PREC><<<grid, kThreads, L::SMEM, st>>>(a.tmA, a.tmB, (float2*)a.C, a.batch, a.M, a.N, a.K, a.kc_blocks,
-                                                     a.status, a.limit_ns);
-  return cudaGetLastError();
+  if (a.fuse.on && (PREC != 3 || a.fuse.w_size > kFuseMaxW)) return cudaErrorInvalidValue;
+  return launch_k(k_gemm_tc<PREC>, dim3(grid), dim3(kThreads), (size_t)L::SMEM, st, a.tmA, a.tmB, (float2*)a.C,
+                  a.batch, a.M, a.N, a.K, a.kc_blocks, a.status, a.limit_ns, a.fuse);
 }
 
 // A single warp waits on an mbarrier that nothing completes, with the same

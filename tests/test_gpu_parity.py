@@ -274,3 +274,29 @@ def test_bf16x3_with_magnitudes_varying_along_k_and_rows(kc, monkeypatch):
     got, st = contract_gpu(net, prec="bf16x3")
     assert st["n_tensor_core_steps"] == 1
     assert rel_err(got, np.matmul(A, B).ravel()) <= REL_TOL
+
+
+@pytest.mark.parametrize("mode", ["off", "k_along_columns", "k_along_rows"])
+def test_epilogue_written_operand_pieces(mode, monkeypatch):
+    """A GEMM whose result is the next GEMM's operand writes that operand's
+    BF16x3 pieces from its epilogue, with the next K along the tile's columns
+    (the layout the lowering prefers) or, with that preference off, along its
+    rows; with the fusion switched off every operand goes through a split
+    launch.  All match the oracle."""
+    monkeypatch.setenv("QTPU_NO_FUSE", "1" if mode == "off" else "0")
+    monkeypatch.setenv("QTPU_FUSE_KEEP_LAYOUT", "1" if mode == "k_along_rows" else "0")
+    from paper_2410_15080_b300.htn import lowering_text
+    seen = set()
+    for net in (synth.ring_htn(n_sub=5, gates_per_edge=2, wires_per_edge=1, k=5, seed=23),
+                synth.ring_htn(n_sub=4, gates_per_edge=2, wires_per_edge=1, k=3, seed=6),
+                synth.ring_htn(seed=3)):
+        t = lowering_text(net.inds(), net.dims(), net.output)
+        n_fused = int(t.splitlines()[-1].split("fused_splits=")[1].split()[0])
+        assert (n_fused > 0) == (mode != "off"), t.splitlines()[-1]
+        seen |= {w for l in t.splitlines() for w in l.split() if w.startswith("k=")}
+        got, _ = contract_gpu(net, prec="bf16x3")
+        assert rel_err(got, oracle_value(net)) <= REL_TOL
+    if mode == "k_along_columns":
+        assert seen == {"k=N"}
+    if mode == "k_along_rows":
+        assert "k=M" in seen
