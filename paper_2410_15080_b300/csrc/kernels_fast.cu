@@ -167,7 +167,7 @@ __device__ __forceinline__ void entry_fan(const GatherArgs& a, const float2* W, 
 
 // ------------------------------------------------------------ dense output
 template <int NB, int DT0, int DT1, bool HW, bool F64OUT>
-__global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __restrict__ out) {
+__global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __restrict__ out, int lanes_log2) {
   using O = Op<NB, DT0, DT1, HW>;
   extern __shared__ float2 W[];  // w_size entries (dynamic shared memory)
   __shared__ int64_t lt[kLoopTab][O::NOPS];
@@ -176,6 +176,45 @@ __global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __
   __syncthreads();
   pdl_wait();
   pdl_launch_dependents();
+  if (lanes_log2 > 0) {
+    // few outputs with a short tabulated loop: 2^lanes_log2 consecutive lanes
+    // share an output, each summing every 2^lanes_log2-th term, then the
+    // partial sums meet by compensated shuffles
+    const uint32_t S = 1u << lanes_log2;
+    const uint64_t total = (uint64_t)a.n_out << lanes_log2;
+    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < total; i0 += step) {
+      const uint64_t i = i0 + (threadIdx.x & 31u);
+      const uint32_t o = (uint32_t)(i >> lanes_log2), sub = (uint32_t)(i & (S - 1));
+      Acc acc;
+      if (o < a.n_out) {
+        int64_t base[O::NOPS];
+        offsets<O::NOPS>(o, a.out, base);
+#pragma unroll 2
+        for (uint32_t l = sub; l < a.n_loop; l += S) {
+          int64_t off[O::NOPS];
+#pragma unroll
+          for (int j = 0; j < O::NOPS; ++j) off[j] = base[j] + lt[l][j];
+          acc.add(O::term(a, W, off));
+        }
+      }
+      float2 v = acc.get();
+      for (uint32_t d = S >> 1; d > 0; d >>= 1) {
+        Acc t;
+        t.hi = v.x;
+        t.lo = v.y;
+        t.add(make_float2(__shfl_xor_sync(0xffffffffu, v.x, d), __shfl_xor_sync(0xffffffffu, v.y, d)));
+        v = t.get();
+      }
+      if (o < a.n_out && sub == 0) {
+        if (F64OUT)
+          ((double*)out)[o] = (double)v.x + (double)v.y;
+        else
+          ((float2*)out)[o] = v;
+      }
+    }
+    return;
+  }
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < a.n_out; o += stride) {
     int64_t base[O::NOPS];
@@ -532,16 +571,21 @@ cudaError_t split_dt(const GatherArgs& a, void* out, int sm, cudaStream_t st) {
 template <int NB, int DT0, int DT1, bool HW>
 cudaError_t dense_dt(const GatherArgs& a, void* out, int sm, cudaStream_t st) {
   if (a.n_out == 0) return cudaSuccess;
-  int64_t g = ((int64_t)a.n_out + 255) / 256;
+  // lanes per output: up to 8 while the SMs are not yet full and each lane
+  // keeps at least 4 terms of a tabulated loop
+  int lg = 0;
+  if (a.loop.n > 0 && a.n_loop <= kLoopTab)
+    while (lg < 3 && (4u << (lg + 1)) <= a.n_loop && ((uint64_t)a.n_out << (lg + 1)) <= (uint64_t)sm * 4096) ++lg;
+  int64_t g = (((int64_t)a.n_out << lg) + 255) / 256;
   if (g > (int64_t)sm * 8) g = (int64_t)sm * 8;
   const size_t sm_bytes = HW ? a.w_size * sizeof(float2) : 0;
   cudaError_t e = cudaSuccess;
   if (a.mode == GW_DENSE_F64) {
     if (sm_bytes > 40960) e = allow_smem(k_dense_fast<NB, DT0, DT1, HW, true>);
-    if (e == cudaSuccess) e = launch_k(k_dense_fast<NB, DT0, DT1, HW, true>, dim3((unsigned)g), dim3(256), sm_bytes, st, a, out);
+    if (e == cudaSuccess) e = launch_k(k_dense_fast<NB, DT0, DT1, HW, true>, dim3((unsigned)g), dim3(256), sm_bytes, st, a, out, lg);
   } else {
     if (sm_bytes > 40960) e = allow_smem(k_dense_fast<NB, DT0, DT1, HW, false>);
-    if (e == cudaSuccess) e = launch_k(k_dense_fast<NB, DT0, DT1, HW, false>, dim3((unsigned)g), dim3(256), sm_bytes, st, a, out);
+    if (e == cudaSuccess) e = launch_k(k_dense_fast<NB, DT0, DT1, HW, false>, dim3((unsigned)g), dim3(256), sm_bytes, st, a, out, lg);
   }
   return e;
 }
