@@ -70,7 +70,7 @@ def measured_traffic(workload: str, kclass: str):
     return e["bytes_per_launch"]
 
 
-def make_network(workload: str, shape: str = "8x1024x1024x1024"):
+def make_network(workload: str, shape: str = "8x1024x1024x1024", observables: int = 64):
     import synth
     if workload == "gemm":
         b, m, n, k = (int(x) for x in shape.split("x"))
@@ -82,10 +82,10 @@ def make_network(workload: str, shape: str = "8x1024x1024x1024"):
     if workload == "mid":
         return synth.ring_htn(), {}
     if workload == "100q":
-        return synth.ring_chords_htn(), {"max_intermediate_bytes": 8 << 30, "n_slices": 1024, "slice_dim": 4,
-                                         "n_candidates": 256}
+        return synth.ring_chords_htn(k=observables), {"max_intermediate_bytes": 8 << 30, "n_slices": 1024,
+                                                      "slice_dim": 4, "n_candidates": 256}
     if workload == "100q-free":
-        return synth.ring_chords_htn(), {"max_intermediate_bytes": 8 << 30, "n_candidates": 256}
+        return synth.ring_chords_htn(k=observables), {"max_intermediate_bytes": 8 << 30, "n_candidates": 256}
     raise SystemExit(f"unknown workload {workload}")
 
 
@@ -363,7 +363,7 @@ def run_ours(args, rank, world):
     from paper_2410_15080_b300.htn import QTPU_CT, QTPU_QT
 
     dev = torch.device("cuda", torch.cuda.current_device())
-    net, plan_kw = make_network(args.workload, args.shape)
+    net, plan_kw = make_network(args.workload, args.shape, args.observables)
     tensors = [(t.inds, torch.from_numpy(np.ascontiguousarray(t.data)).to(dev), QTPU_CT if t.kind == "CT" else QTPU_QT)
                for t in net.tensors]
     h = from_network(tensors, net.output, prec=args.prec, **plan_kw)
@@ -515,7 +515,8 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload] + (f" ({args.shape})" if args.workload == "gemm" else ""),
+        "config": {"workload": WORKLOADS[args.workload] + (f" ({args.shape})" if args.workload == "gemm" else "")
+                   + (f" (k = {args.observables} observables)" if args.workload.startswith("100q") and args.observables != 64 else ""),
                    "sharding": ("slices split over ranks, one all-reduce of the output per step" if sub
                                 else "independent replicas") if world > 1 else "single GPU",
                    "flops_per_step": flops, "prec": args.prec,
@@ -548,6 +549,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--slices-timed", type=int, default=16, help="100q: slices contracted per timed step")
     ap.add_argument("--shape", default="8x1024x1024x1024", help="gemm workload: batch x M x N x K")
+    ap.add_argument("--observables", type=int, default=64,
+                    help="100q workloads: size k of the observable index (64 = the benchmark; smaller for ncu captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

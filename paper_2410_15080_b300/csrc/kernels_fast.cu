@@ -532,6 +532,137 @@ __global__ void __launch_bounds__(256) k_split_fast(const GatherArgs a, void* __
   }
 }
 
+// ------------------------------------------------------------ split, one term
+// The same tiles as k_split_fast for entries of one term (a large operand,
+// times W when small factors are absorbed), software-pipelined: a block loads
+// its next tile into registers before it writes the current one, so the load
+// latency overlaps the piece arithmetic, the stores and the barriers.  The
+// index tables of the next tile are built during the current write.
+template <int DT0, bool HW, int KIND, int NP>
+__global__ void __launch_bounds__(256) k_split_pipe(const GatherArgs a, void* __restrict__ dst) {
+  constexpr int NOPS = 1 + (HW ? 1 : 0);
+  constexpr int PER = kTR * kTK / 256;
+  extern __shared__ float2 W[];  // w_size entries (dynamic shared memory)
+  __shared__ int64_t rowoff[2][kTR][NOPS];
+  __shared__ int64_t koff[2][kTK][NOPS];
+  __shared__ float2 tile[kTR][kTK + 1];
+  if (HW) build_w(a, W);
+  __syncthreads();
+  pdl_wait();
+  pdl_launch_dependents();
+  const uint32_t n_rt = (a.n_rows + kTR - 1) / kTR;
+  const uint32_t n_kt = (a.Kp + kTK - 1) / kTK;
+  const uint32_t n_tiles = n_rt * n_kt;
+  const int64_t piece = (int64_t)a.n_rows * a.Kp;
+  const int tid = threadIdx.x;
+  auto tables = [&](uint32_t t, int buf) {
+    const uint32_t rt = t / n_kt, kt = t - rt * n_kt;
+    const uint32_t r0 = rt * kTR, k0 = kt * kTK;
+    if (tid < kTR) {
+      int64_t o[NOPS];
+      offsets<NOPS>(min(r0 + tid, a.n_rows - 1), a.out, o);
+#pragma unroll
+      for (int j = 0; j < NOPS; ++j) rowoff[buf][tid][j] = o[j];
+    } else if (tid < kTR + kTK) {
+      int64_t o[NOPS];
+      offsets<NOPS>(min(k0 + (tid - kTR), a.K - 1), a.kmodes, o);
+#pragma unroll
+      for (int j = 0; j < NOPS; ++j) koff[buf][tid - kTR][j] = o[j];
+    }
+  };
+  float2 v[PER];
+  auto load = [&](uint32_t t, int buf) {
+    const uint32_t rt = t / n_kt, kt = t - rt * n_kt;
+    const uint32_t r0 = rt * kTR, k0 = kt * kTK;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + u * 256;
+      const int r = a.row_fast ? e % kTR : e / kTK;
+      const int k = a.row_fast ? e / kTR : e % kTK;
+      v[u] = r0 + r < a.n_rows && k0 + k < a.K ? load_pair<DT0>(a.ptr[0], rowoff[buf][r][0] + koff[buf][k][0])
+                                                : make_float2(0.f, 0.f);
+    }
+  };
+  auto stage = [&](int buf) {  // registers -> tile (times W)
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + u * 256;
+      const int r = a.row_fast ? e % kTR : e / kTK;
+      const int k = a.row_fast ? e / kTR : e % kTK;
+      float2 x = v[u];
+      if (HW) x = mul_pair(x, W[rowoff[buf][r][NOPS - 1] + koff[buf][k][NOPS - 1]]);
+      tile[r][k] = x;
+    }
+  };
+  uint32_t t = blockIdx.x;
+  if (t >= n_tiles) return;
+  tables(t, 0);
+  __syncthreads();
+  load(t, 0);
+  stage(0);
+  int buf = 0;
+  if (t + gridDim.x < n_tiles) tables(t + gridDim.x, 1);
+  __syncthreads();
+  for (;;) {
+    const uint32_t nt = t + gridDim.x;
+    const bool more = nt < n_tiles;
+    if (more) load(nt, buf ^ 1);  // in flight during this tile's write
+    const uint32_t rt = t / n_kt, kt = t - rt * n_kt;
+    const uint32_t r0 = rt * kTR, k0 = kt * kTK;
+    {
+      const int r = tid >> 3, kk = (tid & 7) * 8;
+      const uint32_t row = r0 + r, kb = k0 + kk;
+      const bool in = row < a.n_rows && kb < a.Kp;
+      if (KIND == 0) {
+        float m = 0.f;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) m = fmaxf(m, fabsf(tile[r][kk + e].x));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+        const int E = grid_exp(m);
+        if (in) {
+          const int64_t base = (int64_t)row * a.Kp + kb;
+          __nv_bfloat16 h[3][8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            float pc[3];
+            grid_pieces(tile[r][kk + e], E, pc);
+#pragma unroll
+            for (int p = 0; p < 3; ++p) h[p][e] = __float2bfloat16_rn(pc[p]);  // exact
+          }
+          __nv_bfloat16* d = (__nv_bfloat16*)dst;
+#pragma unroll
+          for (int p = 0; p < 3; ++p) *(uint4*)(d + p * piece + base) = *(const uint4*)h[p];
+        }
+      } else if (in) {
+        const int64_t base = (int64_t)row * a.Kp + kb;
+        float f[NP][8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const float2 x = tile[r][kk + e];
+          const float t0 = tf32_rna(x.x);
+          f[0][e] = t0;
+          if (NP > 1) f[NP - 1][e] = tf32_rna(__fadd_rn(__fsub_rn(x.x, t0), x.y));
+        }
+        float* d = (float*)dst;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          *(float4*)(d + p * piece + base) = *(const float4*)&f[p][0];
+          *(float4*)(d + p * piece + base + 4) = *(const float4*)&f[p][4];
+        }
+      }
+    }
+    if (!more) break;
+    __syncthreads();  // the tile and this tile's tables are consumed
+    stage(buf ^ 1);
+    if (nt + gridDim.x < n_tiles) tables(nt + gridDim.x, buf);
+    __syncthreads();
+    buf ^= 1;
+    t = nt;
+  }
+}
+
 // dynamic shared memory above the 48 KB default needs a one-time opt-in
 template <typename K>
 cudaError_t allow_smem(K kernel) {
@@ -563,6 +694,21 @@ cudaError_t split_dt(const GatherArgs& a, void* out, int sm, cudaStream_t st) {
   // the table once
   const int64_t cap = HW && a.w_size > 1024 ? (int64_t)sm * 4 : (int64_t)sm * 8;
   const int g = (int)(tiles < cap ? tiles : cap);
+  if (a.loop.n == 0 && !(HW && a.fan)) {  // one term per entry: the pipelined kernel
+    const size_t sm_bytes = HW ? a.w_size * sizeof(float2) : 0;
+    auto go = [&](auto kernel) -> cudaError_t {
+      if (sm_bytes > 16384) {
+        cudaError_t e = allow_smem(kernel);
+        if (e != cudaSuccess) return e;
+      }
+      // ~64 registers a thread: 4 blocks of 256 per SM stay resident
+      const int gp = (int)(tiles < (int64_t)sm * 4 ? tiles : (int64_t)sm * 4);
+      return launch_k(kernel, dim3(gp), dim3(256), sm_bytes, st, a, out);
+    };
+    if (a.mode == GW_SPLIT_BF16X3) return go(k_split_pipe<DT0, HW, 0, 3>);
+    if (a.mode == GW_SPLIT_TF32X2) return go(k_split_pipe<DT0, HW, 1, 2>);
+    return go(k_split_pipe<DT0, HW, 1, 1>);
+  }
   if (HW && a.fan && a.fan_f == 4) return split_f<DT0, HW, 4>(a, out, g, st);
   if (HW && a.fan && a.fan_f == 2) return split_f<DT0, HW, 2>(a, out, g, st);
   return split_f<DT0, HW, 1>(a, out, g, st);
