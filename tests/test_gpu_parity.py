@@ -300,3 +300,21 @@ def test_epilogue_written_operand_pieces(mode, monkeypatch):
         assert seen == {"k=N"}
     if mode == "k_along_rows":
         assert "k=M" in seen
+
+
+def test_operand_split_with_a_summed_wire_index():
+    """A QT with a wire CT folded in over a summed index (4 terms per operand
+    entry, no fan-out) goes through the pipelined split with its loop table."""
+    rng = np.random.default_rng(31)
+    b, m, n, y = 8, 160, 144, 36
+    A = rng.uniform(-1, 1, (b, m, 4, y))
+    B = rng.uniform(-1, 1, (b, n, 4, y))
+    net = synth.HTN([synth.Tensor("QT", (0, 1, 4, 3), A), synth.Tensor("CT", (4, 5), synth.WIRE_CT.copy()),
+                     synth.Tensor("QT", (0, 2, 5, 3), B)], (0, 1, 2))
+    from paper_2410_15080_b300.htn import lowering_text
+    t = lowering_text(net.inds(), net.dims(), net.output)
+    assert any(" split " in l and " loop=4 " in l and " fan=1 " in l for l in t.splitlines()), t
+    got, st = contract_gpu(net, prec="bf16x3")
+    assert st["n_tensor_core_steps"] == 1
+    ref = np.einsum("bmxy,xk,bnky->bmn", A, synth.WIRE_CT, B).ravel()
+    assert rel_err(got, ref) <= REL_TOL
