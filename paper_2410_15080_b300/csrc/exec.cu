@@ -475,6 +475,29 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       (is_small ? small : big).push_back(t);
     }
     if (big.empty() || big.size() > 2) return false;
+    auto w_entries = [&](const std::vector<int>& sm) {
+      Inds u;
+      for (int t : sm)
+        for (int64_t i : live_inds[t])
+          if (!contains(u, i)) u.push_back(i);
+      return prod(u);
+    };
+    // a W table too large for shared memory: read the small leaf whose
+    // removal shrinks it most directly, as a second large operand
+    if (big.size() == 1 && small.size() > 1 && w_entries(small) > (double)kMaxW) {
+      size_t best = 0;
+      double best_w = 0;
+      for (size_t j = 0; j < small.size(); ++j) {
+        std::vector<int> rest = small;
+        rest.erase(rest.begin() + j);
+        const double w = w_entries(rest);
+        if (j == 0 || w < best_w) best = j, best_w = w;
+      }
+      if (best_w <= (double)kMaxW && (dt_of(small[best]) == DT_F64 || dt_of(small[best]) == DT_F32X2)) {
+        big.push_back(small[best]);
+        small.erase(small.begin() + best);
+      }
+    }
     for (int t : big)
       if (dt_of(t) != DT_F64 && dt_of(t) != DT_F32X2) return false;
     Inds U;
@@ -1182,6 +1205,14 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     }
   }
   ex->side_bytes = side_total;
+  // large W tables are computed once per launch into a buffer of their own
+  ex->wbuf_bytes = 0;
+  for (auto& L : ex->launches)
+    if (L.kind == LK_GATHER && L.has_fast && L.gf.w_size >= kGlobalW && !L.gf.dot &&
+        (L.gf.mode == GW_DENSE_PAIR || L.gf.mode == GW_DENSE_F64)) {
+      L.wg_off = (int64_t)ex->wbuf_bytes;
+      ex->wbuf_bytes += align_up((size_t)L.gf.w_size * sizeof(float2), 256);
+    }
   ex->arena_bytes = std::max<size_t>(arena.top, 256);
   ex->split_a_bytes = split_need_a;
   ex->split_bytes = split_need_a + split_need_b;
@@ -1211,7 +1242,8 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
   if (!dalloc((void**)&ex->arena, ex->arena_bytes) || !dalloc((void**)&ex->splitbuf, ex->split_bytes) ||
       !dalloc((void**)&ex->partial, (size_t)ex->n_slices * std::max<int64_t>(ex->final_size, 1) * 8) ||
       !dalloc((void**)&ex->status, 16) || !dalloc((void**)&ex->out_stage, (size_t)R.g.n_out * 8 + 8) ||
-      !dalloc((void**)&ex->dot_scratch, dot_scratch_entries(ex->sm_count) * sizeof(float2))) {
+      !dalloc((void**)&ex->dot_scratch, dot_scratch_entries(ex->sm_count) * sizeof(float2)) ||
+      !dalloc((void**)&ex->wbuf, ex->wbuf_bytes)) {
     exec_free(ex);
     return fail(QTPU_ENOMEM, "device workspace allocation failed");
   }
@@ -1414,6 +1446,7 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
         GatherArgs g = L.gf;
         for (int j = 0; j < g.nops; ++j) g.ptr[j] = src_ptr(L.gf_src[j]);
         g.scratch = ex->dot_scratch;
+        if (L.wg_off >= 0) g.wg = reinterpret_cast<float2*>(ex->wbuf + L.wg_off);
         cudaError_t e = launch_gather_fast(g, dst_ptr(L.dst, s), ex->sm_count, st);
         if (e != cudaErrorNotSupported) return e;
         cudaGetLastError();
@@ -1575,6 +1608,8 @@ void exec_free(Executor* ex) {
   if (ex->out_stage) cudaFree(ex->out_stage);
   if (ex->dot_scratch) cudaFree(ex->dot_scratch);
   ex->dot_scratch = nullptr;
+  if (ex->wbuf) cudaFree(ex->wbuf);
+  ex->wbuf = nullptr;
   ex->arena = ex->splitbuf = ex->partial = nullptr;
   ex->status = nullptr;
   ex->out_stage = nullptr;

@@ -53,6 +53,8 @@ struct Launch {
   uint32_t opnd_kp[2] = {0, 0};
   // LK_GEMM with gemm.fuse.on: the small leaves of the fused W (patched per slice)
   int fuse_src[kMaxOps] = {};
+  // fast gather/split with a large W table: its byte offset in Executor::wbuf
+  int64_t wg_off = -1;
 };
 
 struct Profiler {
@@ -92,6 +94,8 @@ struct Executor {
   uint32_t* status = nullptr;
   double* out_stage = nullptr;   // staging buffer of the host-buffer entry point
   float2* dot_scratch = nullptr; // per-chunk sums of the dot-reduction kernel
+  uint8_t* wbuf = nullptr;       // precomputed large W tables, one region per launch
+  size_t wbuf_bytes = 0;
   int n_tc_steps = 0;
   int n_fused_steps = 0;         // absorption steps folded into a consumer
   int n_fused_splits = 0;        // operand splits written by the producing GEMM's epilogue
@@ -112,7 +116,7 @@ struct Executor {
   std::vector<cudaEvent_t> side_ev;  // one per side launch, plus fork and join
   double planned_side_bytes = 0;
   size_t workspace_bytes() const {
-    return arena_bytes + split_bytes + side_bytes + (size_t)n_slices * final_size * 8;
+    return arena_bytes + split_bytes + side_bytes + wbuf_bytes + (size_t)n_slices * final_size * 8;
   }
 };
 

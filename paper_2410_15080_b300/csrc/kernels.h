@@ -67,6 +67,8 @@ struct GatherArgs {
   int nops = 1;
   int mode = GW_DENSE_PAIR;
   const void* ptr[kMaxOps] = {};
+  float2* wg = nullptr;  // large W (fast dense path): computed once per launch into
+                         // this global buffer by a small kernel, then copied by every block
   int dt[kMaxOps] = {};
   GModes out, loop, kmodes;
   uint32_t n_out = 1, n_loop = 1;        // dense modes
@@ -101,6 +103,7 @@ cudaError_t launch_gather(const GatherArgs& a, void* out, int sm_count, cudaStre
 // The same computation through the typed fast kernels (shared-memory table of
 // the small factors); cudaErrorNotSupported when no instantiation fits.
 constexpr uint32_t kMaxW = 4096;
+constexpr uint32_t kGlobalW = 1024;  // dense-gather W tables from this size go through GatherArgs::wg
 cudaError_t launch_gather_fast(const GatherArgs& a, void* out, int sm_count, cudaStream_t st);
 
 cudaError_t launch_contract(const void* A, int dtA, const void* B, int dtB, double* out,

@@ -21,6 +21,37 @@ namespace {
 using namespace arith;
 
 // W[u] = prod over the small operands of their entry at u (u dense over a.wmodes)
+// entry u of W
+__device__ __forceinline__ float2 w_entry(const GatherArgs& a, uint32_t u) {
+  const int nsmall = a.nops - a.nbig;
+  int64_t off[kMaxOps];
+  for (int j = 0; j < nsmall; ++j) off[j] = 0;
+  uint32_t o = u;
+  for (int m = a.wmodes.n - 1; m >= 0; --m) {
+    const uint32_t q = fdiv(o, a.wmodes.div[m]);
+    const uint32_t i = o - q * a.wmodes.dim[m];
+    o = q;
+    for (int j = 0; j < nsmall; ++j) off[j] += (int64_t)i * a.wmodes.stride[m][j];
+  }
+  float2 v = load_any(a.ptr[a.nbig], a.dt[a.nbig], off[0]);
+  for (int j = 1; j < nsmall; ++j) v = mul_pair(v, load_any(a.ptr[a.nbig + j], a.dt[a.nbig + j], off[j]));
+  return v;
+}
+
+// a large W, once per launch: one entry per thread
+__global__ void __launch_bounds__(256) k_build_w(const GatherArgs a, float2* __restrict__ wg) {
+  pdl_wait();
+  pdl_launch_dependents();
+  const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < a.w_size) wg[u] = w_entry(a, u);
+}
+
+// W from the buffer filled by the preceding k_build_w launch
+__device__ __forceinline__ void copy_w(const GatherArgs& a, float2* W) {
+  pdl_wait();
+  for (uint32_t u = threadIdx.x; u < a.w_size; u += blockDim.x) W[u] = a.wg[u];
+}
+
 __device__ void build_w(const GatherArgs& a, float2* W) {
   const int nsmall = a.nops - a.nbig;
   for (uint32_t u = threadIdx.x; u < a.w_size; u += blockDim.x) {
@@ -171,7 +202,12 @@ __global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __
   using O = Op<NB, DT0, DT1, HW>;
   extern __shared__ float2 W[];  // w_size entries (dynamic shared memory)
   __shared__ int64_t lt[kLoopTab][O::NOPS];
-  if (HW) build_w(a, W);
+  if (HW) {
+    if (a.wg)
+      copy_w(a, W);
+    else
+      build_w(a, W);
+  }
   build_loop_tab<O::NOPS>(a, lt);
   __syncthreads();
   pdl_wait();
@@ -749,6 +785,10 @@ cudaError_t launch_gather_fast(const GatherArgs& a, void* out, int sm, cudaStrea
   if (a.nbig < 1 || a.nbig > 2 || a.w_size > kMaxW) return cudaErrorNotSupported;
   for (int j = 0; j < a.nbig; ++j)
     if (!typed(a.dt[j])) return cudaErrorNotSupported;
+  if (a.wg && a.w_size) {
+    const cudaError_t e = launch_k(k_build_w, dim3((a.w_size + 255) / 256), dim3(256), 0, st, a, a.wg);
+    if (e != cudaSuccess) return e;
+  }
   const bool split = a.mode == GW_SPLIT_BF16X3 || a.mode == GW_SPLIT_TF32X2 || a.mode == GW_SPLIT_TF32;
   if (split) {
     if (a.nbig != 1) return cudaErrorNotSupported;
