@@ -1183,12 +1183,19 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
   size_t side_total = 0;
   ex->n_side = 0;
   if (side_ok) {
+    bool first = true;
     for (size_t i = 0; i < ex->launches.size(); ++i) {
       Launch& L = ex->launches[i];
       if (L.kind != LK_GATHER || (L.dst != DST_SPLIT_A && L.dst != DST_SPLIT_B)) continue;
       bool leaves_only = true;
       for (int j = 0; j < L.nsrc; ++j) leaves_only = leaves_only && L.src[j] < nl;
       if (!leaves_only) continue;
+      // the first one stays on the main stream: the first GEMM's two leaf
+      // splits then run side by side instead of one after the other
+      if (first) {
+        first = false;
+        continue;
+      }
       const GatherArgs& g = L.has_fast ? L.gf : L.g;
       const size_t bytes = align_up((size_t)np * g.n_rows * g.Kp * es, 1024);
       if (side_total + bytes > ((size_t)4 << 30)) continue;
