@@ -190,3 +190,19 @@ def test_mid_ring_lowering_writes_operands_from_gemm_epilogues():
     assert "launches_per_slice=15" in summary, summary
     # each producer stores the next step's K as its column (N) group
     assert sum("writes-pieces k=N" in l for l in t.splitlines()) == 5
+
+
+def test_100q_absorptions_lower_to_the_typed_fast_path():
+    """In the 100-qubit plan, a QT absorbs five small CTs whose joint index
+    table would exceed the shared-memory limit; one CT is then read as a
+    second large operand and the step takes the typed fast path (its W table
+    is computed once per launch)."""
+    import synth
+    from paper_2410_15080_b300.htn import lowering_text
+    net = synth.ring_chords_htn(materialize=False)
+    t = lowering_text(net.inds(), net.dims(), net.output, max_intermediate_bytes=8 << 30, n_slices=1024,
+                      slice_dim=4, n_candidates=256)
+    lines = [l for l in t.splitlines() if l.startswith("launch") and " contract " in l and " ops=6 " in l]
+    assert lines, t
+    assert all(" fast " in l and " big=2 " in l for l in lines), lines
+    assert all(" generic " not in l for l in t.splitlines())
