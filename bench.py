@@ -1,20 +1,28 @@
 """Benchmark of the h-TN contraction hot path (one JSON line on stdout).
 
-Default workload: the mid-size 60-qubit ring h-TN (8 QTs of [64][144][144]
-FP64, 16 gate cuts + 8 wire cuts, 64 observables) contracted through the
-C ABI with BF16x3 tensor-core GEMMs.  Reported next to it:
+Default workload: the 100-qubit ring + chords h-TN (12 QTs, 28 gate cuts, 12
+wire cuts, 64 observables, 2 GB of FP64 leaves), planned with a peak
+intermediate <= 8 GB over 4^5 = 1024 wire-index slices and contracted in
+full -- every timed step is one complete qtpu_htn_contract over all 1024
+slices -- through the C ABI with BF16x3 tensor-core GEMMs.  Reported next to
+it:
   * the same plan executed step by step with torch FP64 bmm (the plain FP64
-    GPU path), timed the same way;
-  * the FP64 CPU oracle on the host cores (``cpu_baseline``);
+    GPU path), timed on a fixed subset of slices and extrapolated;
+  * the FP64 CPU oracle on the host cores (``cpu_baseline``), on the
+    restricted output k in {0, 1} (2 of the 64 observables), which also gives
+    the relative error of those two output entries;
   * the end-to-end form through ``qtpu_htn_contract_host`` (host buffers,
-    copies inside the timed region);
+    the 2 GB upload and the result download inside the timed region);
   * the roofline of the dominant kernel class, from CUDA events recorded by
     the library around every launch (a separate pass after the timed one);
   * SM clocks sampled with nvidia-smi during the timed region.
+``--workload mid`` selects the mid-size 60-qubit ring (8 QTs, 16 gate + 8
+wire cuts), whose oracle runs in full.
 
-``--impl reference`` times the FP64 CPU oracle alone (the reference arm).
-Multi-GPU (torchrun): every rank contracts its own copy of the workload
-(independent replicas, weak scaling); the time is the max over ranks.
+``--impl reference`` times the FP64 CPU oracle alone (the reference arm) on
+the same workload, metric and unit.  Multi-GPU (torchrun): every rank
+contracts its own copy of the workload (independent replicas, weak scaling,
+no collective on the data path); the time is the max over ranks.
 """
 from __future__ import annotations
 
@@ -34,7 +42,8 @@ sys.path.insert(0, ROOT)
 METRIC = "h-TN contract TFLOP/s & %peak vs plain FP64 GPU path at rel err ≤1e-6"
 WORKLOADS = {
     "mid": "mid-size 60-qubit ring h-TN: 8 QTs [k=64][6,6,4][6,6,4] FP64, 16 gate + 8 wire cuts, 32 tensors",
-    "100q": "100-qubit ring+chords h-TN: 12 QTs, 28 gate + 12 wire cuts, k=64, sliced over 4^5 wire-index values, "
+    "100q": "100-qubit ring+chords h-TN: 12 QTs, 28 gate + 12 wire cuts, k=64, 2 GB FP64 leaves, peak intermediate "
+            "<= 8 GB, sliced over 4^5 = 1024 wire-index values (all slices contracted every step), "
             "order: best of 256 planner candidates by exact FLOPs",
     "100q-free": "100-qubit ring+chords h-TN: 12 QTs, 28 gate + 12 wire cuts, k=64, peak intermediate <= 8 GB, "
                  "slices chosen by the planner, order: best of 256 planner candidates by exact FLOPs",
@@ -219,6 +228,14 @@ def timed_steps(fn, steps, flush):
     return ts
 
 
+def oracle_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+    except Exception:
+        return os.cpu_count()
+
+
 def oracle_seconds(net, budget_s: float):
     """Time the FP64 CPU oracle contracting the workload (full contractions
     repeated until the budget is used).  Returns (seconds per contraction,
@@ -233,12 +250,31 @@ def oracle_seconds(net, budget_s: float):
         if time.perf_counter() - t0 >= budget_s:
             break
     dt = (time.perf_counter() - t0) / reps
-    try:
-        from threadpoolctl import threadpool_info
-        threads = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
-    except Exception:
-        threads = os.cpu_count()
-    return dt, reps, threads
+    return dt, reps, oracle_threads()
+
+
+class RestrictedOracle:
+    """The FP64 CPU oracle on a restricted output: the entries k = v of the
+    observable index for v in ``values`` (each a full contraction of the
+    network with k fixed, in the oracle planner's order for that network).
+    ``flops`` counts the oracle plan's useful FLOPs for those entries."""
+
+    def __init__(self, net, values=(0, 1)):
+        from oracle import planner
+        self.net, self.values = net, tuple(values)
+        self.kid = net.output[0]
+        inds1 = [tuple(i for i in t.inds if i != self.kid) for t in net.tensors]
+        dims1 = {i: d for i, d in net.dims().items() if i != self.kid}
+        self.plan = planner.make_plan(inds1, dims1, (), n_candidates=32)
+        per = int(planner.plan_text(self.plan, inds1).split("flops_total=")[1].split()[0])
+        self.flops = per * len(self.values)
+        self.order = planner.order_of(self.plan)
+
+    def run(self):
+        from oracle import tn
+        t0 = time.perf_counter()
+        r = tn.contract_output_subset(self.net.pairs(), self.net.output, self.order, self.kid, list(self.values))
+        return np.asarray(r).ravel(), time.perf_counter() - t0
 
 
 def cpu_model():
@@ -253,20 +289,31 @@ def cpu_model():
 
 # ----------------------------------------------------------------- arms
 def run_reference(args, rank, world):
-    """The reference arm: the FP64 CPU oracle, timed on the host cores."""
+    """The reference arm: the FP64 CPU oracle, timed on the host cores (rank 0
+    only; other ranks exit without work)."""
     if rank != 0:
         return
-    net, _ = make_network(args.workload)
-    if args.workload != "mid":
-        print(json.dumps({"impl": "reference", "unavailable": "the FP64 CPU oracle needs >1e14 FLOP on this workload"}))
+    net, _ = make_network(args.workload, args.shape, args.observables)
+    if args.workload.startswith("100q"):
+        ro = RestrictedOracle(net)
+        for _ in range(args.warmup if args.warmup <= 3 else 3):
+            ro.run()
+        ts = [ro.run()[1] for _ in range(args.steps)]
+        flops = ro.flops
+        sample = (f"each step: the exact FP64 oracle on the restricted output k in {{0, 1}} (2 of the 64 "
+                  f"observables, {flops / 1e12:.3f} TFLOP of the oracle plan), numpy FP64 on {cpu_model()}")
+    elif args.workload == "mid":
+        from oracle import planner
+        flops = int(planner.plan_text(planner.make_plan(net.inds(), net.dims(), net.output), net.inds())
+                    .split("flops_total=")[1].split()[0])
+        for _ in range(args.warmup):
+            oracle_seconds(net, 0.0)
+        ts = [oracle_seconds(net, 0.0)[0] for _ in range(args.steps)]
+        sample = f"each step: one full contraction of the workload, numpy FP64 on {cpu_model()}"
+    else:
+        print(json.dumps({"impl": "reference", "unavailable": f"no oracle arm for the {args.workload} workload"}))
         return
-    from oracle import planner
-    flops = int(planner.plan_text(planner.make_plan(net.inds(), net.dims(), net.output), net.inds())
-                .split("flops_total=")[1].split()[0])
-    for _ in range(args.warmup):
-        oracle_seconds(net, 0.0)
-    ts = [oracle_seconds(net, 0.0)[0] for _ in range(args.steps)]
-    _, _, threads = oracle_seconds(net, 0.0)
+    threads = oracle_threads()
     ms = 1e3 * statistics.mean(ts)
     val = flops / (ms * 1e-3) / 1e12
     print(json.dumps({
@@ -274,8 +321,7 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "flops_per_step": flops, "l2": "n/a (host)"},
-        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{args.steps} full contractions of the workload, numpy FP64 on {cpu_model()}"},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -366,29 +412,18 @@ def run_ours(args, rank, world):
     net, plan_kw = make_network(args.workload, args.shape, args.observables)
     tensors = [(t.inds, torch.from_numpy(np.ascontiguousarray(t.data)).to(dev), QTPU_CT if t.kind == "CT" else QTPU_QT)
                for t in net.tensors]
+    t_plan = time.perf_counter()
     h = from_network(tensors, net.output, prec=args.prec, **plan_kw)
+    plan_s = time.perf_counter() - t_plan
     st = h.plan_stats()
     out = torch.empty(h.output_size(), dtype=torch.float64, device=dev)
     flush_buf = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MiB > L2
     flush = (lambda: flush_buf.zero_()) if net.nbytes() < (256 << 20) else (lambda: None)
     n_slices = int(h.plan_info().split("slices n=")[1].split()[0])
-    sub = args.workload in ("100q", "100q-free")
-    if sub:
-        # every slice runs the same launches: time a fixed subset of them; with
-        # several ranks each contracts its own S slices and the outputs are
-        # summed over ranks (the slice sum is the path's one exchange step)
-        S = min(args.slices_timed, n_slices // world)
-        flops = st["flops_total"] / n_slices * S
-        first = rank * S
-
-        def step():
-            h.contract_slices(first, S, out)
-            if world > 1:
-                dist.all_reduce(out, op=dist.ReduceOp.SUM)
-    else:
-        S = n_slices
-        flops = st["flops_total"]
-        step = lambda: h.contract(out)  # noqa: E731
+    # one step = one complete contraction (every slice); with several ranks
+    # each contracts its own replica (weak scaling, no collective)
+    flops = st["flops_total"]
+    step = lambda: h.contract(out)  # noqa: E731
 
     for _ in range(args.warmup):
         step()
@@ -406,11 +441,14 @@ def run_ours(args, rank, world):
         dist.all_reduce(tot, op=dist.ReduceOp.MAX)
     ms = tot.item() / args.steps
     value = world * flops / (ms * 1e-3) / 1e12
+    got = out.cpu().numpy()
 
-    # per-kernel-class timing (separate pass, same launches)
+    # per-kernel-class timing (separate pass, same launches; a long step is
+    # profiled twice at most)
+    n_prof = args.steps if ms < 200 else min(args.steps, 2)
     h.profile(True)
     prof = None
-    for _ in range(args.steps):
+    for _ in range(n_prof):
         flush()
         step()
         p = h.profile_read()
@@ -422,20 +460,37 @@ def run_ours(args, rank, world):
                     prof[kk][f] += p[kk][f]
     h.profile(False)
 
-    # parity of this run's output against the FP64 oracle (mid workload)
-    rel = None
-    if args.workload in ("mid", "gemm") and rank == 0:
+    # parity of this run's output against the FP64 oracle: the whole output
+    # (mid, gemm), or the restricted output k in {0, 1} (100-qubit)
+    rel = rel_max = None
+    cpu = None
+    if rank == 0 and args.workload in ("mid", "gemm"):
         from oracle import planner, tn
         p = planner.make_plan(net.inds(), net.dims(), net.output)
         ref = tn.contract_pairwise(net.pairs(), net.output, planner.order_of(p)).ravel()
-        got = out.cpu().numpy()
         rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        rel_max = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+    if rank == 0 and world == 1 and args.workload.startswith("100q"):
+        ro = RestrictedOracle(net)
+        ref, sec = ro.run()
+        sub_got = got[list(ro.values)]
+        rel = float(np.linalg.norm(sub_got - ref) / np.linalg.norm(ref))
+        rel_max = float(np.max(np.abs(sub_got - ref)) / np.max(np.abs(ref)))
+        cpu = {"value": ro.flops / sec / 1e12, "unit": "TFLOP/s", "cores": oracle_threads(), "kind": "oracle",
+               "sample": f"the exact FP64 oracle on the restricted output k in {{0, 1}} (2 of the 64 observables; "
+                         f"{ro.flops / 1e12:.3f} TFLOP of the oracle's own unsliced plan) in {sec:.1f} s, numpy "
+                         f"FP64 on {cpu_model()} ({os.cpu_count()} host cores)"}
+    if rank == 0 and world == 1 and args.workload == "mid":
+        sec, reps, threads = oracle_seconds(net, args.cpu_budget)
+        cpu = {"value": flops / sec / 1e12, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+               "sample": f"{reps} full contractions of the workload in {reps * sec:.1f} s, numpy FP64 on "
+                         f"{cpu_model()} ({os.cpu_count()} host cores)"}
 
     # plain FP64 GPU path: same plan, torch FP64 ops, one launch per step
     fp64 = None
     steps, final_sum = parse_plan(h.plan_info())
     t64 = [(list(i), x.double()) for i, x, _ in tensors]
-    if not sub:
+    if n_slices == 1:
         for _ in range(2):
             fp64_torch_path(t64, list(net.output), steps, final_sum)
         ts64 = timed_steps(lambda: fp64_torch_path(t64, list(net.output), steps, final_sum),
@@ -447,6 +502,7 @@ def run_ours(args, rank, world):
         # the FP64 path on a fixed subset of slices (same shapes), extrapolated
         sliced = [int(x) for x in h.plan_info().split("idx=")[1].split()[0].split(",")]
         dims = net.dims()
+
         def one_slice(s_id):
             vals, r = [], s_id
             for i in reversed(sliced):
@@ -457,59 +513,60 @@ def run_ours(args, rank, world):
         fp64_torch_path(t64, list(net.output), steps, final_sum, one_slice(0))
         ts64 = timed_steps(lambda: [fp64_torch_path(t64, list(net.output), steps, final_sum, one_slice(s))
                                     for s in range(S64)], 2, flush)
-        ms64 = statistics.mean(ts64) / S64 * S
+        ms64 = statistics.mean(ts64) / S64 * n_slices
         fp64 = {"value": flops / (ms64 * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms64,
-                "impl": f"torch FP64 permute+bmm per planned step, {S64} slices timed, extrapolated to {S}",
-                "speedup_of_ours": ms64 / ms}
+                "impl": f"torch FP64 permute+bmm per planned step, {S64} of {n_slices} slices timed, "
+                        f"extrapolated to all", "speedup_of_ours": ms64 / ms}
+    del t64
 
-    # end to end through the C ABI with host buffers
-    e2e = None
-    if not sub:
-        host = [torch.from_numpy(np.ascontiguousarray(t.data)).pin_memory() for t in net.tensors]
-        hout = np.empty(h.output_size(), dtype=np.float64)
+    # end to end through the C ABI with host buffers (pinned): the upload of
+    # every leaf, the contraction and the download of the result per step
+    host = [torch.from_numpy(np.ascontiguousarray(t.data)).pin_memory() for t in net.tensors]
+    hout = np.empty(h.output_size(), dtype=np.float64)
+    h.contract_host(host, hout)
+    n_e2e = max(3, min(args.steps, 10)) if ms < 200 else min(args.steps, 3)
+    te = []
+    for _ in range(n_e2e):
+        flush()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         h.contract_host(host, hout)
-        te = []
-        for _ in range(max(3, min(args.steps, 10))):
-            flush()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            h.contract_host(host, hout)
-            te.append(time.perf_counter() - t0)
-        e2e_ms = 1e3 * statistics.mean(te)
-        h2d = sum(x.numel() * x.element_size() for x in host)
-        e2e = {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h.output_size() * 8}
+        te.append(time.perf_counter() - t0)
+    e2e_ms = 1e3 * statistics.mean(te)
+    h2d = sum(x.numel() * x.element_size() for x in host)
+    e2e = {"value": world * flops / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h.output_size() * 8, "steps": n_e2e}
+    del host
 
     peaks = load_peaks()
+    # a kernel timed inside a long step runs under the sustained power limit
+    sustained = ms >= 200
     dom = max(prof, key=lambda k: prof[k]["ms"])
     d = prof[dom]
     per_launch_ms = d["ms"] / max(d["launches"], 1)
     if dom == "gemm":
         ratio = {"bf16x3": 6, "3xtf32": 6, "tf32": 2}.get(args.prec, 6)  # bf16-MMA equivalents per useful FMA
-        peak = peaks["bf16_tflops"] / ratio
+        pk = peaks["bf16_tflops_sustained"] if sustained else peaks["bf16_tflops"]
+        peak = pk / ratio
         achieved = d["flops"] / d["launches"] / (per_launch_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "kernel": "k_gemm_tc",
-                "peak_note": f"{peaks['src']} bf16 burst / {ratio} (useful FLOPs of {args.prec})"}
+                "peak_note": f"{peaks['src']} bf16 {'sustained' if sustained else 'burst'} / {ratio} "
+                             f"(useful FLOPs of {args.prec})"}
     else:
         achieved = d["bytes"] / d["launches"] / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": dom,
-                "peak_note": f"{peaks['src']} copy bandwidth"}
+                "peak_note": f"{peaks['src']} copy bandwidth; algorithmic bytes = operands read once + results "
+                             f"written once"}
     roof["traffic"] = measured_traffic(args.workload, dom)
     roof["per_launch_ms"] = per_launch_ms
-    roof["launches_per_step"] = d["launches"] / args.steps
-    roof["classes"] = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+    roof["launches_per_step"] = d["launches"] / n_prof
+    roof["classes"] = {k: {"ms_per_step": v["ms"] / n_prof, "launches_per_step": v["launches"] / n_prof,
                            "algorithmic_GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] else None,
-                           "useful_TFLOPs": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] else None}
+                           "useful_TFLOPs": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] else None,
+                           "traffic_per_launch": measured_traffic(args.workload, k)}
                        for k, v in prof.items()}
-
-    cpu = None
-    if rank == 0 and world == 1 and args.workload == "mid":
-        sec, reps, threads = oracle_seconds(net, args.cpu_budget)
-        cpu = {"value": flops / sec / 1e12, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
-               "sample": f"{reps} full contractions of the workload in {reps * sec:.1f} s, numpy FP64 on "
-                         f"{cpu_model()} ({os.cpu_count()} host cores)"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -517,20 +574,21 @@ def run_ours(args, rank, world):
         "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload] + (f" ({args.shape})" if args.workload == "gemm" else "")
                    + (f" (k = {args.observables} observables)" if args.workload.startswith("100q") and args.observables != 64 else ""),
-                   "sharding": ("slices split over ranks, one all-reduce of the output per step" if sub
-                                else "independent replicas") if world > 1 else "single GPU",
+                   "sharding": "independent replicas" if world > 1 else "single GPU",
                    "flops_per_step": flops, "prec": args.prec,
                    "l2": "flushed between timed steps (256 MiB write)" if net.nbytes() < (256 << 20)
                    else "inputs larger than L2", "plan_steps": st["n_steps"],
                    "tensor_core_steps": st["n_tensor_core_steps"], "parallelism": f"replicas x{world}",
-                   "slices": n_slices, "slices_timed": S,
-                   "flops_total_all_slices": st["flops_total"]},
+                   "slices": n_slices, "flops_per_slice": flops / n_slices,
+                   "plan_seconds": plan_s},
         "rel_err_vs_oracle": rel,
+        "rel_err_max_vs_oracle": rel_max,
+        "rel_err_entries": ("all" if args.workload in ("mid", "gemm") else "k in {0, 1} (2 of 64)") if rel is not None else None,
         "roofline": roof,
         "cpu_baseline": cpu,
         "fp64_gpu_path": fp64,
         "e2e": e2e,
-        "gpu_launches": (st["launches_per_contract"] - 1) // n_slices * S * args.steps + args.steps,
+        "gpu_launches": st["launches_per_contract"] * args.steps,
         "clocks": clk.summary(),
     }
     if rank == 0:
@@ -544,10 +602,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="100q", choices=sorted(WORKLOADS))
     ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "3xtf32", "tf32", "fp64"])
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle time for cpu_baseline")
-    ap.add_argument("--slices-timed", type=int, default=16, help="100q: slices contracted per timed step")
     ap.add_argument("--shape", default="8x1024x1024x1024", help="gemm workload: batch x M x N x K")
     ap.add_argument("--observables", type=int, default=64,
                     help="100q workloads: size k of the observable index (64 = the benchmark; smaller for ncu captures)")

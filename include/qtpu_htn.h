@@ -23,7 +23,9 @@
  *
  * Errors: every call returns a qtpu_status and nothing is thrown across the
  * ABI.  qtpu_last_error(h) returns a NUL-terminated message describing the
- * last failure on that handle (valid until the next call on it).  A handle
+ * last failure on that handle (valid until the next call on it);
+ * qtpu_last_error(NULL) describes the last failed call that takes no handle
+ * (create, the allocation-free calls) on the calling thread.  A handle
  * is not thread-safe; the network is immutable after a successful plan.
  */
 #ifndef QTPU_HTN_H
@@ -51,9 +53,19 @@ typedef enum {
 
 typedef enum { QTPU_F32 = 0, QTPU_F64 = 1 } qtpu_dtype;
 
-/* Arithmetic of the large pairwise GEMMs.  All other steps (CT absorption,
- * small or skinny contractions, dot products, the slice sum and the final
- * reduction) always run in FP64 on the CUDA cores. */
+/* Arithmetic of the contraction.  With QTPU_PREC_FP64 every step runs in FP64
+ * on the CUDA cores.  With a tensor-core precision:
+ *   - the large pairwise GEMMs run on the tensor cores in the stated form with
+ *     FP32 accumulation (BF16x3: pieces on a common grid per 64-entry k-block,
+ *     so the leading-product accumulator of up to 1024 k is exact);
+ *   - the other steps that produce intermediates (CT absorption, small or
+ *     skinny contractions, operand gathers) compute in compensated FP32 pairs
+ *     (hi + lo, about 44 significant bits) and store intermediates as pairs;
+ *   - everything that produces values of the output accumulates in FP64 and
+ *     writes FP64: the last step of every slice when it is a gather (the final
+ *     dot product or reduction over signed QPD coefficients; a dot product
+ *     folds pair sub-sums of at most 64 products into its FP64 accumulator),
+ *     and the sum over slices, which reads a GEMM's (hi, lo) result exactly. */
 typedef enum {
   QTPU_PREC_FP64 = 0,   /* every step in FP64 on the CUDA cores               */
   QTPU_PREC_TF32 = 1,   /* tensor cores, operands rounded to TF32 (1 product) */
@@ -217,8 +229,9 @@ qtpu_status qtpu_htn_selftest_timeout(qtpu_htn* h, uint64_t limit_ns);
 
 qtpu_status qtpu_htn_destroy(qtpu_htn* h);
 
-/* Message of the last failure on h (or of the last failed create when h is
- * NULL).  Never NULL. */
+/* Message of the last failure on h (or, when h is NULL, of the calling
+ * thread's last failed call that takes no handle: create and the
+ * allocation-free calls).  Never NULL. */
 const char* qtpu_last_error(const qtpu_htn* h);
 
 /* ------------------------------------------------------------------------
@@ -274,17 +287,44 @@ qtpu_status qtpu_mlp_destroy(qtpu_mlp* m);
  *              device, and uses BF16x3 tensor-core arithmetic (error about
  *              6e-8 relative, as the regular entry points)
  *
- * Scratch needed: 2048 + 6*batch*(M+N)*round_up(K,8) + 8*batch*M*N bytes; a
- * call that needs more returns QTPU_ELIMIT and does nothing.  QTPU_EINVAL on
- * NULL pointers or sizes < 1, QTPU_ECUDA if a CUDA call fails.  The first call
- * on a device resolves the scratch array's device address
- * (cudaGetSymbolAddress) for that device; make that first call before any
- * stream capture.  Every call shares the one array and leaves its contents
- * behind; calls whose GPU work overlaps in time race on it and must be
- * serialised by the caller. */
+ * Scratch needed: at most 2304 + 6*batch*(M+N)*round_up(K,8) + 8*batch*M*N
+ * bytes (the exact figure: qtpu_pairwise_noalloc_scratch_bytes); a call that
+ * needs more than QTPU_NOALLOC_SCRATCH_BYTES returns QTPU_ELIMIT and does
+ * nothing.  QTPU_EINVAL on NULL pointers or sizes < 1, QTPU_ECUDA if a CUDA
+ * call fails.  The first call on a device resolves the scratch array's device
+ * address (cudaGetSymbolAddress) for that device; make that first call before
+ * any stream capture.  Every call shares the one array and leaves its
+ * contents behind; calls whose GPU work overlaps in time race on it and must
+ * be serialised by the caller.  The call returns once the work is enqueued:
+ * a device-side failure (a bounded wait of the GEMM that gave up) is reported
+ * by qtpu_noalloc_status, which a caller that needs to know C is valid calls
+ * after the work.  qtpu_last_error(NULL) returns the message of the last
+ * failed allocation-free call on the calling thread. */
 qtpu_status qtpu_pairwise_contract_noalloc(const double* A, const double* B, double* C,
                                            int batch, int M, int N, int K,
                                            void* cuda_stream);
+
+/* Exact scratch bytes qtpu_pairwise_contract_noalloc needs for these sizes
+ * (compare with QTPU_NOALLOC_SCRATCH_BYTES).  QTPU_EINVAL on a NULL `bytes`
+ * or sizes < 1.  Host only: touches no device. */
+qtpu_status qtpu_pairwise_noalloc_scratch_bytes(int batch, int M, int N, int K,
+                                                size_t* bytes);
+
+/* Wait for cuda_stream and report the device status of the allocation-free
+ * calls enqueued on the current device: QTPU_OK, QTPU_ETIMEOUT if a bounded
+ * device-side wait of the GEMM gave up (C is then not valid), QTPU_ECUDA if
+ * a kernel rejected its arguments or a CUDA call failed.  Reading clears the
+ * status (a failure is reported once).  Allocates nothing: the status word
+ * lives in the fixed scratch array and is copied into a host variable. */
+qtpu_status qtpu_noalloc_status(void* cuda_stream);
+
+/* Failure-path self-test of qtpu_noalloc_status: enqueue on cuda_stream one
+ * warp whose bounded wait (the GEMM pipeline's bounded mbarrier wait) is on a
+ * barrier that nothing completes; after limit_ns (at most 10 s) it gives up
+ * and sets the timeout bit of the allocation-free status word, so the next
+ * qtpu_noalloc_status returns QTPU_ETIMEOUT.  Nothing faults, traps or hangs.
+ * QTPU_EINVAL on a limit of 0 or above 10 s. */
+qtpu_status qtpu_noalloc_selftest_timeout(uint64_t limit_ns, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -35,7 +35,12 @@ struct qtpu_htn {
   std::string err;
 };
 
-static std::string g_create_err = "no error";
+// message of the last failed create or allocation-free call, per thread
+static thread_local std::string g_create_err = "no error";
+
+namespace qtpu {
+void set_global_error(const char* msg) { g_create_err = msg ? msg : "no error"; }
+}  // namespace qtpu
 
 static qtpu_status fail(qtpu_htn* h, qtpu_status s, const std::string& msg) {
   if (h) h->err = msg;

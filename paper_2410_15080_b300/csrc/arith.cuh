@@ -76,6 +76,33 @@ struct Acc {
     const float s = __fadd_rn(hi, lo);
     return make_float2(s, __fsub_rn(lo, __fsub_rn(s, hi)));
   }
+  __device__ __forceinline__ double as_double() const { return (double)hi + (double)lo; }
+};
+
+// FP64 accumulator of FP32-pair terms: used wherever a sum produces a value
+// of the final output (the last step of every slice, the slice sum, the
+// final dot product), because a sum over signed QPD coefficients may cancel
+// and FP64 keeps 53 bits through it.  Each term hi + lo enters exactly (up to
+// one FP64 rounding) and is added in FP64.
+struct AccD {
+  double s = 0.0;
+  __device__ __forceinline__ void add(float2 v) { s += (double)v.x + (double)v.y; }
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double as_double() const { return s; }
+  __device__ __forceinline__ float2 get() const {
+    const float h = (float)s;
+    return make_float2(h, (float)(s - (double)h));
+  }
+};
+
+// FP64 on the output side, FP32 pairs elsewhere
+template <bool F64>
+struct AccSel {
+  using T = Acc;
+};
+template <>
+struct AccSel<true> {
+  using T = AccD;
 };
 
 // ------------------------------------------------------------ BF16x3 pieces

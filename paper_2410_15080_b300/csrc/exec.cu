@@ -698,7 +698,9 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
         }
       }
     }
-    double by = (double)np * rows * g.Kp * es;
+    // algorithmic bytes: the operand read once (the piece planes the split
+    // writes are this implementation's staging, not work of the method)
+    double by = 0;
     for (int s : std::set<int>(src.begin(), src.end())) by += bytes_of(s);
     L->bytes = by;
     *rows_out = (int64_t)rows;
@@ -999,7 +1001,9 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
         LG.gemm.prec = prec;
         LG.gemm.kc_blocks = ex->kc_blocks;
         LG.flops = step_flops + X.flops + Y.flops;
-        LG.bytes = (double)np * (ra + rb) * align_up(Ka, 8) * es + nb * nm * nn * 8.0;
+        // algorithmic bytes: the result written once (its operands are
+        // counted by the splits that read them)
+        LG.bytes = nb * nm * nn * 8.0;
         // the GEMM stores [batch][its N][its M]
         Inds stored = batch;
         const Inds& outer = swap ? m : n;
@@ -1054,7 +1058,9 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       }
     }
     Launch L;
-    if (!gather_launch({&X, &Y}, out_inds, extra, last ? GW_DENSE_PAIR : GW_DENSE_PAIR, dst,
+    // the last step of a slice produces output values: FP64 accumulation and
+    // an FP64 partial (the slice sum then stays in FP64 throughout)
+    if (!gather_launch({&X, &Y}, out_inds, extra, last ? GW_DENSE_F64 : GW_DENSE_PAIR, dst,
                        step_flops + X.flops + Y.flops, KC_CONTRACT, &L))
       return fail(QTPU_ENOTSUP, "internal: a step does not fit the gather kernel (modes or operand views)");
     set_dense(ps.out, out_inds);
@@ -1100,10 +1106,13 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     if (ex->n_slices > 1) loop.push_back(slice_ix);
     for (int64_t i : plan.final_sum)
       if (!sliced.count(i)) loop.push_back(i);
+    // a gather step as last step wrote FP64 partials; a GEMM wrote (hi, lo)
+    // pairs, read exactly into the FP64 sum
+    ex->partial_dt = (!fp64 && ex->launches.back().kind == LK_GEMM) ? DT_F32X2 : DT_F64;
     GatherArgs g;
     g.nops = 1;
     g.mode = GW_DENSE_F64;
-    g.dt[0] = ex->inter_dt;
+    g.dt[0] = ex->partial_dt;
     int64_t st[kMaxOps] = {};
     bool ok = true;
     for (int64_t i : plan.output) {

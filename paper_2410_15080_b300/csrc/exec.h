@@ -84,6 +84,7 @@ struct Executor {
   int64_t n_slices = 1;
   int64_t final_size = 1;        // entries of the last step's result per slice
   int inter_dt = DT_F32X2;       // storage of intermediates
+  int partial_dt = DT_F64;       // storage of the per-slice results (FP64, or pairs after a GEMM)
   size_t split_a_bytes = 0;      // offset of the B operand region
   // device memory (owned)
   uint8_t* arena = nullptr;
@@ -138,6 +139,8 @@ cudaError_t exec_enqueue(Executor* ex, const std::vector<Leaf>& leaves, double* 
 std::string exec_run_slices(Executor* ex, const std::vector<Leaf>& leaves, int64_t first, int64_t count,
                             double* dev_out, cudaStream_t st, int* code);
 void exec_free(Executor* ex);
+// Set the message qtpu_last_error(NULL) returns (calls that take no handle).
+void set_global_error(const char* msg);
 // Sum the timed launches per class (after a stream sync) and reset.
 std::string exec_profile_read(Executor* ex, double* ms, int64_t* launches, double* flops, double* bytes);
 

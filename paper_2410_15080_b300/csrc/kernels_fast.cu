@@ -90,11 +90,15 @@ struct Op {
     if (HW) v = mul_pair(v, W[off[NB]]);
     return v;
   }
-  __device__ static __forceinline__ float2 entry(const GatherArgs& a, const float2* W, const int64_t* base,
-                                                 const int64_t (*lt)[NOPS]) {
-    if (a.loop.n == 0) return term(a, W, base);
+  template <typename ACC>
+  __device__ static __forceinline__ ACC entry(const GatherArgs& a, const float2* W, const int64_t* base,
+                                              const int64_t (*lt)[NOPS]) {
+    ACC acc;
+    if (a.loop.n == 0) {
+      acc.add(term(a, W, base));
+      return acc;
+    }
     if (use_loop_tab(a)) {
-      Acc acc;
 #pragma unroll 4
       for (uint32_t l = 0; l < a.n_loop; ++l) {
         int64_t off[NOPS];
@@ -102,9 +106,8 @@ struct Op {
         for (int j = 0; j < NOPS; ++j) off[j] = base[j] + lt[l][j];
         acc.add(term(a, W, off));
       }
-      return acc.get();
+      return acc;
     }
-    Acc acc;
     int64_t off[NOPS];
 #pragma unroll
     for (int j = 0; j < NOPS; ++j) off[j] = base[j];
@@ -115,7 +118,7 @@ struct Op {
 #pragma unroll
         for (int j = 0; j < NOPS; ++j) off[j] += a.loop.stride[0][j];
       }
-      return acc.get();
+      return acc;
     }
     uint32_t idx[kMaxModes];
     for (int m = 0; m < a.loop.n; ++m) idx[m] = 0;
@@ -135,7 +138,7 @@ struct Op {
         for (int j = 0; j < NOPS; ++j) off[j] += a.loop.stride[m][j];
       }
     }
-    return acc.get();
+    return acc;
   }
 };
 
@@ -200,6 +203,7 @@ __device__ __forceinline__ void entry_fan(const GatherArgs& a, const float2* W, 
 template <int NB, int DT0, int DT1, bool HW, bool F64OUT>
 __global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __restrict__ out, int lanes_log2) {
   using O = Op<NB, DT0, DT1, HW>;
+  using ACC = typename AccSel<F64OUT>::T;  // FP64 when the values are outputs
   extern __shared__ float2 W[];  // w_size entries (dynamic shared memory)
   __shared__ int64_t lt[kLoopTab][O::NOPS];
   if (HW) {
@@ -215,14 +219,14 @@ __global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __
   if (lanes_log2 > 0) {
     // few outputs with a short tabulated loop: 2^lanes_log2 consecutive lanes
     // share an output, each summing every 2^lanes_log2-th term, then the
-    // partial sums meet by compensated shuffles
+    // partial sums meet by shuffles (compensated pairs, or FP64)
     const uint32_t S = 1u << lanes_log2;
     const uint64_t total = (uint64_t)a.n_out << lanes_log2;
     const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < total; i0 += step) {
       const uint64_t i = i0 + (threadIdx.x & 31u);
       const uint32_t o = (uint32_t)(i >> lanes_log2), sub = (uint32_t)(i & (S - 1));
-      Acc acc;
+      ACC acc;
       if (o < a.n_out) {
         int64_t base[O::NOPS];
         offsets<O::NOPS>(o, a.out, base);
@@ -234,6 +238,12 @@ __global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __
           acc.add(O::term(a, W, off));
         }
       }
+      if (F64OUT) {
+        double v = acc.as_double();
+        for (uint32_t d = S >> 1; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+        if (o < a.n_out && sub == 0) ((double*)out)[o] = v;
+        continue;
+      }
       float2 v = acc.get();
       for (uint32_t d = S >> 1; d > 0; d >>= 1) {
         Acc t;
@@ -242,12 +252,7 @@ __global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __
         t.add(make_float2(__shfl_xor_sync(0xffffffffu, v.x, d), __shfl_xor_sync(0xffffffffu, v.y, d)));
         v = t.get();
       }
-      if (o < a.n_out && sub == 0) {
-        if (F64OUT)
-          ((double*)out)[o] = (double)v.x + (double)v.y;
-        else
-          ((float2*)out)[o] = v;
-      }
+      if (o < a.n_out && sub == 0) ((float2*)out)[o] = v;
     }
     return;
   }
@@ -255,11 +260,11 @@ __global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __
   for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < a.n_out; o += stride) {
     int64_t base[O::NOPS];
     offsets<O::NOPS>(o, a.out, base);
-    const float2 v = O::entry(a, W, base, lt);
+    const ACC v = O::template entry<ACC>(a, W, base, lt);
     if (F64OUT)
-      ((double*)out)[o] = (double)v.x + (double)v.y;
+      ((double*)out)[o] = v.as_double();
     else
-      ((float2*)out)[o] = v;
+      ((float2*)out)[o] = v.get();
   }
 }
 
@@ -271,7 +276,17 @@ __global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __
 // operand-1 tile read straight from global memory.
 __host__ __device__ __forceinline__ uint32_t dot_slot(uint32_t u) { return u + (u >> 4); }  // padded: fewer bank conflicts
 
-template <int DT0, int DT1>
+// F64: the values are outputs (the final dot of a slice).  Each thread then
+// sums the products of at most kDotFold tuples (<= kDotFold * 8 terms) as a
+// compensated FP32 pair, folds that sub-sum into an FP64 accumulator, and
+// the block and chunk sums are FP64.  A pair sub-sum of n terms is within
+// about n * 2^-47 of its exact value relative to the sum of the magnitudes,
+// far inside FP64's own bound for the long sum (terms * 2^-53), so the
+// output keeps FP64 accuracy while the FP64 pipe (1/64 of the FP32 rate on
+// B300) runs once per kDotFold tuples instead of once per term.
+constexpr int kDotFold = 8;
+
+template <int DT0, int DT1, bool F64>
 __global__ void __launch_bounds__(256) k_dot_fast(const GatherArgs a) {
   constexpr int PER = kDotMaxTile / 256;
   extern __shared__ float2 dsm[];
@@ -299,6 +314,8 @@ __global__ void __launch_bounds__(256) k_dot_fast(const GatherArgs a) {
   const void* X = a.ptr[0];
   const void* Y = a.ptr[1];
   Acc acc;
+  double accd = 0.0;
+  int fold = 0;
   // register double buffer: the next tuple's loads are in flight while the
   // current tuple is multiplied
   float2 xv[PER], yv[PER];
@@ -341,6 +358,26 @@ __global__ void __launch_bounds__(256) k_dot_fast(const GatherArgs a) {
       const uint32_t u = threadIdx.x + k * 256;
       if (u < T) acc.add(mul_pair(sX[dot_slot(u)], yc[k]));
     }
+    if (F64 && ++fold == kDotFold) {
+      accd += acc.as_double();
+      acc = Acc();
+      fold = 0;
+    }
+  }
+  if (F64) {
+    // FP64 block sum -> scratch[o][c] (the scratch holds doubles here)
+    __shared__ double redd[8];
+    double v = accd + acc.as_double();
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+    if ((threadIdx.x & 31) == 0) redd[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += redd[w];
+      reinterpret_cast<double*>(a.scratch)[(size_t)o * a.chunks + blockIdx.x] = t;
+    }
+    return;
   }
   // block sum (compensated) -> scratch[o][c]
   __shared__ float2 red[8];
@@ -362,19 +399,24 @@ __global__ void __launch_bounds__(256) k_dot_fast(const GatherArgs a) {
   }
 }
 
+// sum of the chunk partials of every output: FP64 partials summed in FP64
+// (F64OUT), or compensated pairs
 template <bool F64OUT>
 __global__ void __launch_bounds__(256) k_dot_finish(const float2* __restrict__ part, uint32_t n_out,
                                                     uint32_t chunks, void* __restrict__ out) {
   pdl_wait();
   pdl_launch_dependents();
   for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < n_out; o += gridDim.x * blockDim.x) {
+    if (F64OUT) {
+      const double* pd = reinterpret_cast<const double*>(part);
+      double s = 0.0;
+      for (uint32_t c = 0; c < chunks; ++c) s += pd[(size_t)o * chunks + c];
+      ((double*)out)[o] = s;
+      continue;
+    }
     Acc acc;
     for (uint32_t c = 0; c < chunks; ++c) acc.add(part[(size_t)o * chunks + c]);
-    const float2 r = acc.get();
-    if (F64OUT)
-      ((double*)out)[o] = (double)r.x + (double)r.y;
-    else
-      ((float2*)out)[o] = r;
+    ((float2*)out)[o] = acc.get();
   }
 }
 
@@ -383,15 +425,16 @@ size_t dot_smem_bytes(uint32_t T) { return (dot_slot(T) + 1) * sizeof(float2) + 
 template <int DT0, int DT1>
 cudaError_t dot_launch(const GatherArgs& a, void* out, cudaStream_t st) {
   const size_t sm_bytes = dot_smem_bytes(a.tile_n);
+  const bool f64 = a.mode == GW_DENSE_F64;
+  auto kern = f64 ? k_dot_fast<DT0, DT1, true> : k_dot_fast<DT0, DT1, false>;
   cudaError_t e = cudaSuccess;
-  if (sm_bytes > 40960)
-    e = cudaFuncSetAttribute(k_dot_fast<DT0, DT1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_bytes);
+  if (sm_bytes > 40960) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_bytes);
   if (e != cudaSuccess) return e;
-  e = launch_k(k_dot_fast<DT0, DT1>, dim3(a.chunks, a.n_out), dim3(256), sm_bytes, st, a);
+  e = launch_k(kern, dim3(a.chunks, a.n_out), dim3(256), sm_bytes, st, a);
   if (e != cudaSuccess) return e;
   const uint32_t g = (a.n_out + 255) / 256;
   const float2* part = a.scratch;
-  if (a.mode == GW_DENSE_F64) return launch_k(k_dot_finish<true>, dim3(g), dim3(256), 0, st, part, a.n_out, a.chunks, out);
+  if (f64) return launch_k(k_dot_finish<true>, dim3(g), dim3(256), 0, st, part, a.n_out, a.chunks, out);
   return launch_k(k_dot_finish<false>, dim3(g), dim3(256), 0, st, part, a.n_out, a.chunks, out);
 }
 
@@ -510,7 +553,7 @@ __global__ void __launch_bounds__(256) k_split_fast(const GatherArgs a, void* __
         int64_t b[NOPS];
 #pragma unroll
         for (int j = 0; j < NOPS; ++j) b[j] = rowoff[r][j] + koff[k][j];
-        v = O::entry(a, W, b, lt);
+        v = O::template entry<Acc>(a, W, b, lt).get();
       }
       tile[r][k] = v;
     }

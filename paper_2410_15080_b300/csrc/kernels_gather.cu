@@ -35,11 +35,15 @@ __device__ __forceinline__ float2 term(const GatherArgs& a, const int64_t* off) 
   return v;
 }
 
-// value of one output entry: base offsets + sum over the loop modes
-template <int NOPS>
-__device__ __forceinline__ float2 entry(const GatherArgs& a, const int64_t* base) {
-  if (a.loop.n == 0) return term<NOPS>(a, base);
-  Acc acc;
+// value of one output entry: base offsets + sum over the loop modes, in the
+// accumulator ACC (FP32 pairs for intermediates, FP64 for output values)
+template <int NOPS, typename ACC>
+__device__ __forceinline__ ACC entry(const GatherArgs& a, const int64_t* base) {
+  ACC acc;
+  if (a.loop.n == 0) {
+    acc.add(term<NOPS>(a, base));
+    return acc;
+  }
   if (a.loop.n == 1) {
     int64_t off[NOPS];
 #pragma unroll
@@ -49,7 +53,7 @@ __device__ __forceinline__ float2 entry(const GatherArgs& a, const int64_t* base
 #pragma unroll
       for (int j = 0; j < NOPS; ++j) off[j] += a.loop.stride[0][j];
     }
-    return acc.get();
+    return acc;
   }
   uint32_t idx[kMaxModes];
   int64_t off[NOPS];
@@ -72,36 +76,62 @@ __device__ __forceinline__ float2 entry(const GatherArgs& a, const int64_t* base
       for (int j = 0; j < NOPS; ++j) off[j] += a.loop.stride[m][j];
     }
   }
-  return acc.get();
+  return acc;
 }
 
 // ------------------------------------------------------------ dense writers
-// out[o] for o < n_out, one thread per entry (FP32 pair or FP64 output)
+// out[o] for o < n_out, one thread per entry (FP32 pair, or FP64 output
+// accumulated in FP64)
 template <int NOPS, bool F64OUT>
 __global__ void __launch_bounds__(256) k_gather_dense(const GatherArgs a, void* __restrict__ out) {
+  using ACC = typename AccSel<F64OUT>::T;
   pdl_wait();
   pdl_launch_dependents();
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < a.n_out; o += stride) {
     int64_t base[NOPS];
     offsets<NOPS>(o, a.out, base);
-    const float2 v = entry<NOPS>(a, base);
+    const ACC v = entry<NOPS, ACC>(a, base);
     if (F64OUT)
-      ((double*)out)[o] = (double)v.x + (double)v.y;
+      ((double*)out)[o] = v.as_double();
     else
-      ((float2*)out)[o] = v;
+      ((float2*)out)[o] = v.get();
   }
 }
 
-// one block per output entry for long sums (deterministic fixed-shape tree)
+// one block per output entry for long sums (deterministic fixed-shape tree);
+// with F64OUT every partial sum, the shuffles and the block sum are FP64
 template <int NOPS, bool F64OUT>
 __global__ void __launch_bounds__(256) k_gather_block(const GatherArgs a, void* __restrict__ out) {
   __shared__ float2 red[8];
+  __shared__ double redd[8];
   pdl_wait();
   pdl_launch_dependents();
   for (uint32_t o = blockIdx.x; o < a.n_out; o += gridDim.x) {
     int64_t base[NOPS];
     offsets<NOPS>(o, a.out, base);
+    if (F64OUT) {
+      AccD acc;
+      for (uint32_t l = threadIdx.x; l < a.n_loop; l += blockDim.x) {
+        int64_t lo[NOPS];
+        offsets<NOPS>(l, a.loop, lo);
+#pragma unroll
+        for (int j = 0; j < NOPS; ++j) lo[j] += base[j];
+        acc.add(term<NOPS>(a, lo));
+      }
+      double v = acc.s;
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+      if ((threadIdx.x & 31) == 0) redd[threadIdx.x >> 5] = v;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += redd[w];
+        ((double*)out)[o] = t;
+      }
+      __syncthreads();
+      continue;
+    }
     Acc acc;
     for (uint32_t l = threadIdx.x; l < a.n_loop; l += blockDim.x) {
       int64_t lo[NOPS];
@@ -124,11 +154,7 @@ __global__ void __launch_bounds__(256) k_gather_block(const GatherArgs a, void* 
     if (threadIdx.x == 0) {
       Acc t;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t.add(red[w]);
-      const float2 r = t.get();
-      if (F64OUT)
-        ((double*)out)[o] = (double)r.x + (double)r.y;
-      else
-        ((float2*)out)[o] = r;
+      ((float2*)out)[o] = t.get();
     }
     __syncthreads();
   }
@@ -185,7 +211,7 @@ __global__ void __launch_bounds__(256) k_gather_split(const GatherArgs a, void* 
         int64_t b[NOPS];
 #pragma unroll
         for (int j = 0; j < NOPS; ++j) b[j] = rowoff[r][j] + koff[k][j];
-        v = entry<NOPS>(a, b);
+        v = entry<NOPS, Acc>(a, b).get();
       }
       tile[r][k] = v;
     }

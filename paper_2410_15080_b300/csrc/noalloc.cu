@@ -17,6 +17,13 @@
 // in the same call), except the status word, which each call clears.  Calls
 // whose GPU work overlaps (on different streams, or from different threads)
 // race on the scratch: serialise them.
+//
+// Device-side failures: the GEMM's bounded waits (and a kernel that rejects
+// its arguments) record a bit in the status word at the start of the scratch
+// instead of faulting.  qtpu_noalloc_status waits for the caller's stream,
+// copies that word to the host (no allocation: one 4-byte copy into a host
+// variable), clears it and maps it to a status code, so a caller learns that
+// C is not valid.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -25,6 +32,7 @@
 #include <mutex>
 
 #include "../../include/qtpu_htn.h"
+#include "exec.h"
 #include "kernels.h"
 
 namespace qtpu {
@@ -51,7 +59,25 @@ bool push(GModes& t, uint32_t d, int64_t s) {
   return true;
 }
 
-qtpu_status fail(qtpu_status s, const char*) { return s; }
+qtpu_status fail(qtpu_status s, const char* msg) {
+  set_global_error(msg);
+  return s;
+}
+
+// device address of the scratch array on the current device (resolved once per
+// device with that device current), or nullptr
+void* scratch_base(int* dev_out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  *dev_out = dev;
+  std::lock_guard<std::mutex> g(g_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return nullptr;
+    g_scratch_addr[dev] = p;
+  }
+  return g_scratch_addr[dev];
+}
 
 }  // namespace
 
@@ -76,22 +102,12 @@ extern "C" qtpu_status qtpu_pairwise_contract_noalloc(const double* A, const dou
   size_t a_off, b_off, c_off;
   const size_t need = noalloc_need(batch, M, N, K, &a_off, &b_off, &c_off);
   if (need > kNoallocScratchBytes) return fail(QTPU_ELIMIT, "noalloc: the sizes need more than the fixed scratch");
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return fail(QTPU_ECUDA, "noalloc: no current device");
   // one-time set-up per device (the first call on a device): resolve the
   // array's device address with that device current
-  void* base = nullptr;
-  {
-    std::lock_guard<std::mutex> g(g_mu);
-    if (!g_scratch_addr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess) return QTPU_ECUDA;
-      g_scratch_addr[dev] = p;
-    }
-    base = g_scratch_addr[dev];
-  }
+  int dev = 0;
+  void* base = scratch_base(&dev);
+  if (!base) return fail(QTPU_ECUDA, "noalloc: no current device or the scratch address cannot be resolved");
+  cudaError_t e = cudaSuccess;
   int sm = 148;
   cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -151,5 +167,44 @@ extern "C" qtpu_status qtpu_pairwise_contract_noalloc(const double* A, const dou
   if (e == cudaSuccess) e = launch_gemm(g, sm, st);
   if (e == cudaSuccess) e = launch_gather(gc, C, sm, st);
   if (e != cudaSuccess) return fail(QTPU_ECUDA, "noalloc: launch failed");
+  set_global_error("no error");
+  return QTPU_OK;
+}
+
+extern "C" qtpu_status qtpu_pairwise_noalloc_scratch_bytes(int batch, int M, int N, int K, size_t* bytes) {
+  if (!bytes) return fail(QTPU_EINVAL, "noalloc: bytes is NULL");
+  if (batch < 1 || M < 1 || N < 1 || K < 1) return fail(QTPU_EINVAL, "noalloc: sizes must be >= 1");
+  size_t a_off, b_off, c_off;
+  *bytes = noalloc_need(batch, M, N, K, &a_off, &b_off, &c_off);
+  return QTPU_OK;
+}
+
+extern "C" qtpu_status qtpu_noalloc_status(void* cuda_stream) {
+  int dev = 0;
+  void* base = scratch_base(&dev);
+  if (!base) return fail(QTPU_ECUDA, "noalloc: no current device or the scratch address cannot be resolved");
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return fail(QTPU_ECUDA, cudaGetErrorString(e));
+  uint32_t st = 0;
+  e = cudaMemcpy(&st, base, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(QTPU_ECUDA, cudaGetErrorString(e));
+  if (st) {
+    e = cudaMemset(base, 0, 4);  // reported once
+    if (e != cudaSuccess) return fail(QTPU_ECUDA, cudaGetErrorString(e));
+  }
+  if (st & (ST_TIMEOUT_TMA | ST_TIMEOUT_MMA | ST_TIMEOUT_EPI | ST_TIMEOUT_DEP))
+    return fail(QTPU_ETIMEOUT, "noalloc: a bounded device-side wait gave up; C is not valid");
+  if (st) return fail(QTPU_ECUDA, "noalloc: a kernel rejected its arguments; C is not valid");
+  set_global_error("no error");
+  return QTPU_OK;
+}
+
+extern "C" qtpu_status qtpu_noalloc_selftest_timeout(uint64_t limit_ns, void* cuda_stream) {
+  if (limit_ns == 0 || limit_ns > 10000000000ull) return fail(QTPU_EINVAL, "noalloc: limit must be in (0, 10 s]");
+  int dev = 0;
+  void* base = scratch_base(&dev);
+  if (!base) return fail(QTPU_ECUDA, "noalloc: no current device or the scratch address cannot be resolved");
+  cudaError_t e = launch_bounded_wait_probe((uint32_t*)base, limit_ns, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return fail(QTPU_ECUDA, cudaGetErrorString(e));
   return QTPU_OK;
 }

@@ -23,7 +23,9 @@ QTPU_QT, QTPU_CT = 0, 1
 SYMBOLS = ["qtpu_htn_create", "qtpu_htn_add_tensor", "qtpu_htn_set_output", "qtpu_htn_plan",
            "qtpu_htn_plan_info", "qtpu_htn_lowering_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats", "qtpu_htn_contract",
            "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_contract_slices", "qtpu_htn_sync", "qtpu_htn_selftest_timeout", "qtpu_htn_destroy",
-           "qtpu_htn_profile", "qtpu_htn_profile_read", "qtpu_pairwise_contract_noalloc", "qtpu_last_error",
+           "qtpu_htn_profile", "qtpu_htn_profile_read", "qtpu_pairwise_contract_noalloc",
+           "qtpu_pairwise_noalloc_scratch_bytes", "qtpu_noalloc_status", "qtpu_noalloc_selftest_timeout",
+           "qtpu_last_error",
            "qtpu_mlp_create", "qtpu_mlp_num_params", "qtpu_mlp_params", "qtpu_mlp_forward",
            "qtpu_mlp_gradients", "qtpu_mlp_train_step", "qtpu_mlp_destroy"]
 KERNEL_CLASSES = ["contract", "split", "gemm", "reduce"]
@@ -72,6 +74,9 @@ def lib():
         L.qtpu_htn_sync.argtypes = [vp]
         L.qtpu_htn_selftest_timeout.argtypes = [vp, C.c_uint64]
         L.qtpu_pairwise_contract_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]
+        L.qtpu_pairwise_noalloc_scratch_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]
+        L.qtpu_noalloc_status.argtypes = [vp]
+        L.qtpu_noalloc_selftest_timeout.argtypes = [C.c_uint64, vp]
         L.qtpu_htn_destroy.argtypes = [vp]
         fp = C.POINTER(C.c_float)
         L.qtpu_mlp_create.argtypes = [C.POINTER(vp), C.c_int, vp, C.c_int, C.c_int, C.c_uint64]
@@ -320,8 +325,30 @@ def pairwise_contract_noalloc(A, B, C_out, stream: int | None = None):
     st = L.qtpu_pairwise_contract_noalloc(C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()),
                                           C.c_void_p(C_out.data_ptr()), b, m, n, k, C.c_void_p(stream or 0))
     if st != QTPU_OK:
-        raise QtpuError(st, "qtpu_pairwise_contract_noalloc failed")
+        raise QtpuError(st, L.qtpu_last_error(None).decode())
     return C_out
+
+
+def noalloc_status(stream: int | None = None):
+    """Wait for the stream and raise if an allocation-free call on the current
+    device recorded a device-side failure (see qtpu_noalloc_status)."""
+    L = lib()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    st = L.qtpu_noalloc_status(C.c_void_p(stream or 0))
+    if st != QTPU_OK:
+        raise QtpuError(st, L.qtpu_last_error(None).decode())
+
+
+def noalloc_scratch_bytes(batch: int, m: int, n: int, k: int) -> int:
+    """Exact scratch bytes the allocation-free call needs for these sizes."""
+    L = lib()
+    b = C.c_size_t(0)
+    st = L.qtpu_pairwise_noalloc_scratch_bytes(batch, m, n, k, C.byref(b))
+    if st != QTPU_OK:
+        raise QtpuError(st, L.qtpu_last_error(None).decode())
+    return b.value
 
 
 def lowering_text(tensor_inds, dims: dict, output, prec="bf16x3", dtypes=None, **plan_kw) -> str:

@@ -10,5 +10,5 @@ a numpy array whose axes follow ``inds``, plus the ``output`` index ids.
 """
 from .networks import (  # noqa: F401
     HTN, Tensor, GATE_CT, WIRE_CT, ring_htn, ring_chords_htn, random_htn,
-    random_batch, rank1_htn, tiny_random_htn,
+    random_batch, rank1_htn, rank1_qts_htn, tiny_random_htn,
 )

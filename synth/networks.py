@@ -215,6 +215,30 @@ def rank1_htn(net: HTN, seed: int = 0, signed: bool = True):
     return HTN(tensors, net.output, name=net.name + "_rank1", meta=dict(net.meta)), factors
 
 
+def rank1_qts_htn(net: HTN, seed: int = 0, lo: float = 0.5, hi: float = 1.5):
+    """The same network with every QT replaced by an outer product of seeded
+    positive vectors (entries ~U[lo, hi]), one per axis, while the QPD
+    coefficient tensors keep their exact signed entries.  Each cut's sum then
+    factorises (sum_g u_g c_g v_g for a gate cut, u^T C v for a wire cut), so
+    the contraction has a closed form, and the only signs are the QPD
+    coefficients'.  Returns (network, factors) with factors[t][ax] the vector
+    of QT t's axis ax (None for a CT)."""
+    rng = np.random.default_rng([seed, 0xC7])
+    tensors, factors = [], []
+    for t in net.tensors:
+        if t.kind == "CT":
+            tensors.append(t)
+            factors.append(None)
+            continue
+        vecs = [rng.uniform(lo, hi, size=n) for n in t.data.shape]
+        arr = np.ones((), dtype=np.float64)
+        for v in vecs:
+            arr = np.multiply.outer(arr, v)
+        tensors.append(Tensor(t.kind, t.inds, np.ascontiguousarray(arr).astype(t.data.dtype)))
+        factors.append(vecs)
+    return HTN(tensors, net.output, name=net.name + "_rank1qt", meta=dict(net.meta)), factors
+
+
 def tiny_random_htn(seed: int, n_tensors=4, n_indices=6, max_dim=3,
                     n_output=1, max_rank=4) -> HTN:
     """A tiny random network with hyper-indices (an index on 1..3 tensors),

@@ -41,3 +41,17 @@ def oracle_value(net):
     from oracle import planner, tn
     p = planner.make_plan(net.inds(), net.dims(), net.output)
     return tn.contract_pairwise(net.pairs(), net.output, planner.order_of(p)).ravel()
+
+
+def oracle_restricted(net, values=(0, 1)):
+    """Exact FP64 oracle entries of the output with the (single) observable
+    index fixed to each of ``values``: one full contraction of the network
+    per value, in the oracle planner's best-of-32 order for the network
+    without that index (cheap enough for the full-size 100-qubit network)."""
+    from oracle import planner, tn
+    kid = net.output[0]
+    inds1 = [tuple(i for i in t.inds if i != kid) for t in net.tensors]
+    dims1 = {i: d for i, d in net.dims().items() if i != kid}
+    p = planner.make_plan(inds1, dims1, (), n_candidates=32)
+    return np.asarray(tn.contract_output_subset(net.pairs(), net.output, planner.order_of(p), kid,
+                                                list(values))).ravel()

@@ -222,6 +222,27 @@ def test_100q_rank1_closed_form_full_size():
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("plan", ["1024 wire slices", "planner's own slices"])
+def test_100q_full_size_random_signed_entries_vs_oracle(plan):
+    """The full-size 100-qubit network (12 QTs, 28 gate + 12 wire cuts, k = 64,
+    2 GB of QTs with signed entries ~U[-1, 1], contracted with the exact
+    signed QPD coefficient tensors) against the exact FP64 oracle on the
+    restricted output k in {0, 1}, element by element: the 1024-slice plan of
+    the benchmark and the planner's own slicing under the 8 GB limit."""
+    from tests.gpu_util import oracle_restricted
+    net = synth.ring_chords_htn(seed=0)
+    kw = dict(max_intermediate_bytes=8 << 30, n_candidates=256)
+    if plan == "1024 wire slices":
+        kw.update(n_slices=1024, slice_dim=4)
+    got, st = contract_gpu(net, prec="bf16x3", **kw)
+    ref = oracle_restricted(net, (0, 1))
+    assert st["n_tensor_core_steps"] >= 5
+    err = rel_err(got[:2], ref)
+    assert err <= REL_TOL, (err, got[:2], ref, st)
+    assert np.max(np.abs(got[:2] - ref)) / np.max(np.abs(ref)) <= REL_TOL
+
+
+@pytest.mark.slow
 def test_100q_full_size_slicing_invariance():
     """Full-size 100-qubit network with random entries: the result does not
     depend on how the contraction is sliced (1024 wire-index slices vs 256),

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import tn
+from oracle import planner, tn
 
 
 def _all_orders(n):
@@ -106,6 +106,67 @@ def rank1_closed_form(net, factors):
         shape[p] = dims[o]
         out = out * v.reshape(shape)
     return scal * out
+
+
+def rank1_qts_closed_form(net, factors):
+    """Closed form of a network of rank-1 QTs and CTs that share no index with
+    each other: out[o] = prod of the QT vectors on the output indices, times,
+    for every CT, the CT contracted with the product of the QT vectors on
+    each of its indices, times, for every other summed index, sum_x prod of
+    the QT vectors on it.  Also returns the same with |CT| entries (the sum
+    of magnitudes of the terms), whose ratio to |out| bounds the cancellation."""
+    dims = net.dims()
+    carriers = {}
+    for t, tens in enumerate(net.tensors):
+        if tens.kind == "QT":
+            for ax, i in enumerate(tens.inds):
+                carriers.setdefault(i, []).append(factors[t][ax])
+    vec = {i: np.prod(np.stack(c), axis=0) for i, c in carriers.items()}
+    scal = mag = 1.0
+    on_ct = set()
+    for tens in net.tensors:
+        if tens.kind != "CT":
+            continue
+        assert not (set(tens.inds) & on_ct), "CTs share an index"
+        on_ct |= set(tens.inds)
+        x, xa = tens.data, np.abs(tens.data)
+        for ax, i in enumerate(tens.inds):
+            shape = [1] * x.ndim
+            shape[ax] = dims[i]
+            x = x * vec[i].reshape(shape)
+            xa = xa * np.abs(vec[i]).reshape(shape)
+        scal *= x.sum()
+        mag *= xa.sum()
+    for i in dims:
+        if i in net.output or i in on_ct:
+            continue
+        scal *= vec[i].sum()
+        mag *= np.abs(vec[i]).sum()
+    out = np.ones(tuple(dims[o] for o in net.output))
+    for p, o in enumerate(net.output):
+        shape = [1] * len(net.output)
+        shape[p] = dims[o]
+        out = out * vec[o].reshape(shape)
+    return scal * out, mag * np.abs(out)
+
+
+def test_rank1_qts_closed_form_with_signed_cts():
+    """Rank-1 QTs with the exact signed QPD coefficient tensors: the closed
+    form equals the plain pairwise contraction and the brute-force sum."""
+    base = synth.ring_htn(n_sub=2, gates_per_edge=1, wires_per_edge=1, k=3, seed=2)
+    net, fac = synth.rank1_qts_htn(base, seed=4)
+    want, mag = rank1_qts_closed_form(net, fac)
+    assert np.all(mag >= np.abs(want))
+    got = tn.brute_force(net.pairs(), net.output)
+    np.testing.assert_allclose(got, want, rtol=1e-12)
+    p = planner.make_plan(net.inds(), net.dims(), net.output)
+    got2 = tn.contract_pairwise(net.pairs(), net.output, planner.order_of(p))
+    np.testing.assert_allclose(got2, want, rtol=1e-12)
+    # a sign flip of one gate coefficient changes the value (the CT signs enter)
+    bad = synth.HTN([synth.Tensor(t.kind, t.inds, t.data * np.where(np.arange(t.data.size) == 3, -1, 1)
+                                  .reshape(t.data.shape) if t.kind == "CT" and len(t.inds) == 1 else t.data)
+                     for t in net.tensors], net.output)
+    assert not np.allclose(tn.brute_force(bad.pairs(), bad.output), want, rtol=1e-6)
 
 
 def test_rank1_closed_form():
