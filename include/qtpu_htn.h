@@ -91,6 +91,9 @@ typedef struct {
                                       the fewest total FLOPs (ties: the lower
                                       seed); candidates that cannot meet the
                                       limit are skipped                      */
+  uint64_t reuse_bytes;            /* sliced plans: device memory for results
+                                      kept across slices (0 = 64 GiB); see
+                                      qtpu_htn_plan                           */
 } qtpu_plan_opts;
 
 /* Create an empty network bound to CUDA device `device` and the CUDA stream
@@ -127,7 +130,20 @@ qtpu_status qtpu_htn_set_output(qtpu_htn* h, int n, const int64_t* index_ids);
  * max_intermediate_bytes and the slice count reaches n_slices.  opts may be
  * NULL (defaults: no limit, no slicing, BF16X3, greedy).  QTPU_ESTATE with no
  * tensors, QTPU_EINVAL on an unknown output id, QTPU_ELIMIT if the limit
- * cannot be met, QTPU_ENOTSUP on a size of 2^255 or more. */
+ * cannot be met, QTPU_ENOTSUP on a size of 2^255 or more.
+ *
+ * Slice reuse (a sliced plan with a tensor-core precision): a pairwise step
+ * whose operands do not carry every sliced index has the same value for all
+ * slices that agree on the sliced indices below it.  Such a result (and the
+ * operand pieces made from it) is computed once per value of those indices
+ * and kept in a device buffer of its own for the slices that need it; the
+ * slices of a full contraction are visited in a nested order of the sliced
+ * indices chosen to need the fewest kept bytes.  The plan (its text and
+ * FLOPs) is unchanged; the FLOPs actually executed are reported by
+ * qtpu_htn_exec_stats.  The kept bytes stay within reuse_bytes: over it, the
+ * largest kept results keep one copy and are recomputed when an outer index
+ * changes; if even that does not fit, every slice is computed in full.  Each
+ * slice's result is the same arithmetic either way. */
 qtpu_status qtpu_htn_plan(qtpu_htn* h, const qtpu_plan_opts* opts);
 
 /* Canonical plan text (order, index groups, per-slice sizes and FLOPs,
@@ -156,6 +172,15 @@ qtpu_status qtpu_htn_plan_stats(const qtpu_htn* h, double* flops_total,
                                 int* n_steps, int* n_tensor_core_steps,
                                 uint64_t* workspace_bytes,
                                 int64_t* launches_per_contract);
+
+/* What one full contract call executes: the useful FLOPs (2 per multiply-add)
+ * after slice reuse, the same with every slice computed in full (the plan's
+ * total), the device bytes of results kept across slices, and the kernel
+ * launches.  Available after plan, also on a host-only handle.  Any pointer
+ * may be NULL; QTPU_ESTATE before plan. */
+qtpu_status qtpu_htn_exec_stats(const qtpu_htn* h, double* flops_executed,
+                                double* flops_all_slices, uint64_t* kept_bytes,
+                                int64_t* launches);
 
 /* Kernel classes reported by qtpu_htn_profile_read. */
 typedef enum {

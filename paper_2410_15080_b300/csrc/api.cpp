@@ -164,7 +164,7 @@ qtpu_status qtpu_htn_plan(qtpu_htn* h, const qtpu_plan_opts* opts) {
     // a host-only handle lowers the plan too (no device work), so its
     // launch list can be inspected
     int code = QTPU_OK;
-    std::string m = exec_build(&h->ex, h->plan, h->leaves, h->dims, (int)o.prec, &code, h->host_only);
+    std::string m = exec_build(&h->ex, h->plan, h->leaves, h->dims, (int)o.prec, &code, h->host_only, o.reuse_bytes);
     if (code != QTPU_OK && !h->host_only) return fail(h, (qtpu_status)code, m);
     if (code != QTPU_OK) h->ex.lowered = false;  // planning still succeeded
     h->built = !h->host_only;
@@ -216,6 +216,17 @@ qtpu_status qtpu_htn_plan_stats(const qtpu_htn* h, double* flops_total, int* n_s
   if (n_steps) *n_steps = (int)h->plan.steps.size();
   if (n_tc) *n_tc = h->built ? h->ex.n_tc_steps : 0;
   if (ws) *ws = h->built ? (uint64_t)h->ex.workspace_bytes() : 0;
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_exec_stats(const qtpu_htn* h, double* flops_executed, double* flops_all_slices,
+                                uint64_t* kept_bytes, int64_t* launches) {
+  if (!h) return QTPU_EINVAL;
+  if (!h->planned || !h->ex.lowered) return QTPU_ESTATE;
+  if (flops_executed) *flops_executed = h->ex.flops_executed;
+  if (flops_all_slices) *flops_all_slices = h->ex.flops_no_reuse;
+  if (kept_bytes) *kept_bytes = (uint64_t)h->ex.memo_total;
+  if (launches) *launches = h->ex.launches_per_contract;
   return QTPU_OK;
 }
 

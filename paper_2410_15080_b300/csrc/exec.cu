@@ -341,7 +341,7 @@ struct Repr {
 }  // namespace
 
 std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& leaves, const DimMap& dims,
-                       int prec, int* code, bool dry_run) {
+                       int prec, int* code, bool dry_run, uint64_t reuse_bytes) {
   *code = QTPU_OK;
   ex->prec = prec;
   ex->n_leaves = plan.n_leaves;
@@ -368,6 +368,40 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     for (size_t p = 0; p < plan.sliced.size(); ++p)
       for (size_t a = 0; a < leaves[t].ids.size(); ++a)
         if (leaves[t].ids[a] == plan.sliced[p]) ex->leaf_slice[t].push_back({(int)p, leaves[t].strides[a]});
+
+  // Slice reuse: the sliced positions each tensor's value depends on (those
+  // carried by the leaves below it).  A step result that does not depend on
+  // every sliced position is the same for many slices; it is kept in a
+  // buffer of its own (outside the transient arena) and recomputed only when
+  // the values of its positions change (see plan_reuse).
+  const int nsp = (int)plan.sliced.size();
+  const uint64_t full_dep = nsp >= 64 ? ~0ull : ((1ull << nsp) - 1);
+  bool reuse = ex->n_slices > 1 && nsp <= 62 && !fp64;
+  if (const char* e = std::getenv("QTPU_NO_REUSE")) reuse = reuse && std::atoi(e) == 0;
+  ex->reuse_budget = reuse_bytes ? reuse_bytes : ((uint64_t)64 << 30);
+  std::unordered_map<int, uint64_t> tdep;
+  for (int t = 0; t < nl; ++t)
+    for (auto& ps : ex->leaf_slice[t]) tdep[t] |= 1ull << ps.first;
+  for (const PlanStep& ps : plan.steps) tdep[ps.out] = tdep[ps.x] | tdep[ps.y];
+  auto depof = [&](int t) -> uint64_t {
+    auto it = tdep.find(t);
+    return it == tdep.end() ? 0 : it->second;
+  };
+  if (reuse) {
+    // estimate of the kept bytes with one copy each (step results plus their
+    // operand pieces); reuse is off when even that does not fit the budget
+    double est = 0;
+    for (const PlanStep& ps : plan.steps) {
+      if (depof(ps.out) == full_dep) continue;
+      double e = 8;
+      for (int64_t i : ps.batch) e *= sliced.count(i) ? 1 : (double)dims.get(i);
+      for (int64_t i : ps.m) e *= sliced.count(i) ? 1 : (double)dims.get(i);
+      for (int64_t i : ps.n) e *= sliced.count(i) ? 1 : (double)dims.get(i);
+      est += 2 * e;
+    }
+    if (est > (double)ex->reuse_budget) reuse = false;
+  }
+  auto kept = [&](int t) { return reuse && t >= nl && depof(t) != full_dep; };
 
   // per-slice layout of every stored tensor: leaves keep their strides, step
   // results are dense over their non-sliced indices in [batch, M, N] order
@@ -420,6 +454,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
   std::map<int, std::pair<size_t, size_t>> where;
   std::map<int, size_t> offs;
   auto place = [&](int t) {
+    if (kept(t)) return;  // in its own buffer (laid out after lowering)
     const size_t b = (size_t)extent[t] * 8;
     const size_t o = arena.alloc(b);
     where[t] = {o, b};
@@ -608,6 +643,8 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     L->kclass = kclass;
     L->nsrc = g.nops;
     for (int j = 0; j < g.nops; ++j) L->src[j] = src[j];
+    L->dep = 0;
+    for (int j = 0; j < g.nops; ++j) L->dep |= depof(src[j]);
     L->dst = dst;
     L->g = g;
     L->flops = flops;
@@ -663,6 +700,8 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     L->kclass = KC_SPLIT;
     L->nsrc = g.nops;
     for (int j = 0; j < g.nops; ++j) L->src[j] = src[j];
+    L->dep = 0;
+    for (int j = 0; j < g.nops; ++j) L->dep |= depof(src[j]);
     L->dst = dst;
     L->g = g;
     if (!fast_off) {
@@ -859,6 +898,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       Launch L;
       L.kind = LK_CONTRACT64;
       L.kclass = KC_CONTRACT;
+      L.dep = depof(ps.out);
       L.nsrc = 2;
       L.src[0] = ps.x;
       L.src[1] = ps.y;
@@ -987,6 +1027,8 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
           LP.gemm.fuse = side ? FB : FA;
           const std::vector<int>& sm = side ? smB : smA;
           for (size_t j = 0; j < sm.size(); ++j) LP.fuse_src[j] = sm[j];
+          // the pieces it now writes carry the absorbed factors' slices too
+          for (int t : sm) LP.dep |= depof(t);
           LG.opnd_fused[side] = T;
           LG.opnd_kp[side] = (uint32_t)align_up(Ka, 8);
           ex->n_fused_splits++;
@@ -994,6 +1036,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
         LG.kind = LK_GEMM;
         LG.kclass = KC_GEMM;
         LG.dst = dst;
+        LG.dep = depof(ps.out);
         LG.gemm.batch = (int)nb;
         LG.gemm.M = (int)gM;
         LG.gemm.N = (int)gN;
@@ -1046,6 +1089,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       if (r->virt && ((int)(X.ops.size() + Y.ops.size()) > kMaxOps || reuse > 4.0)) {
         const int tid = next_tmp++;
         const Inds vin = live_inds[r == &X ? ps.x : ps.y];
+        for (int o : r->ops) tdep[tid] |= depof(o);
         Launch L;
         if (!gather_launch({r}, vin, {}, GW_DENSE_PAIR, tid, r->flops, KC_CONTRACT, &L))
           return fail(QTPU_ENOTSUP, "internal: cannot lower a fused tensor");
@@ -1181,7 +1225,135 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     R.c64 = c;
   }
   ex->reduce = R;
-  ex->launches_per_contract = (plan.steps.empty() ? 0 : (int64_t)ex->launches.size() * ex->n_slices) + 1;
+
+  // ---- slice reuse: which launches keep their output, in how many copies,
+  // and the nested order of the sliced positions for a full contraction.
+  // A kept launch L depends on the positions D.  In the nested loop (order
+  // pi, outermost first) let P be the longest prefix of pi inside D: with
+  // copies indexed by the positions D \ P, every value of D is computed once
+  // per contraction (valid while P is unchanged, and P changes only in the
+  // outer loops); pi is chosen to minimise the kept bytes.  Over the budget,
+  // the largest launches fall back to one copy recomputed whenever a
+  // position up to its innermost one in pi changes.
+  ex->loop_order.clear();
+  for (int p = 0; p < nsp; ++p) ex->loop_order.push_back(p);
+  ex->inter_memo.assign(next_tmp - nl + 1, -1);
+  ex->memo_total = 0;
+  std::vector<size_t> lbytes(ex->launches.size(), 0);
+  for (size_t i = 0; i < ex->launches.size(); ++i) {
+    Launch& L = ex->launches[i];
+    L.memo = false;
+    L.copies = 1;
+    L.runs = ex->n_slices;
+    L.epoch_pos.clear();
+    L.copy_pos.clear();
+    if (!reuse) continue;
+    if (L.dst >= nl) {
+      L.memo = kept(L.dst);
+      if (L.memo) {
+        lbytes[i] = align_up((size_t)extent[L.dst] * 8, 1024);
+        ex->inter_memo[L.dst - nl] = (int)i;
+      }
+    } else if (L.kind == LK_GATHER && (L.dst == DST_SPLIT_A || L.dst == DST_SPLIT_B) && L.dep != full_dep) {
+      L.memo = true;
+      lbytes[i] = align_up((size_t)np * L.g.n_rows * L.g.Kp * es, 1024);
+    }
+  }
+  if (reuse) {
+    const std::vector<int64_t>& sd = ex->slice_dims;
+    auto prefix_len = [&](const std::vector<int>& pi, uint64_t D) {
+      size_t k = 0;
+      while (k < pi.size() && ((D >> pi[k]) & 1)) ++k;
+      return k;
+    };
+    auto kept_bytes = [&](const std::vector<int>& pi) {
+      double tot = 0;
+      for (size_t i = 0; i < ex->launches.size(); ++i) {
+        const Launch& L = ex->launches[i];
+        if (!L.memo) continue;
+        const size_t k = prefix_len(pi, L.dep);
+        double c = 1;
+        for (size_t j = k; j < pi.size(); ++j)
+          if ((L.dep >> pi[j]) & 1) c *= (double)sd[pi[j]];
+        tot += c * (double)lbytes[i];
+      }
+      return tot;
+    };
+    std::vector<int> pi = ex->loop_order, best = pi;
+    double best_b = kept_bytes(pi);
+    if (nsp <= 7) {
+      std::sort(pi.begin(), pi.end());
+      do {
+        const double b = kept_bytes(pi);
+        if (b < best_b) best_b = b, best = pi;
+      } while (std::next_permutation(pi.begin(), pi.end()));
+    } else {  // pairwise swaps until no improvement
+      for (bool more = true; more;) {
+        more = false;
+        for (int a = 0; a < nsp; ++a)
+          for (int b = a + 1; b < nsp; ++b) {
+            std::vector<int> q = best;
+            std::swap(q[a], q[b]);
+            const double v = kept_bytes(q);
+            if (v < best_b) best_b = v, best = q, more = true;
+          }
+      }
+    }
+    ex->loop_order = best;
+    std::vector<int> pos_of(nsp);
+    for (int j = 0; j < nsp; ++j) pos_of[best[j]] = j;
+    // per kept launch: copies over D \ P, epoch P
+    std::vector<std::pair<double, size_t>> by_size;
+    for (size_t i = 0; i < ex->launches.size(); ++i) {
+      Launch& L = ex->launches[i];
+      if (!L.memo) continue;
+      const size_t k = prefix_len(best, L.dep);
+      for (size_t j = 0; j < best.size(); ++j) {
+        if (!((L.dep >> best[j]) & 1)) continue;
+        (j < k ? L.epoch_pos : L.copy_pos).push_back(best[j]);
+      }
+      L.copies = 1;
+      for (int p : L.copy_pos) L.copies *= sd[p];
+      by_size.push_back({(double)L.copies * (double)lbytes[i], i});
+    }
+    double total = 0;
+    for (auto& b : by_size) total += b.first;
+    std::sort(by_size.begin(), by_size.end(), [](const std::pair<double, size_t>& a, const std::pair<double, size_t>& b) {
+      return a.first > b.first || (a.first == b.first && a.second < b.second);
+    });
+    for (auto& b : by_size) {
+      if (total <= (double)ex->reuse_budget) break;
+      Launch& L = ex->launches[b.second];
+      if (L.copies == 1) continue;
+      // one copy, valid while every position up to its innermost one holds
+      int m = -1;
+      for (int j = 0; j < nsp; ++j)
+        if ((L.dep >> best[j]) & 1) m = j;
+      L.epoch_pos.assign(best.begin(), best.begin() + (m + 1));
+      L.copy_pos.clear();
+      total -= b.first - (double)lbytes[b.second];
+      L.copies = 1;
+    }
+    size_t off = 0;
+    for (size_t i = 0; i < ex->launches.size(); ++i) {
+      Launch& L = ex->launches[i];
+      if (!L.memo) continue;
+      L.memo_bytes = lbytes[i];
+      L.memo_off = off;
+      off += (size_t)L.copies * lbytes[i];
+      L.runs = 1;
+      for (int p : L.epoch_pos) L.runs *= sd[p];
+      for (int p : L.copy_pos) L.runs *= sd[p];
+    }
+    ex->memo_total = off;
+  }
+  ex->flops_executed = ex->flops_no_reuse = 0;
+  ex->launches_per_contract = 1;
+  for (const Launch& L : ex->launches) {
+    ex->flops_executed += L.flops * (double)L.runs;
+    ex->flops_no_reuse += L.flops * (double)ex->n_slices;
+    ex->launches_per_contract += L.runs;
+  }
 
   // ---- concurrent leaf splits: in an unsliced plan, a GEMM operand gathered
   // from leaves only does not depend on the chain; give it its own buffer
@@ -1259,7 +1431,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       !dalloc((void**)&ex->partial, (size_t)ex->n_slices * std::max<int64_t>(ex->final_size, 1) * 8) ||
       !dalloc((void**)&ex->status, 16) || !dalloc((void**)&ex->out_stage, (size_t)R.g.n_out * 8 + 8) ||
       !dalloc((void**)&ex->dot_scratch, dot_scratch_entries(ex->sm_count) * sizeof(float2)) ||
-      !dalloc((void**)&ex->wbuf, ex->wbuf_bytes)) {
+      !dalloc((void**)&ex->wbuf, ex->wbuf_bytes) || !dalloc((void**)&ex->memobuf, ex->memo_total)) {
     exec_free(ex);
     return fail(QTPU_ENOMEM, "device workspace allocation failed");
   }
@@ -1298,20 +1470,40 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
   ex->inter_off.assign(next_tmp - nl + 1, 0);
   for (auto& kv : offs)
     if (kv.first >= nl) ex->inter_off[kv.first - nl] = kv.second;
-  // tensor maps of the split buffers (fixed addresses)
+  // tensor maps of the split buffers (fixed addresses); an operand buffer
+  // kept across slices gets one map per copy
   for (size_t i = 0; i < ex->launches.size(); ++i) {
     Launch& L = ex->launches[i];
     if (L.kind != LK_GEMM) continue;
     uint8_t* base[2];
     int64_t kp[2];
     for (int side = 0; side < 2; ++side) {
+      int owner = -1;
       if (L.opnd_split[side] >= 0) {
         const Launch& S = ex->launches[L.opnd_split[side]];
-        base[side] = S.side >= 0 ? ex->sidebuf + S.side_off : ex->splitbuf + (side ? ex->split_a_bytes : 0);
+        if (S.memo) owner = L.opnd_split[side];
+        base[side] = S.memo ? ex->memobuf + S.memo_off
+                            : (S.side >= 0 ? ex->sidebuf + S.side_off : ex->splitbuf + (side ? ex->split_a_bytes : 0));
         kp[side] = S.g.Kp;
       } else {
-        base[side] = ex->arena + ex->inter_off[L.opnd_fused[side] - nl];
+        const int T = L.opnd_fused[side];
+        owner = ex->inter_memo[T - nl];
+        base[side] = owner >= 0 ? ex->memobuf + ex->launches[owner].memo_off : ex->arena + ex->inter_off[T - nl];
         kp[side] = L.opnd_kp[side];
+      }
+      L.opnd_memo[side] = owner;
+      L.tm_copies[side].clear();
+      const int64_t rows = side ? L.gemm.N : L.gemm.M;
+      const int box = side ? gemm_block_n() : 128;
+      if (owner >= 0) {
+        const Launch& O = ex->launches[owner];
+        L.tm_copies[side].resize((size_t)O.copies);
+        for (int64_t c = 0; c < O.copies; ++c)
+          if (!make_operand_map(&L.tm_copies[side][c], base[side] + (size_t)c * O.memo_bytes, prec, L.gemm.batch,
+                                rows, L.gemm.K, kp[side], box)) {
+            exec_free(ex);
+            return fail(QTPU_ECUDA, "cuTensorMapEncodeTiled failed");
+          }
       }
     }
     if (!make_operand_map(&L.gemm.tmA, base[0], prec, L.gemm.batch, L.gemm.M, L.gemm.K, kp[0], 128) ||
@@ -1399,13 +1591,27 @@ std::string exec_describe(const Executor* ex) {
     for (int j = 0; j < L.nsrc; ++j) o << (j ? "," : "") << L.src[j];
     if (L.kind == LK_GEMM) o << "-";
     o << " dst=" << L.dst << (L.side >= 0 ? " side" : "") << " flops=" << (long long)L.flops
-      << " bytes=" << (long long)L.bytes << "\n";
+      << " bytes=" << (long long)L.bytes;
+    if (L.memo) {
+      o << " kept copies=" << L.copies << " runs=" << L.runs << " copy_pos=";
+      for (size_t j = 0; j < L.copy_pos.size(); ++j) o << (j ? "," : "") << L.copy_pos[j];
+      if (L.copy_pos.empty()) o << "-";
+      o << " epoch_pos=";
+      for (size_t j = 0; j < L.epoch_pos.size(); ++j) o << (j ? "," : "") << L.epoch_pos[j];
+      if (L.epoch_pos.empty()) o << "-";
+    }
+    o << "\n";
   };
   for (size_t i = 0; i < ex->launches.size(); ++i) one(ex->launches[i], i);
   o << "reduce slices=" << ex->n_slices << " out=" << ex->reduce.g.n_out << " loop=" << ex->reduce.g.n_loop << "\n";
   o << "summary launches_per_slice=" << ex->launches.size() << " tensor_core_steps=" << ex->n_tc_steps
     << " fused_steps=" << ex->n_fused_steps << " fused_splits=" << ex->n_fused_splits << " side_splits=" << ex->n_side << " arena_bytes=" << ex->arena_bytes
     << " split_bytes=" << ex->split_bytes << "\n";
+  o << "reuse kept_bytes=" << ex->memo_total << " loop_order=";
+  for (size_t j = 0; j < ex->loop_order.size(); ++j) o << (j ? "," : "") << ex->loop_order[j];
+  if (ex->loop_order.empty()) o << "-";
+  o << " launches_per_contract=" << ex->launches_per_contract << " flops_executed=" << (long long)ex->flops_executed
+    << " flops_all_slices=" << (long long)ex->flops_no_reuse << "\n";
   return o.str();
 }
 
@@ -1437,13 +1643,29 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
   std::vector<int64_t> loff(nl, 0);
   std::vector<int64_t> digit(ex->slice_dims.size(), 0);
   cudaError_t ce = cudaSuccess;
+  // slice reuse: copy index and epoch of a kept launch under the current
+  // values of the sliced positions
+  auto mixed = [&](const std::vector<int>& pos) {
+    int64_t v = 0;
+    for (int p : pos) v = v * ex->slice_dims[p] + digit[p];
+    return v;
+  };
+  auto kept_ptr = [&](const Launch& L) -> uint8_t* {
+    return ex->memobuf + L.memo_off + (size_t)mixed(L.copy_pos) * L.memo_bytes;
+  };
+  std::vector<std::vector<int64_t>> stored(ex->launches.size());
+  for (size_t i = 0; i < ex->launches.size(); ++i)
+    if (ex->launches[i].memo) stored[i].assign((size_t)ex->launches[i].copies, -1);
   auto src_ptr = [&](int t) -> const void* {
     if (t < nl) return (const uint8_t*)leaves[t].ptr + loff[t] * (int64_t)dt_bytes(leaves[t].dt);
+    const int owner = (size_t)(t - nl) < ex->inter_memo.size() ? ex->inter_memo[t - nl] : -1;
+    if (owner >= 0) return kept_ptr(ex->launches[owner]);
     return ex->arena + ex->inter_off[t - nl];
   };
   const bool sided = ex->n_side > 0 && count == ex->n_slices && ex->n_slices == 1;
   const Launch* cur = nullptr;
   auto dst_ptr = [&](int d, int64_t s) -> void* {
+    if (cur && cur->memo && d != DST_OUT && d != DST_PARTIAL) return kept_ptr(*cur);
     switch (d) {
       case DST_SIDE: return ex->sidebuf + cur->side_off;
       case DST_PARTIAL: return ex->partial + (size_t)s * ex->final_size * 8;
@@ -1474,6 +1696,8 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
     if (L.kind == LK_GEMM) {
       GemmArgs g = L.gemm;
       g.C = dst_ptr(L.dst, s);
+      if (L.opnd_memo[0] >= 0) g.tmA = L.tm_copies[0][(size_t)mixed(ex->launches[L.opnd_memo[0]].copy_pos)];
+      if (L.opnd_memo[1] >= 0) g.tmB = L.tm_copies[1][(size_t)mixed(ex->launches[L.opnd_memo[1]].copy_pos)];
       for (int j = 0; g.fuse.on && j < g.fuse.nsmall; ++j) g.fuse.wptr[j] = src_ptr(L.fuse_src[j]);
       return launch_gemm(g, ex->sm_count, st);
     }
@@ -1508,18 +1732,34 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
     if (ce == cudaSuccess) ce = run_one(ex->reduce, 0, true);
     return ce;
   }
-  for (int64_t s = first; s < first + count && ce == cudaSuccess && !ex->launches.empty(); ++s) {
-    int64_t r = s;
-    for (int j = (int)ex->slice_dims.size() - 1; j >= 0; --j) {
-      digit[j] = r % ex->slice_dims[j];
-      r /= ex->slice_dims[j];
+  // A full contraction visits the slices in the nested order loop_order
+  // (outermost first), a range in slice-id order (last sliced index
+  // fastest); either way each slice's result lands in partial[its id].
+  const bool nested = first == 0 && count == ex->n_slices && ex->memo_total > 0;
+  const int nsp = (int)ex->slice_dims.size();
+  for (int64_t it = 0; it < count && ce == cudaSuccess && !ex->launches.empty(); ++it) {
+    int64_t r = nested ? it : first + it;
+    for (int k = nsp - 1; k >= 0; --k) {
+      const int p = nested ? ex->loop_order[k] : k;
+      digit[p] = r % ex->slice_dims[p];
+      r /= ex->slice_dims[p];
     }
+    int64_t s = 0;  // the slice id
+    for (int p = 0; p < nsp; ++p) s = s * ex->slice_dims[p] + digit[p];
     for (int t = 0; t < nl; ++t) {
       int64_t o = 0;
       for (auto& ps : ex->leaf_slice[t]) o += digit[ps.first] * ps.second;
       loff[t] = o;
     }
-    for (auto& L : ex->launches) {
+    for (size_t i = 0; i < ex->launches.size(); ++i) {
+      const Launch& L = ex->launches[i];
+      if (L.memo) {
+        // a copy computed in the current epoch is still valid
+        int64_t& st_ep = stored[i][(size_t)mixed(L.copy_pos)];
+        const int64_t ep = mixed(L.epoch_pos);
+        if (st_ep == ep) continue;
+        st_ep = ep;
+      }
       ce = run_one(L, s, false);
       if (ce != cudaSuccess) break;
     }
@@ -1626,6 +1866,8 @@ void exec_free(Executor* ex) {
   ex->dot_scratch = nullptr;
   if (ex->wbuf) cudaFree(ex->wbuf);
   ex->wbuf = nullptr;
+  if (ex->memobuf) cudaFree(ex->memobuf);
+  ex->memobuf = nullptr;
   ex->arena = ex->splitbuf = ex->partial = nullptr;
   ex->status = nullptr;
   ex->out_stage = nullptr;

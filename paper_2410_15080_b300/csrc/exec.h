@@ -55,6 +55,21 @@ struct Launch {
   int fuse_src[kMaxOps] = {};
   // fast gather/split with a large W table: its byte offset in Executor::wbuf
   int64_t wg_off = -1;
+  // slice reuse: the sliced positions this launch's value depends on; a
+  // launch that does not depend on all of them is kept (memo) in its own
+  // buffer across slices, `copies` copies indexed by the values of the
+  // positions copy_pos, and runs only when no copy for the current values is
+  // valid -- a stored copy is valid while the positions epoch_pos keep the
+  // values it was computed with
+  uint64_t dep = 0;
+  bool memo = false;
+  std::vector<int> epoch_pos, copy_pos;
+  int64_t copies = 1;
+  size_t memo_off = 0, memo_bytes = 0;  // copy 0 in Executor::memobuf, bytes per copy
+  int64_t runs = 1;                     // executions per full contraction
+  // LK_GEMM whose operand buffer is kept with copies: one map per copy
+  std::vector<CUtensorMap> tm_copies[2];
+  int opnd_memo[2] = {-1, -1};          // launch index owning that operand buffer
 };
 
 struct Profiler {
@@ -116,15 +131,27 @@ struct Executor {
   cudaStream_t side_stream = nullptr;
   std::vector<cudaEvent_t> side_ev;  // one per side launch, plus fork and join
   double planned_side_bytes = 0;
+  // slice reuse (sliced plans): nested order of the sliced positions for a
+  // full contraction (outermost first), the buffer of kept results, and per
+  // intermediate (id - n_leaves) the launch whose kept output holds it (-1:
+  // the transient arena)
+  std::vector<int> loop_order;
+  uint8_t* memobuf = nullptr;
+  size_t memo_total = 0;
+  uint64_t reuse_budget = 0;
+  std::vector<int> inter_memo;
+  double flops_executed = 0;     // useful FLOPs one full contraction executes
+  double flops_no_reuse = 0;     // the same with every slice computed in full
   size_t workspace_bytes() const {
-    return arena_bytes + split_bytes + side_bytes + wbuf_bytes + (size_t)n_slices * final_size * 8;
+    return arena_bytes + split_bytes + side_bytes + wbuf_bytes + memo_total + (size_t)n_slices * final_size * 8;
   }
 };
 
 // Build launch descriptors and allocate the workspace.  Returns an empty
 // string on success, else an error message (*code receives a qtpu_status).
+// reuse_bytes: device memory for results kept across slices (0 = default).
 std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& leaves, const DimMap& dims,
-                       int prec, int* code, bool dry_run = false);
+                       int prec, int* code, bool dry_run = false, uint64_t reuse_bytes = 0);
 // One line per launch of the lowered contraction (kind, operands, shape,
 // useful FLOPs, algorithmic bytes) -- available after exec_build, also on a
 // dry run.

@@ -21,7 +21,8 @@ PREC = {"fp64": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3}
 QTPU_QT, QTPU_CT = 0, 1
 
 SYMBOLS = ["qtpu_htn_create", "qtpu_htn_add_tensor", "qtpu_htn_set_output", "qtpu_htn_plan",
-           "qtpu_htn_plan_info", "qtpu_htn_lowering_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats", "qtpu_htn_contract",
+           "qtpu_htn_plan_info", "qtpu_htn_lowering_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats",
+           "qtpu_htn_exec_stats", "qtpu_htn_contract",
            "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_contract_slices", "qtpu_htn_sync", "qtpu_htn_selftest_timeout", "qtpu_htn_destroy",
            "qtpu_htn_profile", "qtpu_htn_profile_read", "qtpu_pairwise_contract_noalloc",
            "qtpu_pairwise_noalloc_scratch_bytes", "qtpu_noalloc_status", "qtpu_noalloc_selftest_timeout",
@@ -40,7 +41,8 @@ class QtpuError(RuntimeError):
 class PlanOpts(C.Structure):
     _fields_ = [("max_intermediate_bytes", C.c_uint64), ("n_slices", C.c_uint32),
                 ("slice_dim", C.c_uint32), ("prec", C.c_int), ("cost_model", C.c_int),
-                ("seed", C.c_uint64), ("autotune_table", C.c_char_p), ("n_candidates", C.c_uint32)]
+                ("seed", C.c_uint64), ("autotune_table", C.c_char_p), ("n_candidates", C.c_uint32),
+                ("reuse_bytes", C.c_uint64)]
 
 
 _lib = None
@@ -64,6 +66,8 @@ def lib():
         L.qtpu_htn_output_size.argtypes = [vp, i64p]
         L.qtpu_htn_plan_stats.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int),
                                           C.POINTER(C.c_int), C.POINTER(C.c_uint64), i64p]
+        L.qtpu_htn_exec_stats.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                          C.POINTER(C.c_uint64), i64p]
         L.qtpu_htn_profile.argtypes = [vp, C.c_int]
         dp = C.POINTER(C.c_double)
         L.qtpu_htn_profile_read.argtypes = [vp, C.c_int, dp, i64p, dp, dp]
@@ -144,8 +148,9 @@ class HTN:
         self._check(self._L.qtpu_htn_set_output(self._h, len(inds), _arr(inds)))
 
     def plan(self, prec: str = "bf16x3", max_intermediate_bytes: int = 0, n_slices: int = 0,
-             slice_dim: int = 0, seed: int = 0, n_candidates: int = 0):
-        o = PlanOpts(max_intermediate_bytes, n_slices, slice_dim, PREC[prec], 0, seed, None, n_candidates)
+             slice_dim: int = 0, seed: int = 0, n_candidates: int = 0, reuse_bytes: int = 0):
+        o = PlanOpts(max_intermediate_bytes, n_slices, slice_dim, PREC[prec], 0, seed, None, n_candidates,
+                     reuse_bytes)
         self._check(self._L.qtpu_htn_plan(self._h, C.byref(o)))
 
     def plan_info(self) -> str:
@@ -173,6 +178,14 @@ class HTN:
                                                 C.byref(nl)))
         return {"flops_total": f.value, "n_steps": ns.value, "n_tensor_core_steps": nt.value,
                 "workspace_bytes": ws.value, "launches_per_contract": nl.value}
+
+    def exec_stats(self) -> dict:
+        """FLOPs one contract call executes (after slice reuse) and without
+        reuse, kept bytes, kernel launches."""
+        fe, fa, kb, nl = C.c_double(), C.c_double(), C.c_uint64(), C.c_int64()
+        self._check(self._L.qtpu_htn_exec_stats(self._h, C.byref(fe), C.byref(fa), C.byref(kb), C.byref(nl)))
+        return {"flops_executed": fe.value, "flops_all_slices": fa.value, "kept_bytes": kb.value,
+                "launches": nl.value}
 
     def profile(self, enable: bool = True):
         self._check(self._L.qtpu_htn_profile(self._h, 1 if enable else 0))

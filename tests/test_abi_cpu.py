@@ -185,7 +185,7 @@ def test_mid_ring_lowering_writes_operands_from_gemm_epilogues():
     from paper_2410_15080_b300.htn import lowering_text
     net = synth.ring_htn()
     t = lowering_text(net.inds(), net.dims(), net.output)
-    summary = t.splitlines()[-1]
+    summary = next(l for l in t.splitlines() if l.startswith("summary "))
     assert "tensor_core_steps=6" in summary and "fused_splits=5" in summary, summary
     assert "launches_per_slice=15" in summary, summary
     # each producer stores the next step's K as its column (N) group
@@ -206,3 +206,70 @@ def test_100q_absorptions_lower_to_the_typed_fast_path():
     assert lines, t
     assert all(" fast " in l and " big=2 " in l for l in lines), lines
     assert all(" generic " not in l for l in t.splitlines())
+
+
+def _host_handle(net, **plan_kw):
+    from paper_2410_15080_b300.htn import HTN
+    h = HTN(device=-1)
+    for t in net.tensors:
+        h.add_tensor(t.inds, list(t.data.shape))
+    h.set_output(net.output)
+    h.plan("bf16x3", **plan_kw)
+    return h
+
+
+def test_slice_reuse_executes_each_distinct_value_once():
+    """Slice reuse on the 100-qubit 1024-slice plan: the FLOPs one contraction
+    executes are the plan's per-slice FLOPs of every launch times the number
+    of distinct values of the sliced indices it depends on, far below the
+    plan's total; with no budget every slice is computed in full."""
+    import synth
+    net = synth.ring_chords_htn(materialize=False)
+    kw = dict(max_intermediate_bytes=8 << 30, n_slices=1024, slice_dim=4, n_candidates=256)
+    h = _host_handle(net, **kw)
+    st = h.exec_stats()
+    plan_total = h.plan_stats()["flops_total"]
+    t = h.lowering_info()
+    h.close()
+    assert st["flops_all_slices"] == pytest.approx(plan_total, rel=1e-12)
+    assert st["flops_executed"] < plan_total / 10
+    assert 0 < st["kept_bytes"] <= 64 << 30
+    # recompute the executed FLOPs from the launch list: each launch's FLOPs
+    # times its runs (1024 for a launch that is not kept)
+    fe, n_launch = 0.0, 1
+    for l in t.splitlines():
+        if not l.startswith("launch "):
+            continue
+        f = dict(w.split("=", 1) for w in l.split() if "=" in w)
+        runs = int(f["runs"]) if "runs" in f else 1024
+        if "runs" in f:  # a kept launch runs once per distinct value of its positions
+            c = int(f["copies"])
+            ep = [] if f["epoch_pos"] == "-" else f["epoch_pos"].split(",")
+            cp = [] if f["copy_pos"] == "-" else f["copy_pos"].split(",")
+            assert c == 4 ** len(cp) and runs == 4 ** (len(ep) + len(cp)) and runs < 1024
+        fe += int(f["flops"]) * runs
+        n_launch += runs
+    assert fe == pytest.approx(st["flops_executed"], rel=1e-12)
+    assert n_launch == st["launches"]
+    h2 = _host_handle(net, reuse_bytes=1, **kw)
+    st2 = h2.exec_stats()
+    h2.close()
+    assert st2["flops_executed"] == pytest.approx(plan_total, rel=1e-12) and st2["kept_bytes"] == 0
+
+
+def test_slice_reuse_budget_falls_back_to_one_copy():
+    """Under a budget below the all-copies layout, the largest kept launches
+    keep one copy (more runs), the kept bytes respect the budget, and the
+    executed FLOPs lie between the unlimited-reuse and no-reuse figures."""
+    import synth
+    net = synth.ring_chords_htn(materialize=False)
+    kw = dict(max_intermediate_bytes=8 << 30, n_slices=1024, slice_dim=4, n_candidates=256)
+    full = _host_handle(net, **kw)
+    sf = full.exec_stats()
+    full.close()
+    budget = sf["kept_bytes"] // 2
+    h = _host_handle(net, reuse_bytes=budget, **kw)
+    s = h.exec_stats()
+    h.close()
+    assert s["kept_bytes"] <= budget
+    assert sf["flops_executed"] < s["flops_executed"] < sf["flops_all_slices"]

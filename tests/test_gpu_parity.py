@@ -312,8 +312,9 @@ def test_epilogue_written_operand_pieces(mode, monkeypatch):
                 synth.ring_htn(n_sub=4, gates_per_edge=2, wires_per_edge=1, k=3, seed=6),
                 synth.ring_htn(seed=3)):
         t = lowering_text(net.inds(), net.dims(), net.output)
-        n_fused = int(t.splitlines()[-1].split("fused_splits=")[1].split()[0])
-        assert (n_fused > 0) == (mode != "off"), t.splitlines()[-1]
+        summary = next(l for l in t.splitlines() if l.startswith("summary "))
+        n_fused = int(summary.split("fused_splits=")[1].split()[0])
+        assert (n_fused > 0) == (mode != "off"), summary
         seen |= {w for l in t.splitlines() for w in l.split() if w.startswith("k=")}
         got, _ = contract_gpu(net, prec="bf16x3")
         assert rel_err(got, oracle_value(net)) <= REL_TOL
@@ -339,3 +340,72 @@ def test_operand_split_with_a_summed_wire_index():
     assert st["n_tensor_core_steps"] == 1
     ref = np.einsum("bmxy,xk,bnky->bmn", A, synth.WIRE_CT, B).ravel()
     assert rel_err(got, ref) <= REL_TOL
+
+
+def _reuse_net():
+    # ring + chords topology with smaller bonds, 16 observables: with 256 wire
+    # slices 6 steps run on the tensor cores, 5 of them kept across slices,
+    # several with operand pieces kept in multiple copies
+    return synth.ring_chords_htn(k=16, seed=9, gates_per_chord=1)
+
+
+@pytest.mark.parametrize("reuse", ["all copies", "one copy", "off"])
+def test_slice_reuse_matches_oracle(reuse):
+    """Results kept across slices (all copies, the one-copy fallback under a
+    small budget, or reuse off) give the oracle's value; with reuse the
+    contraction executes fewer FLOPs than the plan's total."""
+    from paper_2410_15080_b300.htn import HTN, lowering_text
+    net = _reuse_net()
+    ref = oracle_value(net)
+    kw = dict(n_slices=256, slice_dim=4)
+    probe = HTN(device=-1)
+    for t in net.tensors:
+        probe.add_tensor(t.inds, list(t.data.shape))
+    probe.set_output(net.output)
+    probe.plan("bf16x3", **kw)
+    full = probe.exec_stats()
+    probe.close()
+    assert full["kept_bytes"] > 0
+    t = lowering_text(net.inds(), net.dims(), net.output, **kw)
+    assert sum(" gemm " in l and " kept " in l for l in t.splitlines()) >= 3
+    assert sum(" split " in l and " kept " in l and " copies=1 " not in l for l in t.splitlines()) >= 2
+    budget = {"all copies": 0, "one copy": max(1, full["kept_bytes"] // 3), "off": 1}[reuse]
+    import torch
+    from paper_2410_15080_b300 import from_network
+    from tests.gpu_util import to_device
+    h = from_network(to_device(net), net.output, prec="bf16x3", reuse_bytes=budget, **kw)
+    st = h.exec_stats()
+    out = h.contract()
+    h.sync()
+    got = out.cpu().numpy()
+    # a second call (the kept copies are recomputed per call) gives the same bits
+    out2 = h.contract()
+    h.sync()
+    torch.cuda.synchronize()
+    assert np.array_equal(out2.cpu().numpy(), got)
+    h.close()
+    assert rel_err(got, ref) <= REL_TOL, st
+    if reuse == "off":
+        assert st["kept_bytes"] == 0 and st["flops_executed"] == pytest.approx(st["flops_all_slices"])
+    else:
+        assert 0 < st["kept_bytes"] and st["flops_executed"] < st["flops_all_slices"]
+    if reuse == "one copy":
+        assert st["kept_bytes"] <= budget and st["flops_executed"] > full["flops_executed"]
+
+
+def test_slice_ranges_with_reuse_add_up():
+    """Slice ranges (visited in slice-id order, recomputing kept results when
+    their indices change) add up to the full contraction (nested order)."""
+    import torch
+    from paper_2410_15080_b300 import from_network
+    from tests.gpu_util import to_device
+    net = _reuse_net()
+    h = from_network(to_device(net), net.output, prec="bf16x3", n_slices=256, slice_dim=4)
+    full = h.contract().clone()
+    parts = [h.contract_slices(a, b - a).clone() for a, b in [(0, 37), (37, 200), (200, 256)]]
+    h.sync()
+    torch.cuda.synchronize()
+    tot = sum(p.cpu().numpy() for p in parts)
+    h.close()
+    assert rel_err(tot, full.cpu().numpy()) <= 1e-12
+    assert rel_err(full.cpu().numpy(), oracle_value(net)) <= REL_TOL
