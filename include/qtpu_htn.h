@@ -91,9 +91,10 @@ typedef struct {
                                       the fewest total FLOPs (ties: the lower
                                       seed); candidates that cannot meet the
                                       limit are skipped                      */
-  uint64_t reuse_bytes;            /* sliced plans: device memory for results
-                                      kept across slices (0 = 64 GiB); see
-                                      qtpu_htn_plan                           */
+  uint64_t reuse_bytes;            /* sliced plans: device memory for
+                                      intermediates with the copies slice
+                                      reuse keeps (0 = 64 GiB, 1 = reuse
+                                      off); see qtpu_htn_plan                 */
 } qtpu_plan_opts;
 
 /* Create an empty network bound to CUDA device `device` and the CUDA stream
@@ -132,18 +133,18 @@ qtpu_status qtpu_htn_set_output(qtpu_htn* h, int n, const int64_t* index_ids);
  * tensors, QTPU_EINVAL on an unknown output id, QTPU_ELIMIT if the limit
  * cannot be met, QTPU_ENOTSUP on a size of 2^255 or more.
  *
- * Slice reuse (a sliced plan with a tensor-core precision): a pairwise step
- * whose operands do not carry every sliced index has the same value for all
- * slices that agree on the sliced indices below it.  Such a result (and the
- * operand pieces made from it) is computed once per value of those indices
- * and kept in a device buffer of its own for the slices that need it; the
- * slices of a full contraction are visited in a nested order of the sliced
- * indices chosen to need the fewest kept bytes.  The plan (its text and
- * FLOPs) is unchanged; the FLOPs actually executed are reported by
- * qtpu_htn_exec_stats.  The kept bytes stay within reuse_bytes: over it, the
- * largest kept results keep one copy and are recomputed when an outer index
- * changes; if even that does not fit, every slice is computed in full.  Each
- * slice's result is the same arithmetic either way. */
+ * Slice reuse (sliced plans): a step's value depends only on the sliced
+ * indices carried by the leaves below it, and not on those an earlier step
+ * already contracted.  Every launch therefore runs once per value of the
+ * sliced indices its inputs depend on; a step that contracts a sliced index
+ * adds its result up over that index's values (compensated FP32 pairs, like
+ * a K chunk of the tensor-core accumulation; the last step adds every value
+ * into an FP64 partial), and its result is kept in one copy per value of the
+ * sliced indices it still depends on.  Where those copies would exceed
+ * reuse_bytes, some sliced indices are held fixed in an outer loop instead
+ * (all of them: one slice at a time, the plan's own schedule).  The plan (its
+ * text and FLOPs) is unchanged; qtpu_htn_exec_stats reports what a
+ * contraction executes.  reuse_bytes = 1 turns reuse off. */
 qtpu_status qtpu_htn_plan(qtpu_htn* h, const qtpu_plan_opts* opts);
 
 /* Canonical plan text (order, index groups, per-slice sizes and FLOPs,
@@ -166,8 +167,9 @@ qtpu_status qtpu_htn_output_size(const qtpu_htn* h, int64_t* n);
 
 /* Useful FLOPs of the planned contraction (2 per multiply-add, all slices),
  * as a double; the number of pairwise steps and of steps that run on the
- * tensor cores; the device workspace the handle owns; and the number of
- * kernel launches one contract call makes.  Any pointer may be NULL. */
+ * tensor cores (0 on a host-only handle); the device workspace the handle
+ * owns (on a host-only handle: would own); and the number of kernel
+ * launches one contract call makes.  Any pointer may be NULL. */
 qtpu_status qtpu_htn_plan_stats(const qtpu_htn* h, double* flops_total,
                                 int* n_steps, int* n_tensor_core_steps,
                                 uint64_t* workspace_bytes,
@@ -175,7 +177,8 @@ qtpu_status qtpu_htn_plan_stats(const qtpu_htn* h, double* flops_total,
 
 /* What one full contract call executes: the useful FLOPs (2 per multiply-add)
  * after slice reuse, the same with every slice computed in full (the plan's
- * total), the device bytes of results kept across slices, and the kernel
+ * total), the extra device bytes that slice reuse uses for kept copies of
+ * intermediates (beyond computing one slice at a time), and the kernel
  * launches.  Available after plan, also on a host-only handle.  Any pointer
  * may be NULL; QTPU_ESTATE before plan. */
 qtpu_status qtpu_htn_exec_stats(const qtpu_htn* h, double* flops_executed,

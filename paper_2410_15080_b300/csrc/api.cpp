@@ -211,11 +211,11 @@ qtpu_status qtpu_htn_plan_stats(const qtpu_htn* h, double* flops_total, int* n_s
                                 uint64_t* ws, int64_t* launches) {
   if (!h) return QTPU_EINVAL;
   if (!h->planned) return QTPU_ESTATE;
-  if (launches) *launches = h->built ? h->ex.launches_per_contract : 0;
+  if (launches) *launches = h->ex.lowered ? h->ex.launches_per_contract : 0;
   if (flops_total) *flops_total = h->plan.flops_total.to_double();
   if (n_steps) *n_steps = (int)h->plan.steps.size();
   if (n_tc) *n_tc = h->built ? h->ex.n_tc_steps : 0;
-  if (ws) *ws = h->built ? (uint64_t)h->ex.workspace_bytes() : 0;
+  if (ws) *ws = h->ex.lowered ? (uint64_t)h->ex.workspace_bytes() : 0;
   return QTPU_OK;
 }
 
@@ -225,7 +225,7 @@ qtpu_status qtpu_htn_exec_stats(const qtpu_htn* h, double* flops_executed, doubl
   if (!h->planned || !h->ex.lowered) return QTPU_ESTATE;
   if (flops_executed) *flops_executed = h->ex.flops_executed;
   if (flops_all_slices) *flops_all_slices = h->ex.flops_no_reuse;
-  if (kept_bytes) *kept_bytes = (uint64_t)h->ex.memo_total;
+  if (kept_bytes) *kept_bytes = (uint64_t)h->ex.kept_bytes;
   if (launches) *launches = h->ex.launches_per_contract;
   return QTPU_OK;
 }

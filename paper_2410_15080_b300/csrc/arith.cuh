@@ -95,6 +95,22 @@ struct AccD {
   }
 };
 
+// (hi, lo) pair plus (hi, lo) pair, compensated and renormalised
+__device__ __forceinline__ float2 pair_sum(float2 a, float2 b) {
+  Acc t;
+  t.hi = a.x;
+  t.lo = a.y;
+  t.add(b);
+  return t.get();
+}
+// store an output value, or add it to the stored one
+__device__ __forceinline__ void store_out(float2* out, uint32_t o, float2 v, int accum) {
+  out[o] = accum ? pair_sum(out[o], v) : v;
+}
+__device__ __forceinline__ void store_out(double* out, uint32_t o, double v, int accum) {
+  out[o] = accum ? out[o] + v : v;
+}
+
 // FP64 on the output side, FP32 pairs elsewhere
 template <bool F64>
 struct AccSel {

@@ -369,39 +369,41 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       for (size_t a = 0; a < leaves[t].ids.size(); ++a)
         if (leaves[t].ids[a] == plan.sliced[p]) ex->leaf_slice[t].push_back({(int)p, leaves[t].strides[a]});
 
-  // Slice reuse: the sliced positions each tensor's value depends on (those
-  // carried by the leaves below it).  A step result that does not depend on
-  // every sliced position is the same for many slices; it is kept in a
-  // buffer of its own (outside the transient arena) and recomputed only when
-  // the values of its positions change (see plan_reuse).
+  // Slice reuse.  tout[t] is the set of sliced positions the value of tensor
+  // t depends on: those carried by the leaves below it, minus those its steps
+  // have already contracted (a sliced index is an index of the network like
+  // any other; the step that contracts it sums its values one slice value
+  // after another).  A launch loops over the values of the positions its
+  // inputs depend on (din) and keeps one copy of its result per value of the
+  // positions the result depends on (dout), adding up over the positions it
+  // contracts; a position can instead be held fixed in an outer loop (a
+  // block) to save memory.  Every distinct value of a result is then
+  // computed once per block.
   const int nsp = (int)plan.sliced.size();
-  const uint64_t full_dep = nsp >= 64 ? ~0ull : ((1ull << nsp) - 1);
-  bool reuse = ex->n_slices > 1 && nsp <= 62 && !fp64;
+  if (nsp > 62) return fail(QTPU_ENOTSUP, "more than 62 sliced indices");
+  bool reuse = ex->n_slices > 1;
   if (const char* e = std::getenv("QTPU_NO_REUSE")) reuse = reuse && std::atoi(e) == 0;
+  if (reuse_bytes == 1) reuse = false;
   ex->reuse_budget = reuse_bytes ? reuse_bytes : ((uint64_t)64 << 30);
-  std::unordered_map<int, uint64_t> tdep;
-  for (int t = 0; t < nl; ++t)
-    for (auto& ps : ex->leaf_slice[t]) tdep[t] |= 1ull << ps.first;
-  for (const PlanStep& ps : plan.steps) tdep[ps.out] = tdep[ps.x] | tdep[ps.y];
-  auto depof = [&](int t) -> uint64_t {
-    auto it = tdep.find(t);
-    return it == tdep.end() ? 0 : it->second;
-  };
-  if (reuse) {
-    // estimate of the kept bytes with one copy each (step results plus their
-    // operand pieces); reuse is off when even that does not fit the budget
-    double est = 0;
-    for (const PlanStep& ps : plan.steps) {
-      if (depof(ps.out) == full_dep) continue;
-      double e = 8;
-      for (int64_t i : ps.batch) e *= sliced.count(i) ? 1 : (double)dims.get(i);
-      for (int64_t i : ps.m) e *= sliced.count(i) ? 1 : (double)dims.get(i);
-      for (int64_t i : ps.n) e *= sliced.count(i) ? 1 : (double)dims.get(i);
-      est += 2 * e;
+  std::map<int64_t, int> spos;  // sliced index id -> position
+  for (int p = 0; p < nsp; ++p) spos[plan.sliced[p]] = p;
+  auto smask = [&](const Inds& v) {
+    uint64_t m = 0;
+    for (int64_t i : v) {
+      auto it = spos.find(i);
+      if (it != spos.end()) m |= 1ull << it->second;
     }
-    if (est > (double)ex->reuse_budget) reuse = false;
-  }
-  auto kept = [&](int t) { return reuse && t >= nl && depof(t) != full_dep; };
+    return m;
+  };
+  std::unordered_map<int, uint64_t> tout;
+  for (int t = 0; t < nl; ++t)
+    for (auto& ps : ex->leaf_slice[t]) tout[t] |= 1ull << ps.first;
+  for (const PlanStep& ps : plan.steps)
+    tout[ps.out] = (tout[ps.x] | tout[ps.y]) & ~(smask(ps.k) | smask(ps.sa) | smask(ps.sb));
+  auto toutof = [&](int t) -> uint64_t {
+    auto it = tout.find(t);
+    return it == tout.end() ? 0 : it->second;
+  };
 
   // per-slice layout of every stored tensor: leaves keep their strides, step
   // results are dense over their non-sliced indices in [batch, M, N] order
@@ -450,21 +452,19 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
   auto dt_of = [&](int t) { return t < nl ? leaves[t].dt : ex->inter_dt; };
   auto bytes_of = [&](int t) { return prod(live_inds[t]) * (double)dt_bytes(dt_of(t)); };
 
-  Arena arena;
-  std::map<int, std::pair<size_t, size_t>> where;
+  // intermediates' lifetimes in launch order (+1 placed, -1 released); the
+  // arena is laid out after lowering, when the copies of each are known
+  std::vector<std::pair<int, int>> events;
+  std::set<int> placed;
   std::map<int, size_t> offs;
   auto place = [&](int t) {
-    if (kept(t)) return;  // in its own buffer (laid out after lowering)
-    const size_t b = (size_t)extent[t] * 8;
-    const size_t o = arena.alloc(b);
-    where[t] = {o, b};
-    offs[t] = o;
+    events.push_back({t, 1});
+    placed.insert(t);
   };
   auto release = [&](int t) {
-    auto it = where.find(t);
-    if (t >= nl && it != where.end()) {
-      arena.release(it->second.first, it->second.second);
-      where.erase(it);
+    if (t >= nl && placed.count(t)) {
+      events.push_back({t, -1});
+      placed.erase(t);
     }
   };
   // every operand view must stay inside its tensor's storage
@@ -643,8 +643,9 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     L->kclass = kclass;
     L->nsrc = g.nops;
     for (int j = 0; j < g.nops; ++j) L->src[j] = src[j];
-    L->dep = 0;
-    for (int j = 0; j < g.nops; ++j) L->dep |= depof(src[j]);
+    L->din = 0;
+    for (int j = 0; j < g.nops; ++j) L->din |= toutof(src[j]);
+    L->dout = dst >= nl ? toutof(dst) : 0;
     L->dst = dst;
     L->g = g;
     L->flops = flops;
@@ -700,8 +701,9 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     L->kclass = KC_SPLIT;
     L->nsrc = g.nops;
     for (int j = 0; j < g.nops; ++j) L->src[j] = src[j];
-    L->dep = 0;
-    for (int j = 0; j < g.nops; ++j) L->dep |= depof(src[j]);
+    L->din = 0;
+    for (int j = 0; j < g.nops; ++j) L->din |= toutof(src[j]);
+    L->dout = L->din;  // pieces are never summed over slice values
     L->dst = dst;
     L->g = g;
     if (!fast_off) {
@@ -786,6 +788,8 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     const GemmOut& P = it->second;
     const Launch& LP = ex->launches[P.li];
     if (LP.kind != LK_GEMM || LP.gemm.fuse.on || LP.gemm.prec != 3 || (P.K + 63) / 64 > 16) return false;
+    // pieces cannot be added up: the producer must not sum over slice values
+    if (LP.din != LP.dout) return false;
     int k_is_m;
     if (K == P.inner)
       k_is_m = 1;
@@ -898,7 +902,8 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       Launch L;
       L.kind = LK_CONTRACT64;
       L.kclass = KC_CONTRACT;
-      L.dep = depof(ps.out);
+      L.din = toutof(ps.x) | toutof(ps.y);
+      L.dout = last ? 0 : toutof(ps.out);
       L.nsrc = 2;
       L.src[0] = ps.x;
       L.src[1] = ps.y;
@@ -1028,15 +1033,20 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
           const std::vector<int>& sm = side ? smB : smA;
           for (size_t j = 0; j < sm.size(); ++j) LP.fuse_src[j] = sm[j];
           // the pieces it now writes carry the absorbed factors' slices too
-          for (int t : sm) LP.dep |= depof(t);
+          for (int t : sm) LP.din |= toutof(t), LP.dout |= toutof(t);
           LG.opnd_fused[side] = T;
           LG.opnd_kp[side] = (uint32_t)align_up(Ka, 8);
           ex->n_fused_splits++;
         }
+        // the last step of a sliced plan writes an intermediate that one more
+        // launch adds into the FP64 partial (the slice sum stays FP64)
+        const bool last_sliced = last && nsp > 0;
         LG.kind = LK_GEMM;
         LG.kclass = KC_GEMM;
-        LG.dst = dst;
-        LG.dep = depof(ps.out);
+        LG.dst = last_sliced ? ps.out : dst;
+        for (const Repr* R : {&X, &Y})
+          for (int o : R->ops) LG.din |= toutof(o);
+        LG.dout = (last && !last_sliced) ? 0 : toutof(ps.out);
         LG.gemm.batch = (int)nb;
         LG.gemm.M = (int)gM;
         LG.gemm.N = (int)gN;
@@ -1054,7 +1064,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
         stored.insert(stored.end(), outer.begin(), outer.end());
         stored.insert(stored.end(), inner.begin(), inner.end());
         set_dense(ps.out, stored);
-        if (!last) place(ps.out);
+        if (!last || last_sliced) place(ps.out);
         for (int o : X.ops) release(o);
         for (int o : Y.ops) release(o);
         for (int t : {TA, TB})
@@ -1072,6 +1082,13 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
         ex->n_tc_steps++;
         repr[ps.out] = Repr();
         repr[ps.out].ops = {ps.out};
+        if (last_sliced) {
+          Launch LF;
+          if (!gather_launch({&repr[ps.out]}, stored, {}, GW_DENSE_F64, DST_PARTIAL, 0, KC_REDUCE, &LF))
+            return fail(QTPU_ENOTSUP, "internal: the last result does not fit the gather kernel");
+          ex->launches.push_back(LF);
+          release(ps.out);
+        }
         continue;
       }
     }
@@ -1089,7 +1106,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       if (r->virt && ((int)(X.ops.size() + Y.ops.size()) > kMaxOps || reuse > 4.0)) {
         const int tid = next_tmp++;
         const Inds vin = live_inds[r == &X ? ps.x : ps.y];
-        for (int o : r->ops) tdep[tid] |= depof(o);
+        tout[tid] = toutof(r == &X ? ps.x : ps.y);
         Launch L;
         if (!gather_launch({r}, vin, {}, GW_DENSE_PAIR, tid, r->flops, KC_CONTRACT, &L))
           return fail(QTPU_ENOTSUP, "internal: cannot lower a fused tensor");
@@ -1138,20 +1155,19 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
   } else {
     const int last = plan.steps.back().out;
     ex->final_size = extent[last];
-    // partial[slice][final] as a stored tensor with a slice index
+    // partial[final]: the last launch adds every slice's result into it (in
+    // FP64 when it is a gather), then this reduction sums the leftover
+    // indices in a fixed order into the output order
     const int pid = next_tmp++;
-    const int64_t slice_ix = -1;
     live_inds[pid] = live_inds[last];
     stride[pid] = stride[last];
-    stride[pid][slice_ix] = ex->final_size;
-    extent[pid] = ex->n_slices * ex->final_size;
+    extent[pid] = ex->final_size;
     slice_max[pid] = 0;
     Inds loop;
-    if (ex->n_slices > 1) loop.push_back(slice_ix);
     for (int64_t i : plan.final_sum)
       if (!sliced.count(i)) loop.push_back(i);
-    // a gather step as last step wrote FP64 partials; a GEMM wrote (hi, lo)
-    // pairs, read exactly into the FP64 sum
+    // a gather as last launch writes FP64; a GEMM (unsliced plans only) its
+    // (hi, lo) pairs, read exactly into the FP64 sum
     ex->partial_dt = (!fp64 && ex->launches.back().kind == LK_GEMM) ? DT_F32X2 : DT_F64;
     GatherArgs g;
     g.nops = 1;
@@ -1165,7 +1181,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     }
     for (int64_t i : loop) {
       st[0] = sof(pid, i);
-      ok &= gpush(g.loop, i == slice_ix ? ex->n_slices : dims.get(i), st, 1);
+      ok &= gpush(g.loop, dims.get(i), st, 1);
     }
     if (!ok) return fail(QTPU_ENOTSUP, "the output does not fit the reduction kernel");
     gmerge(g.out, 1);
@@ -1181,35 +1197,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     R.src[0] = pid;
     R.dst = DST_OUT;
     R.g = g;
-    // reduction over a range of slices: slice mode first and never merged
-    {
-      GatherArgs h = g;
-      h.loop = GModes();
-      st[0] = ex->final_size;
-      ok &= gpush(h.loop, ex->n_slices, st, 1);
-      if (ex->n_slices == 1) {  // keep a slice mode even for one slice
-        h.loop.dim[0] = 1;
-        h.loop.stride[0][0] = ex->final_size;
-        h.loop.n = 1;
-      }
-      GModes rest;
-      for (int64_t i : plan.final_sum) {
-        if (sliced.count(i)) continue;
-        st[0] = sof(pid, i);
-        ok &= gpush(rest, dims.get(i), st, 1);
-      }
-      gmerge(rest, 1);
-      for (int q = 0; q < rest.n && h.loop.n < kMaxModes; ++q) {
-        h.loop.dim[h.loop.n] = rest.dim[q];
-        h.loop.stride[h.loop.n][0] = rest.stride[q][0];
-        h.loop.n++;
-      }
-      for (int q = 0; q < h.loop.n; ++q) h.loop.div[q] = make_fastdiv(h.loop.dim[q]);
-      h.n_loop = (uint32_t)gsize(h.loop);
-      ex->reduce_range = h;
-      ex->has_reduce_range = ok && h.loop.n <= kMaxModes;
-    }
-    R.bytes = (double)ex->n_slices * ex->final_size * 8 + (double)g.n_out * 8;
+    R.bytes = (double)ex->final_size * 8 + (double)g.n_out * 8;
     offs[pid] = 0;  // resolved to the partial buffer at run time
   }
   if (fp64) {
@@ -1226,129 +1214,130 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
   }
   ex->reduce = R;
 
-  // ---- slice reuse: which launches keep their output, in how many copies,
-  // and the nested order of the sliced positions for a full contraction.
-  // A kept launch L depends on the positions D.  In the nested loop (order
-  // pi, outermost first) let P be the longest prefix of pi inside D: with
-  // copies indexed by the positions D \ P, every value of D is computed once
-  // per contraction (valid while P is unchanged, and P changes only in the
-  // outer loops); pi is chosen to minimise the kept bytes.  Over the budget,
-  // the largest launches fall back to one copy recomputed whenever a
-  // position up to its innermost one in pi changes.
-  ex->loop_order.clear();
-  for (int p = 0; p < nsp; ++p) ex->loop_order.push_back(p);
-  ex->inter_memo.assign(next_tmp - nl + 1, -1);
-  ex->memo_total = 0;
-  std::vector<size_t> lbytes(ex->launches.size(), 0);
+  // ---- slice reuse schedule (see the comment at tout): groups, blocked
+  // positions, copies and the arena layout.
+  // A GEMM forms a group with the splits of its operands; every other launch
+  // is a group of its own.
+  ex->groups.clear();
   for (size_t i = 0; i < ex->launches.size(); ++i) {
-    Launch& L = ex->launches[i];
-    L.memo = false;
-    L.copies = 1;
-    L.runs = ex->n_slices;
-    L.epoch_pos.clear();
-    L.copy_pos.clear();
-    if (!reuse) continue;
-    if (L.dst >= nl) {
-      L.memo = kept(L.dst);
-      if (L.memo) {
-        lbytes[i] = align_up((size_t)extent[L.dst] * 8, 1024);
-        ex->inter_memo[L.dst - nl] = (int)i;
-      }
-    } else if (L.kind == LK_GATHER && (L.dst == DST_SPLIT_A || L.dst == DST_SPLIT_B) && L.dep != full_dep) {
-      L.memo = true;
-      lbytes[i] = align_up((size_t)np * L.g.n_rows * L.g.Kp * es, 1024);
-    }
+    const Launch& L = ex->launches[i];
+    if (L.kind == LK_GATHER && (L.dst == DST_SPLIT_A || L.dst == DST_SPLIT_B)) continue;
+    Group G;
+    G.main = (int)i;
+    if (L.kind == LK_GEMM) G.split[0] = L.opnd_split[0], G.split[1] = L.opnd_split[1];
+    ex->groups.push_back(G);
   }
-  if (reuse) {
-    const std::vector<int64_t>& sd = ex->slice_dims;
-    auto prefix_len = [&](const std::vector<int>& pi, uint64_t D) {
-      size_t k = 0;
-      while (k < pi.size() && ((D >> pi[k]) & 1)) ++k;
-      return k;
-    };
-    auto kept_bytes = [&](const std::vector<int>& pi) {
-      double tot = 0;
-      for (size_t i = 0; i < ex->launches.size(); ++i) {
-        const Launch& L = ex->launches[i];
-        if (!L.memo) continue;
-        const size_t k = prefix_len(pi, L.dep);
-        double c = 1;
-        for (size_t j = k; j < pi.size(); ++j)
-          if ((L.dep >> pi[j]) & 1) c *= (double)sd[pi[j]];
-        tot += c * (double)lbytes[i];
+  std::vector<int> producer(next_tmp + 1, -1);
+  for (size_t i = 0; i < ex->launches.size(); ++i)
+    if (ex->launches[i].dst >= nl) producer[ex->launches[i].dst] = (int)i;
+  const std::vector<int64_t>& sd = ex->slice_dims;
+  auto count_of = [&](uint64_t m) {
+    double c = 1;
+    for (int p = 0; p < nsp; ++p)
+      if ((m >> p) & 1) c *= (double)sd[p];
+    return c;
+  };
+  auto tbytes = [&](int t) { return align_up((size_t)extent[t] * 8, 1024); };
+  auto copies_of = [&](int t, uint64_t F) {
+    const int pr = producer[t];
+    return pr < 0 ? 1.0 : count_of(ex->launches[pr].dout & ~F);
+  };
+  // arena layout with the copies of every intermediate under blocked set F
+  auto layout = [&](uint64_t F, std::map<int, size_t>* off_out) -> double {
+    Arena ar;
+    std::map<int, size_t> off;
+    std::map<int, size_t> sz;
+    for (auto& ev : events) {
+      const int t = ev.first;
+      if (ev.second > 0) {
+        const double c = copies_of(t, F);
+        if ((double)tbytes(t) * c > 1e15) return 1e30;
+        sz[t] = (size_t)c * tbytes(t);
+        off[t] = ar.alloc(sz[t]);
+      } else {
+        ar.release(off[t], sz[t]);
       }
-      return tot;
+    }
+    if (off_out) *off_out = off;
+    return (double)ar.top;
+  };
+  auto cost_of = [&](uint64_t F) {
+    double c = 0;
+    for (const Launch& L : ex->launches) c += L.flops * count_of(L.din | F);
+    return c;
+  };
+  const uint64_t all_pos = nsp ? ((nsp >= 64 ? ~0ull : (1ull << nsp) - 1)) : 0;
+  uint64_t F = all_pos;  // every position blocked: each slice on its own
+  if (reuse && nsp > 0) {
+    double best_c = cost_of(F);
+    const double budget = (double)ex->reuse_budget;
+    auto consider = [&](uint64_t f) {
+      const double c = cost_of(f);
+      if (c < best_c && layout(f, nullptr) <= budget) best_c = c, F = f;
     };
-    std::vector<int> pi = ex->loop_order, best = pi;
-    double best_b = kept_bytes(pi);
-    if (nsp <= 7) {
-      std::sort(pi.begin(), pi.end());
-      do {
-        const double b = kept_bytes(pi);
-        if (b < best_b) best_b = b, best = pi;
-      } while (std::next_permutation(pi.begin(), pi.end()));
-    } else {  // pairwise swaps until no improvement
+    if (nsp <= 12) {
+      for (uint64_t f = 0; f < all_pos; ++f) consider(f);
+    } else {  // release blocked positions one at a time while it fits
       for (bool more = true; more;) {
         more = false;
-        for (int a = 0; a < nsp; ++a)
-          for (int b = a + 1; b < nsp; ++b) {
-            std::vector<int> q = best;
-            std::swap(q[a], q[b]);
-            const double v = kept_bytes(q);
-            if (v < best_b) best_b = v, best = q, more = true;
+        const uint64_t base = F;
+        for (int p = 0; p < nsp; ++p)
+          if ((base >> p) & 1) {
+            const uint64_t f = base & ~(1ull << p);
+            const double c0 = best_c;
+            consider(f);
+            if (best_c < c0) more = true;
           }
       }
     }
-    ex->loop_order = best;
-    std::vector<int> pos_of(nsp);
-    for (int j = 0; j < nsp; ++j) pos_of[best[j]] = j;
-    // per kept launch: copies over D \ P, epoch P
-    std::vector<std::pair<double, size_t>> by_size;
-    for (size_t i = 0; i < ex->launches.size(); ++i) {
-      Launch& L = ex->launches[i];
-      if (!L.memo) continue;
-      const size_t k = prefix_len(best, L.dep);
-      for (size_t j = 0; j < best.size(); ++j) {
-        if (!((L.dep >> best[j]) & 1)) continue;
-        (j < k ? L.epoch_pos : L.copy_pos).push_back(best[j]);
-      }
-      L.copies = 1;
-      for (int p : L.copy_pos) L.copies *= sd[p];
-      by_size.push_back({(double)L.copies * (double)lbytes[i], i});
-    }
-    double total = 0;
-    for (auto& b : by_size) total += b.first;
-    std::sort(by_size.begin(), by_size.end(), [](const std::pair<double, size_t>& a, const std::pair<double, size_t>& b) {
-      return a.first > b.first || (a.first == b.first && a.second < b.second);
-    });
-    for (auto& b : by_size) {
-      if (total <= (double)ex->reuse_budget) break;
-      Launch& L = ex->launches[b.second];
-      if (L.copies == 1) continue;
-      // one copy, valid while every position up to its innermost one holds
-      int m = -1;
-      for (int j = 0; j < nsp; ++j)
-        if ((L.dep >> best[j]) & 1) m = j;
-      L.epoch_pos.assign(best.begin(), best.begin() + (m + 1));
-      L.copy_pos.clear();
-      total -= b.first - (double)lbytes[b.second];
-      L.copies = 1;
-    }
-    size_t off = 0;
-    for (size_t i = 0; i < ex->launches.size(); ++i) {
-      Launch& L = ex->launches[i];
-      if (!L.memo) continue;
-      L.memo_bytes = lbytes[i];
-      L.memo_off = off;
-      off += (size_t)L.copies * lbytes[i];
-      L.runs = 1;
-      for (int p : L.epoch_pos) L.runs *= sd[p];
-      for (int p : L.copy_pos) L.runs *= sd[p];
-    }
-    ex->memo_total = off;
   }
+  ex->fixed = F;
+  std::map<int, size_t> toff;
+  ex->arena_bytes = std::max<size_t>((size_t)layout(F, &toff), 256);
+  {
+    const double per_slice = layout(all_pos, nullptr);
+    ex->kept_bytes = (double)ex->arena_bytes > per_slice ? (size_t)((double)ex->arena_bytes - per_slice) : 0;
+  }
+  ex->stored.assign(next_tmp - nl + 1, Stored());
+  for (auto& kv : toff) {
+    const int t = kv.first;
+    if (t < nl) continue;
+    Stored& S = ex->stored[t - nl];
+    S.off = kv.second;
+    S.bytes = tbytes(t);
+    const int pr = producer[t];
+    if (pr >= 0)
+      for (int q = 0; q < nsp; ++q)
+        if (((ex->launches[pr].dout & ~F) >> q) & 1) S.cpos.push_back(q);
+    offs[t] = kv.second;
+  }
+  // group loop orders and executions per contraction
+  const double blocks = count_of(F);
   ex->flops_executed = ex->flops_no_reuse = 0;
   ex->launches_per_contract = 1;
+  for (Group& G : ex->groups) {
+    Launch& M = ex->launches[G.main];
+    uint64_t A = 0, B = 0;
+    double ba = 0, bb = 0;
+    if (G.split[0] >= 0) A = ex->launches[G.split[0]].din & ~F, ba = ex->launches[G.split[0]].bytes;
+    if (G.split[1] >= 0) B = ex->launches[G.split[1]].din & ~F, bb = ex->launches[G.split[1]].bytes;
+    if (bb > ba) std::swap(A, B);  // the larger split's positions outermost
+    G.order.clear();
+    for (uint64_t part : {A & B, A & ~B, B & ~A, (M.din & ~F) & ~(A | B)})
+      for (int q = 0; q < nsp; ++q)
+        if ((part >> q) & 1) G.order.push_back(q);
+    M.runs = (int64_t)(count_of(M.din & ~F) * blocks);
+    for (int sp : G.split) {
+      if (sp < 0) continue;
+      Launch& S = ex->launches[sp];
+      int last_j = -1;
+      for (size_t j = 0; j < G.order.size(); ++j)
+        if (((S.din & ~F) >> G.order[j]) & 1) last_j = (int)j;
+      double r = 1;
+      for (int j = 0; j <= last_j; ++j) r *= (double)sd[G.order[j]];
+      S.runs = (int64_t)(r * blocks);
+    }
+  }
   for (const Launch& L : ex->launches) {
     ex->flops_executed += L.flops * (double)L.runs;
     ex->flops_no_reuse += L.flops * (double)ex->n_slices;
@@ -1401,7 +1390,6 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       L.wg_off = (int64_t)ex->wbuf_bytes;
       ex->wbuf_bytes += align_up((size_t)L.gf.w_size * sizeof(float2), 256);
     }
-  ex->arena_bytes = std::max<size_t>(arena.top, 256);
   ex->split_a_bytes = split_need_a;
   ex->split_bytes = split_need_a + split_need_b;
   ex->lowered = true;
@@ -1411,7 +1399,6 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
   cudaError_t ce = cudaSetDevice(ex->device);
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&ex->sm_count, cudaDevAttrMultiProcessorCount, ex->device);
   if (ce != cudaSuccess) return fail(QTPU_ECUDA, std::string("cuda: ") + cudaGetErrorString(ce));
-  ex->arena_bytes = std::max<size_t>(arena.top, 256);
   ex->split_a_bytes = split_need_a;
   ex->split_bytes = split_need_a + split_need_b;
   // QTPU_TEST_FAIL_ALLOC=1 makes the workspace allocation fail (a host-side
@@ -1428,10 +1415,10 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     return true;
   };
   if (!dalloc((void**)&ex->arena, ex->arena_bytes) || !dalloc((void**)&ex->splitbuf, ex->split_bytes) ||
-      !dalloc((void**)&ex->partial, (size_t)ex->n_slices * std::max<int64_t>(ex->final_size, 1) * 8) ||
+      !dalloc((void**)&ex->partial, (size_t)std::max<int64_t>(ex->final_size, 1) * 8) ||
       !dalloc((void**)&ex->status, 16) || !dalloc((void**)&ex->out_stage, (size_t)R.g.n_out * 8 + 8) ||
       !dalloc((void**)&ex->dot_scratch, dot_scratch_entries(ex->sm_count) * sizeof(float2)) ||
-      !dalloc((void**)&ex->wbuf, ex->wbuf_bytes) || !dalloc((void**)&ex->memobuf, ex->memo_total)) {
+      !dalloc((void**)&ex->wbuf, ex->wbuf_bytes)) {
     exec_free(ex);
     return fail(QTPU_ENOMEM, "device workspace allocation failed");
   }
@@ -1470,37 +1457,36 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
   ex->inter_off.assign(next_tmp - nl + 1, 0);
   for (auto& kv : offs)
     if (kv.first >= nl) ex->inter_off[kv.first - nl] = kv.second;
-  // tensor maps of the split buffers (fixed addresses); an operand buffer
-  // kept across slices gets one map per copy
+  // tensor maps of the split buffers (fixed addresses); an operand whose
+  // pieces are a kept result with several copies gets one map per copy
   for (size_t i = 0; i < ex->launches.size(); ++i) {
     Launch& L = ex->launches[i];
     if (L.kind != LK_GEMM) continue;
     uint8_t* base[2];
     int64_t kp[2];
     for (int side = 0; side < 2; ++side) {
-      int owner = -1;
+      L.opnd_owner[side] = -1;
+      L.tm_copies[side].clear();
       if (L.opnd_split[side] >= 0) {
         const Launch& S = ex->launches[L.opnd_split[side]];
-        if (S.memo) owner = L.opnd_split[side];
-        base[side] = S.memo ? ex->memobuf + S.memo_off
-                            : (S.side >= 0 ? ex->sidebuf + S.side_off : ex->splitbuf + (side ? ex->split_a_bytes : 0));
+        base[side] = S.side >= 0 ? ex->sidebuf + S.side_off : ex->splitbuf + (side ? ex->split_a_bytes : 0);
         kp[side] = S.g.Kp;
-      } else {
-        const int T = L.opnd_fused[side];
-        owner = ex->inter_memo[T - nl];
-        base[side] = owner >= 0 ? ex->memobuf + ex->launches[owner].memo_off : ex->arena + ex->inter_off[T - nl];
-        kp[side] = L.opnd_kp[side];
+        continue;
       }
-      L.opnd_memo[side] = owner;
-      L.tm_copies[side].clear();
-      const int64_t rows = side ? L.gemm.N : L.gemm.M;
-      const int box = side ? gemm_block_n() : 128;
-      if (owner >= 0) {
-        const Launch& O = ex->launches[owner];
-        L.tm_copies[side].resize((size_t)O.copies);
-        for (int64_t c = 0; c < O.copies; ++c)
-          if (!make_operand_map(&L.tm_copies[side][c], base[side] + (size_t)c * O.memo_bytes, prec, L.gemm.batch,
-                                rows, L.gemm.K, kp[side], box)) {
+      const int T = L.opnd_fused[side];
+      const Stored& St = ex->stored[T - nl];
+      base[side] = ex->arena + St.off;
+      kp[side] = L.opnd_kp[side];
+      int64_t nc = 1;
+      for (int q : St.cpos) nc *= ex->slice_dims[q];
+      if (nc > 1) {
+        L.opnd_owner[side] = T;
+        const int64_t rows = side ? L.gemm.N : L.gemm.M;
+        const int box = side ? gemm_block_n() : 128;
+        L.tm_copies[side].resize((size_t)nc);
+        for (int64_t c = 0; c < nc; ++c)
+          if (!make_operand_map(&L.tm_copies[side][c], base[side] + (size_t)c * St.bytes, prec, L.gemm.batch, rows,
+                                L.gemm.K, kp[side], box)) {
             exec_free(ex);
             return fail(QTPU_ECUDA, "cuTensorMapEncodeTiled failed");
           }
@@ -1592,13 +1578,14 @@ std::string exec_describe(const Executor* ex) {
     if (L.kind == LK_GEMM) o << "-";
     o << " dst=" << L.dst << (L.side >= 0 ? " side" : "") << " flops=" << (long long)L.flops
       << " bytes=" << (long long)L.bytes;
-    if (L.memo) {
-      o << " kept copies=" << L.copies << " runs=" << L.runs << " copy_pos=";
-      for (size_t j = 0; j < L.copy_pos.size(); ++j) o << (j ? "," : "") << L.copy_pos[j];
-      if (L.copy_pos.empty()) o << "-";
-      o << " epoch_pos=";
-      for (size_t j = 0; j < L.epoch_pos.size(); ++j) o << (j ? "," : "") << L.epoch_pos[j];
-      if (L.epoch_pos.empty()) o << "-";
+    if (!ex->slice_dims.empty()) {
+      auto pos = [&](uint64_t m) {
+        std::string r;
+        for (size_t q = 0; q < ex->slice_dims.size(); ++q)
+          if ((m >> q) & 1) r += (r.empty() ? "" : ",") + std::to_string(q);
+        return r.empty() ? std::string("-") : r;
+      };
+      o << " din=" << pos(L.din) << " dout=" << pos(L.dout) << " runs=" << L.runs;
     }
     o << "\n";
   };
@@ -1607,9 +1594,13 @@ std::string exec_describe(const Executor* ex) {
   o << "summary launches_per_slice=" << ex->launches.size() << " tensor_core_steps=" << ex->n_tc_steps
     << " fused_steps=" << ex->n_fused_steps << " fused_splits=" << ex->n_fused_splits << " side_splits=" << ex->n_side << " arena_bytes=" << ex->arena_bytes
     << " split_bytes=" << ex->split_bytes << "\n";
-  o << "reuse kept_bytes=" << ex->memo_total << " loop_order=";
-  for (size_t j = 0; j < ex->loop_order.size(); ++j) o << (j ? "," : "") << ex->loop_order[j];
-  if (ex->loop_order.empty()) o << "-";
+  o << "reuse blocked=";
+  {
+    std::string r;
+    for (size_t q = 0; q < ex->slice_dims.size(); ++q)
+      if ((ex->fixed >> q) & 1) r += (r.empty() ? "" : ",") + std::to_string(q);
+    o << (r.empty() ? "-" : r);
+  }
   o << " launches_per_contract=" << ex->launches_per_contract << " flops_executed=" << (long long)ex->flops_executed
     << " flops_all_slices=" << (long long)ex->flops_no_reuse << "\n";
   return o.str();
@@ -1635,47 +1626,95 @@ std::string exec_profile_read(Executor* ex, double* ms, int64_t* launches, doubl
 }
 
 namespace {
-// Enqueue every launch of one contraction on `st`; the result goes to `out`.
+// A block of the slice space: per sliced position the value range [lo, hi).
+struct Block {
+  std::vector<int64_t> lo, hi;
+};
+
+// The blocks of slices [first, first + count) in slice-id order (slice id =
+// mixed radix of the position values, last position fastest): the largest
+// aligned runs, each a run of values of one position with every later
+// position free and every earlier one fixed.
+std::vector<Block> range_blocks(const std::vector<int64_t>& dims, int64_t first, int64_t count) {
+  const int n = (int)dims.size();
+  std::vector<int64_t> span(n + 1, 1);  // span[j]: slices per value of position j-1
+  for (int j = n - 1; j >= 0; --j) span[j] = span[j + 1] * dims[j];
+  std::vector<Block> out;
+  int64_t a = first;
+  const int64_t b = first + count;
+  while (a < b) {
+    // the coarsest position j whose whole values fit at a
+    int j = n;
+    while (j > 0 && a % span[j - 1] == 0 && a + span[j - 1] <= b) --j;
+    Block B;
+    B.lo.assign(n, 0);
+    B.hi.assign(n, 0);
+    int64_t r = a;
+    for (int q = n - 1; q >= 0; --q) {
+      B.lo[q] = r % dims[q];
+      r /= dims[q];
+    }
+    if (j == n) {  // a single slice
+      for (int q = 0; q < n; ++q) B.hi[q] = B.lo[q] + 1;
+      a += 1;
+    } else {
+      // position j-1 (if any) runs over as many values as fit; later free
+      for (int q = 0; q < n; ++q) B.hi[q] = B.lo[q] + 1;
+      for (int q = j; q < n; ++q) B.lo[q] = 0, B.hi[q] = dims[q];
+      if (j > 0) {
+        const int64_t m = std::min<int64_t>((b - a) / span[j], dims[j - 1] - B.lo[j - 1]);
+        B.hi[j - 1] = B.lo[j - 1] + m;
+        a += m * span[j];
+      } else {
+        a += span[0];
+      }
+    }
+    out.push_back(B);
+  }
+  return out;
+}
+
+// Enqueue every launch of one contraction (or of slices [first, first +
+// count)) on `st`; the result goes to `out`.  Sliced plans run the groups of
+// the slice-reuse schedule once per block: a group loops over the values of
+// its main launch's din (within the block), re-running a split only when
+// its own din values change, and the main launch adds up over the positions
+// it contracts (the last launch over everything, into the FP64 partial).
 cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* out, cudaStream_t st,
                         int64_t first = 0, int64_t count = -1) {
   if (count < 0) count = ex->n_slices;
   const int nl = (int)leaves.size();
+  const int nsp = (int)ex->slice_dims.size();
   std::vector<int64_t> loff(nl, 0);
-  std::vector<int64_t> digit(ex->slice_dims.size(), 0);
+  std::vector<int64_t> digit(nsp, 0);
   cudaError_t ce = cudaSuccess;
-  // slice reuse: copy index and epoch of a kept launch under the current
-  // values of the sliced positions
-  auto mixed = [&](const std::vector<int>& pos) {
-    int64_t v = 0;
-    for (int p : pos) v = v * ex->slice_dims[p] + digit[p];
-    return v;
+  // copy index of an intermediate under the current position values
+  auto copy_of = [&](const Stored& S) {
+    int64_t c = 0;
+    for (int q : S.cpos) c = c * ex->slice_dims[q] + digit[q];
+    return c;
   };
-  auto kept_ptr = [&](const Launch& L) -> uint8_t* {
-    return ex->memobuf + L.memo_off + (size_t)mixed(L.copy_pos) * L.memo_bytes;
+  auto inter_ptr = [&](int t) -> uint8_t* {
+    const Stored& S = ex->stored[t - nl];
+    return ex->arena + S.off + (size_t)copy_of(S) * S.bytes;
   };
-  std::vector<std::vector<int64_t>> stored(ex->launches.size());
-  for (size_t i = 0; i < ex->launches.size(); ++i)
-    if (ex->launches[i].memo) stored[i].assign((size_t)ex->launches[i].copies, -1);
   auto src_ptr = [&](int t) -> const void* {
     if (t < nl) return (const uint8_t*)leaves[t].ptr + loff[t] * (int64_t)dt_bytes(leaves[t].dt);
-    const int owner = (size_t)(t - nl) < ex->inter_memo.size() ? ex->inter_memo[t - nl] : -1;
-    if (owner >= 0) return kept_ptr(ex->launches[owner]);
-    return ex->arena + ex->inter_off[t - nl];
+    return inter_ptr(t);
   };
   const bool sided = ex->n_side > 0 && count == ex->n_slices && ex->n_slices == 1;
   const Launch* cur = nullptr;
-  auto dst_ptr = [&](int d, int64_t s) -> void* {
-    if (cur && cur->memo && d != DST_OUT && d != DST_PARTIAL) return kept_ptr(*cur);
+  auto dst_ptr = [&](int d) -> void* {
     switch (d) {
       case DST_SIDE: return ex->sidebuf + cur->side_off;
-      case DST_PARTIAL: return ex->partial + (size_t)s * ex->final_size * 8;
+      case DST_PARTIAL: return ex->partial;
       case DST_SPLIT_A: return ex->splitbuf;
       case DST_SPLIT_B: return ex->splitbuf + ex->split_a_bytes;
       case DST_OUT: return out;
-      default: return ex->arena + ex->inter_off[d - nl];
+      default: return inter_ptr(d);
     }
   };
-  auto run_one_on = [&](const Launch& L, int64_t s, bool reduce, cudaStream_t st) -> cudaError_t {
+  auto run_one_on = [&](const Launch& L, bool reduce, int accum, cudaStream_t st) -> cudaError_t {
     cur = &L;
     Timed t(ex->prof, st, L.kclass, L.flops, L.bytes);
     const bool from_partial = reduce && !ex->launches.empty();
@@ -1684,30 +1723,35 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
         GatherArgs g = L.gf;
         for (int j = 0; j < g.nops; ++j) g.ptr[j] = src_ptr(L.gf_src[j]);
         g.scratch = ex->dot_scratch;
+        g.accum = accum;
         if (L.wg_off >= 0) g.wg = reinterpret_cast<float2*>(ex->wbuf + L.wg_off);
-        cudaError_t e = launch_gather_fast(g, dst_ptr(L.dst, s), ex->sm_count, st);
+        cudaError_t e = launch_gather_fast(g, dst_ptr(L.dst), ex->sm_count, st);
         if (e != cudaErrorNotSupported) return e;
         cudaGetLastError();
       }
       GatherArgs g = L.g;
+      g.accum = accum;
       for (int j = 0; j < L.nsrc; ++j) g.ptr[j] = from_partial ? (const void*)ex->partial : src_ptr(L.src[j]);
-      return launch_gather(g, dst_ptr(L.dst, s), ex->sm_count, st);
+      return launch_gather(g, dst_ptr(L.dst), ex->sm_count, st);
     }
     if (L.kind == LK_GEMM) {
       GemmArgs g = L.gemm;
-      g.C = dst_ptr(L.dst, s);
-      if (L.opnd_memo[0] >= 0) g.tmA = L.tm_copies[0][(size_t)mixed(ex->launches[L.opnd_memo[0]].copy_pos)];
-      if (L.opnd_memo[1] >= 0) g.tmB = L.tm_copies[1][(size_t)mixed(ex->launches[L.opnd_memo[1]].copy_pos)];
+      g.C = dst_ptr(L.dst);
+      g.accum = accum;
+      if (L.opnd_owner[0] >= 0) g.tmA = L.tm_copies[0][(size_t)copy_of(ex->stored[L.opnd_owner[0] - nl])];
+      if (L.opnd_owner[1] >= 0) g.tmB = L.tm_copies[1][(size_t)copy_of(ex->stored[L.opnd_owner[1] - nl])];
       for (int j = 0; g.fuse.on && j < g.fuse.nsmall; ++j) g.fuse.wptr[j] = src_ptr(L.fuse_src[j]);
       return launch_gemm(g, ex->sm_count, st);
     }
+    ContractArgs c = L.c64;
+    c.accum = accum;
     const void* A = from_partial ? (const void*)ex->partial : src_ptr(L.src[0]);
     const void* B = reduce ? nullptr : src_ptr(L.src[1]);
-    const int dta = L.src[0] < nl ? leaves[L.src[0]].dt : ex->inter_dt;
+    const int dta = from_partial ? ex->partial_dt : (L.src[0] < nl ? leaves[L.src[0]].dt : ex->inter_dt);
     const int dtb = reduce ? DT_F64 : (L.src[1] < nl ? leaves[L.src[1]].dt : ex->inter_dt);
-    return launch_contract(A, dta, B, dtb, (double*)dst_ptr(L.dst, s), L.c64, ex->sm_count, st);
+    return launch_contract(A, dta, B, dtb, (double*)dst_ptr(L.dst), c, ex->sm_count, st);
   };
-  auto run_one = [&](const Launch& L, int64_t s, bool reduce) { return run_one_on(L, s, reduce, st); };
+  auto run_one = [&](const Launch& L, bool reduce, int accum) { return run_one_on(L, reduce, accum, st); };
   if (sided) {
     // fork: every leaf-only split on the side stream first, one event each
     cudaStream_t ss = ex->side_stream;
@@ -1717,7 +1761,7 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
     for (auto& L : ex->launches) {
       if (ce != cudaSuccess) break;
       if (L.side < 0) continue;
-      ce = run_one_on(L, 0, false, ss);
+      ce = run_one_on(L, false, 0, ss);
       if (ce == cudaSuccess) ce = cudaEventRecord(ex->side_ev[L.side], ss);
     }
     for (auto& L : ex->launches) {
@@ -1725,60 +1769,101 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
       if (L.side >= 0) continue;
       for (int w : L.wait_side)
         if (w >= 0 && ce == cudaSuccess) ce = cudaStreamWaitEvent(st, ex->side_ev[w], 0);
-      if (ce == cudaSuccess) ce = run_one(L, 0, false);
+      if (ce == cudaSuccess) ce = run_one(L, false, 0);
     }
     if (ce == cudaSuccess) ce = cudaEventRecord(join, ss);
     if (ce == cudaSuccess) ce = cudaStreamWaitEvent(st, join, 0);
-    if (ce == cudaSuccess) ce = run_one(ex->reduce, 0, true);
+    if (ce == cudaSuccess) ce = run_one(ex->reduce, true, 0);
     return ce;
   }
-  // A full contraction visits the slices in the nested order loop_order
-  // (outermost first), a range in slice-id order (last sliced index
-  // fastest); either way each slice's result lands in partial[its id].
-  const bool nested = first == 0 && count == ex->n_slices && ex->memo_total > 0;
-  const int nsp = (int)ex->slice_dims.size();
-  for (int64_t it = 0; it < count && ce == cudaSuccess && !ex->launches.empty(); ++it) {
-    int64_t r = nested ? it : first + it;
-    for (int k = nsp - 1; k >= 0; --k) {
-      const int p = nested ? ex->loop_order[k] : k;
-      digit[p] = r % ex->slice_dims[p];
-      r /= ex->slice_dims[p];
+  // blocks: a slice range in id order, split further over the blocked
+  // positions (each blocked position takes one value per block)
+  std::vector<Block> blocks;
+  if (nsp == 0) {
+    blocks.push_back(Block());
+  } else {
+    for (const Block& R : range_blocks(ex->slice_dims, first, count)) {
+      std::vector<int> free_fixed;
+      for (int q = 0; q < nsp; ++q)
+        if (((ex->fixed >> q) & 1) && R.hi[q] - R.lo[q] > 1) free_fixed.push_back(q);
+      int64_t n = 1;
+      for (int q : free_fixed) n *= R.hi[q] - R.lo[q];
+      for (int64_t k = 0; k < n; ++k) {
+        Block B = R;
+        int64_t r = k;
+        for (int j = (int)free_fixed.size() - 1; j >= 0; --j) {
+          const int q = free_fixed[j];
+          const int64_t w = R.hi[q] - R.lo[q];
+          B.lo[q] = R.lo[q] + r % w;
+          B.hi[q] = B.lo[q] + 1;
+          r /= w;
+        }
+        blocks.push_back(B);
+      }
     }
-    int64_t s = 0;  // the slice id
-    for (int p = 0; p < nsp; ++p) s = s * ex->slice_dims[p] + digit[p];
+  }
+  bool final_written = false;
+  const size_t n_launch = ex->launches.size();
+  std::vector<int64_t> split_epoch(n_launch, -1);
+  auto set_leaf_offsets = [&]() {
     for (int t = 0; t < nl; ++t) {
       int64_t o = 0;
       for (auto& ps : ex->leaf_slice[t]) o += digit[ps.first] * ps.second;
       loff[t] = o;
     }
-    for (size_t i = 0; i < ex->launches.size(); ++i) {
-      const Launch& L = ex->launches[i];
-      if (L.memo) {
-        // a copy computed in the current epoch is still valid
-        int64_t& st_ep = stored[i][(size_t)mixed(L.copy_pos)];
-        const int64_t ep = mixed(L.epoch_pos);
-        if (st_ep == ep) continue;
-        st_ep = ep;
-      }
-      ce = run_one(L, s, false);
+  };
+  for (const Block& B : blocks) {
+    if (ce != cudaSuccess) break;
+    for (int q = 0; q < nsp; ++q) digit[q] = B.lo[q];
+    for (const Group& G : ex->groups) {
       if (ce != cudaSuccess) break;
+      const Launch& M = ex->launches[G.main];
+      // the group's positions that vary in this block, outermost first
+      std::vector<int> var;
+      for (int q : G.order)
+        if (B.hi[q] - B.lo[q] > 1) var.push_back(q);
+      for (int q = 0; q < nsp; ++q)
+        if (((M.din >> q) & 1)) digit[q] = B.lo[q];
+      for (int sp : G.split)
+        if (sp >= 0) split_epoch[sp] = -1;
+      int64_t n = 1;
+      for (int q : var) n *= B.hi[q] - B.lo[q];
+      for (int64_t k = 0; k < n && ce == cudaSuccess; ++k) {
+        int64_t r = k;
+        for (int j = (int)var.size() - 1; j >= 0; --j) {
+          const int q = var[j];
+          const int64_t w = B.hi[q] - B.lo[q];
+          digit[q] = B.lo[q] + r % w;
+          r /= w;
+        }
+        set_leaf_offsets();
+        for (int sp : G.split) {
+          if (sp < 0 || ce != cudaSuccess) continue;
+          const Launch& S = ex->launches[sp];
+          int64_t ep = 0;  // the values of the split's own positions
+          for (int q = 0; q < nsp; ++q)
+            if ((S.din >> q) & 1) ep = ep * ex->slice_dims[q] + digit[q];
+          if (ep == split_epoch[sp]) continue;
+          split_epoch[sp] = ep;
+          ce = run_one(S, false, 0);
+        }
+        if (ce != cudaSuccess) break;
+        // add up over the positions the launch contracts: every visit after
+        // the first with the same dout values (the last launch: every visit
+        // after the contraction's first)
+        int accum = 0;
+        if (M.dst == DST_PARTIAL) {
+          accum = final_written ? 1 : 0;
+          final_written = true;
+        } else {
+          for (int q = 0; q < nsp; ++q)
+            if ((((M.din & ~M.dout) >> q) & 1) && digit[q] != B.lo[q]) accum = 1;
+        }
+        ce = run_one(M, false, accum);
+      }
     }
   }
-  if (ce == cudaSuccess) {
-    std::fill(loff.begin(), loff.end(), 0);
-    if (first == 0 && count == ex->n_slices) {
-      ce = run_one(ex->reduce, 0, true);
-    } else {
-      // sum of the slices in [first, first + count) only
-      GatherArgs g = ex->reduce_range;
-      g.ptr[0] = ex->partial + (size_t)first * ex->final_size * 8;
-      g.loop.dim[0] = (uint32_t)count;
-      g.loop.div[0] = make_fastdiv((uint32_t)count);
-      g.n_loop = g.n_loop / (uint32_t)ex->n_slices * (uint32_t)count;
-      Timed t(ex->prof, st, KC_REDUCE, 0, (double)count * ex->final_size * 8);
-      ce = launch_gather(g, out, ex->sm_count, st);
-    }
-  }
+  if (ce == cudaSuccess) ce = run_one(ex->reduce, true, 0);
   return ce;
 }
 }  // namespace
@@ -1836,7 +1921,7 @@ cudaError_t exec_enqueue(Executor* ex, const std::vector<Leaf>& leaves, double* 
 std::string exec_run_slices(Executor* ex, const std::vector<Leaf>& leaves, int64_t first, int64_t count,
                             double* dev_out, cudaStream_t st, int* code) {
   *code = QTPU_OK;
-  if (ex->launches.empty() || !ex->has_reduce_range || ex->n_slices > 0xFFFFFFFFll) {
+  if (ex->launches.empty()) {
     *code = QTPU_ENOTSUP;
     return "slice ranges need a network with at least one pairwise step";
   }
@@ -1866,8 +1951,6 @@ void exec_free(Executor* ex) {
   ex->dot_scratch = nullptr;
   if (ex->wbuf) cudaFree(ex->wbuf);
   ex->wbuf = nullptr;
-  if (ex->memobuf) cudaFree(ex->memobuf);
-  ex->memobuf = nullptr;
   ex->arena = ex->splitbuf = ex->partial = nullptr;
   ex->status = nullptr;
   ex->out_stage = nullptr;

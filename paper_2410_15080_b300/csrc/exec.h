@@ -1,5 +1,6 @@
 // Executor: turns a Plan into a list of kernel launches on one device/stream.
 #pragma once
+#include <algorithm>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -55,21 +56,34 @@ struct Launch {
   int fuse_src[kMaxOps] = {};
   // fast gather/split with a large W table: its byte offset in Executor::wbuf
   int64_t wg_off = -1;
-  // slice reuse: the sliced positions this launch's value depends on; a
-  // launch that does not depend on all of them is kept (memo) in its own
-  // buffer across slices, `copies` copies indexed by the values of the
-  // positions copy_pos, and runs only when no copy for the current values is
-  // valid -- a stored copy is valid while the positions epoch_pos keep the
-  // values it was computed with
-  uint64_t dep = 0;
-  bool memo = false;
-  std::vector<int> epoch_pos, copy_pos;
-  int64_t copies = 1;
-  size_t memo_off = 0, memo_bytes = 0;  // copy 0 in Executor::memobuf, bytes per copy
-  int64_t runs = 1;                     // executions per full contraction
-  // LK_GEMM whose operand buffer is kept with copies: one map per copy
+  // slice reuse: the sliced positions the launch loops over (the values its
+  // inputs depend on) and those its result depends on (one kept copy per
+  // value); it adds up over din \ dout.  runs = executions per contraction.
+  uint64_t din = 0, dout = 0;
+  int64_t runs = 1;
+  // LK_GEMM whose operand is a kept result with several copies (pieces
+  // written by the producing GEMM's epilogue): one map per copy, and the
+  // intermediate holding them
   std::vector<CUtensorMap> tm_copies[2];
-  int opnd_memo[2] = {-1, -1};          // launch index owning that operand buffer
+  int opnd_owner[2] = {-1, -1};
+};
+
+// One unit of the slice-reuse schedule: a launch, preceded (for a GEMM) by
+// the splits of its operands.  The group loops over the values of the main
+// launch's din in `order` (last fastest); a split runs only when the values
+// of its own din change.
+struct Group {
+  int main = -1;
+  int split[2] = {-1, -1};
+  std::vector<int> order;
+};
+
+// Where an intermediate lives: arena offset of copy 0, bytes per copy, and
+// the sliced positions indexing its copies (those its value depends on,
+// outside the blocked positions).
+struct Stored {
+  size_t off = 0, bytes = 0;
+  std::vector<int> cpos;
 };
 
 struct Profiler {
@@ -90,8 +104,6 @@ struct Executor {
   int n_leaves = 0;
   std::vector<Launch> launches;  // one slice, in order
   Launch reduce;                 // slice sum + final reduction -> dev_out
-  GatherArgs reduce_range;       // the same over a range of slices (slice mode first)
-  bool has_reduce_range = false;
   std::vector<size_t> inter_off; // arena byte offset per intermediate (id - n_leaves)
   // per leaf: (slice position, stride) of each sliced index it carries
   std::vector<std::vector<std::pair<int, int64_t>>> leaf_slice;
@@ -131,19 +143,17 @@ struct Executor {
   cudaStream_t side_stream = nullptr;
   std::vector<cudaEvent_t> side_ev;  // one per side launch, plus fork and join
   double planned_side_bytes = 0;
-  // slice reuse (sliced plans): nested order of the sliced positions for a
-  // full contraction (outermost first), the buffer of kept results, and per
-  // intermediate (id - n_leaves) the launch whose kept output holds it (-1:
-  // the transient arena)
-  std::vector<int> loop_order;
-  uint8_t* memobuf = nullptr;
-  size_t memo_total = 0;
+  // slice reuse (sliced plans): the schedule's groups, the positions held
+  // fixed per block (bit mask), the layout of every intermediate
+  std::vector<Group> groups;
+  uint64_t fixed = 0;
   uint64_t reuse_budget = 0;
-  std::vector<int> inter_memo;
+  size_t kept_bytes = 0;         // arena bytes beyond the one-slice-at-a-time layout
+  std::vector<Stored> stored;    // per intermediate (id - n_leaves)
   double flops_executed = 0;     // useful FLOPs one full contraction executes
   double flops_no_reuse = 0;     // the same with every slice computed in full
   size_t workspace_bytes() const {
-    return arena_bytes + split_bytes + side_bytes + wbuf_bytes + memo_total + (size_t)n_slices * final_size * 8;
+    return arena_bytes + split_bytes + side_bytes + wbuf_bytes + (size_t)std::max<int64_t>(final_size, 1) * 8;
   }
 };
 

@@ -32,6 +32,7 @@ struct ModeTab {
 struct ContractArgs {
   ModeTab out, loop;
   int64_t n_out = 1, n_loop = 1;
+  int accum = 0;  // add to the output instead of overwriting it
 };
 
 enum DType { DT_F32 = 0, DT_F64 = 1, DT_F32X2 = 2 /* (hi, lo) float pair per entry */ };
@@ -95,6 +96,9 @@ struct GatherArgs {
   int dot = 0;
   uint32_t tile_n = 0, n_outer = 0, chunks = 0;
   float2* scratch = nullptr;
+  // dense modes: add to the output instead of overwriting it (a sum over a
+  // sliced index that the step contracts, accumulated slice value by value)
+  int accum = 0;
 };
 constexpr uint32_t kDotMaxTile = 2048;
 // scratch entries a dot launch may use (float2)
@@ -142,6 +146,7 @@ struct GemmArgs {
   uint32_t* status = nullptr;
   uint64_t limit_ns = 2000000000ull;
   GemmFuse fuse;         // fuse.on: C receives the consumer's piece planes
+  int accum = 0;         // add the product to the stored (hi, lo) result (not with fuse)
 };
 cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st);
 // one warp waiting (bounded) on a barrier nothing completes: sets ST_TIMEOUT_DEP

@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __
       if (F64OUT) {
         double v = acc.as_double();
         for (uint32_t d = S >> 1; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-        if (o < a.n_out && sub == 0) ((double*)out)[o] = v;
+        if (o < a.n_out && sub == 0) store_out((double*)out, o, v, a.accum);
         continue;
       }
       float2 v = acc.get();
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __
         t.add(make_float2(__shfl_xor_sync(0xffffffffu, v.x, d), __shfl_xor_sync(0xffffffffu, v.y, d)));
         v = t.get();
       }
-      if (o < a.n_out && sub == 0) ((float2*)out)[o] = v;
+      if (o < a.n_out && sub == 0) store_out((float2*)out, o, v, a.accum);
     }
     return;
   }
@@ -262,9 +262,9 @@ __global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __
     offsets<O::NOPS>(o, a.out, base);
     const ACC v = O::template entry<ACC>(a, W, base, lt);
     if (F64OUT)
-      ((double*)out)[o] = v.as_double();
+      store_out((double*)out, o, v.as_double(), a.accum);
     else
-      ((float2*)out)[o] = v.get();
+      store_out((float2*)out, o, v.get(), a.accum);
   }
 }
 
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(256) k_dot_fast(const GatherArgs a) {
 // (F64OUT), or compensated pairs
 template <bool F64OUT>
 __global__ void __launch_bounds__(256) k_dot_finish(const float2* __restrict__ part, uint32_t n_out,
-                                                    uint32_t chunks, void* __restrict__ out) {
+                                                    uint32_t chunks, void* __restrict__ out, int accum) {
   pdl_wait();
   pdl_launch_dependents();
   for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < n_out; o += gridDim.x * blockDim.x) {
@@ -411,12 +411,12 @@ __global__ void __launch_bounds__(256) k_dot_finish(const float2* __restrict__ p
       const double* pd = reinterpret_cast<const double*>(part);
       double s = 0.0;
       for (uint32_t c = 0; c < chunks; ++c) s += pd[(size_t)o * chunks + c];
-      ((double*)out)[o] = s;
+      store_out((double*)out, o, s, accum);
       continue;
     }
     Acc acc;
     for (uint32_t c = 0; c < chunks; ++c) acc.add(part[(size_t)o * chunks + c]);
-    ((float2*)out)[o] = acc.get();
+    store_out((float2*)out, o, acc.get(), accum);
   }
 }
 
@@ -434,8 +434,8 @@ cudaError_t dot_launch(const GatherArgs& a, void* out, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const uint32_t g = (a.n_out + 255) / 256;
   const float2* part = a.scratch;
-  if (f64) return launch_k(k_dot_finish<true>, dim3(g), dim3(256), 0, st, part, a.n_out, a.chunks, out);
-  return launch_k(k_dot_finish<false>, dim3(g), dim3(256), 0, st, part, a.n_out, a.chunks, out);
+  if (f64) return launch_k(k_dot_finish<true>, dim3(g), dim3(256), 0, st, part, a.n_out, a.chunks, out, a.accum);
+  return launch_k(k_dot_finish<false>, dim3(g), dim3(256), 0, st, part, a.n_out, a.chunks, out, a.accum);
 }
 
 // ------------------------------------------------------------ split output

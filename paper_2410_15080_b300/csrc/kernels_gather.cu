@@ -93,9 +93,9 @@ __global__ void __launch_bounds__(256) k_gather_dense(const GatherArgs a, void* 
     offsets<NOPS>(o, a.out, base);
     const ACC v = entry<NOPS, ACC>(a, base);
     if (F64OUT)
-      ((double*)out)[o] = v.as_double();
+      store_out((double*)out, o, v.as_double(), a.accum);
     else
-      ((float2*)out)[o] = v.get();
+      store_out((float2*)out, o, v.get(), a.accum);
   }
 }
 
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(256) k_gather_block(const GatherArgs a, void* 
       if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += redd[w];
-        ((double*)out)[o] = t;
+        store_out((double*)out, o, t, a.accum);
       }
       __syncthreads();
       continue;
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(256) k_gather_block(const GatherArgs a, void* 
     if (threadIdx.x == 0) {
       Acc t;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t.add(red[w]);
-      ((float2*)out)[o] = t.get();
+      store_out((float2*)out, o, t.get(), a.accum);
     }
     __syncthreads();
   }

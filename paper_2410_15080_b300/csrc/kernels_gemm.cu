@@ -276,7 +276,7 @@ template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               float2* __restrict__ Cout, int batch, int M, int N, int K, int kc_blocks, uint32_t* status,
-              uint64_t limit_ns, const __grid_constant__ GemmFuse fz) {
+              uint64_t limit_ns, const __grid_constant__ GemmFuse fz, int accum) {
   using C = Cfg<PREC>;
   using L = Layout<PREC>;
   extern __shared__ uint8_t smem_raw[];
@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int j = 0; j < 8; ++j) {
               if (c0 + j < N) {
                 float2 v = two_sum(__uint_as_float(rx[j]), C::NPROD > 1 ? __uint_as_float(ry[j]) : 0.f);
-                if (ch > 0) v = pair_add(dst[(long long)j * M], v);
+                if (ch > 0 || accum) v = pair_add(dst[(long long)j * M], v);
                 dst[(long long)j * M] = v;
               }
             }
@@ -530,9 +530,9 @@ cudaError_t launch_t(const GemmArgs& a, int sm_count, cudaStream_t st) {
   const long long tiles = (long long)a.batch * ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
   if (tiles <= 0) return cudaSuccess;
   const int grid = (int)(tiles < sm_count ? tiles : sm_count);
-  if (a.fuse.on && (PREC != 3 || a.fuse.w_size > kFuseMaxW)) return cudaErrorInvalidValue;
+  if (a.fuse.on && (PREC != 3 || a.fuse.w_size > kFuseMaxW || a.accum)) return cudaErrorInvalidValue;
   return launch_k(k_gemm_tc<PREC>, dim3(grid), dim3(kThreads), (size_t)L::SMEM, st, a.tmA, a.tmB, (float2*)a.C,
-                  a.batch, a.M, a.N, a.K, a.kc_blocks, a.status, a.limit_ns, a.fuse);
+                  a.batch, a.M, a.N, a.K, a.kc_blocks, a.status, a.limit_ns, a.fuse, a.accum);
 }
 
 // A single warp waits on an mbarrier that nothing completes, with the same

@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(256) k_contract_thread(const TA* __restrict__ 
   for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < a.n_out; o += stride) {
     int64_t oa, ob;
     decompose(o, a.out, oa, ob);
-    out[o] = loop_sum<TA, TB, HAS_B>(A, B, oa, ob, a);
+    const double v = loop_sum<TA, TB, HAS_B>(A, B, oa, ob, a);
+    out[o] = a.accum ? out[o] + v : v;
   }
 }
 
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(256) k_contract_block(const TA* __restrict__ A
     if (threadIdx.x == 0) {
       double t = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-      out[o] = t;
+      out[o] = a.accum ? out[o] + t : t;
     }
     __syncthreads();
   }

@@ -219,34 +219,56 @@ def _host_handle(net, **plan_kw):
 
 
 def test_slice_reuse_executes_each_distinct_value_once():
-    """Slice reuse on the 100-qubit 1024-slice plan: the FLOPs one contraction
-    executes are the plan's per-slice FLOPs of every launch times the number
-    of distinct values of the sliced indices it depends on, far below the
-    plan's total; with no budget every slice is computed in full."""
+    """Slice reuse on the 100-qubit 1024-slice plan.  A launch runs once per
+    value of the sliced indices its inputs still depend on (a step that
+    contracts a sliced index adds up over its values), so a contraction
+    executes the FLOPs of the same contraction tree unsliced: the plan's
+    per-slice FLOPs of each step times the values of the sliced indices among
+    its operands' indices, far below the plan's total.  With reuse off every
+    slice is computed in full."""
     import synth
+    from oracle import planner
     net = synth.ring_chords_htn(materialize=False)
     kw = dict(max_intermediate_bytes=8 << 30, n_slices=1024, slice_dim=4, n_candidates=256)
     h = _host_handle(net, **kw)
     st = h.exec_stats()
     plan_total = h.plan_stats()["flops_total"]
     t = h.lowering_info()
+    ptext = h.plan_info()
     h.close()
     assert st["flops_all_slices"] == pytest.approx(plan_total, rel=1e-12)
-    assert st["flops_executed"] < plan_total / 10
-    assert 0 < st["kept_bytes"] <= 64 << 30
-    # recompute the executed FLOPs from the launch list: each launch's FLOPs
-    # times its runs (1024 for a launch that is not kept)
+    # the unsliced FLOPs of the plan's own tree, from the oracle planner's cost
+    # rule (every index at its full dim)
+    dims = net.dims()
+    tensors = {i: tuple(x) for i, x in enumerate(net.inds())}
+    unsliced = 0
+    for l in ptext.splitlines():
+        f = l.split()
+        if f[0] != "step":
+            continue
+        x, y, o = int(f[2]), int(f[3]), int(f[5])
+        g = {k: () if v == "-" else tuple(int(i) for i in v.split(",")) for k, v in
+             (w.split("=") for w in f[6:12])}
+        unsliced += planner.step_flops(dims, tensors[x], tensors[y], g["batch"], g["m"], g["n"], g["k"],
+                                       g["sa"], g["sb"])
+        tensors[o] = g["batch"] + g["m"] + g["n"]
+    assert unsliced < plan_total / 25
+    # the executor attributes absorbed CT steps to the launch that folds them
+    # in, which may loop over more slice values: at most a sliver above
+    assert unsliced <= st["flops_executed"] <= 1.001 * unsliced
+    # the executed FLOPs recomputed from the launch list: FLOPs times runs; a
+    # main launch runs once per value of its din, a split at least that often
     fe, n_launch = 0.0, 1
     for l in t.splitlines():
         if not l.startswith("launch "):
             continue
         f = dict(w.split("=", 1) for w in l.split() if "=" in w)
-        runs = int(f["runs"]) if "runs" in f else 1024
-        if "runs" in f:  # a kept launch runs once per distinct value of its positions
-            c = int(f["copies"])
-            ep = [] if f["epoch_pos"] == "-" else f["epoch_pos"].split(",")
-            cp = [] if f["copy_pos"] == "-" else f["copy_pos"].split(",")
-            assert c == 4 ** len(cp) and runs == 4 ** (len(ep) + len(cp)) and runs < 1024
+        runs = int(f["runs"])
+        din = [] if f["din"] == "-" else f["din"].split(",")
+        if " split " in l:
+            assert runs >= 4 ** len(din)
+        else:
+            assert runs == 4 ** len(din)
         fe += int(f["flops"]) * runs
         n_launch += runs
     assert fe == pytest.approx(st["flops_executed"], rel=1e-12)
@@ -257,19 +279,22 @@ def test_slice_reuse_executes_each_distinct_value_once():
     assert st2["flops_executed"] == pytest.approx(plan_total, rel=1e-12) and st2["kept_bytes"] == 0
 
 
-def test_slice_reuse_budget_falls_back_to_one_copy():
-    """Under a budget below the all-copies layout, the largest kept launches
-    keep one copy (more runs), the kept bytes respect the budget, and the
+def test_slice_reuse_budget_blocks_sliced_indices():
+    """Under a budget below the all-copies layout, some sliced indices are
+    held fixed in an outer loop: the workspace respects the budget and the
     executed FLOPs lie between the unlimited-reuse and no-reuse figures."""
     import synth
     net = synth.ring_chords_htn(materialize=False)
     kw = dict(max_intermediate_bytes=8 << 30, n_slices=1024, slice_dim=4, n_candidates=256)
     full = _host_handle(net, **kw)
     sf = full.exec_stats()
+    wf = full.plan_stats()["workspace_bytes"]
     full.close()
-    budget = sf["kept_bytes"] // 2
+    budget = (wf - sf["kept_bytes"]) + sf["kept_bytes"] // 3
     h = _host_handle(net, reuse_bytes=budget, **kw)
     s = h.exec_stats()
+    t = h.lowering_info()
     h.close()
-    assert s["kept_bytes"] <= budget
+    assert "reuse blocked=-" not in t
+    assert s["kept_bytes"] < sf["kept_bytes"]
     assert sf["flops_executed"] < s["flops_executed"] < sf["flops_all_slices"]
