@@ -216,7 +216,12 @@ qtpu_status qtpu_htn_contract(qtpu_htn* h, double* dev_out);
 /* End-to-end form with HOST buffers: copies host_ptrs[t] (one per tensor,
  * dense row-major in the tensor's dtype, ideally pinned) into the device
  * buffers given to add_tensor, contracts, copies the FP64 result to host_out
- * and waits for the stream.  Returns the device status like qtpu_htn_sync. */
+ * and waits for the stream.  The uploads run on a copy stream of the handle,
+ * in the order the contraction first reads the tensors, after the work
+ * already enqueued on the handle's stream; each kernel waits only for the
+ * uploads of the tensors it reads, so the contraction overlaps the later
+ * uploads (its launches are direct, not the replayed graph).  Returns the
+ * device status like qtpu_htn_sync. */
 qtpu_status qtpu_htn_contract_host(qtpu_htn* h, const void* const* host_ptrs,
                                    double* host_out);
 

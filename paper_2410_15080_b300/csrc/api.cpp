@@ -33,6 +33,11 @@ struct qtpu_htn {
   Executor ex;
   bool built = false;
   std::string err;
+  // contract_host: a copy stream for the leaf uploads, one event per leaf,
+  // and an event that orders the uploads after earlier work on the stream
+  cudaStream_t up_stream = nullptr;
+  std::vector<cudaEvent_t> leaf_ev;
+  cudaEvent_t up_start = nullptr;
 };
 
 // message of the last failed create or allocation-free call, per thread
@@ -284,20 +289,45 @@ qtpu_status qtpu_htn_contract_host(qtpu_htn* h, const void* const* host_ptrs, do
   if (!host_ptrs || !host_out) return fail(h, QTPU_EINVAL, "NULL host buffer");
   cudaError_t e = cudaSetDevice(h->device);
   if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
-  for (size_t t = 0; t < h->leaves.size(); ++t) {
-    const Leaf& L = h->leaves[t];
+  for (size_t t = 0; t < h->leaves.size(); ++t)
     if (!host_ptrs[t]) return fail(h, QTPU_EINVAL, "NULL host buffer");
+  const size_t nl = h->leaves.size();
+  if (!h->up_stream) {
+    e = cudaStreamCreateWithFlags(&h->up_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->up_start, cudaEventDisableTiming);
+    for (size_t t = 0; t < nl && e == cudaSuccess; ++t) {
+      cudaEvent_t ev;
+      e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) h->leaf_ev.push_back(ev);
+    }
+    if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
+  }
+  // The uploads run on a copy stream, leaf by leaf in the order the schedule
+  // first reads them, after the work already enqueued on the handle's stream
+  // (which may still read the device buffers); each launch of the
+  // contraction waits only for the leaves it reads, so the contraction starts
+  // while later leaves are still being copied.
+  e = cudaEventRecord(h->up_start, h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->up_stream, h->up_start, 0);
+  for (int t : exec_leaf_order(&h->ex, (int)nl)) {
+    if (e != cudaSuccess) break;
+    const Leaf& L = h->leaves[t];
     int64_t n = 1;
     for (int64_t d : L.dims) n *= d;
     e = cudaMemcpyAsync((void*)L.ptr, host_ptrs[t], (size_t)n * (L.dt == DT_F64 ? 8 : 4), cudaMemcpyHostToDevice,
-                        h->stream);
-    if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
+                        h->up_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->leaf_ev[t], h->up_stream);
   }
+  if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
   int64_t no = 1;
   qtpu_htn_output_size(h, &no);
   double* dout = h->ex.out_stage;  // allocated with the workspace by plan
-  qtpu_status s = qtpu_htn_contract(h, dout);
-  if (s != QTPU_OK) return s;
+  int code = QTPU_OK;
+  std::string m = exec_run_host(&h->ex, h->leaves, dout, h->stream, h->leaf_ev.data(), &code);
+  if (code != QTPU_OK) return fail(h, (qtpu_status)code, m);
+  // every upload is done before the call returns (a leaf no launch reads too)
+  for (size_t t = 0; t < nl && e == cudaSuccess; ++t) e = cudaStreamWaitEvent(h->stream, h->leaf_ev[t], 0);
+  if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
   e = cudaMemcpyAsync(host_out, dout, (size_t)no * 8, cudaMemcpyDeviceToHost, h->stream);
   if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
   return qtpu_htn_sync(h);
@@ -474,6 +504,9 @@ qtpu_status qtpu_htn_destroy(qtpu_htn* h) {
     cudaSetDevice(h->device);
     exec_free(&h->ex);
   }
+  for (cudaEvent_t ev : h->leaf_ev) cudaEventDestroy(ev);
+  if (h->up_start) cudaEventDestroy(h->up_start);
+  if (h->up_stream) cudaStreamDestroy(h->up_stream);
   delete h;
   return QTPU_OK;
 }

@@ -1315,33 +1315,51 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
   const double blocks = count_of(F);
   ex->flops_executed = ex->flops_no_reuse = 0;
   ex->launches_per_contract = 1;
+  ex->n_split_slots = 1;
+  std::vector<double> launches_of(ex->launches.size(), 0);
   for (Group& G : ex->groups) {
     Launch& M = ex->launches[G.main];
+    // a GEMM sums the values of the positions it contracts inside one launch
+    // (operand pair per value): those positions go innermost, and each split
+    // that depends on them fills one slot per value
+    G.sum_pos = M.kind == LK_GEMM ? (M.din & ~M.dout & ~F) : 0;
     uint64_t A = 0, B = 0;
     double ba = 0, bb = 0;
-    if (G.split[0] >= 0) A = ex->launches[G.split[0]].din & ~F, ba = ex->launches[G.split[0]].bytes;
-    if (G.split[1] >= 0) B = ex->launches[G.split[1]].din & ~F, bb = ex->launches[G.split[1]].bytes;
+    if (G.split[0] >= 0) A = ex->launches[G.split[0]].din & ~F & ~G.sum_pos, ba = ex->launches[G.split[0]].bytes;
+    if (G.split[1] >= 0) B = ex->launches[G.split[1]].din & ~F & ~G.sum_pos, bb = ex->launches[G.split[1]].bytes;
     if (bb > ba) std::swap(A, B);  // the larger split's positions outermost
     G.order.clear();
-    for (uint64_t part : {A & B, A & ~B, B & ~A, (M.din & ~F) & ~(A | B)})
+    for (uint64_t part : {A & B, A & ~B, B & ~A, (M.din & ~F) & ~(A | B) & ~G.sum_pos, G.sum_pos})
       for (int q = 0; q < nsp; ++q)
         if ((part >> q) & 1) G.order.push_back(q);
+    const double V = count_of(G.sum_pos);
     M.runs = (int64_t)(count_of(M.din & ~F) * blocks);
+    launches_of[G.main] = (double)M.runs / V * std::ceil(V / kGemmVals);
+    if (G.sum_pos) ex->n_split_slots = std::max<int>(ex->n_split_slots, (int)std::min<double>(V, kGemmVals));
+    // a split reruns when the outer positions up to its innermost own one
+    // change; one that depends on a contracted position fills a slot per value
+    std::vector<int> outer_order;
+    for (int q : G.order)
+      if (!((G.sum_pos >> q) & 1)) outer_order.push_back(q);
     for (int sp : G.split) {
       if (sp < 0) continue;
       Launch& S = ex->launches[sp];
       int last_j = -1;
-      for (size_t j = 0; j < G.order.size(); ++j)
-        if (((S.din & ~F) >> G.order[j]) & 1) last_j = (int)j;
+      for (size_t j = 0; j < outer_order.size(); ++j)
+        if (((S.din & ~F) >> outer_order[j]) & 1) last_j = (int)j;
       double r = 1;
-      for (int j = 0; j <= last_j; ++j) r *= (double)sd[G.order[j]];
+      for (int j = 0; j <= last_j; ++j) r *= (double)sd[outer_order[j]];
+      if (S.din & G.sum_pos) r *= V;
       S.runs = (int64_t)(r * blocks);
+      launches_of[sp] = (double)S.runs;
     }
   }
-  for (const Launch& L : ex->launches) {
+  for (size_t i = 0; i < ex->launches.size(); ++i) {
+    Launch& L = ex->launches[i];
+    L.n_launch = (int64_t)(launches_of[i] > 0 ? launches_of[i] : (double)L.runs);
     ex->flops_executed += L.flops * (double)L.runs;
     ex->flops_no_reuse += L.flops * (double)ex->n_slices;
-    ex->launches_per_contract += L.runs;
+    ex->launches_per_contract += L.n_launch;
   }
 
   // ---- concurrent leaf splits: in an unsliced plan, a GEMM operand gathered
@@ -1390,8 +1408,10 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       L.wg_off = (int64_t)ex->wbuf_bytes;
       ex->wbuf_bytes += align_up((size_t)L.gf.w_size * sizeof(float2), 256);
     }
-  ex->split_a_bytes = split_need_a;
-  ex->split_bytes = split_need_a + split_need_b;
+  ex->split_slot[0] = split_need_a;
+  ex->split_slot[1] = split_need_b;
+  ex->split_a_bytes = split_need_a * ex->n_split_slots;
+  ex->split_bytes = (split_need_a + split_need_b) * ex->n_split_slots;
   ex->lowered = true;
   if (dry_run) return "";
 
@@ -1399,8 +1419,6 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
   cudaError_t ce = cudaSetDevice(ex->device);
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&ex->sm_count, cudaDevAttrMultiProcessorCount, ex->device);
   if (ce != cudaSuccess) return fail(QTPU_ECUDA, std::string("cuda: ") + cudaGetErrorString(ce));
-  ex->split_a_bytes = split_need_a;
-  ex->split_bytes = split_need_a + split_need_b;
   // QTPU_TEST_FAIL_ALLOC=1 makes the workspace allocation fail (a host-side
   // injection point for the out-of-memory path)
   const char* fa = std::getenv("QTPU_TEST_FAIL_ALLOC");
@@ -1471,6 +1489,17 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
         const Launch& S = ex->launches[L.opnd_split[side]];
         base[side] = S.side >= 0 ? ex->sidebuf + S.side_off : ex->splitbuf + (side ? ex->split_a_bytes : 0);
         kp[side] = S.g.Kp;
+        // one map per split slot (slot 0 is the map set below)
+        const int64_t rows = side ? L.gemm.N : L.gemm.M;
+        const int box = side ? gemm_block_n() : 128;
+        for (int v = 1; v < ex->n_split_slots && S.side < 0; ++v) {
+          CUtensorMap* m = side ? &L.gemm.maps.b[v] : &L.gemm.maps.a[v];
+          if (!make_operand_map(m, base[side] + (size_t)v * ex->split_slot[side], prec, L.gemm.batch, rows, L.gemm.K,
+                                kp[side], box)) {
+            exec_free(ex);
+            return fail(QTPU_ECUDA, "cuTensorMapEncodeTiled failed");
+          }
+        }
         continue;
       }
       const int T = L.opnd_fused[side];
@@ -1492,8 +1521,9 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
           }
       }
     }
-    if (!make_operand_map(&L.gemm.tmA, base[0], prec, L.gemm.batch, L.gemm.M, L.gemm.K, kp[0], 128) ||
-        !make_operand_map(&L.gemm.tmB, base[1], prec, L.gemm.batch, L.gemm.N, L.gemm.K, kp[1], gemm_block_n())) {
+    if (!make_operand_map(&L.gemm.maps.a[0], base[0], prec, L.gemm.batch, L.gemm.M, L.gemm.K, kp[0], 128) ||
+        !make_operand_map(&L.gemm.maps.b[0], base[1], prec, L.gemm.batch, L.gemm.N, L.gemm.K, kp[1],
+                          gemm_block_n())) {
       exec_free(ex);
       return fail(QTPU_ECUDA, "cuTensorMapEncodeTiled failed");
     }
@@ -1585,7 +1615,7 @@ std::string exec_describe(const Executor* ex) {
           if ((m >> q) & 1) r += (r.empty() ? "" : ",") + std::to_string(q);
         return r.empty() ? std::string("-") : r;
       };
-      o << " din=" << pos(L.din) << " dout=" << pos(L.dout) << " runs=" << L.runs;
+      o << " din=" << pos(L.din) << " dout=" << pos(L.dout) << " runs=" << L.runs << " launches=" << L.n_launch;
     }
     o << "\n";
   };
@@ -1680,14 +1710,33 @@ std::vector<Block> range_blocks(const std::vector<int64_t>& dims, int64_t first,
 // its main launch's din (within the block), re-running a split only when
 // its own din values change, and the main launch adds up over the positions
 // it contracts (the last launch over everything, into the FP64 partial).
+//
+// leaf_ready (optional, one event per leaf): each launch first makes its
+// stream wait for the events of the leaves it reads (their uploads), once
+// per stream.
 cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* out, cudaStream_t st,
-                        int64_t first = 0, int64_t count = -1) {
+                        int64_t first = 0, int64_t count = -1, const cudaEvent_t* leaf_ready = nullptr) {
   if (count < 0) count = ex->n_slices;
   const int nl = (int)leaves.size();
   const int nsp = (int)ex->slice_dims.size();
   std::vector<int64_t> loff(nl, 0);
   std::vector<int64_t> digit(nsp, 0);
   cudaError_t ce = cudaSuccess;
+  std::vector<std::vector<cudaStream_t>> waited(leaf_ready ? nl : 0);
+  auto wait_leaf = [&](int t, cudaStream_t s) -> cudaError_t {
+    if (!leaf_ready || t < 0 || t >= nl) return cudaSuccess;
+    for (cudaStream_t w : waited[t])
+      if (w == s) return cudaSuccess;
+    waited[t].push_back(s);
+    return cudaStreamWaitEvent(s, leaf_ready[t], 0);
+  };
+  auto wait_sources = [&](const Launch& L, cudaStream_t s) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < L.nsrc && e == cudaSuccess; ++j) e = wait_leaf(L.src[j], s);
+    if (L.kind == LK_GEMM && L.gemm.fuse.on)
+      for (int j = 0; j < L.gemm.fuse.nsmall && e == cudaSuccess; ++j) e = wait_leaf(L.fuse_src[j], s);
+    return e;
+  };
   // copy index of an intermediate under the current position values
   auto copy_of = [&](const Stored& S) {
     int64_t c = 0;
@@ -1704,17 +1753,29 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
   };
   const bool sided = ex->n_side > 0 && count == ex->n_slices && ex->n_slices == 1;
   const Launch* cur = nullptr;
+  int cur_slot = 0;  // split slot of the launch being enqueued
+  // operand maps of the values a GEMM launch sums (nullptr: its own maps)
+  struct ValMaps {
+    int n = 0;
+    const CUtensorMap* a[kGemmVals];
+    const CUtensorMap* b[kGemmVals];
+  };
+  const ValMaps* cur_vals = nullptr;
   auto dst_ptr = [&](int d) -> void* {
     switch (d) {
       case DST_SIDE: return ex->sidebuf + cur->side_off;
       case DST_PARTIAL: return ex->partial;
-      case DST_SPLIT_A: return ex->splitbuf;
-      case DST_SPLIT_B: return ex->splitbuf + ex->split_a_bytes;
+      case DST_SPLIT_A: return ex->splitbuf + (size_t)cur_slot * ex->split_slot[0];
+      case DST_SPLIT_B: return ex->splitbuf + ex->split_a_bytes + (size_t)cur_slot * ex->split_slot[1];
       case DST_OUT: return out;
       default: return inter_ptr(d);
     }
   };
   auto run_one_on = [&](const Launch& L, bool reduce, int accum, cudaStream_t st) -> cudaError_t {
+    if (!reduce) {
+      const cudaError_t we = wait_sources(L, st);
+      if (we != cudaSuccess) return we;
+    }
     cur = &L;
     Timed t(ex->prof, st, L.kclass, L.flops, L.bytes);
     const bool from_partial = reduce && !ex->launches.empty();
@@ -1738,8 +1799,13 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
       GemmArgs g = L.gemm;
       g.C = dst_ptr(L.dst);
       g.accum = accum;
-      if (L.opnd_owner[0] >= 0) g.tmA = L.tm_copies[0][(size_t)copy_of(ex->stored[L.opnd_owner[0] - nl])];
-      if (L.opnd_owner[1] >= 0) g.tmB = L.tm_copies[1][(size_t)copy_of(ex->stored[L.opnd_owner[1] - nl])];
+      if (cur_vals) {
+        g.nval = cur_vals->n;
+        for (int v = 0; v < cur_vals->n; ++v) g.maps.a[v] = *cur_vals->a[v], g.maps.b[v] = *cur_vals->b[v];
+      } else {
+        if (L.opnd_owner[0] >= 0) g.maps.a[0] = L.tm_copies[0][(size_t)copy_of(ex->stored[L.opnd_owner[0] - nl])];
+        if (L.opnd_owner[1] >= 0) g.maps.b[0] = L.tm_copies[1][(size_t)copy_of(ex->stored[L.opnd_owner[1] - nl])];
+      }
       for (int j = 0; g.fuse.on && j < g.fuse.nsmall; ++j) g.fuse.wptr[j] = src_ptr(L.fuse_src[j]);
       return launch_gemm(g, ex->sm_count, st);
     }
@@ -1804,12 +1870,21 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
   }
   bool final_written = false;
   const size_t n_launch = ex->launches.size();
-  std::vector<int64_t> split_epoch(n_launch, -1);
+  // per split and slot: the values of the split's positions it last ran with
+  std::vector<std::vector<int64_t>> split_epoch(n_launch);
   auto set_leaf_offsets = [&]() {
     for (int t = 0; t < nl; ++t) {
       int64_t o = 0;
       for (auto& ps : ex->leaf_slice[t]) o += digit[ps.first] * ps.second;
       loff[t] = o;
+    }
+  };
+  auto set_digits = [&](const std::vector<int>& pos, int64_t k, const Block& B) {
+    for (int j = (int)pos.size() - 1; j >= 0; --j) {
+      const int q = pos[j];
+      const int64_t w = B.hi[q] - B.lo[q];
+      digit[q] = B.lo[q] + k % w;
+      k /= w;
     }
   };
   for (const Block& B : blocks) {
@@ -1818,48 +1893,79 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
     for (const Group& G : ex->groups) {
       if (ce != cudaSuccess) break;
       const Launch& M = ex->launches[G.main];
-      // the group's positions that vary in this block, outermost first
-      std::vector<int> var;
+      // positions that vary in this block: the outer ones (a loop of
+      // launches) and, for a GEMM, the contracted ones (summed inside each
+      // launch, up to kGemmVals operand pairs at a time)
+      std::vector<int> outer, inner;
       for (int q : G.order)
-        if (B.hi[q] - B.lo[q] > 1) var.push_back(q);
+        if (B.hi[q] - B.lo[q] > 1) (((G.sum_pos >> q) & 1) ? inner : outer).push_back(q);
+      uint64_t inner_mask = 0;
+      for (int q : inner) inner_mask |= 1ull << q;
       for (int q = 0; q < nsp; ++q)
-        if (((M.din >> q) & 1)) digit[q] = B.lo[q];
+        if ((M.din >> q) & 1) digit[q] = B.lo[q];
       for (int sp : G.split)
-        if (sp >= 0) split_epoch[sp] = -1;
-      int64_t n = 1;
-      for (int q : var) n *= B.hi[q] - B.lo[q];
-      for (int64_t k = 0; k < n && ce == cudaSuccess; ++k) {
-        int64_t r = k;
-        for (int j = (int)var.size() - 1; j >= 0; --j) {
-          const int q = var[j];
-          const int64_t w = B.hi[q] - B.lo[q];
-          digit[q] = B.lo[q] + r % w;
-          r /= w;
+        if (sp >= 0) split_epoch[sp].assign((size_t)ex->n_split_slots, -1);
+      int64_t n_outer = 1, n_inner = 1;
+      for (int q : outer) n_outer *= B.hi[q] - B.lo[q];
+      for (int q : inner) n_inner *= B.hi[q] - B.lo[q];
+      for (int64_t ko = 0; ko < n_outer && ce == cudaSuccess; ++ko) {
+        set_digits(outer, ko, B);
+        for (int64_t c0 = 0; c0 < n_inner && ce == cudaSuccess; c0 += kGemmVals) {
+          const int nv = (int)std::min<int64_t>(kGemmVals, n_inner - c0);
+          ValMaps vm;
+          vm.n = nv;
+          for (int j = 0; j < nv && ce == cudaSuccess; ++j) {
+            set_digits(inner, c0 + j, B);
+            set_leaf_offsets();
+            int slot_of[2] = {0, 0};
+            for (int side = 0; side < 2; ++side) {
+              const int sp = G.split[side];
+              if (sp < 0) continue;
+              const Launch& S = ex->launches[sp];
+              const int slot = (S.din & inner_mask) ? j : 0;
+              slot_of[side] = slot;
+              int64_t ep = 0;  // the values of the split's own positions
+              for (int q = 0; q < nsp; ++q)
+                if ((S.din >> q) & 1) ep = ep * ex->slice_dims[q] + digit[q];
+              if (ep == split_epoch[sp][slot]) continue;
+              split_epoch[sp][slot] = ep;
+              cur_slot = slot;
+              ce = run_one(S, false, 0);
+              cur_slot = 0;
+              if (ce != cudaSuccess) break;
+            }
+            if (M.kind == LK_GEMM) {
+              for (int side = 0; side < 2; ++side) {
+                const CUtensorMap* m;
+                if (M.opnd_split[side] >= 0)
+                  m = side ? &M.gemm.maps.b[slot_of[side]] : &M.gemm.maps.a[slot_of[side]];
+                else if (M.opnd_owner[side] >= 0)
+                  m = &M.tm_copies[side][(size_t)copy_of(ex->stored[M.opnd_owner[side] - nl])];
+                else
+                  m = side ? &M.gemm.maps.b[0] : &M.gemm.maps.a[0];
+                (side ? vm.b : vm.a)[j] = m;
+              }
+            }
+          }
+          if (ce != cudaSuccess) break;
+          // add up over the positions the launch contracts: a GEMM over its
+          // later batches of values; any other launch on every visit after
+          // the first with the same dout values; the last launch on every
+          // visit after the contraction's first
+          int accum = 0;
+          if (M.dst == DST_PARTIAL) {
+            accum = final_written ? 1 : 0;
+            final_written = true;
+          } else if (M.kind == LK_GEMM && inner_mask) {
+            accum = c0 > 0 ? 1 : 0;
+          } else {
+            for (int q = 0; q < nsp; ++q)
+              if ((((M.din & ~M.dout) >> q) & 1) && digit[q] != B.lo[q]) accum = 1;
+          }
+          cur_vals = (M.kind == LK_GEMM) ? &vm : nullptr;
+          ce = run_one(M, false, accum);
+          cur_vals = nullptr;
         }
-        set_leaf_offsets();
-        for (int sp : G.split) {
-          if (sp < 0 || ce != cudaSuccess) continue;
-          const Launch& S = ex->launches[sp];
-          int64_t ep = 0;  // the values of the split's own positions
-          for (int q = 0; q < nsp; ++q)
-            if ((S.din >> q) & 1) ep = ep * ex->slice_dims[q] + digit[q];
-          if (ep == split_epoch[sp]) continue;
-          split_epoch[sp] = ep;
-          ce = run_one(S, false, 0);
-        }
-        if (ce != cudaSuccess) break;
-        // add up over the positions the launch contracts: every visit after
-        // the first with the same dout values (the last launch: every visit
-        // after the contraction's first)
-        int accum = 0;
-        if (M.dst == DST_PARTIAL) {
-          accum = final_written ? 1 : 0;
-          final_written = true;
-        } else {
-          for (int q = 0; q < nsp; ++q)
-            if ((((M.din & ~M.dout) >> q) & 1) && digit[q] != B.lo[q]) accum = 1;
-        }
-        ce = run_one(M, false, accum);
       }
     }
   }
@@ -1912,6 +2018,36 @@ std::string exec_run(Executor* ex, const std::vector<Leaf>& leaves, double* dev_
     return std::string("launch failed: ") + cudaGetErrorString(ce);
   }
   return "";
+}
+
+std::string exec_run_host(Executor* ex, const std::vector<Leaf>& leaves, double* dev_out, cudaStream_t st,
+                          const cudaEvent_t* leaf_ready, int* code) {
+  *code = QTPU_OK;
+  cudaError_t ce = enqueue_all(ex, leaves, dev_out, st, 0, -1, leaf_ready);
+  if (ce != cudaSuccess) {
+    *code = QTPU_ECUDA;
+    return std::string("launch failed: ") + cudaGetErrorString(ce);
+  }
+  return "";
+}
+
+std::vector<int> exec_leaf_order(const Executor* ex, int n_leaves) {
+  std::vector<int> order;
+  std::vector<char> seen(n_leaves, 0);
+  auto add = [&](int t) {
+    if (t >= 0 && t < n_leaves && !seen[t]) seen[t] = 1, order.push_back(t);
+  };
+  // the side-stream splits run first in an unsliced plan
+  for (const Launch& L : ex->launches)
+    if (L.side >= 0)
+      for (int j = 0; j < L.nsrc; ++j) add(L.src[j]);
+  for (const Launch& L : ex->launches) {
+    for (int j = 0; j < L.nsrc; ++j) add(L.src[j]);
+    if (L.kind == LK_GEMM && L.gemm.fuse.on)
+      for (int j = 0; j < L.gemm.fuse.nsmall; ++j) add(L.fuse_src[j]);
+  }
+  for (int t = 0; t < n_leaves; ++t) add(t);
+  return order;
 }
 
 cudaError_t exec_enqueue(Executor* ex, const std::vector<Leaf>& leaves, double* out, cudaStream_t st) {

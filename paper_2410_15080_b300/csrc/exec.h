@@ -60,7 +60,8 @@ struct Launch {
   // inputs depend on) and those its result depends on (one kept copy per
   // value); it adds up over din \ dout.  runs = executions per contraction.
   uint64_t din = 0, dout = 0;
-  int64_t runs = 1;
+  int64_t runs = 1;      // its operand products per contraction (FLOPs = flops x runs)
+  int64_t n_launch = 1;  // its kernel launches per contraction (a GEMM sums up to kGemmVals runs)
   // LK_GEMM whose operand is a kept result with several copies (pieces
   // written by the producing GEMM's epilogue): one map per copy, and the
   // intermediate holding them
@@ -76,6 +77,9 @@ struct Group {
   int main = -1;
   int split[2] = {-1, -1};
   std::vector<int> order;
+  // a GEMM group: the positions it contracts (outside the blocked ones),
+  // summed inside one launch over up to kGemmVals operand pairs
+  uint64_t sum_pos = 0;
 };
 
 // Where an intermediate lives: arena offset of copy 0, bytes per copy, and
@@ -113,6 +117,10 @@ struct Executor {
   int inter_dt = DT_F32X2;       // storage of intermediates
   int partial_dt = DT_F64;       // storage of the per-slice results (FP64, or pairs after a GEMM)
   size_t split_a_bytes = 0;      // offset of the B operand region
+  // operand splits of one GEMM launch over several values of a sliced index
+  // it contracts each get a slot: slot bytes per side, slots
+  size_t split_slot[2] = {0, 0};
+  int n_split_slots = 1;
   // device memory (owned)
   uint8_t* arena = nullptr;
   size_t arena_bytes = 0;
@@ -168,6 +176,12 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
 std::string exec_describe(const Executor* ex);
 // Enqueue the whole contraction; writes output_size FP64 entries to dev_out.
 std::string exec_run(Executor* ex, const std::vector<Leaf>& leaves, double* dev_out, cudaStream_t st, int* code);
+// The same with direct launches, each waiting for the events (one per leaf,
+// recorded after that leaf's upload) of the leaves it reads.
+std::string exec_run_host(Executor* ex, const std::vector<Leaf>& leaves, double* dev_out, cudaStream_t st,
+                          const cudaEvent_t* leaf_ready, int* code);
+// Leaves in the order the schedule first reads them (upload order).
+std::vector<int> exec_leaf_order(const Executor* ex, int n_leaves);
 // Enqueue one whole contraction on `st` with direct launches, result to out
 // (used to capture several networks into one graph).
 cudaError_t exec_enqueue(Executor* ex, const std::vector<Leaf>& leaves, double* out, cudaStream_t st);

@@ -135,10 +135,19 @@ struct GemmFuse {
   uint32_t w_size = 0;
 };
 
+// A GEMM may add up the products of several operand pairs (one per value of
+// a sliced index the step contracts): C = sum_v A_v B_v, all accumulated in
+// TMEM before one epilogue.
+constexpr int kGemmVals = 8;
+struct GemmMaps {
+  CUtensorMap a[kGemmVals], b[kGemmVals];  // 4-D maps over [pieces][batch][rows][Kp]
+};
+
 // prec: 1 = TF32 (1 piece, 1 product), 2 = 3xTF32 (2 pieces, 3 products),
 //       3 = BF16x3 (3 pieces, 6 products)
 struct GemmArgs {
-  CUtensorMap tmA, tmB;  // 4-D maps over [pieces][batch][rows][Kp]
+  GemmMaps maps;         // operand pair v in maps.a[v], maps.b[v], v < nval
+  int nval = 1;
   void* C = nullptr;     // [batch][N][M] (hi, lo) float pairs, dense (M fastest)
   int batch = 0, M = 0, N = 0, K = 0;
   int kc_blocks = 0;     // k-blocks per TMEM accumulation chunk (0 = all)

@@ -274,7 +274,7 @@ __device__ void fused_epilogue(const GemmFuse& fz, const float2* fW, uint8_t* sm
 
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+    k_gemm_tc(const __grid_constant__ GemmMaps maps, int nval,
               float2* __restrict__ Cout, int batch, int M, int N, int K, int kc_blocks, uint32_t* status,
               uint64_t limit_ns, const __grid_constant__ GemmFuse fz, int accum) {
   using C = Cfg<PREC>;
@@ -294,7 +294,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int lane = threadIdx.x & 31;
   const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
   const int n_tiles = batch * mt * nt;  // host checks n_tiles < 2^31
-  const int nkb = (K + C::KB - 1) / C::KB;
+  // k-blocks of one operand pair, and of all nval pairs in sequence (pair v
+  // owns k-blocks [v * nkb1, (v + 1) * nkb1))
+  const int nkb1 = (K + C::KB - 1) / C::KB;
+  const int nkb = nkb1 * nval;
   // the fused split takes the whole K in one accumulator chunk (host: K <= 1024)
   const int kc0 = (PREC == 3 && fz.on) ? nkb : (kc_blocks > 0 ? kc_blocks : C::KC);
   const int kc = kc0 < nkb ? kc0 : nkb;
@@ -317,9 +320,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     tmem_alloc(tmem_holder, kTmemCols);
     tmem_relinquish();
   }
-  if (warp == 0 && lane == 0) {
-    tma_prefetch_desc(&tmA);
-    tma_prefetch_desc(&tmB);
+  if (warp == 0 && lane < nval) {
+    tma_prefetch_desc(&maps.a[lane]);
+    tma_prefetch_desc(&maps.b[lane]);
   }
   tc_fence_before();
   __syncthreads();
@@ -370,10 +373,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           mbar_arrive_expect_tx(&full[stage], L::STAGE);
           uint8_t* sA = smem + stage * L::STAGE;
           uint8_t* sB = sA + C::NP * L::A_PIECE;
+          const int v = kb / nkb1, kb1 = kb - v * nkb1;
 #pragma unroll
           for (int p = 0; p < C::NP; ++p) {
-            tma_load_4d(sA + p * L::A_PIECE, &tmA, &full[stage], kb * C::KB, mtile * BM, b, p);
-            tma_load_4d(sB + p * L::B_PIECE, &tmB, &full[stage], kb * C::KB, ntile * BN, b, p);
+            tma_load_4d(sA + p * L::A_PIECE, &maps.a[v], &full[stage], kb1 * C::KB, mtile * BM, b, p);
+            tma_load_4d(sB + p * L::B_PIECE, &maps.b[v], &full[stage], kb1 * C::KB, ntile * BN, b, p);
           }
           issued[stage] = 1;
           issued_phase[stage] = phase;
@@ -530,8 +534,9 @@ cudaError_t launch_t(const GemmArgs& a, int sm_count, cudaStream_t st) {
   const long long tiles = (long long)a.batch * ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
   if (tiles <= 0) return cudaSuccess;
   const int grid = (int)(tiles < sm_count ? tiles : sm_count);
-  if (a.fuse.on && (PREC != 3 || a.fuse.w_size > kFuseMaxW || a.accum)) return cudaErrorInvalidValue;
-  return launch_k(k_gemm_tc<PREC>, dim3(grid), dim3(kThreads), (size_t)L::SMEM, st, a.tmA, a.tmB, (float2*)a.C,
+  if (a.fuse.on && (PREC != 3 || a.fuse.w_size > kFuseMaxW || a.accum || a.nval != 1)) return cudaErrorInvalidValue;
+  if (a.nval < 1 || a.nval > kGemmVals) return cudaErrorInvalidValue;
+  return launch_k(k_gemm_tc<PREC>, dim3(grid), dim3(kThreads), (size_t)L::SMEM, st, a.maps, a.nval, (float2*)a.C,
                   a.batch, a.M, a.N, a.K, a.kc_blocks, a.status, a.limit_ns, a.fuse, a.accum);
 }
 

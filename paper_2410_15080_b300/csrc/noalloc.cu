@@ -151,8 +151,8 @@ extern "C" qtpu_status qtpu_pairwise_contract_noalloc(const double* A, const dou
   gc.n_loop = 1;
   if (!ok || (uint64_t)batch * M * N > 0x7FFFFFFFull) return fail(QTPU_ENOTSUP, "noalloc: shape too large");
   GemmArgs g;
-  if (!make_operand_map(&g.tmA, s + a_off, 3, batch, M, K, Kp, 128) ||
-      !make_operand_map(&g.tmB, s + b_off, 3, batch, N, K, Kp, gemm_block_n()))
+  if (!make_operand_map(&g.maps.a[0], s + a_off, 3, batch, M, K, Kp, 128) ||
+      !make_operand_map(&g.maps.b[0], s + b_off, 3, batch, N, K, Kp, gemm_block_n()))
     return fail(QTPU_ECUDA, "noalloc: cuTensorMapEncodeTiled failed");
   g.C = s + c_off;
   g.batch = batch;

@@ -265,12 +265,18 @@ def test_slice_reuse_executes_each_distinct_value_once():
         f = dict(w.split("=", 1) for w in l.split() if "=" in w)
         runs = int(f["runs"])
         din = [] if f["din"] == "-" else f["din"].split(",")
+        dout = [] if f["dout"] == "-" else f["dout"].split(",")
         if " split " in l:
             assert runs >= 4 ** len(din)
         else:
             assert runs == 4 ** len(din)
+        if " gemm " in l:
+            # one launch sums the values of the sliced indices it contracts
+            assert int(f["launches"]) == runs // 4 ** (len(din) - len(dout))
+        else:
+            assert int(f["launches"]) == runs
         fe += int(f["flops"]) * runs
-        n_launch += runs
+        n_launch += int(f["launches"])
     assert fe == pytest.approx(st["flops_executed"], rel=1e-12)
     assert n_launch == st["launches"]
     h2 = _host_handle(net, reuse_bytes=1, **kw)

@@ -394,8 +394,9 @@ def test_slice_reuse_matches_oracle(reuse):
 
 
 def test_slice_ranges_with_reuse_add_up():
-    """Slice ranges (visited in slice-id order, recomputing kept results when
-    their indices change) add up to the full contraction (nested order)."""
+    """Slice ranges (run as aligned blocks of the slice space) add up to the
+    full contraction; both match the oracle (their sums over sliced indices
+    are added in different orders, so they agree to rounding, not bits)."""
     import torch
     from paper_2410_15080_b300 import from_network
     from tests.gpu_util import to_device
@@ -407,8 +408,10 @@ def test_slice_ranges_with_reuse_add_up():
     torch.cuda.synchronize()
     tot = sum(p.cpu().numpy() for p in parts)
     h.close()
-    assert rel_err(tot, full.cpu().numpy()) <= 1e-12
-    assert rel_err(full.cpu().numpy(), oracle_value(net)) <= REL_TOL
+    ref = oracle_value(net)
+    assert rel_err(tot, ref) <= REL_TOL
+    assert rel_err(full.cpu().numpy(), ref) <= REL_TOL
+    assert rel_err(tot, full.cpu().numpy()) <= 2 * REL_TOL
 
 
 def test_sliced_mid_ring_with_reuse_and_epilogue_pieces():
