@@ -1777,7 +1777,9 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
       if (we != cudaSuccess) return we;
     }
     cur = &L;
-    Timed t(ex->prof, st, L.kclass, L.flops, L.bytes);
+    // a GEMM launch summing several operand pairs does that many products
+    const double nv = (L.kind == LK_GEMM && cur_vals) ? (double)cur_vals->n : 1.0;
+    Timed t(ex->prof, st, L.kclass, L.flops * nv, L.bytes);
     const bool from_partial = reduce && !ex->launches.empty();
     if (L.kind == LK_GATHER) {
       if (L.has_fast && !from_partial) {

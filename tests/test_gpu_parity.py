@@ -104,13 +104,31 @@ def test_mid_ring_bf16x3():
 
 @pytest.mark.parametrize("prec", ["fp64", "tf32", "3xtf32"])
 def test_mid_ring_other_precisions(prec):
+    """The other precision forms on the mid-size ring, held to a few times
+    their measured error on B300 (FP64 3.3e-16, 3xTF32 1.6e-6, TF32 6.3e-4):
+    3xTF32 and TF32 do not meet 1e-6 and are reported, not claimed."""
     net = synth.ring_htn()
     ref = oracle_value(net)
     got, _ = contract_gpu(net, prec=prec)
     err = rel_err(got, ref)
     print(f"mid ring {prec} rel err", err)
-    bound = {"fp64": FP64_TOL, "3xtf32": 1e-4, "tf32": 0.5}[prec]
+    bound = {"fp64": FP64_TOL, "3xtf32": 5e-6, "tf32": 3e-3}[prec]
     assert err <= bound
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_signed_qpd_cts_rank1_qts_fp64_path(seed):
+    """Rank-1 positive QTs contracted with the exact signed QPD coefficient
+    tensors on the mid-size ring: every cut's sum cancels (the sum of
+    magnitudes over the whole contraction is ~1e18 times the value), so the
+    tensor-core forms lose accuracy in proportion; the FP64 path matches the
+    closed form to 1e-9 (measured 1.5e-11 and 7.1e-12)."""
+    from tests.test_oracle_tn import rank1_qts_closed_form
+    net, fac = synth.rank1_qts_htn(synth.ring_htn(), seed=seed)
+    want, mag = rank1_qts_closed_form(net, fac)
+    assert np.max(mag.ravel() / np.abs(want.ravel())) > 1e15
+    got, _ = contract_gpu(net, prec="fp64")
+    assert rel_err(got, want.ravel()) <= 1e-9
 
 
 def test_sliced_equals_unsliced():
