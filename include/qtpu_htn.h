@@ -75,12 +75,13 @@ typedef enum {
 
 typedef enum { QTPU_QT = 0, QTPU_CT = 1 } qtpu_kind; /* informational */
 
-typedef struct {
+typedef struct qtpu_plan_opts {
   uint64_t max_intermediate_bytes; /* 0 = no limit; 8 bytes per entry         */
   uint32_t n_slices;               /* minimum slice count; 0 or 1 = minimal   */
   uint32_t slice_dim;              /* only slice indices of this dim; 0 = any */
   qtpu_prec prec;
-  int cost_model;                  /* 0 = exact FLOP cost (greedy)            */
+  int cost_model;                  /* 0 = exact FLOP cost; 1 = learned cost
+                                      model (see qtpu_htn_plan)               */
   uint64_t seed;                   /* 0: greedy; else randomised greedy (the
                                       pair drawn among the 3 best keys by
                                       SplitMix64(seed)), for plan candidates */
@@ -95,6 +96,8 @@ typedef struct {
                                       intermediates with the copies slice
                                       reuse keeps (0 = 64 GiB, 1 = reuse
                                       off); see qtpu_htn_plan                 */
+  const char* cost_model_path;     /* cost_model = 1: weights file (NULL =
+                                      costmodel_b300.bin next to the library) */
 } qtpu_plan_opts;
 
 /* Create an empty network bound to CUDA device `device` and the CUDA stream
@@ -144,7 +147,20 @@ qtpu_status qtpu_htn_set_output(qtpu_htn* h, int n, const int64_t* index_ids);
  * reuse_bytes, some sliced indices are held fixed in an outer loop instead
  * (all of them: one slice at a time, the plan's own schedule).  The plan (its
  * text and FLOPs) is unchanged; qtpu_htn_exec_stats reports what a
- * contraction executes.  reuse_bytes = 1 turns reuse off. */
+ * contraction executes.  reuse_bytes = 1 turns reuse off.
+ *
+ * Learned cost model (cost_model = 1, device handles only): the planner makes
+ * n_candidates plans (64 if n_candidates <= 1; seeds seed .. seed+n-1 under
+ * the same slicing options), lowers each without device memory, and a small
+ * perceptron (weights from cost_model_path, trained on this library's own
+ * per-launch timings) predicts the device time of every launch of every
+ * candidate on the device; the plan with the smallest predicted contraction
+ * time among those whose executed FLOPs are within the model's stored factor
+ * of the fewest is kept (the exact FLOP count bounds the model).  The plan
+ * text is then that seed's plan with its search line.  The choice never
+ * changes a computed value: every plan is contracted by the same kernels.
+ * QTPU_EINVAL if the weights file is missing or invalid, QTPU_ENOTSUP on a
+ * host-only handle. */
 qtpu_status qtpu_htn_plan(qtpu_htn* h, const qtpu_plan_opts* opts);
 
 /* Canonical plan text (order, index groups, per-slice sizes and FLOPs,
@@ -185,6 +201,16 @@ qtpu_status qtpu_htn_exec_stats(const qtpu_htn* h, double* flops_executed,
                                 double* flops_all_slices, uint64_t* kept_bytes,
                                 int64_t* launches);
 
+/* Features of every lowered launch for the learned cost model: row i (of
+ * QTPU_N_LAUNCH_FEATURES floats, written to features + i * that count for
+ * i < max_rows) describes launch i of the launch list (kind, work, shape,
+ * tile fill, access pattern), launches[i] (may be NULL) how many kernel
+ * launches of it one contraction makes; *n_rows receives the number of
+ * launches.  Available after plan, also on a host-only handle. */
+#define QTPU_N_LAUNCH_FEATURES 32
+qtpu_status qtpu_htn_launch_features(const qtpu_htn* h, int max_rows, float* features,
+                                     int64_t* launches, int* n_rows);
+
 /* Kernel classes reported by qtpu_htn_profile_read. */
 typedef enum {
   QTPU_K_CONTRACT = 0, /* FP64 pairwise step on the CUDA cores            */
@@ -205,6 +231,13 @@ qtpu_status qtpu_htn_profile(qtpu_htn* h, int enable);
  * the last read, and reset the counters.  Any array may be NULL. */
 qtpu_status qtpu_htn_profile_read(qtpu_htn* h, int n, double* ms, int64_t* launches,
                                   double* flops, double* bytes);
+
+/* Wait for the stream, then return every launch timed since the last read,
+ * in order: launch_index[i] its index in the launch list (-1: the final
+ * reduction) and ms[i] its device time; *n receives the count.  If max is
+ * below the count nothing is written or reset (call again with room for *n
+ * entries); otherwise the timings are reset like qtpu_htn_profile_read. */
+qtpu_status qtpu_htn_profile_launches(qtpu_htn* h, int max, int* launch_index, double* ms, int* n);
 
 /* Contract: enqueue the whole contraction on the handle's stream and write
  * the FP64 result (output_size entries) to the device buffer dev_out.

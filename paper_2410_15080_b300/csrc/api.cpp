@@ -149,13 +149,21 @@ qtpu_status qtpu_htn_plan(qtpu_htn* h, const qtpu_plan_opts* opts) {
   o.prec = QTPU_PREC_BF16X3;
   if (opts) o = *opts;
   if (o.prec < QTPU_PREC_FP64 || o.prec > QTPU_PREC_BF16X3) return fail(h, QTPU_EINVAL, "bad precision");
-  if (o.cost_model != 0) return fail(h, QTPU_ENOTSUP, "only the exact cost model is available");
+  if (o.cost_model != 0 && o.cost_model != 1) return fail(h, QTPU_EINVAL, "cost_model must be 0 or 1");
+  if (o.cost_model == 1 && h->host_only)
+    return fail(h, QTPU_ENOTSUP, "the learned cost model runs its perceptron on the device");
   for (int64_t i : h->output)
     if (!h->dims.has(i)) return fail(h, QTPU_EINVAL, "output index " + std::to_string(i) + " is on no tensor");
   std::vector<Inds> li;
   for (auto& L : h->leaves) li.push_back(L.ids);
   int r;
-  if (o.n_candidates > 1) {
+  if (o.cost_model == 1) {
+    std::string err;
+    const int st = plan_by_cost_model(li, h->dims, h->output, o, h->leaves, h->device, (void*)h->stream, &h->plan,
+                                      &err);
+    if (st != QTPU_OK) return fail(h, (qtpu_status)st, err);
+    r = PLAN_OK;
+  } else if (o.n_candidates > 1) {
     uint64_t chosen = 0;
     r = make_plan_best(li, h->dims, h->output, o.max_intermediate_bytes, o.n_slices, o.slice_dim, o.seed,
                        o.n_candidates, &h->plan, &chosen);
@@ -232,6 +240,41 @@ qtpu_status qtpu_htn_exec_stats(const qtpu_htn* h, double* flops_executed, doubl
   if (flops_all_slices) *flops_all_slices = h->ex.flops_no_reuse;
   if (kept_bytes) *kept_bytes = (uint64_t)h->ex.kept_bytes;
   if (launches) *launches = h->ex.launches_per_contract;
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_launch_features(const qtpu_htn* h, int max_rows, float* features, int64_t* launches,
+                                     int* n_rows) {
+  if (!h || max_rows < 0 || (max_rows > 0 && !features)) return QTPU_EINVAL;
+  if (!h->planned || !h->ex.lowered) return QTPU_ESTATE;
+  const int n = (int)h->ex.launches.size();
+  if (n_rows) *n_rows = n;
+  for (int i = 0; i < n && i < max_rows; ++i) {
+    exec_launch_features(&h->ex, (size_t)i, features + (size_t)i * kLaunchFeatures);
+    if (launches) launches[i] = h->ex.launches[i].n_launch;
+  }
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_profile_launches(qtpu_htn* h, int max, int* launch_index, double* ms, int* n) {
+  if (!h || max < 0 || !n) return QTPU_EINVAL;
+  if (h->host_only || !h->built) return fail(h, QTPU_ESTATE, "nothing to read");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess && h->ex.own) e = cudaStreamSynchronize(h->ex.own);
+  if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
+  if ((size_t)max < h->ex.prof.used) {  // too small: report the count, keep the timings
+    *n = (int)h->ex.prof.used;
+    return QTPU_OK;
+  }
+  std::vector<int> idx;
+  std::vector<double> t;
+  std::string err = exec_profile_launches(&h->ex, &idx, &t);
+  if (!err.empty()) return fail(h, QTPU_ECUDA, err);
+  *n = (int)idx.size();
+  for (int i = 0; i < *n && i < max; ++i) {
+    if (launch_index) launch_index[i] = idx[i];
+    if (ms) ms[i] = t[i];
+  }
   return QTPU_OK;
 }
 

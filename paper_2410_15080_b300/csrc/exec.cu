@@ -1540,7 +1540,7 @@ struct Timed {
   size_t i = 0;
   bool on;
   unsigned flags = 0;  // external record nodes inside a stream capture
-  Timed(Profiler& pr, cudaStream_t s, int kind, double fl, double by) : p(pr), st(s), on(pr.on) {
+  Timed(Profiler& pr, cudaStream_t s, int kind, double fl, double by, int li = -1) : p(pr), st(s), on(pr.on) {
     if (!on) return;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
@@ -1555,11 +1555,13 @@ struct Timed {
         p.ev.push_back(e);
       }
       p.kind.push_back(0);
+      p.lidx.push_back(-1);
       p.flops.push_back(0);
       p.bytes.push_back(0);
     }
     i = p.used++;
     p.kind[i] = kind;
+    p.lidx[i] = li;
     p.flops[i] = fl;
     p.bytes[i] = by;
     cudaEventRecordWithFlags(p.ev[2 * i], st, flags);
@@ -1653,6 +1655,92 @@ std::string exec_profile_read(Executor* ex, double* ms, int64_t* launches, doubl
   }
   p.used = 0;
   return "";
+}
+
+std::string exec_profile_launches(Executor* ex, std::vector<int>* index, std::vector<double>* ms) {
+  index->clear();
+  ms->clear();
+  Profiler& p = ex->prof;
+  for (size_t i = 0; i < p.used; ++i) {
+    float t = 0;
+    cudaError_t e = cudaEventElapsedTime(&t, p.ev[2 * i], p.ev[2 * i + 1]);
+    if (e != cudaSuccess) {
+      p.used = 0;
+      return std::string("cudaEventElapsedTime: ") + cudaGetErrorString(e);
+    }
+    index->push_back(p.lidx[i]);
+    ms->push_back(t);
+  }
+  p.used = 0;
+  return "";
+}
+
+void exec_launch_features(const Executor* ex, size_t i, float* f) {
+  for (int j = 0; j < kLaunchFeatures; ++j) f[j] = 0.f;
+  const Launch& L = ex->launches[i];
+  auto lg = [](double x) { return (float)std::log2(1.0 + std::max(0.0, x)); };
+  const double nv = L.kind == LK_GEMM ? std::max(1.0, (double)L.runs / (double)std::max<int64_t>(L.n_launch, 1)) : 1.0;
+  f[31] = 1.f;
+  f[6] = lg(L.flops * nv);
+  f[7] = lg(L.bytes);
+  const bool accum = L.din != L.dout;
+  f[22] = accum ? 1.f : 0.f;
+  if (L.kind == LK_GEMM) {
+    const GemmArgs& g = L.gemm;
+    f[0] = 1.f;
+    f[8] = lg((double)g.batch * g.M * g.N);
+    f[9] = lg((double)g.K * nv);
+    f[10] = 2.f;
+    f[13] = lg(g.M);
+    f[14] = lg(g.N);
+    f[15] = lg(g.K);
+    f[16] = lg(g.batch);
+    f[17] = (float)nv;
+    const double mt = std::ceil(g.M / 128.0), nt = std::ceil(g.N / (double)gemm_block_n());
+    f[18] = (float)(g.M / (128.0 * mt));
+    f[19] = (float)(g.N / ((double)gemm_block_n() * nt));
+    f[20] = (float)(g.K / (64.0 * std::ceil(g.K / 64.0)));
+    f[21] = g.fuse.on ? 1.f : 0.f;
+    f[25] = lg((double)g.batch * mt * nt);
+    return;
+  }
+  if (L.kind == LK_CONTRACT64) {
+    f[5] = 1.f;
+    f[8] = lg((double)L.c64.n_out);
+    f[9] = lg((double)L.c64.n_loop);
+    f[10] = (float)L.nsrc;
+    f[28] = 1.f;
+    return;
+  }
+  const GatherArgs& g = L.has_fast ? L.gf : L.g;
+  const bool split = g.mode >= GW_SPLIT_BF16X3;
+  if (split)
+    f[1] = 1.f;
+  else if (L.has_fast && g.dot)
+    f[3] = 1.f;
+  else if (L.has_fast)
+    f[2] = 1.f;
+  else
+    f[4] = 1.f;
+  f[8] = split ? lg((double)g.n_rows * g.Kp) : lg((double)g.n_out);
+  f[9] = lg((double)g.n_loop);
+  f[10] = (float)g.nops;
+  f[11] = lg((double)g.w_size);
+  f[12] = (float)g.fan_f;
+  auto min_stride = [](const GModes& t) {
+    int64_t m = 0;
+    for (int q = 0; q < t.n; ++q)
+      if (t.stride[q][0] > 0 && (m == 0 || t.stride[q][0] < m)) m = t.stride[q][0];
+    return (double)m;
+  };
+  f[23] = lg(min_stride(g.out));
+  f[24] = lg(min_stride(split ? g.kmodes : g.loop));
+  f[25] = split ? lg(std::ceil(g.n_rows / 32.0) * std::ceil(g.Kp / 64.0)) : lg(g.n_out / 256.0);
+  f[26] = (float)g.row_fast;
+  f[27] = (float)(g.tile_n / 2048.0);
+  f[28] = g.dt[0] == DT_F64 ? 1.f : 0.f;
+  f[29] = L.has_fast ? 0.f : 1.f;
+  f[30] = lg((double)g.loop.n);
 }
 
 namespace {
@@ -1779,7 +1867,8 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
     cur = &L;
     // a GEMM launch summing several operand pairs does that many products
     const double nv = (L.kind == LK_GEMM && cur_vals) ? (double)cur_vals->n : 1.0;
-    Timed t(ex->prof, st, L.kclass, L.flops * nv, L.bytes);
+    Timed t(ex->prof, st, L.kclass, L.flops * nv, L.bytes,
+            reduce ? -1 : (int)(&L - ex->launches.data()));
     const bool from_partial = reduce && !ex->launches.empty();
     if (L.kind == LK_GATHER) {
       if (L.has_fast && !from_partial) {

@@ -8,6 +8,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "../../include/qtpu_htn.h"
 #include "kernels.h"
 #include "planner.h"
 
@@ -94,6 +95,7 @@ struct Profiler {
   bool on = false;
   std::vector<cudaEvent_t> ev;  // pairs
   std::vector<int> kind;
+  std::vector<int> lidx;        // launch index (-1: the reduction)
   std::vector<double> flops, bytes;
   size_t used = 0;
   size_t graph_events = 0;  // event pairs inside the profiling graph
@@ -192,7 +194,19 @@ std::string exec_run_slices(Executor* ex, const std::vector<Leaf>& leaves, int64
 void exec_free(Executor* ex);
 // Set the message qtpu_last_error(NULL) returns (calls that take no handle).
 void set_global_error(const char* msg);
+// The learned cost model's plan choice (qtpu_plan_opts.cost_model = 1); returns
+// a qtpu_status, *err on failure.
+int plan_by_cost_model(const std::vector<Inds>& li, const DimMap& dims, const Inds& output,
+                       const qtpu_plan_opts& o, const std::vector<Leaf>& leaves, int device, void* stream,
+                       Plan* chosen, std::string* err);
 // Sum the timed launches per class (after a stream sync) and reset.
 std::string exec_profile_read(Executor* ex, double* ms, int64_t* launches, double* flops, double* bytes);
+// Every timed launch (launch index, ms) in order (after a stream sync), and reset.
+std::string exec_profile_launches(Executor* ex, std::vector<int>* index, std::vector<double>* ms);
+
+// Features of one lowered launch for the learned cost model: kind, work,
+// shape, tile fill and access pattern (kLaunchFeatures floats).
+constexpr int kLaunchFeatures = 32;
+void exec_launch_features(const Executor* ex, size_t i, float* f);
 
 }  // namespace qtpu

@@ -22,7 +22,7 @@ QTPU_QT, QTPU_CT = 0, 1
 
 SYMBOLS = ["qtpu_htn_create", "qtpu_htn_add_tensor", "qtpu_htn_set_output", "qtpu_htn_plan",
            "qtpu_htn_plan_info", "qtpu_htn_lowering_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats",
-           "qtpu_htn_exec_stats", "qtpu_htn_contract",
+           "qtpu_htn_exec_stats", "qtpu_htn_launch_features", "qtpu_htn_profile_launches", "qtpu_htn_contract",
            "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_contract_slices", "qtpu_htn_sync", "qtpu_htn_selftest_timeout", "qtpu_htn_destroy",
            "qtpu_htn_profile", "qtpu_htn_profile_read", "qtpu_pairwise_contract_noalloc",
            "qtpu_pairwise_noalloc_scratch_bytes", "qtpu_noalloc_status", "qtpu_noalloc_selftest_timeout",
@@ -42,7 +42,7 @@ class PlanOpts(C.Structure):
     _fields_ = [("max_intermediate_bytes", C.c_uint64), ("n_slices", C.c_uint32),
                 ("slice_dim", C.c_uint32), ("prec", C.c_int), ("cost_model", C.c_int),
                 ("seed", C.c_uint64), ("autotune_table", C.c_char_p), ("n_candidates", C.c_uint32),
-                ("reuse_bytes", C.c_uint64)]
+                ("reuse_bytes", C.c_uint64), ("cost_model_path", C.c_char_p)]
 
 
 _lib = None
@@ -68,6 +68,9 @@ def lib():
                                           C.POINTER(C.c_int), C.POINTER(C.c_uint64), i64p]
         L.qtpu_htn_exec_stats.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_uint64), i64p]
+        L.qtpu_htn_launch_features.argtypes = [vp, C.c_int, vp, i64p, C.POINTER(C.c_int)]
+        L.qtpu_htn_profile_launches.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                                C.POINTER(C.c_int)]
         L.qtpu_htn_profile.argtypes = [vp, C.c_int]
         dp = C.POINTER(C.c_double)
         L.qtpu_htn_profile_read.argtypes = [vp, C.c_int, dp, i64p, dp, dp]
@@ -148,9 +151,10 @@ class HTN:
         self._check(self._L.qtpu_htn_set_output(self._h, len(inds), _arr(inds)))
 
     def plan(self, prec: str = "bf16x3", max_intermediate_bytes: int = 0, n_slices: int = 0,
-             slice_dim: int = 0, seed: int = 0, n_candidates: int = 0, reuse_bytes: int = 0):
-        o = PlanOpts(max_intermediate_bytes, n_slices, slice_dim, PREC[prec], 0, seed, None, n_candidates,
-                     reuse_bytes)
+             slice_dim: int = 0, seed: int = 0, n_candidates: int = 0, reuse_bytes: int = 0,
+             cost_model: int = 0, cost_model_path: str | None = None):
+        o = PlanOpts(max_intermediate_bytes, n_slices, slice_dim, PREC[prec], cost_model, seed, None, n_candidates,
+                     reuse_bytes, cost_model_path.encode() if cost_model_path else None)
         self._check(self._L.qtpu_htn_plan(self._h, C.byref(o)))
 
     def plan_info(self) -> str:
@@ -186,6 +190,28 @@ class HTN:
         self._check(self._L.qtpu_htn_exec_stats(self._h, C.byref(fe), C.byref(fa), C.byref(kb), C.byref(nl)))
         return {"flops_executed": fe.value, "flops_all_slices": fa.value, "kept_bytes": kb.value,
                 "launches": nl.value}
+
+    def launch_features(self):
+        """(features [n_launch, 32] float32, kernel launches per contraction of
+        each) of the lowered launch list."""
+        import numpy as np
+        n = C.c_int(0)
+        self._check(self._L.qtpu_htn_launch_features(self._h, 0, None, None, C.byref(n)))
+        f = np.zeros((max(n.value, 1), 32), dtype=np.float32)
+        cnt = np.zeros(max(n.value, 1), dtype=np.int64)
+        self._check(self._L.qtpu_htn_launch_features(self._h, n.value, C.c_void_p(f.ctypes.data),
+                                                     cnt.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(n)))
+        return f[:n.value], cnt[:n.value]
+
+    def profile_launches(self):
+        """(launch index, ms) of every launch timed since the last read."""
+        n = C.c_int(0)
+        self._check(self._L.qtpu_htn_profile_launches(self._h, 0, None, None, C.byref(n)))
+        cap = max(n.value, 1)
+        idx = (C.c_int * cap)()
+        ms = (C.c_double * cap)()
+        self._check(self._L.qtpu_htn_profile_launches(self._h, cap, idx, ms, C.byref(n)))
+        return list(idx)[:n.value], list(ms)[:n.value]
 
     def profile(self, enable: bool = True):
         self._check(self._L.qtpu_htn_profile(self._h, 1 if enable else 0))

@@ -304,3 +304,34 @@ def test_slice_reuse_budget_blocks_sliced_indices():
     assert "reuse blocked=-" not in t
     assert s["kept_bytes"] < sf["kept_bytes"]
     assert sf["flops_executed"] < s["flops_executed"] < sf["flops_all_slices"]
+
+
+def test_launch_features_of_the_lowered_launch_list():
+    """One feature row per launch of the launch list (kind one-hot, work,
+    shape, tile fill), with the kernel launches per contraction of each; the
+    learned cost model needs a device handle."""
+    import synth
+    from paper_2410_15080_b300.htn import HTN, QtpuError, QTPU_ENOTSUP
+    net = synth.ring_htn()
+    h = _host_handle(net)
+    f, n = h.launch_features()
+    t = h.lowering_info()
+    launches = [l for l in t.splitlines() if l.startswith("launch ")]
+    assert f.shape == (len(launches), 32) and (n == 1).all()
+    kinds = f[:, :6].argmax(1)
+    assert (f[:, :6].sum(1) == 1).all() and (f[:, 31] == 1).all()
+    for row, k, l in zip(f, kinds, launches):
+        if " gemm " in l:
+            assert k == 0 and 0 < row[18] <= 1 and 0 < row[20] <= 1
+        elif " split " in l:
+            assert k == 1
+    assert sum(" gemm " in l for l in launches) == int((kinds == 0).sum()) == 6
+    h.close()
+    h2 = HTN(device=-1)
+    for tt in net.tensors:
+        h2.add_tensor(tt.inds, list(tt.data.shape))
+    h2.set_output(net.output)
+    with pytest.raises(QtpuError) as ei:
+        h2.plan("bf16x3", cost_model=1)
+    assert ei.value.status == QTPU_ENOTSUP
+    h2.close()

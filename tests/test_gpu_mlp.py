@@ -54,18 +54,37 @@ def test_adam_training_reduces_the_loss():
     m.close()
 
 
-def test_cost_model_pipeline_picks_a_plan_that_contracts_exactly():
-    """Train on measured candidate plans of a few networks, choose for a new
-    one: the chosen plan's result equals the oracle (the model only chooses)."""
+def test_cost_model_pipeline_picks_a_plan_that_contracts_exactly(tmp_path):
+    """Per-launch samples of a few networks' candidate plans, a small model
+    trained on them and saved, then qtpu_htn_plan with cost_model = 1 on a new
+    network: the chosen plan is one of the randomised candidates (its text is
+    the oracle planner's plan for the chosen seed) and it contracts to the
+    oracle's value (the model only chooses)."""
+    import re
+    from oracle import planner
     from paper_2410_15080_b300 import costmodel as cm
-    X, y, groups, flops = cm.gen_dataset(cm.train_networks(3), per_net=8)
-    assert np.isfinite(y).all()
+    from paper_2410_15080_b300 import from_network
+    from tests.gpu_util import to_device
+    nets = cm.train_networks(3)
+    X, y, cand = cm.gen_dataset(nets, cm.candidate_kws(2, [{}, {"n_slices": 4}]))
+    assert len(X) == sum(c["n_samples"] for c in cand) and np.isfinite(y).all()
+    # every timed launch has the features of its launch list row
+    assert X.shape[1] == cm.N_FEATURES and all(len(c["feats"]) >= c["n_samples"] for c in cand)
     model = cm.CostModel(hidden=64)
-    losses = model.train(X, y, epochs=40, batch=8)
+    losses = model.train(X, y, epochs=30, batch=64)
     assert losses[-1] < losses[0]
+    model.factor = cm.select_factor(model, cand)
+    path = str(tmp_path / "cm.bin")
+    model.save(path)
     net = cm.eval_networks(1)[0]
-    f = cm.select_factor(model.predict(X), y, flops, groups)
-    cands, im, ie, pred = cm.choose(model, net, f)
-    assert len(cands) == 64 and np.isfinite(pred).all()
-    _, out = cm.measure(cm.to_device(net), net.output, cands[im][0], reps=1)
-    assert rel_err(out.cpu().numpy(), oracle_value(net)) <= REL_TOL
+    h = from_network(to_device(net), net.output, prec="bf16x3", n_candidates=8, cost_model=1, cost_model_path=path)
+    text = h.plan_info()
+    out = h.contract()
+    h.sync()
+    got = out.cpu().numpy()
+    h.close()
+    seed = int(re.search(r"search candidates=8 seed=(\d+)", text).group(1))
+    p = planner.make_plan(net.inds(), net.dims(), net.output, seed=seed)
+    p.search = (8, seed)
+    assert planner.plan_text(p, net.inds()) == text
+    assert rel_err(got, oracle_value(net)) <= REL_TOL
