@@ -259,15 +259,43 @@ qtpu_status qtpu_htn_contract_host(qtpu_htn* h, const void* const* host_ptrs,
                                    double* host_out);
 
 /* Contract n planned networks (of any shapes) and write dev_out[i] for each.
- * All n contractions run as ONE CUDA graph: each network's launches form one
- * branch, spread over 16 parallel branches (networks own disjoint
- * workspaces), so small latency-bound networks overlap.  The graph is built
- * on the first call for a given (handles, outputs) list and replayed by later
- * calls with the same list; it is ordered after the work already enqueued on
- * cuda_stream (NULL = the first handle's stream), which waits for it.
- * Handles must be distinct and share one device. */
+ * All n contractions run as ONE CUDA graph.  Every network whose launches are
+ * all gathers (unsliced, no tensor-core step) becomes a set of tasks of one
+ * persistent kernel: its blocks claim work units (256 outputs of a launch, or
+ * one output of a long sum) in task order, level by level across the
+ * networks, and each unit first waits -- bounded by a time limit -- until the
+ * same network's previous launch is complete.  The other networks' launches
+ * form branches of the graph, spread over parallel streams (networks own
+ * disjoint workspaces).  The graph is built on the first call for a given
+ * (handles, outputs, options) list and replayed by later calls with the same
+ * list; it is ordered after the work already enqueued on cuda_stream (NULL =
+ * the first handle's stream), which waits for it.  Handles must be distinct
+ * and share one device.  A wait of the persistent kernel that gives up marks
+ * every network whose result it left incomplete: qtpu_htn_sync on that handle
+ * returns QTPU_ETIMEOUT. */
 qtpu_status qtpu_htn_contract_batch(qtpu_htn* const* hs, int n,
                                     double* const* dev_out, void* cuda_stream);
+
+typedef struct {
+  int persistent;            /* 1 (default): the persistent kernel for the
+                                gather-only networks; 0: graph branches only */
+  uint64_t wait_limit_ns;    /* bound of the persistent kernel's dependency
+                                waits; 0 = 2 s, at most 10 s                 */
+  int test_stall_network;    /* test hook: >= 0 makes one dependency of that
+                                network's tasks never complete, so its wait
+                                gives up after wait_limit_ns; -1 = off        */
+} qtpu_batch_opts;
+
+/* qtpu_htn_contract_batch with options (opts NULL = the defaults). */
+qtpu_status qtpu_htn_contract_batch_ex(qtpu_htn* const* hs, int n,
+                                       double* const* dev_out, void* cuda_stream,
+                                       const qtpu_batch_opts* opts);
+
+/* For the most recent batch graph of this (handles, outputs) list: how many
+ * networks the persistent kernel contracts and its task count.  QTPU_ESTATE
+ * if no such graph exists. */
+qtpu_status qtpu_htn_batch_info(qtpu_htn* const* hs, int n, double* const* dev_out,
+                                int* n_persistent, int* n_tasks);
 
 /* Contract only slices [first, first + count) of the planned contraction
  * (slices are the value assignments of the sliced indices, last sliced index

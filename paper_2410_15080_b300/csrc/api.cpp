@@ -377,18 +377,29 @@ qtpu_status qtpu_htn_contract_host(qtpu_htn* h, const void* const* host_ptrs, do
 }
 
 // ---------------------------------------------------------------- batches
-// Many networks in one CUDA graph: every network's launch sequence is
-// captured on one of kBranches parallel streams (networks own disjoint
-// workspaces, so they may run concurrently), followed by the copy of its
-// output; the graph is cached per (handles, outputs) and replayed with one
-// graph launch.
+// Many networks in one CUDA graph.  Networks whose launches are all gathers
+// (unsliced) become tasks of one persistent kernel (batch.cu) on branch 0;
+// every other network's launch sequence is captured on one of kBranches
+// parallel streams (networks own disjoint workspaces, so they may run
+// concurrently), followed by the copy of its output.  The graph is cached per
+// (handles, outputs, options) and replayed with one graph launch.
 namespace {
 constexpr int kBranches = 16;
 struct BatchGraph {
   std::vector<qtpu_htn*> hs;
   std::vector<double*> outs;
   int device = 0;
+  int persistent = 1;
+  uint64_t limit_ns = 0;
+  int stall = -1;
   cudaGraphExec_t exec = nullptr;
+  // persistent kernel: tasks, unit prefix, counters
+  int n_tasks = 0, n_persistent = 0;
+  BatchTask* d_tasks = nullptr;
+  uint64_t* d_start = nullptr;
+  unsigned long long* d_next = nullptr;
+  uint32_t* d_done = nullptr;
+  int* d_abort = nullptr;
 };
 struct BatchState {
   std::mutex mu;
@@ -401,6 +412,8 @@ BatchState g_batch;
 
 void batch_free(BatchGraph* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (void* p : {(void*)b->d_tasks, (void*)b->d_start, (void*)b->d_next, (void*)b->d_done, (void*)b->d_abort})
+    if (p) cudaFree(p);
   delete b;
 }
 
@@ -428,11 +441,65 @@ void batch_forget(qtpu_htn* h) {
     }
   }
 }
+
+// The persistent kernel's tasks: level by level across the eligible networks
+// (task l of every network, then l + 1, ...), each depending on the same
+// network's previous task.  Returns a CUDA error; eligible[i] is set for the
+// networks the kernel contracts.
+cudaError_t batch_build_tasks(BatchGraph* b, qtpu_htn* const* hs, int n, double* const* dev_out, int stall,
+                              std::vector<char>* eligible) {
+  std::vector<std::vector<BatchTask>> per(n);
+  eligible->assign(n, 0);
+  size_t max_len = 0;
+  for (int i = 0; i < n; ++i) {
+    if (exec_batch_tasks(&hs[i]->ex, hs[i]->leaves, dev_out[i], &per[i])) {
+      (*eligible)[i] = 1;
+      max_len = std::max(max_len, per[i].size());
+      b->n_persistent++;
+    }
+  }
+  std::vector<BatchTask> tasks;
+  std::vector<uint64_t> start(1, 0);
+  std::vector<int> last(n, -1);
+  for (size_t l = 0; l < max_len; ++l)
+    for (int i = 0; i < n; ++i) {
+      if (!(*eligible)[i] || l >= per[i].size()) continue;
+      BatchTask T = per[i][l];
+      T.dep = last[i];
+      T.dep_units = T.dep >= 0 ? tasks[T.dep].n_units : 0;
+      // test hook: one dependency of this network never completes
+      if (i == stall && T.dep >= 0) T.dep_units = tasks[T.dep].n_units + 1;
+      last[i] = (int)tasks.size();
+      tasks.push_back(T);
+      start.push_back(start.back() + T.n_units);
+    }
+  b->n_tasks = (int)tasks.size();
+  if (!b->n_tasks) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void**)&b->d_tasks, tasks.size() * sizeof(BatchTask));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_start, start.size() * sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_next, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_done, tasks.size() * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_abort, sizeof(int));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_tasks, tasks.data(), tasks.size() * sizeof(BatchTask), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_start, start.data(), start.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
+  return e;
+}
 }  // namespace
 
 qtpu_status qtpu_htn_contract_batch(qtpu_htn* const* hs, int n, double* const* dev_out, void* cuda_stream) {
+  return qtpu_htn_contract_batch_ex(hs, n, dev_out, cuda_stream, nullptr);
+}
+
+qtpu_status qtpu_htn_contract_batch_ex(qtpu_htn* const* hs, int n, double* const* dev_out, void* cuda_stream,
+                                       const qtpu_batch_opts* opts) {
   if (n < 0 || (n > 0 && (!hs || !dev_out))) return QTPU_EINVAL;
   if (n == 0) return QTPU_OK;
+  qtpu_batch_opts o{1, 0, -1};
+  if (opts) o = *opts;
+  if (o.wait_limit_ns == 0) o.wait_limit_ns = 2000000000ull;
+  if (o.wait_limit_ns > 10000000000ull) return fail(hs[0], QTPU_EINVAL, "wait limit above 10 s");
   for (int i = 0; i < n; ++i) {
     qtpu_htn* h = hs[i];
     if (!h) return QTPU_EINVAL;
@@ -453,9 +520,28 @@ qtpu_status qtpu_htn_contract_batch(qtpu_htn* const* hs, int n, double* const* d
   BatchGraph* b = nullptr;
   for (BatchGraph* c : g_batch.cache)
     if (c->device == dev && (int)c->hs.size() == n && std::equal(c->hs.begin(), c->hs.end(), hs) &&
-        std::equal(c->outs.begin(), c->outs.end(), dev_out))
+        std::equal(c->outs.begin(), c->outs.end(), dev_out) && c->persistent == (o.persistent != 0) &&
+        c->limit_ns == o.wait_limit_ns && c->stall == o.test_stall_network)
       b = c;
   if (!b) {
+    b = new BatchGraph();
+    b->hs.assign(hs, hs + n);
+    b->outs.assign(dev_out, dev_out + n);
+    b->device = dev;
+    b->persistent = o.persistent != 0;
+    b->limit_ns = o.wait_limit_ns;
+    b->stall = o.test_stall_network;
+    std::vector<char> eligible(n, 0);
+    if (b->persistent) {
+      e = batch_build_tasks(b, hs, n, dev_out, o.test_stall_network, &eligible);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        batch_free(b);
+        return fail(hs[0], QTPU_ENOMEM, std::string("batch tasks: ") + cudaGetErrorString(e));
+      }
+    }
+    int sm = 148;
+    cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
     cudaStream_t cs = g_batch.cap[dev];
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
@@ -463,9 +549,22 @@ qtpu_status qtpu_htn_contract_batch(qtpu_htn* const* hs, int n, double* const* d
       cudaError_t e1 = cudaEventRecord(g_batch.fork[dev], cs);
       for (int i = 0; i < kBranches && e1 == cudaSuccess; ++i)
         e1 = cudaStreamWaitEvent(g_batch.br[dev][i], g_batch.fork[dev], 0);
+      if (e1 == cudaSuccess && b->n_tasks) {
+        cudaStream_t s0 = g_batch.br[dev][0];
+        e1 = cudaMemsetAsync(b->d_next, 0, sizeof(unsigned long long), s0);
+        if (e1 == cudaSuccess) e1 = cudaMemsetAsync(b->d_done, 0, (size_t)b->n_tasks * 4, s0);
+        if (e1 == cudaSuccess) e1 = cudaMemsetAsync(b->d_abort, 0, sizeof(int), s0);
+        if (e1 == cudaSuccess)
+          e1 = launch_batch_persistent(b->d_tasks, b->n_tasks, b->d_start, b->d_next, b->d_done, o.wait_limit_ns,
+                                       b->d_abort, sm * 4, s0);
+      }
+      int k = 0;
       for (int i = 0; i < n && e1 == cudaSuccess; ++i) {
+        if (eligible[i]) continue;
         qtpu_htn* h = hs[i];
-        cudaStream_t bs = g_batch.br[dev][i % kBranches];
+        // branch 0 carries the persistent kernel when there is one
+        const int br = b->n_tasks ? 1 + (k++ % (kBranches - 1)) : (k++ % kBranches);
+        cudaStream_t bs = g_batch.br[dev][br];
         int64_t no = 1;
         qtpu_htn_output_size(h, &no);
         e1 = exec_enqueue(&h->ex, h->leaves, h->ex.out_stage, bs);
@@ -479,15 +578,13 @@ qtpu_status qtpu_htn_contract_batch(qtpu_htn* const* hs, int n, double* const* d
       e = cudaStreamEndCapture(cs, &graph);
       if (e1 != cudaSuccess) e = e1;
     }
-    cudaGraphExec_t ge = nullptr;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return fail(hs[0], QTPU_ECUDA, std::string("batch graph: ") + cudaGetErrorString(e));
-    b = new BatchGraph();
-    b->hs.assign(hs, hs + n);
-    b->outs.assign(dev_out, dev_out + n);
-    b->device = dev;
-    b->exec = ge;
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      batch_free(b);
+      return fail(hs[0], QTPU_ECUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    }
     g_batch.cache.push_back(b);
     if (g_batch.cache.size() > 4) {
       batch_free(g_batch.cache.front());
@@ -502,6 +599,22 @@ qtpu_status qtpu_htn_contract_batch(qtpu_htn* const* hs, int n, double* const* d
   if (e == cudaSuccess) e = cudaStreamWaitEvent(user, g_batch.out[dev], 0);
   if (e != cudaSuccess) return fail(hs[0], QTPU_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
   return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_batch_info(qtpu_htn* const* hs, int n, double* const* dev_out, int* n_persistent,
+                                int* n_tasks) {
+  if (!hs || !dev_out || n < 1) return QTPU_EINVAL;
+  std::lock_guard<std::mutex> g(g_batch.mu);
+  for (auto it = g_batch.cache.rbegin(); it != g_batch.cache.rend(); ++it) {
+    BatchGraph* c = *it;
+    if ((int)c->hs.size() == n && std::equal(c->hs.begin(), c->hs.end(), hs) &&
+        std::equal(c->outs.begin(), c->outs.end(), dev_out)) {
+      if (n_persistent) *n_persistent = c->n_persistent;
+      if (n_tasks) *n_tasks = c->n_tasks;
+      return QTPU_OK;
+    }
+  }
+  return QTPU_ESTATE;
 }
 
 qtpu_status qtpu_htn_profile(qtpu_htn* h, int enable) {

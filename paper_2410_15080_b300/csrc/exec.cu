@@ -2122,6 +2122,39 @@ std::string exec_run_host(Executor* ex, const std::vector<Leaf>& leaves, double*
   return "";
 }
 
+bool exec_batch_tasks(const Executor* ex, const std::vector<Leaf>& leaves, double* dev_out,
+                      std::vector<BatchTask>* out) {
+  out->clear();
+  if (!ex->lowered || ex->n_slices != 1 || ex->launches.empty()) return false;
+  for (const Launch& L : ex->launches)
+    if (L.kind != LK_GATHER || L.g.mode >= GW_SPLIT_BF16X3 || L.side >= 0) return false;
+  const int nl = (int)leaves.size();
+  auto src_ptr = [&](int t) -> const void* {
+    if (t < nl) return leaves[t].ptr;
+    return ex->arena + ex->stored[t - nl].off;
+  };
+  auto add = [&](const GatherArgs& g0, const int* src, int nsrc, bool from_partial, void* dst) {
+    BatchTask T;
+    T.g = g0;
+    for (int j = 0; j < nsrc; ++j) T.g.ptr[j] = from_partial ? (const void*)ex->partial : src_ptr(src[j]);
+    T.g.accum = 0;
+    T.dst = dst;
+    T.f64out = g0.mode == GW_DENSE_F64 ? 1 : 0;
+    T.block_mode = (g0.n_loop >= 1024 && g0.n_out <= (uint32_t)ex->sm_count * 16) ? 1 : 0;
+    T.n_units = T.block_mode ? g0.n_out : (g0.n_out + 255) / 256;
+    T.status = ex->status;
+    if (T.n_units == 0) T.n_units = 1;  // an empty task still completes one unit
+    out->push_back(T);
+  };
+  for (const Launch& L : ex->launches) {
+    void* dst = L.dst == DST_PARTIAL ? (void*)ex->partial
+                                     : (L.dst == DST_OUT ? (void*)dev_out : (void*)(ex->arena + ex->stored[L.dst - nl].off));
+    add(L.g, L.src, L.nsrc, false, dst);
+  }
+  add(ex->reduce.g, ex->reduce.src, ex->reduce.nsrc, true, dev_out);
+  return true;
+}
+
 std::vector<int> exec_leaf_order(const Executor* ex, int n_leaves) {
   std::vector<int> order;
   std::vector<char> seen(n_leaves, 0);

@@ -182,6 +182,11 @@ std::string exec_run(Executor* ex, const std::vector<Leaf>& leaves, double* dev_
 // recorded after that leaf's upload) of the leaves it reads.
 std::string exec_run_host(Executor* ex, const std::vector<Leaf>& leaves, double* dev_out, cudaStream_t st,
                           const cudaEvent_t* leaf_ready, int* code);
+// Tasks of one network for the persistent batched kernel (unsliced, gather
+// launches only), its final reduction writing dev_out; false if the network
+// is not eligible.
+bool exec_batch_tasks(const Executor* ex, const std::vector<Leaf>& leaves, double* dev_out,
+                      std::vector<BatchTask>* out);
 // Leaves in the order the schedule first reads them (upload order).
 std::vector<int> exec_leaf_order(const Executor* ex, int n_leaves);
 // Enqueue one whole contraction on `st` with direct launches, result to out

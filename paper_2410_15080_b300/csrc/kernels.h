@@ -163,6 +163,25 @@ cudaError_t launch_bounded_wait_probe(uint32_t* status, uint64_t limit_ns, cudaS
 // one-time per-device setup of the GEMM kernels (shared-memory attribute)
 cudaError_t gemm_prepare();
 
+// One task of the persistent batched kernel: a gather launch of one network
+// with its operand pointers resolved.  Dense tasks have one work unit per 256
+// outputs; block-mode tasks (long sums over few outputs) one per output.  A
+// unit runs after `dep_units` units of task `dep` (the network's previous
+// launch) are done.
+struct BatchTask {
+  GatherArgs g;
+  void* dst = nullptr;
+  uint32_t n_units = 0;
+  int block_mode = 0;
+  int f64out = 0;
+  int dep = -1;
+  uint32_t dep_units = 0;
+  uint32_t* status = nullptr;  // the network's status word
+};
+cudaError_t launch_batch_persistent(const BatchTask* tasks, int n_tasks, const uint64_t* unit_start,
+                                    unsigned long long* next_unit, uint32_t* done, uint64_t limit_ns, int* abort_flag,
+                                    int grid, cudaStream_t st);
+
 // Build the 4-D TMA map of a split operand buffer (returns false on failure).
 bool make_operand_map(CUtensorMap* map, void* base, int prec, int64_t batch, int64_t rows, int64_t K,
                       int64_t Kp, int box_rows);

@@ -23,7 +23,7 @@ QTPU_QT, QTPU_CT = 0, 1
 SYMBOLS = ["qtpu_htn_create", "qtpu_htn_add_tensor", "qtpu_htn_set_output", "qtpu_htn_plan",
            "qtpu_htn_plan_info", "qtpu_htn_lowering_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats",
            "qtpu_htn_exec_stats", "qtpu_htn_launch_features", "qtpu_htn_profile_launches", "qtpu_htn_contract",
-           "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_contract_slices", "qtpu_htn_sync", "qtpu_htn_selftest_timeout", "qtpu_htn_destroy",
+           "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_contract_batch_ex", "qtpu_htn_batch_info", "qtpu_htn_contract_slices", "qtpu_htn_sync", "qtpu_htn_selftest_timeout", "qtpu_htn_destroy",
            "qtpu_htn_profile", "qtpu_htn_profile_read", "qtpu_pairwise_contract_noalloc",
            "qtpu_pairwise_noalloc_scratch_bytes", "qtpu_noalloc_status", "qtpu_noalloc_selftest_timeout",
            "qtpu_last_error",
@@ -43,6 +43,10 @@ class PlanOpts(C.Structure):
                 ("slice_dim", C.c_uint32), ("prec", C.c_int), ("cost_model", C.c_int),
                 ("seed", C.c_uint64), ("autotune_table", C.c_char_p), ("n_candidates", C.c_uint32),
                 ("reuse_bytes", C.c_uint64), ("cost_model_path", C.c_char_p)]
+
+
+class BatchOpts(C.Structure):
+    _fields_ = [("persistent", C.c_int), ("wait_limit_ns", C.c_uint64), ("test_stall_network", C.c_int)]
 
 
 _lib = None
@@ -77,6 +81,9 @@ def lib():
         L.qtpu_htn_contract.argtypes = [vp, vp]
         L.qtpu_htn_contract_host.argtypes = [vp, C.POINTER(vp), vp]
         L.qtpu_htn_contract_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), vp]
+        L.qtpu_htn_contract_batch_ex.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), vp, C.POINTER(BatchOpts)]
+        L.qtpu_htn_batch_info.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(C.c_int),
+                                          C.POINTER(C.c_int)]
         L.qtpu_htn_contract_slices.argtypes = [vp, C.c_int64, C.c_int64, vp]
         L.qtpu_htn_sync.argtypes = [vp]
         L.qtpu_htn_selftest_timeout.argtypes = [vp, C.c_uint64]
@@ -271,13 +278,29 @@ class HTN:
             pass
 
 
-def contract_batch(htns: Sequence[HTN], outs, stream: int | None = None):
+def contract_batch(htns: Sequence[HTN], outs, stream: int | None = None, persistent: bool = True,
+                   wait_limit_ns: int = 0, test_stall_network: int = -1):
+    """Contract many planned networks in one CUDA graph (see the C header)."""
     L = lib()
     hs = (C.c_void_p * len(htns))(*[h._h.value for h in htns])
     ps = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
-    st = L.qtpu_htn_contract_batch(hs, len(htns), ps, C.c_void_p(stream or 0))
+    o = BatchOpts(1 if persistent else 0, wait_limit_ns, test_stall_network)
+    st = L.qtpu_htn_contract_batch_ex(hs, len(htns), ps, C.c_void_p(stream or 0), C.byref(o))
     if st != QTPU_OK:
-        raise QtpuError(st, "contract_batch failed")
+        raise QtpuError(st, "contract_batch failed: " + htns[0]._L.qtpu_last_error(htns[0]._h).decode())
+
+
+def batch_info(htns: Sequence[HTN], outs) -> dict:
+    """Networks the persistent kernel contracts and its task count, for the
+    most recent batch graph of these handles and outputs."""
+    L = lib()
+    hs = (C.c_void_p * len(htns))(*[h._h.value for h in htns])
+    ps = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+    npers, ntask = C.c_int(0), C.c_int(0)
+    st = L.qtpu_htn_batch_info(hs, len(htns), ps, C.byref(npers), C.byref(ntask))
+    if st != QTPU_OK:
+        raise QtpuError(st, "no batch graph for these handles")
+    return {"persistent_networks": npers.value, "tasks": ntask.value}
 
 
 class MLP:
