@@ -80,6 +80,11 @@ def measured_traffic(workload: str, kclass: str):
     return e["bytes_per_launch"]
 
 
+def gemm_tiles_used() -> str:
+    t = os.path.join(ROOT, "paper_2410_15080_b300", "gemm_tiles_b300.txt")
+    return "measured tile table gemm_tiles_b300.txt" if os.path.exists(t) else "padding rule (no tile table)"
+
+
 def make_network(workload: str, shape: str = "8x1024x1024x1024", observables: int = 64):
     import synth
     if workload == "gemm":
@@ -378,6 +383,26 @@ def run_batch(args, rank, world):
         loop()
     tl = timed_steps(loop, max(3, min(args.steps, 10)), flush)
     ms_loop = statistics.mean(tl)
+    # a launch-bound batch: 512 networks of QTs of at most 2^14 entries, every
+    # one run by the persistent kernel, against the same graph without it
+    small = synth.random_batch(512, seed=0, max_qt_entries=1 << 14)
+    hs_s, outs_s = [], []
+    for n in small:
+        ts = [(t.inds, torch.from_numpy(np.ascontiguousarray(t.data)).to(dev), QTPU_CT if t.kind == "CT" else QTPU_QT)
+              for t in n.tensors]
+        h = from_network(ts, n.output, prec=args.prec, max_intermediate_bytes=(1 << 23) * 8)
+        hs_s.append(h)
+        outs_s.append(torch.empty(h.output_size(), dtype=torch.float64, device=dev))
+    for _ in range(3):
+        contract_batch(hs_s, outs_s)
+    ms_sp = statistics.mean(timed_steps(lambda: contract_batch(hs_s, outs_s), max(3, min(args.steps, 10)), flush))
+    info_s = batch_info(hs_s, outs_s)
+    for _ in range(3):
+        contract_batch(hs_s, outs_s, persistent=False)
+    ms_sg = statistics.mean(timed_steps(lambda: contract_batch(hs_s, outs_s, persistent=False),
+                                        max(3, min(args.steps, 10)), flush))
+    for h in hs_s:
+        h.close()
     # parity of a sample against the oracle
     rel = 0.0
     if rank == 0:
@@ -406,6 +431,10 @@ def run_batch(args, rank, world):
                                 "speedup_of_persistent": ms_graph / ms},
         "one_call_per_network": {"ms_per_step": ms_loop, "value": flops / (ms_loop * 1e-3) / 1e12,
                                  "speedup_of_batch": ms_loop / ms},
+        "small_network_batch": {"networks": len(small), "max_qt_entries": 1 << 14,
+                                "persistent_networks": info_s["persistent_networks"],
+                                "ms_persistent": ms_sp, "ms_graph_branches_only": ms_sg,
+                                "speedup_of_persistent": ms_sg / ms_sp},
         "cpu_baseline": None, "fp64_gpu_path": None, "e2e": None,
         "gpu_launches": launches * args.steps,
         "clocks": clk.summary(),
@@ -603,6 +632,7 @@ def run_ours(args, rank, world):
                    + (f" (k = {args.observables} observables)" if args.workload.startswith("100q") and args.observables != 64 else ""),
                    "sharding": "independent replicas" if world > 1 else "single GPU",
                    "flops_per_step": flops, "prec": args.prec,
+                   "gemm_tiles": gemm_tiles_used(),
                    "l2": "flushed between timed steps (256 MiB write)" if net.nbytes() < (256 << 20)
                    else "inputs larger than L2", "plan_steps": st["n_steps"],
                    "tensor_core_steps": st["n_tensor_core_steps"], "parallelism": f"replicas x{world}",

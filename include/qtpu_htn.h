@@ -85,7 +85,10 @@ typedef struct qtpu_plan_opts {
   uint64_t seed;                   /* 0: greedy; else randomised greedy (the
                                       pair drawn among the 3 best keys by
                                       SplitMix64(seed)), for plan candidates */
-  const char* autotune_table;      /* reserved; may be NULL                   */
+  const char* autotune_table;      /* GEMM tile table file (see qtpu_htn_plan
+                                      and qtpu_htn_autotune); NULL = the
+                                      gemm_tiles_b300.txt next to the library
+                                      if present; "" = none                   */
   uint32_t n_candidates;           /* > 1: plan with seeds seed, seed+1, ...,
                                       seed+n-1 (seed 0 = greedy) under the same
                                       slicing options and keep the plan with
@@ -160,8 +163,41 @@ qtpu_status qtpu_htn_set_output(qtpu_htn* h, int n, const int64_t* index_ids);
  * text is then that seed's plan with its search line.  The choice never
  * changes a computed value: every plan is contracted by the same kernels.
  * QTPU_EINVAL if the weights file is missing or invalid, QTPU_ENOTSUP on a
- * host-only handle. */
+ * host-only handle.
+ *
+ * GEMM tiles: each tensor-core step (a batched GEMM of the step's batch, m,
+ * n and k index groups, section 4.2) runs with the 128-row M tile along m
+ * or along n and an N tile of 128, 112, 96, 80, 64 or 48 columns.  A step
+ * whose consumer takes its result as split pieces from its epilogue keeps
+ * the orientation that consumer needs and 128 columns.  Every other step
+ * takes the entry of the tile table (autotune_table) for its problem
+ * (prec, batch, m, n, k) when there is one, else the padding rule: the
+ * fewest tiles weighted by N + 128 for a tile of N columns.  QTPU_EINVAL
+ * if a given table cannot be read or has a malformed line.  The choice never
+ * changes a computed value beyond rounding order. */
 qtpu_status qtpu_htn_plan(qtpu_htn* h, const qtpu_plan_opts* opts);
+
+/* Measure the GEMM tiles of this handle's lowered plan on CUDA device
+ * `device` (-1: the handle's own; a host-only handle's lowered plan can be
+ * timed on any device, without its tensors' data): for every tensor-core
+ * step's problem, each valid orientation and N tile is timed (the median of
+ * `reps` launches, 1..1000, after one warm-up) on synthetic operand pieces of
+ * the step's shape and operand-pair count, in device memory this call
+ * allocates and frees; the fastest choice per problem
+ * is merged into the tile table file `table_path` (created if missing;
+ * entries of other problems are kept) as lines
+ *   prec batch m n k : swap bn ms ms_rule ms_base
+ * (swap 1: m runs along the N tile; median milliseconds of the choice, of
+ * the padding rule's choice and of 128-column tiles with m along M unless
+ * m < 64; only the first seven fields are required when a table is read).
+ * Plan another handle with autotune_table = table_path to use it.
+ * *n_problems (may be NULL) receives the number of problems timed.  It
+ * runs on a stream of its own and synchronises it; other work on the device
+ * at the same time distorts the timings.  QTPU_ESTATE before plan,
+ * QTPU_ENOTSUP for device -1 on a host-only handle, QTPU_EINVAL on a NULL or
+ * empty path, bad reps, or an unreadable table, QTPU_ENOMEM / QTPU_ECUDA on
+ * device errors, QTPU_ETIMEOUT if a timed GEMM's bounded wait gave up. */
+qtpu_status qtpu_htn_autotune(qtpu_htn* h, int device, const char* table_path, int reps, int* n_problems);
 
 /* Canonical plan text (order, index groups, per-slice sizes and FLOPs,
  * slices, totals).  Writes at most len bytes including the NUL; *needed (if

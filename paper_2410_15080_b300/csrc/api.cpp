@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -154,13 +156,28 @@ qtpu_status qtpu_htn_plan(qtpu_htn* h, const qtpu_plan_opts* opts) {
     return fail(h, QTPU_ENOTSUP, "the learned cost model runs its perceptron on the device");
   for (int64_t i : h->output)
     if (!h->dims.has(i)) return fail(h, QTPU_EINVAL, "output index " + std::to_string(i) + " is on no tensor");
+  // GEMM tile table: the given file (it must load), or the measured table
+  // beside the library when there is one ("" = the padding rule alone)
+  TileTable tiles;
+  {
+    const bool given = o.autotune_table != nullptr;
+    const std::string tp = given ? std::string(o.autotune_table) : default_tile_table_path();
+    if (!tp.empty()) {
+      FILE* fp = std::fopen(tp.c_str(), "r");
+      if (fp) std::fclose(fp);
+      if (fp || given) {
+        const std::string m = load_tile_table(tp, &tiles);
+        if (!m.empty()) return fail(h, QTPU_EINVAL, m);
+      }
+    }
+  }
   std::vector<Inds> li;
   for (auto& L : h->leaves) li.push_back(L.ids);
   int r;
   if (o.cost_model == 1) {
     std::string err;
-    const int st = plan_by_cost_model(li, h->dims, h->output, o, h->leaves, h->device, (void*)h->stream, &h->plan,
-                                      &err);
+    const int st = plan_by_cost_model(li, h->dims, h->output, o, h->leaves, h->device, (void*)h->stream, &tiles,
+                                      &h->plan, &err);
     if (st != QTPU_OK) return fail(h, (qtpu_status)st, err);
     r = PLAN_OK;
   } else if (o.n_candidates > 1) {
@@ -177,12 +194,39 @@ qtpu_status qtpu_htn_plan(qtpu_htn* h, const qtpu_plan_opts* opts) {
     // a host-only handle lowers the plan too (no device work), so its
     // launch list can be inspected
     int code = QTPU_OK;
-    std::string m = exec_build(&h->ex, h->plan, h->leaves, h->dims, (int)o.prec, &code, h->host_only, o.reuse_bytes);
+    std::string m =
+        exec_build(&h->ex, h->plan, h->leaves, h->dims, (int)o.prec, &code, h->host_only, o.reuse_bytes, &tiles);
     if (code != QTPU_OK && !h->host_only) return fail(h, (qtpu_status)code, m);
     if (code != QTPU_OK) h->ex.lowered = false;  // planning still succeeded
     h->built = !h->host_only;
   }
   h->planned = true;
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_autotune(qtpu_htn* h, int device, const char* table_path, int reps, int* n_problems) {
+  if (!h) return QTPU_EINVAL;
+  if (n_problems) *n_problems = 0;
+  if (!table_path || !*table_path) return fail(h, QTPU_EINVAL, "table_path is NULL or empty");
+  if (reps < 1 || reps > 1000) return fail(h, QTPU_EINVAL, "reps outside 1..1000");
+  if (!h->planned) return fail(h, QTPU_ESTATE, "autotune before plan");
+  if (device < 0 && h->host_only) return fail(h, QTPU_ENOTSUP, "host-only handle: give a device to time on");
+  if (!h->ex.lowered) return fail(h, QTPU_ESTATE, "no lowered plan");
+  cudaError_t e = cudaSetDevice(device < 0 ? h->device : device);
+  if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
+  TileTable t;
+  FILE* fp = std::fopen(table_path, "r");
+  if (fp) {
+    std::fclose(fp);
+    const std::string m = load_tile_table(table_path, &t);
+    if (!m.empty()) return fail(h, QTPU_EINVAL, m);
+  }
+  int n = 0, code = QTPU_OK;
+  std::string m = exec_autotune(&h->ex, reps, &t, &n, &code);
+  if (code != QTPU_OK) return fail(h, (qtpu_status)code, m);
+  m = save_tile_table(table_path, t);
+  if (!m.empty()) return fail(h, QTPU_EINVAL, m);
+  if (n_problems) *n_problems = n;
   return QTPU_OK;
 }
 
@@ -429,6 +473,15 @@ bool batch_streams(int dev) {
          cudaEventCreateWithFlags(&g_batch.out[dev], cudaEventDisableTiming) == cudaSuccess;
 }
 
+// blocks of the persistent kernel per SM (QTPU_BATCH_BLOCKS_PER_SM overrides
+// the default of 4, the fastest of 1, 2 and 4 measured on a batch of small
+// networks)
+int batch_grid(int sm) {
+  int per = 4;
+  if (const char* s = getenv("QTPU_BATCH_BLOCKS_PER_SM")) per = std::max(1, std::min(8, atoi(s)));
+  return sm * per;
+}
+
 void batch_forget(qtpu_htn* h) {
   std::lock_guard<std::mutex> g(g_batch.mu);
   for (size_t i = 0; i < g_batch.cache.size();) {
@@ -556,7 +609,7 @@ qtpu_status qtpu_htn_contract_batch_ex(qtpu_htn* const* hs, int n, double* const
         if (e1 == cudaSuccess) e1 = cudaMemsetAsync(b->d_abort, 0, sizeof(int), s0);
         if (e1 == cudaSuccess)
           e1 = launch_batch_persistent(b->d_tasks, b->n_tasks, b->d_start, b->d_next, b->d_done, o.wait_limit_ns,
-                                       b->d_abort, sm * 4, s0);
+                                       b->d_abort, batch_grid(sm), s0);
       }
       int k = 0;
       for (int i = 0; i < n && e1 == cudaSuccess; ++i) {

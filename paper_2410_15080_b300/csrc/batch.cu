@@ -51,16 +51,30 @@ __device__ __forceinline__ void offsets_n(uint32_t o, const GModes& t, int nops,
   }
 }
 
+// one output: the loop modes walked with running offsets (no divisions)
 template <typename ACC>
 __device__ ACC dense_entry(const GatherArgs& a, uint32_t o) {
-  int64_t base[kMaxOps];
-  offsets_n(o, a.out, a.nops, base);
+  int64_t off[kMaxOps];
+  offsets_n(o, a.out, a.nops, off);
   ACC acc;
-  for (uint32_t l = 0; l < a.n_loop; ++l) {
-    int64_t off[kMaxOps];
-    offsets_n(l, a.loop, a.nops, off);
-    for (int j = 0; j < a.nops; ++j) off[j] += base[j];
+  if (a.loop.n == 0) {
     acc.add(term_cg(a, off));
+    return acc;
+  }
+  uint32_t idx[kMaxModes];
+  for (int m = 0; m < a.loop.n; ++m) idx[m] = 0;
+  for (uint32_t l = 0; l < a.n_loop; ++l) {
+    acc.add(term_cg(a, off));
+    int m = a.loop.n - 1;
+    ++idx[m];
+    for (int j = 0; j < a.nops; ++j) off[j] += a.loop.stride[m][j];
+    while (m > 0 && idx[m] == a.loop.dim[m]) {
+      for (int j = 0; j < a.nops; ++j) off[j] -= (int64_t)a.loop.dim[m] * a.loop.stride[m][j];
+      idx[m] = 0;
+      --m;
+      ++idx[m];
+      for (int j = 0; j < a.nops; ++j) off[j] += a.loop.stride[m][j];
+    }
   }
   return acc;
 }

@@ -146,16 +146,20 @@ __device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t* r) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Shared-memory matrix descriptor, K-major operand, 128-byte swizzle:
-// rows of 128 B, 8-row atoms of 1024 B (stride byte offset), tile base
-// 1024-B aligned; version field = 1 (sm_100 family).
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+// Shared-memory matrix descriptor, K-major operand, swizzled rows of ROW
+// bytes (128: SWIZZLE_128B, layout code 2; 64: SWIZZLE_64B, code 4): 8-row
+// atoms of 8 * ROW bytes (stride byte offset), tile base aligned to the
+// atom; the leading byte offset is unused for swizzled K-major operands;
+// version field = 1 (sm_100 family).
+template <int ROW>
+__device__ __forceinline__ uint64_t smem_desc_k(uint32_t saddr) {
+  static_assert(ROW == 128 || ROW == 64, "swizzle row");
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);        // start address
-  d |= (uint64_t)1 << 16;                        // leading byte offset (unused for SW128 K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset
+  d |= (uint64_t)1 << 16;                        // leading byte offset
+  d |= (uint64_t)((8 * ROW) >> 4) << 32;         // stride byte offset
   d |= (uint64_t)1 << 46;                        // descriptor version
-  d |= (uint64_t)2 << 61;                        // SWIZZLE_128B
+  d |= (uint64_t)(ROW == 128 ? 2 : 4) << 61;     // layout (swizzle) code
   return d;
 }
 

@@ -86,7 +86,7 @@ std::string default_cost_model_path() {
 // qtpu_status.
 int plan_by_cost_model(const std::vector<Inds>& li, const DimMap& dims, const Inds& output,
                        const qtpu_plan_opts& o, const std::vector<Leaf>& leaves, int device, void* stream,
-                       Plan* chosen, std::string* err) {
+                       const TileTable* tiles, Plan* chosen, std::string* err) {
   CmFile cm;
   const std::string path = o.cost_model_path ? std::string(o.cost_model_path) : default_cost_model_path();
   if (!load_model(path, &cm, err)) return QTPU_EINVAL;
@@ -115,7 +115,7 @@ int plan_by_cost_model(const std::vector<Inds>& li, const DimMap& dims, const In
     Executor ex;
     ex.device = device;
     int code = QTPU_OK;
-    exec_build(&ex, c.plan, leaves, dims, (int)o.prec, &code, true, o.reuse_bytes);
+    exec_build(&ex, c.plan, leaves, dims, (int)o.prec, &code, true, o.reuse_bytes, tiles);
     if (code != QTPU_OK || !ex.lowered) continue;
     c.seed = s;
     c.flops = ex.flops_executed;

@@ -154,8 +154,10 @@ bool make_operand_map(CUtensorMap* map, void* base, int prec, int64_t batch, int
   cuuint64_t gstr[3] = {(cuuint64_t)(Kp * es), (cuuint64_t)(rows * Kp * es), (cuuint64_t)(batch * rows * Kp * es)};
   cuuint32_t box[4] = {(cuuint32_t)kb, (cuuint32_t)box_rows, 1, 1};
   cuuint32_t est[4] = {1, 1, 1, 1};
+  // the swizzle span is the stage's row: kb elements
+  const CUtensorMapSwizzle swz = kb * es == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
   CUresult r = enc(map, prec == 3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base,
-                   gdim, gstr, box, est, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   gdim, gstr, box, est, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -341,7 +343,7 @@ struct Repr {
 }  // namespace
 
 std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& leaves, const DimMap& dims,
-                       int prec, int* code, bool dry_run, uint64_t reuse_bytes) {
+                       int prec, int* code, bool dry_run, uint64_t reuse_bytes, const TileTable* tiles) {
   *code = QTPU_OK;
   ex->prec = prec;
   ex->n_leaves = plan.n_leaves;
@@ -787,7 +789,8 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     if (T < 0 || it == gemm_out.end()) return false;
     const GemmOut& P = it->second;
     const Launch& LP = ex->launches[P.li];
-    if (LP.kind != LK_GEMM || LP.gemm.fuse.on || LP.gemm.prec != 3 || (P.K + 63) / 64 > 16) return false;
+    if (LP.kind != LK_GEMM || LP.gemm.fuse.on || LP.gemm.prec != 3 || LP.gemm.bn != 128 || (P.K + 63) / 64 > 16)
+      return false;
     // pieces cannot be added up: the producer must not sum over slice values
     if (LP.din != LP.dout) return false;
     int k_is_m;
@@ -947,21 +950,30 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     // C^T = B^T A^T, so the 128-row tile runs along the longer dimension)
     const double lim = 2147483647.0;
     bool swap = nm < 64 && nn >= 64;
+    int bn = 128;
+    bool oriented = false;  // fixed by the fused split of the consumer
     // when the next GEMM will contract this result over exactly the m (or n)
     // indices, make that group the stored outer (N) one: the epilogue then
     // writes the next operand's pieces along each thread's own columns
-    if (!fuse_off && !fuse_keep_layout && prec == 3 && !last) {
+    // (with QTPU_FUSE_KEEP_LAYOUT the default orientation stays).  Such a
+    // result keeps the 128-column tile the fused epilogue needs: dropping a
+    // split launch saves more than a narrower tile.
+    if (!fuse_off && prec == 3 && !last) {
       const Inds ck = consumer_k(ps.out, s);
       const std::set<int64_t> cks(ck.begin(), ck.end());
       int pref = -1;
       if (!ck.empty() && cks == std::set<int64_t>(m.begin(), m.end())) pref = 1;
       if (!ck.empty() && cks == std::set<int64_t>(n.begin(), n.end())) pref = 0;
-      if (pref >= 0 && (pref ? nn : nm) >= 64 && (pref ? nm : nn) >= 16) swap = pref == 1;
+      if (pref >= 0) {
+        if (!fuse_keep_layout && (pref ? nn : nm) >= 64 && (pref ? nm : nn) >= 16) swap = pref == 1;
+        oriented = true;
+      }
     }
+    if (!oriented) choose_tile(tiles, prec, nb, nm, nn, nk, &swap, &bn);
     const double gM = swap ? nn : nm, gN = swap ? nm : nn;
     const bool tc = sa.empty() && sb.empty() && gM >= 64 && gN >= 16 && nk >= 8 &&
                     nb * nm * nn * nk >= (double)(1 << 22) && nb < lim && nm < lim && nn < lim && nk < lim &&
-                    nb * std::ceil(gM / 128.0) * std::ceil(gN / (double)gemm_block_n()) < lim;
+                    nb * std::ceil(gM / 128.0) * std::ceil(gN / (double)bn) < lim;
     if (tc) {
       // Mode order inside each split operand is free (K only has to agree
       // between the two): rows follow their operand's source strides, and K
@@ -1030,6 +1042,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
           const int T = side ? TB : TA;
           Launch& LP = ex->launches[gemm_out[T].li];
           LP.gemm.fuse = side ? FB : FA;
+          LP.tile_fixed = true;
           const std::vector<int>& sm = side ? smB : smA;
           for (size_t j = 0; j < sm.size(); ++j) LP.fuse_src[j] = sm[j];
           // the pieces it now writes carry the absorbed factors' slices too
@@ -1052,6 +1065,10 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
         LG.gemm.N = (int)gN;
         LG.gemm.K = (int)Ka;
         LG.gemm.prec = prec;
+        LG.gemm.bn = bn;
+        LG.tile_key[0] = prec, LG.tile_key[1] = (int64_t)nb, LG.tile_key[2] = (int64_t)nm;
+        LG.tile_key[3] = (int64_t)nn, LG.tile_key[4] = (int64_t)nk;
+        LG.tile_fixed = oriented;
         LG.gemm.kc_blocks = ex->kc_blocks;
         LG.flops = step_flops + X.flops + Y.flops;
         // algorithmic bytes: the result written once (its operands are
@@ -1491,7 +1508,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
         kp[side] = S.g.Kp;
         // one map per split slot (slot 0 is the map set below)
         const int64_t rows = side ? L.gemm.N : L.gemm.M;
-        const int box = side ? gemm_block_n() : 128;
+        const int box = side ? L.gemm.bn : 128;
         for (int v = 1; v < ex->n_split_slots && S.side < 0; ++v) {
           CUtensorMap* m = side ? &L.gemm.maps.b[v] : &L.gemm.maps.a[v];
           if (!make_operand_map(m, base[side] + (size_t)v * ex->split_slot[side], prec, L.gemm.batch, rows, L.gemm.K,
@@ -1511,7 +1528,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       if (nc > 1) {
         L.opnd_owner[side] = T;
         const int64_t rows = side ? L.gemm.N : L.gemm.M;
-        const int box = side ? gemm_block_n() : 128;
+        const int box = side ? L.gemm.bn : 128;
         L.tm_copies[side].resize((size_t)nc);
         for (int64_t c = 0; c < nc; ++c)
           if (!make_operand_map(&L.tm_copies[side][c], base[side] + (size_t)c * St.bytes, prec, L.gemm.batch, rows,
@@ -1523,7 +1540,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     }
     if (!make_operand_map(&L.gemm.maps.a[0], base[0], prec, L.gemm.batch, L.gemm.M, L.gemm.K, kp[0], 128) ||
         !make_operand_map(&L.gemm.maps.b[0], base[1], prec, L.gemm.batch, L.gemm.N, L.gemm.K, kp[1],
-                          gemm_block_n())) {
+                          L.gemm.bn)) {
       exec_free(ex);
       return fail(QTPU_ECUDA, "cuTensorMapEncodeTiled failed");
     }
@@ -1578,7 +1595,8 @@ std::string exec_describe(const Executor* ex) {
   auto one = [&](const Launch& L, size_t i) {
     o << "launch " << i << " " << cls[L.kclass] << " ";
     if (L.kind == LK_GEMM) {
-      o << "gemm batch=" << L.gemm.batch << " M=" << L.gemm.M << " N=" << L.gemm.N << " K=" << L.gemm.K;
+      o << "gemm batch=" << L.gemm.batch << " M=" << L.gemm.M << " N=" << L.gemm.N << " K=" << L.gemm.K
+        << " bn=" << L.gemm.bn;
       if (L.gemm.fuse.on) o << " writes-pieces k=" << (L.gemm.fuse.k_is_m ? "M" : "N") << " w=" << L.gemm.fuse.w_size;
     } else if (L.kind == LK_CONTRACT64) {
       o << "fp64 out=" << L.c64.n_out << " loop=" << L.c64.n_loop;
@@ -1696,9 +1714,9 @@ void exec_launch_features(const Executor* ex, size_t i, float* f) {
     f[15] = lg(g.K);
     f[16] = lg(g.batch);
     f[17] = (float)nv;
-    const double mt = std::ceil(g.M / 128.0), nt = std::ceil(g.N / (double)gemm_block_n());
+    const double mt = std::ceil(g.M / 128.0), nt = std::ceil(g.N / (double)g.bn);
     f[18] = (float)(g.M / (128.0 * mt));
-    f[19] = (float)(g.N / ((double)gemm_block_n() * nt));
+    f[19] = (float)(g.N / ((double)g.bn * nt));
     f[20] = (float)(g.K / (64.0 * std::ceil(g.K / 64.0)));
     f[21] = g.fuse.on ? 1.f : 0.f;
     f[25] = lg((double)g.batch * mt * nt);
@@ -2126,8 +2144,18 @@ bool exec_batch_tasks(const Executor* ex, const std::vector<Leaf>& leaves, doubl
                       std::vector<BatchTask>* out) {
   out->clear();
   if (!ex->lowered || ex->n_slices != 1 || ex->launches.empty()) return false;
-  for (const Launch& L : ex->launches)
+  // small networks only: the persistent kernel runs the generic gather; a
+  // launch above this many terms keeps the typed kernels of a graph branch
+  // (measured on B300: a batch of 512 networks of <= 2^14-entry QTs runs
+  // 2.1x faster in the persistent kernel than as graph branches; in a batch
+  // whose time is set by networks with GEMMs, moving networks with launches
+  // above 2^16 terms into it only lengthened the batch)
+  double max_terms = (double)(1 << 16);
+  if (const char* e = std::getenv("QTPU_BATCH_MAX_TERMS")) max_terms = std::atof(e);
+  for (const Launch& L : ex->launches) {
     if (L.kind != LK_GATHER || L.g.mode >= GW_SPLIT_BF16X3 || L.side >= 0) return false;
+    if ((double)L.g.n_out * (double)L.g.n_loop > max_terms) return false;
+  }
   const int nl = (int)leaves.size();
   auto src_ptr = [&](int t) -> const void* {
     if (t < nl) return leaves[t].ptr;

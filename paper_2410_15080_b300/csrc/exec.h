@@ -1,7 +1,9 @@
 // Executor: turns a Plan into a list of kernel launches on one device/stream.
 #pragma once
 #include <algorithm>
+#include <array>
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -68,6 +70,11 @@ struct Launch {
   // intermediate holding them
   std::vector<CUtensorMap> tm_copies[2];
   int opnd_owner[2] = {-1, -1};
+  // LK_GEMM: its problem as the tile table keys it (prec, batch, m, n, k:
+  // the step's own index-group sizes, before orientation), and whether the
+  // orientation and N tile are fixed (by a fused-split consumer)
+  int64_t tile_key[5] = {};
+  bool tile_fixed = false;
 };
 
 // One unit of the slice-reuse schedule: a launch, preceded (for a GEMM) by
@@ -170,8 +177,39 @@ struct Executor {
 // Build launch descriptors and allocate the workspace.  Returns an empty
 // string on success, else an error message (*code receives a qtpu_status).
 // reuse_bytes: device memory for results kept across slices (0 = default).
+// GEMM tile table: per problem (prec, batch, m, n, k -- m and n the sizes of
+// the step's own index groups), the orientation (swap: m along the N tile)
+// and the N tile, with the measured times of that choice and of the padding
+// rule's choice.
+struct TileChoice {
+  int swap = 0;
+  int bn = 128;
+  double ms = 0, ms_rule = 0, ms_base = 0;
+};
+using TileKey = std::array<int64_t, 5>;
+using TileTable = std::map<TileKey, TileChoice>;
+// "" on success; the file holds lines "prec batch m n k : swap bn [ms ms_rule
+// ms_base]"
+std::string load_tile_table(const std::string& path, TileTable* t);
+std::string save_tile_table(const std::string& path, const TileTable& t);
+// the gemm_tiles_b300.txt beside the library
+std::string default_tile_table_path();
+// Orientation and N tile of a GEMM step: the table's entry when it has one
+// (for m x n or n x m), else the padding rule: the fewest tiles weighted by
+// (N + 128) for a tile of N columns -- on B300 a tile's time grows far less
+// than its width (112-column tiles of a 1296 x 1296 x 576 step took 0.98 of
+// the time of 128-column ones) -- ties keeping *swap as given and the wider
+// tile.
+void choose_tile(const TileTable* t, int prec, double nb, double nm, double nn, double nk, bool* swap, int* bn);
+
 std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& leaves, const DimMap& dims,
-                       int prec, int* code, bool dry_run = false, uint64_t reuse_bytes = 0);
+                       int prec, int* code, bool dry_run = false, uint64_t reuse_bytes = 0,
+                       const TileTable* tiles = nullptr);
+// Time every GEMM problem of the lowered plan (fixed tiles excepted) in each
+// valid orientation and N tile on synthetic operand pieces on the current
+// device, `reps` timed launches each (median), and store the fastest choice
+// per problem in *t.  *n receives the number of problems timed.
+std::string exec_autotune(const Executor* ex, int reps, TileTable* t, int* n, int* code);
 // One line per launch of the lowered contraction (kind, operands, shape,
 // useful FLOPs, algorithmic bytes) -- available after exec_build, also on a
 // dry run.
@@ -203,7 +241,7 @@ void set_global_error(const char* msg);
 // a qtpu_status, *err on failure.
 int plan_by_cost_model(const std::vector<Inds>& li, const DimMap& dims, const Inds& output,
                        const qtpu_plan_opts& o, const std::vector<Leaf>& leaves, int device, void* stream,
-                       Plan* chosen, std::string* err);
+                       const TileTable* tiles, Plan* chosen, std::string* err);
 // Sum the timed launches per class (after a stream sync) and reset.
 std::string exec_profile_read(Executor* ex, double* ms, int64_t* launches, double* flops, double* bytes);
 // Every timed launch (launch index, ms) in order (after a stream sync), and reset.

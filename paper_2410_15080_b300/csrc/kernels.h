@@ -156,6 +156,7 @@ struct GemmArgs {
   uint64_t limit_ns = 2000000000ull;
   GemmFuse fuse;         // fuse.on: C receives the consumer's piece planes
   int accum = 0;         // add the product to the stored (hi, lo) result (not with fuse)
+  int bn = 128;          // N tile, one of kGemmBlockN (fuse: 128 only)
 };
 cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st);
 // one warp waiting (bounded) on a barrier nothing completes: sets ST_TIMEOUT_DEP
@@ -186,7 +187,10 @@ cudaError_t launch_batch_persistent(const BatchTask* tasks, int n_tasks, const u
 bool make_operand_map(CUtensorMap* map, void* base, int prec, int64_t batch, int64_t rows, int64_t K,
                       int64_t Kp, int box_rows);
 
-int gemm_block_n();        // N tile of the GEMM kernel
+// N tiles of the GEMM kernel (the M tile is 128 rows); B operand maps use a
+// box of bn rows
+constexpr int kGemmBlockN[6] = {128, 112, 96, 80, 64, 48};
+bool gemm_bn_supported(int bn);
 int gemm_k_block(int prec);  // K elements per pipeline stage
 
 }  // namespace qtpu

@@ -12,21 +12,30 @@
 // (measured: the error grows linearly with K), so (1) the leading product
 // x0*y0 has its own accumulator X and the smaller cross terms share Y, and
 // (2) BF16x3 pieces are cut on a grid shared by each operand row's 64-entry
-// k-block (see grid_pieces): every k-block's sum of leading products, and a
-// chunk of up to 16 k-blocks on one grid, is then exact in X, so one chunk
-// covers K <= 1024 and the accumulators are drained once per tile.  Longer
-// K (and the TF32 forms, 4 or 32 k-blocks per chunk) add each chunk's X + Y
-// to the stored result with compensated (TwoSum) FP32 arithmetic; FP64 math
-// is avoided (FP64 throughput on B300 is ~1/64 of FP32).
+// block of k (see grid_pieces): every block's sum of leading products, and a
+// chunk of up to 1024 k on one grid, is then exact in X, so one chunk covers
+// K <= 1024 and the accumulators are drained once per tile.  Longer K (and
+// the TF32 forms, 128 or 1024 k per chunk) add each chunk's X + Y to the
+// stored result with compensated (TwoSum) FP32 arithmetic; FP64 math is
+// avoided (FP64 throughput on B300 is ~1/64 of FP32).
+//
+// The N tile BN is a template parameter (128, 112, 96, 80, 64 or 48 columns;
+// the executor picks it per GEMM, with the orientation, from a measured tile
+// table or by padding): a 216-wide side fills two 112-column tiles to 96 %
+// where 128-column tiles fill 84 %.  The M tile is 128 rows.  K-steps of the
+// last k-block of each operand pair that lie wholly beyond K are not issued
+// (their operands are zero), so K = 216 costs 224 columns of MMA, not 256.
 //
 // One CTA per SM, persistent over (batch, m-tile, n-tile) tiles:
 //   warp 0      TMA producer (one lane): pieces of A and B for one k-block
-//               per pipeline stage, completion counted on an mbarrier;
-//   warp 1      TMEM owner and MMA issuer (one lane): per k-block, 4 UMMA
+//               (KB k: 64 for BF16x3, 32 for TF32) per pipeline stage,
+//               completion counted on an mbarrier; as many stages as fit
+//               (2 for BF16x3 with 128-column tiles, 3 with 64 or 48);
+//   warp 1      TMEM owner and MMA issuer (one lane): per k-block, its UMMA
 //               K-steps x the product list, into one of two TMEM
 //               accumulators (double-buffered so the epilogue of one chunk
 //               overlaps the MMAs of the next);
-//   warps 2..17 epilogue: tcgen05.ld 32 lanes x 32 columns of both
+//   warps 2..17 epilogue: tcgen05.ld 32 lanes x 8-column groups of both
 //               accumulators, X + Y as an exact (hi, lo) float pair (TwoSum)
 //               stored, or added to the stored pair for later chunks.
 // Every wait is bounded (global timer); on give-up the kernel sets a status
@@ -44,50 +53,64 @@ namespace qtpu {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BN = 128;
+constexpr int kFuseBN = 128;                   // N tile of the fused-split epilogue
 constexpr int kEpiWarps = 16;
-constexpr int kEpiCols = BN / (kEpiWarps / 4);  // columns per epilogue thread
+constexpr int kFuseEpiCols = kFuseBN / (kEpiWarps / 4);  // columns per fused-epilogue thread
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer, MMA, 16 epilogue warps
-constexpr int kRowBytes = 128;                 // one swizzle row: 64 BF16 or 32 TF32
-constexpr uint32_t kTmemCols = 512;            // 2 buffers x (X, Y) x BN columns
+constexpr uint32_t kTmemCols = 512;            // 2 buffers x (X, Y) x BN columns (BN <= 128)
+constexpr int kSmemLimit = 232448;             // dynamic shared memory per CTA (227 KB)
 
 // Product list: entry 0 is the leading product x0*y0 (accumulator X), the
 // rest are the cross terms (accumulator Y, a factor 2^-8 or 2^-11 smaller).
 template <int PREC>
 struct Cfg;
+// KB: k per pipeline stage (one 128-byte swizzled shared-memory row: 64
+// BF16 or 32 TF32; measured on B300, 32-k BF16x3 stages in 64-byte swizzle,
+// twice as many in flight, ran the 100-qubit GEMMs 8-20 % slower); KC:
+// stages per accumulator chunk.
 template <>
 struct Cfg<3> {  // BF16x3: pieces of 8 significant bits, products of weight >= 2^-16
-  static constexpr int NP = 3, NPROD = 6, ES = 2, KB = 64, UK = 16, FMT = 1, STAGES = 2, KC = 16;
+  static constexpr int NP = 3, NPROD = 6, ES = 2, KB = 64, UK = 16, FMT = 1, KC = 16;
   __device__ static int pa(int i) { const int t[6] = {0, 0, 1, 0, 1, 2}; return t[i]; }
   __device__ static int pb(int i) { const int t[6] = {0, 1, 0, 2, 1, 0}; return t[i]; }
 };
 template <>
 struct Cfg<2> {  // 3xTF32: pieces of 11 significant bits, products of weight >= 2^-11
-  static constexpr int NP = 2, NPROD = 3, ES = 4, KB = 32, UK = 8, FMT = 2, STAGES = 3, KC = 4;
+  static constexpr int NP = 2, NPROD = 3, ES = 4, KB = 32, UK = 8, FMT = 2, KC = 4;
   __device__ static int pa(int i) { const int t[3] = {0, 0, 1}; return t[i]; }
   __device__ static int pb(int i) { const int t[3] = {0, 1, 0}; return t[i]; }
 };
 template <>
 struct Cfg<1> {  // TF32: one piece, one product
-  static constexpr int NP = 1, NPROD = 1, ES = 4, KB = 32, UK = 8, FMT = 2, STAGES = 4, KC = 32;
+  static constexpr int NP = 1, NPROD = 1, ES = 4, KB = 32, UK = 8, FMT = 2, KC = 32;
   __device__ static int pa(int) { return 0; }
   __device__ static int pb(int) { return 0; }
 };
 
-template <int PREC>
+// Shared memory: the pipeline stages (as many as fit, at most 4), the
+// barriers and, for the fused-split epilogue (BF16x3, BN = 128 only), its
+// tables.
+template <int PREC, int BN>
 struct Layout {
   using C = Cfg<PREC>;
-  static constexpr int A_PIECE = BM * kRowBytes;
-  static constexpr int B_PIECE = BN * kRowBytes;
+  static constexpr bool FUSE = PREC == 3 && BN == kFuseBN;
+  static constexpr int ROW = C::KB * C::ES;  // bytes per smem row (= swizzle span)
+  static_assert(ROW == 64 || ROW == 128, "64- or 128-byte swizzle rows");
+  static constexpr int A_PIECE = BM * ROW;
+  static constexpr int B_PIECE = BN * ROW;
   static constexpr int STAGE = C::NP * (A_PIECE + B_PIECE);
-  static constexpr int BAR_OFF = C::STAGES * STAGE;
-  // full[S], empty[S], accfull[2], accempty[2], mma_done
-  static constexpr int N_BARS = 2 * C::STAGES + 5;
-  // fused split (BF16x3 only): W table, per-tile digit tables, maxima
-  static constexpr int FUSE_OFF = (BAR_OFF + N_BARS * 8 + 16 + 15) / 16 * 16;
   static constexpr int FUSE_W = (int)kFuseMaxW * 8;
-  static constexpr int FUSE_BYTES = PREC == 3 ? FUSE_W + 4 * 128 * 4 + 4 * 128 * 4 + 16 : 0;
+  static constexpr int FUSE_BYTES = FUSE ? FUSE_W + 4 * 128 * 4 + 4 * 128 * 4 + 16 : 0;
+  static constexpr int FIT = (kSmemLimit - 1024 - 256 - FUSE_BYTES) / STAGE;
+  static constexpr int STAGES = FIT < 8 ? FIT : 8;
+  static_assert(STAGES >= 2, "two pipeline stages must fit");
+  static_assert(BN % 16 == 0 && BN >= 16 && 4 * BN <= (int)kTmemCols, "UMMA N tile");
+  static constexpr int BAR_OFF = STAGES * STAGE;
+  // full[S], empty[S], accfull[2], accempty[2], mma_done
+  static constexpr int N_BARS = 2 * STAGES + 5;
+  static constexpr int FUSE_OFF = (BAR_OFF + N_BARS * 8 + 16 + 15) / 16 * 16;
   static constexpr int SMEM = FUSE_OFF + FUSE_BYTES + 1024;
+  static_assert(SMEM <= kSmemLimit, "shared memory");
 };
 
 __device__ __forceinline__ void set_abort(volatile int* abort, uint32_t* status, uint32_t bit) {
@@ -133,11 +156,13 @@ __device__ __forceinline__ void digits(uint32_t x, const GModes& t, int* r, int*
 // read the accumulator, which is handed back after pass 2.  Every epilogue
 // warp reaches every named barrier of a tile; a timeout (abort) ends the tile
 // loop for all of them after the second barrier.
-template <int PREC>
+template <int PREC, int BN>
 __device__ void fused_epilogue(const GemmFuse& fz, const float2* fW, uint8_t* smem, uint32_t tmem, uint64_t* accfull,
                                uint64_t* accempty, volatile int* abort, uint32_t* status, uint64_t limit_ns, int batch,
                                int M, int N, int mt, int nt, int n_tiles, __nv_bfloat16* out) {
-  using L = Layout<PREC>;
+  using L = Layout<PREC, BN>;
+  static_assert(BN == kFuseBN, "the fused epilogue's tables are laid out for 128-column tiles");
+  constexpr int kEpiCols = kFuseEpiCols;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ew = warp - 2, q = warp & 3, h = ew >> 2;
   const int et = threadIdx.x - 64;
@@ -272,19 +297,20 @@ __device__ void fused_epilogue(const GemmFuse& fz, const float2* fW, uint8_t* sm
   }
 }
 
-template <int PREC>
+template <int PREC, int BN>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ GemmMaps maps, int nval,
               float2* __restrict__ Cout, int batch, int M, int N, int K, int kc_blocks, uint32_t* status,
               uint64_t limit_ns, const __grid_constant__ GemmFuse fz, int accum) {
   using C = Cfg<PREC>;
-  using L = Layout<PREC>;
+  using L = Layout<PREC, BN>;
+  constexpr int NG = BN / 8;  // 8-column groups of a tile
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + L::BAR_OFF);
   uint64_t* full = bars;
-  uint64_t* empty = bars + C::STAGES;
-  uint64_t* accfull = bars + 2 * C::STAGES;
+  uint64_t* empty = bars + L::STAGES;
+  uint64_t* accfull = bars + 2 * L::STAGES;
   uint64_t* accempty = accfull + 2;
   uint64_t* mma_done = accempty + 2;
   uint32_t* tmem_holder = (uint32_t*)(bars + L::N_BARS);
@@ -299,12 +325,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int nkb1 = (K + C::KB - 1) / C::KB;
   const int nkb = nkb1 * nval;
   // the fused split takes the whole K in one accumulator chunk (host: K <= 1024)
-  const int kc0 = (PREC == 3 && fz.on) ? nkb : (kc_blocks > 0 ? kc_blocks : C::KC);
+  const int kc0 = (L::FUSE && fz.on) ? nkb : (kc_blocks > 0 ? kc_blocks : C::KC);
   const int kc = kc0 < nkb ? kc0 : nkb;
   const int nchunks = (nkb + kc - 1) / kc;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < C::STAGES; ++s) {
+    for (int s = 0; s < L::STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -329,7 +355,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
   float2* fW = reinterpret_cast<float2*>(smem + L::FUSE_OFF);
-  if (PREC == 3 && fz.on && fz.w_size) {  // product of the absorbed small leaves
+  if (L::FUSE && fz.on && fz.w_size) {  // product of the absorbed small leaves
     for (uint32_t u = threadIdx.x; u < fz.w_size; u += blockDim.x) {
       int64_t off[kMaxOps];
       for (int j = 0; j < fz.nsmall; ++j) off[j] = 0;
@@ -355,9 +381,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ------------------------------------------------------------ producer
       int stage = 0;
       uint32_t phase = 0;
-      int issued[C::STAGES];
-      uint32_t issued_phase[C::STAGES];
-      for (int s = 0; s < C::STAGES; ++s) issued[s] = 0, issued_phase[s] = 0;
+      int issued[L::STAGES];
+      uint32_t issued_phase[L::STAGES];
+      for (int s = 0; s < L::STAGES; ++s) issued[s] = 0, issued_phase[s] = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         const int ntile = (int)(t % nt);
@@ -381,11 +407,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           issued[stage] = 1;
           issued_phase[stage] = phase;
-          if (++stage == C::STAGES) stage = 0, phase ^= 1;
+          if (++stage == L::STAGES) stage = 0, phase ^= 1;
         }
       }
       if (!ok) {  // let copies already in flight land before the CTA exits
-        for (int s = 0; s < C::STAGES; ++s)
+        for (int s = 0; s < L::STAGES; ++s)
           if (issued[s]) {
             volatile int no_abort = 0;
             mbar_wait_bounded(&full[s], issued_phase[s], limit_ns, &no_abort);
@@ -422,13 +448,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const uint32_t sA = smem_u32(smem + stage * L::STAGE);
             const uint32_t sB = sA + C::NP * L::A_PIECE;
+            // K-steps of this pair's k-block that start below K (the rest
+            // multiply zeros)
+            const int krem = K - (kb % nkb1) * C::KB;
+            const int nkk = krem >= C::KB ? C::KB / C::UK : (krem + C::UK - 1) / C::UK;
 #pragma unroll
             for (int kk = 0; kk < C::KB / C::UK; ++kk) {
+              if (kk >= nkk) break;
               const bool first = (kb == kb0 && kk == 0);
 #pragma unroll
               for (int pr = 0; pr < C::NPROD; ++pr) {
-                const uint64_t ad = smem_desc_sw128(sA + C::pa(pr) * L::A_PIECE + kk * C::UK * C::ES);
-                const uint64_t bd = smem_desc_sw128(sB + C::pb(pr) * L::B_PIECE + kk * C::UK * C::ES);
+                const uint64_t ad = smem_desc_k<L::ROW>(sA + C::pa(pr) * L::A_PIECE + kk * C::UK * C::ES);
+                const uint64_t bd = smem_desc_k<L::ROW>(sB + C::pb(pr) * L::B_PIECE + kk * C::UK * C::ES);
                 const uint32_t accum = (first && pr <= 1) ? 0u : 1u;
                 const uint32_t d = pr == 0 ? dX : dY;
                 if (C::FMT == 1)
@@ -439,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             umma_commit(&empty[stage]);
             any = true;
-            if (++stage == C::STAGES) stage = 0, phase ^= 1;
+            if (++stage == L::STAGES) stage = 0, phase ^= 1;
           }
           if (ok) umma_commit(&accfull[acc]);
         }
@@ -452,15 +483,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // -------------------------------------------------------------- epilogue
-    if (PREC == 3 && fz.on) {
-      fused_epilogue<PREC>(fz, fW, smem, tmem, accfull, accempty, abort, status, limit_ns, batch, M, N, mt, nt,
-                           n_tiles, reinterpret_cast<__nv_bfloat16*>(Cout));
-    } else {
-    // warp w owns TMEM lane quarter (w % 4) and column group h of the tile;
-    // per chunk each thread loads its row's kEpiCols columns of X and Y,
-    // hands the accumulator back to the MMA warp, and stores X + Y as an
-    // exact (hi, lo) pair -- added to the stored pair for chunks after the
-    // first (the same thread owns the same outputs in every chunk).
+    bool fused = false;
+    if constexpr (L::FUSE) {
+      if (fz.on) {
+        fused_epilogue<PREC, BN>(fz, fW, smem, tmem, accfull, accempty, abort, status, limit_ns, batch, M, N, mt,
+                                 nt, n_tiles, reinterpret_cast<__nv_bfloat16*>(Cout));
+        fused = true;
+      }
+    }
+    if (!fused) {
+    // warp w owns TMEM lane quarter (w % 4) and the 8-column groups
+    // h, h + 4, h + 8, ... of the tile; per chunk each thread loads its row's
+    // columns of X and Y group by group, hands the accumulator back to the
+    // MMA warp after its last group, and stores X + Y as an exact (hi, lo)
+    // pair -- added to the stored pair for chunks after the first (the same
+    // thread owns the same outputs in every chunk).
     const int ew = warp - 2;
     const int q = warp & 3;
     const int h = ew >> 2;
@@ -475,7 +512,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // lanes of a warp write 32 consecutive rows, 256 contiguous bytes
       const int row = mtile * BM + q * 32 + lane;
       float2* cb = Cout + (long long)b * M * N + row;
-      const int n0 = ntile * BN + h * kEpiCols;
+      const int n0 = ntile * BN;
       for (int ch = 0; ch < nchunks; ++ch, ++item) {
         const int acc = (int)(item & 1);
         const uint32_t aph = (uint32_t)((item >> 1) & 1);
@@ -487,16 +524,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t tX = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 2 * BN + h * kEpiCols);
+        const uint32_t tX = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 2 * BN);
         // groups of 8 columns: X and Y of a group in 16 registers (all
         // register indices compile-time constants)
 #pragma unroll 1
-        for (int g = 0; g < kEpiCols / 8; ++g) {
+        for (int g = h; g < NG; g += 4) {
           uint32_t rx[8], ry[8];
           tmem_ld8_nowait(tX + g * 8, rx);
           if (C::NPROD > 1) tmem_ld8_nowait(tX + BN + g * 8, ry);
           tmem_wait_ld();
-          if (g == kEpiCols / 8 - 1) {  // the accumulator is free for the next chunk
+          if (g + 4 >= NG) {  // this warp's last group: the accumulator is free for the next chunk
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&accempty[acc]);
@@ -528,16 +565,43 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <int PREC>
+template <int PREC, int BN>
 cudaError_t launch_t(const GemmArgs& a, int sm_count, cudaStream_t st) {
-  using L = Layout<PREC>;
+  using L = Layout<PREC, BN>;
   const long long tiles = (long long)a.batch * ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
   if (tiles <= 0) return cudaSuccess;
   const int grid = (int)(tiles < sm_count ? tiles : sm_count);
-  if (a.fuse.on && (PREC != 3 || a.fuse.w_size > kFuseMaxW || a.accum || a.nval != 1)) return cudaErrorInvalidValue;
+  if (a.fuse.on && (!L::FUSE || a.fuse.w_size > kFuseMaxW || a.accum || a.nval != 1)) return cudaErrorInvalidValue;
   if (a.nval < 1 || a.nval > kGemmVals) return cudaErrorInvalidValue;
-  return launch_k(k_gemm_tc<PREC>, dim3(grid), dim3(kThreads), (size_t)L::SMEM, st, a.maps, a.nval, (float2*)a.C,
-                  a.batch, a.M, a.N, a.K, a.kc_blocks, a.status, a.limit_ns, a.fuse, a.accum);
+  return launch_k(k_gemm_tc<PREC, BN>, dim3(grid), dim3(kThreads), (size_t)L::SMEM, st, a.maps, a.nval,
+                  (float2*)a.C, a.batch, a.M, a.N, a.K, a.kc_blocks, a.status, a.limit_ns, a.fuse, a.accum);
+}
+
+template <int PREC, int BN>
+cudaError_t prepare_t() {
+  return cudaFuncSetAttribute(k_gemm_tc<PREC, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Layout<PREC, BN>::SMEM);
+}
+
+// the N tiles instantiated, in kGemmBlockN order
+template <int PREC>
+cudaError_t launch_p(const GemmArgs& a, int sm_count, cudaStream_t st) {
+  switch (a.bn) {
+    case 128: return launch_t<PREC, 128>(a, sm_count, st);
+    case 112: return launch_t<PREC, 112>(a, sm_count, st);
+    case 96: return launch_t<PREC, 96>(a, sm_count, st);
+    case 80: return launch_t<PREC, 80>(a, sm_count, st);
+    case 64: return launch_t<PREC, 64>(a, sm_count, st);
+    case 48: return launch_t<PREC, 48>(a, sm_count, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <int PREC>
+cudaError_t prepare_p() {
+  cudaError_t e = cudaSuccess;
+  for (cudaError_t x : {prepare_t<PREC, 128>(), prepare_t<PREC, 112>(), prepare_t<PREC, 96>(), prepare_t<PREC, 80>(),
+                        prepare_t<PREC, 64>(), prepare_t<PREC, 48>()})
+    if (e == cudaSuccess) e = x;
+  return e;
 }
 
 // A single warp waits on an mbarrier that nothing completes, with the same
@@ -564,23 +628,25 @@ cudaError_t launch_bounded_wait_probe(uint32_t* status, uint64_t limit_ns, cudaS
   return cudaGetLastError();
 }
 
-int gemm_block_n() { return BN; }
+bool gemm_bn_supported(int bn) {
+  for (int b : kGemmBlockN)
+    if (b == bn) return true;
+  return false;
+}
 
 cudaError_t gemm_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, Layout<1>::SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Layout<2>::SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_gemm_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, Layout<3>::SMEM);
+  cudaError_t e = prepare_p<1>();
+  if (e == cudaSuccess) e = prepare_p<2>();
+  if (e == cudaSuccess) e = prepare_p<3>();
   return e;
 }
 int gemm_k_block(int prec) { return prec == 3 ? Cfg<3>::KB : Cfg<1>::KB; }
 
 cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st) {
   switch (a.prec) {
-    case 1: return launch_t<1>(a, sm_count, st);
-    case 2: return launch_t<2>(a, sm_count, st);
-    case 3: return launch_t<3>(a, sm_count, st);
+    case 1: return launch_p<1>(a, sm_count, st);
+    case 2: return launch_p<2>(a, sm_count, st);
+    case 3: return launch_p<3>(a, sm_count, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -152,7 +152,7 @@ extern "C" qtpu_status qtpu_pairwise_contract_noalloc(const double* A, const dou
   if (!ok || (uint64_t)batch * M * N > 0x7FFFFFFFull) return fail(QTPU_ENOTSUP, "noalloc: shape too large");
   GemmArgs g;
   if (!make_operand_map(&g.maps.a[0], s + a_off, 3, batch, M, K, Kp, 128) ||
-      !make_operand_map(&g.maps.b[0], s + b_off, 3, batch, N, K, Kp, gemm_block_n()))
+      !make_operand_map(&g.maps.b[0], s + b_off, 3, batch, N, K, Kp, g.bn))
     return fail(QTPU_ECUDA, "noalloc: cuTensorMapEncodeTiled failed");
   g.C = s + c_off;
   g.batch = batch;

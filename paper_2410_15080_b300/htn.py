@@ -21,7 +21,7 @@ PREC = {"fp64": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3}
 QTPU_QT, QTPU_CT = 0, 1
 
 SYMBOLS = ["qtpu_htn_create", "qtpu_htn_add_tensor", "qtpu_htn_set_output", "qtpu_htn_plan",
-           "qtpu_htn_plan_info", "qtpu_htn_lowering_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats",
+           "qtpu_htn_plan_info", "qtpu_htn_autotune", "qtpu_htn_lowering_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats",
            "qtpu_htn_exec_stats", "qtpu_htn_launch_features", "qtpu_htn_profile_launches", "qtpu_htn_contract",
            "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_contract_batch_ex", "qtpu_htn_batch_info", "qtpu_htn_contract_slices", "qtpu_htn_sync", "qtpu_htn_selftest_timeout", "qtpu_htn_destroy",
            "qtpu_htn_profile", "qtpu_htn_profile_read", "qtpu_pairwise_contract_noalloc",
@@ -159,10 +159,21 @@ class HTN:
 
     def plan(self, prec: str = "bf16x3", max_intermediate_bytes: int = 0, n_slices: int = 0,
              slice_dim: int = 0, seed: int = 0, n_candidates: int = 0, reuse_bytes: int = 0,
-             cost_model: int = 0, cost_model_path: str | None = None):
-        o = PlanOpts(max_intermediate_bytes, n_slices, slice_dim, PREC[prec], cost_model, seed, None, n_candidates,
+             cost_model: int = 0, cost_model_path: str | None = None, autotune_table: str | None = None):
+        """autotune_table: GEMM tile table file (None: the measured table next
+        to the library if present; "": the padding rule alone)."""
+        o = PlanOpts(max_intermediate_bytes, n_slices, slice_dim, PREC[prec], cost_model, seed,
+                     None if autotune_table is None else autotune_table.encode(), n_candidates,
                      reuse_bytes, cost_model_path.encode() if cost_model_path else None)
         self._check(self._L.qtpu_htn_plan(self._h, C.byref(o)))
+
+    def autotune(self, table_path: str, reps: int = 5, device: int = -1) -> int:
+        """Time every valid GEMM tile choice of the lowered plan on `device`
+        (-1: the handle's) and merge the fastest per problem into
+        `table_path`; returns the number of problems timed."""
+        n = C.c_int(0)
+        self._check(self._L.qtpu_htn_autotune(self._h, device, table_path.encode(), reps, C.byref(n)))
+        return n.value
 
     def plan_info(self) -> str:
         need = C.c_size_t(0)

@@ -335,3 +335,77 @@ def test_launch_features_of_the_lowered_launch_list():
         h2.plan("bf16x3", cost_model=1)
     assert ei.value.status == QTPU_ENOTSUP
     h2.close()
+
+
+def _gemm_launches(h):
+    """batch, M, N, K and bn of every GEMM launch of the lowered plan"""
+    out = []
+    for line in h.lowering_info().splitlines():
+        f = line.split()
+        if len(f) > 2 and f[2] == "gemm":
+            out.append({k: int(v) for k, v in (w.split("=", 1) for w in f if "=" in w)
+                        if k in ("batch", "M", "N", "K", "bn")})
+    return out
+
+
+def _one_gemm_net(b=2, m=300, n=200, k=333):
+    A = np.zeros((b, m, k))
+    B = np.zeros((b, k, n))
+    return synth.HTN([synth.Tensor("QT", (0, 1, 3), A), synth.Tensor("QT", (0, 3, 2), B)], (0, 1, 2))
+
+
+def test_tile_table_sets_orientation_and_n_tile(tmp_path):
+    """A tile table entry (keyed either way round) decides the GEMM's
+    orientation and N tile; without one the padding rule decides."""
+    net = _one_gemm_net()
+    for swap, bn in [(0, 48), (1, 80), (1, 128), (0, 112)]:
+        path = tmp_path / "t.txt"
+        path.write_text(f"# comment\n3 2 300 200 333 : {swap} {bn} 0.1 0.2\n3 2 200 300 333 : {1 - swap} {bn}\n")
+        h = _host_handle(net, autotune_table=str(path))
+        g = _gemm_launches(h)
+        h.close()
+        assert len(g) == 1 and g[0]["bn"] == bn and g[0]["M"] == (200 if swap else 300), g
+    # padding rule: M = 300 -> 3 row tiles, N = 200 -> 2 tiles of 112
+    # columns, 6 x (112 + 128); 128-column tiles weigh 6 x 256, and 300 along
+    # the N tile takes 2 row tiles x 3 tiles of 112 (or 4 of 80)
+    h = _host_handle(net, autotune_table="")
+    g = _gemm_launches(h)
+    h.close()
+    assert g[0]["bn"] == 112 and g[0]["M"] == 300
+
+
+def test_malformed_tile_table_is_rejected(tmp_path):
+    net = _one_gemm_net()
+    for text in ["3 2 300 200 333 : 1 100\n", "3 2 300 200 : 1 128\n", "3 2 300 200 333 : 2 128\n"]:
+        path = tmp_path / "bad.txt"
+        path.write_text(text)
+        with pytest.raises(htn.QtpuError) as e:
+            _host_handle(net, autotune_table=str(path))
+        assert e.value.status == htn.QTPU_EINVAL
+    with pytest.raises(htn.QtpuError) as e:
+        _host_handle(net, autotune_table=str(tmp_path / "missing.txt"))
+    assert e.value.status == htn.QTPU_EINVAL
+
+
+def test_autotune_needs_a_device_handle(tmp_path):
+    h = _host_handle(_one_gemm_net())
+    with pytest.raises(htn.QtpuError) as e:
+        h.autotune(str(tmp_path / "t.txt"))
+    h.close()
+    assert e.value.status == htn.QTPU_ENOTSUP
+
+
+def test_padding_rule_on_the_100_qubit_plan():
+    """The 4-pair GEMMs of the 100-qubit plan (m = 216, n = 7776) run with
+    the 7776 side along the 128-row tiles and 216 in two 112-column tiles;
+    the 1296 x 1296 steps keep 128 columns (11 x 11 tiles of 256 against
+    11 x 12 of 240), the 144 x 5184 steps take 80."""
+    net = synth.ring_chords_htn(materialize=False)
+    h = _host_handle(net, max_intermediate_bytes=8 << 30, n_slices=1024, slice_dim=4, n_candidates=256,
+                     autotune_table="")
+    g = _gemm_launches(h)
+    h.close()
+    shapes = {(x["M"], x["N"], x["K"], x["bn"]) for x in g}
+    assert (7776, 216, 216, 112) in shapes
+    assert (1296, 1296, 576, 128) in shapes
+    assert (5184, 144, 36, 80) in shapes

@@ -1,0 +1,119 @@
+"""GEMM tiles on the GPU: every orientation and N tile of the tensor-core GEMM
+(forced through a tile table) against FP64 numpy matmul, in the three
+tensor-core precisions; and the tile autotuner (qtpu_htn_autotune) writing
+a table that a later plan follows, with the result still matching the
+oracle."""
+import numpy as np
+import pytest
+
+import synth
+from tests.gpu_util import REL_TOL, oracle_value, rel_err, to_device
+
+pytestmark = pytest.mark.gpu
+
+BNS = (128, 112, 96, 80, 64, 48)
+PREC_CODE = {"tf32": 1, "3xtf32": 2, "bf16x3": 3}
+TOL = {"bf16x3": REL_TOL, "3xtf32": 1e-5, "tf32": 1e-2}
+# ragged M/N against 128-row tiles and every N tile; K = 333 and 1100 end
+# inside a k-block (the K-steps past K are skipped) and K = 1100 takes two
+# accumulator chunks in BF16x3
+SHAPES = [(3, 300, 200, 333), (2, 520, 144, 1100), (4, 216, 776, 216)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_15080_b300 import build
+    build.build()
+
+
+def _gemm_lines(h):
+    """batch, M, N, K and bn of every GEMM launch of the lowered plan"""
+    out = []
+    for line in h.lowering_info().splitlines():
+        f = line.split()
+        if len(f) > 2 and f[2] == "gemm":
+            d = {}
+            for w in f:
+                if "=" in w:
+                    k, v = w.split("=", 1)
+                    if k in ("batch", "M", "N", "K", "bn"):
+                        d[k] = int(v)
+            out.append(d)
+    return out
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=[str(s) for s in SHAPES])
+@pytest.mark.parametrize("prec", ["bf16x3", "3xtf32", "tf32"])
+def test_every_orientation_and_n_tile(shape, prec, tmp_path):
+    import torch
+    from paper_2410_15080_b300 import from_network
+    b, m, n, k = shape
+    rng = np.random.default_rng(sum(shape))
+    A = rng.uniform(-1, 1, (b, m, k))
+    B = rng.uniform(-1, 1, (b, k, n))
+    net = synth.HTN([synth.Tensor("QT", (0, 1, 3), A), synth.Tensor("QT", (0, 3, 2), B)], (0, 1, 2))
+    ref = np.matmul(A, B).ravel()
+    dev = to_device(net)
+    seen = set()
+    for swap in (0, 1):
+        for bn in BNS:
+            # the entry keyed both ways, so it applies whichever operand the
+            # plan takes first (the other key's swap is the complement)
+            path = tmp_path / f"t_{swap}_{bn}.txt"
+            p = PREC_CODE[prec]
+            path.write_text(f"{p} {b} {m} {n} {k} : {swap} {bn}\n{p} {b} {n} {m} {k} : {1 - swap} {bn}\n")
+            h = from_network(dev, net.output, prec=prec, autotune_table=str(path))
+            g = _gemm_lines(h)
+            assert len(g) == 1 and g[0]["bn"] == bn and g[0]["M"] == (n if swap else m), g
+            out = h.contract()
+            h.sync()
+            torch.cuda.synchronize()
+            err = rel_err(out.cpu().numpy(), ref)
+            h.close()
+            assert err <= TOL[prec], (swap, bn, err)
+            seen.add((swap, bn))
+    assert len(seen) == 12
+
+
+def test_autotune_writes_a_table_the_plan_follows(tmp_path):
+    """The mid-size ring (8 QTs of [64][144][144], 6 tensor-core steps):
+    autotune its plan, re-plan with the table, contract, compare with the
+    oracle."""
+    import torch
+    from paper_2410_15080_b300 import from_network
+    net = synth.ring_htn()
+    dev = to_device(net)
+    path = tmp_path / "tiles.txt"
+    h = from_network(dev, net.output, prec="bf16x3", autotune_table="")
+    n = h.autotune(str(path), reps=3)
+    h.close()
+    assert n >= 1
+    rows = {}
+    for line in path.read_text().splitlines():
+        if line.startswith("#"):
+            continue
+        key, val = line.split(":")
+        kk = tuple(int(x) for x in key.split())
+        sw, bn, ms, ms_rule, ms_base = val.split()
+        assert int(bn) in BNS and int(sw) in (0, 1)
+        # the padding rule's choice and the 128-column one are among those timed
+        assert 0 < float(ms) <= min(float(ms_rule), float(ms_base))
+        rows[kk] = (int(sw), int(bn))
+    assert len(rows) == n
+    h2 = from_network(dev, net.output, prec="bf16x3", autotune_table=str(path))
+    # every GEMM launch runs its problem's tuned choice (or is a fixed
+    # 128-column producer of a fused split)
+    for g in _gemm_lines(h2):
+        match = [(sw, bn) for (p, b, m, n_, k), (sw, bn) in rows.items()
+                 if p == 3 and b == g["batch"] and k == g["K"] and {m, n_} == {g["M"], g["N"]}
+                 and g["M"] == (n_ if sw else m)]
+        assert any(bn == g["bn"] for _, bn in match) or g["bn"] == 128, (g, rows)
+    out = h2.contract()
+    h2.sync()
+    torch.cuda.synchronize()
+    err = rel_err(out.cpu().numpy(), oracle_value(net))
+    h2.close()
+    assert err <= REL_TOL
