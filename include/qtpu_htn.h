@@ -73,7 +73,9 @@ typedef enum {
   QTPU_PREC_BF16X3 = 3  /* tensor cores, 3-piece BF16 split, 6 products       */
 } qtpu_prec;
 
-typedef enum { QTPU_QT = 0, QTPU_CT = 1 } qtpu_kind; /* informational */
+/* informational for contraction (both kinds contract alike); QPD sampling
+ * samples rank-1 CTs between two QTs (qtpu_htn_qpd_sample) */
+typedef enum { QTPU_QT = 0, QTPU_CT = 1 } qtpu_kind;
 
 typedef struct qtpu_plan_opts {
   uint64_t max_intermediate_bytes; /* 0 = no limit; 8 bytes per entry         */
@@ -295,9 +297,13 @@ qtpu_status qtpu_htn_contract_host(qtpu_htn* h, const void* const* host_ptrs,
                                    double* host_out);
 
 /* Contract n planned networks (of any shapes) and write dev_out[i] for each.
- * All n contractions run as ONE CUDA graph.  Every network whose launches are
- * all gathers (unsliced, no tensor-core step) becomes a set of tasks of one
- * persistent kernel: its blocks claim work units (256 outputs of a launch, or
+ * All n contractions run as ONE CUDA graph.  Small networks whose launches
+ * are all gathers (unsliced, no tensor-core step, no launch above 2^16 terms)
+ * can become tasks of one persistent kernel -- by default when they are at
+ * least 3/4 of the batch (a launch-bound batch; on B300 a batch of 512 such
+ * networks ran 2.5x faster so, while in a batch bound by networks with
+ * tensor-core steps it lengthened the batch by 2.5 %): its blocks claim work
+ * units (256 outputs of a launch, or
  * one output of a long sum) in task order, level by level across the
  * networks, and each unit first waits -- bounded by a time limit -- until the
  * same network's previous launch is complete.  The other networks' launches
@@ -313,8 +319,10 @@ qtpu_status qtpu_htn_contract_batch(qtpu_htn* const* hs, int n,
                                     double* const* dev_out, void* cuda_stream);
 
 typedef struct {
-  int persistent;            /* 1 (default): the persistent kernel for the
-                                gather-only networks; 0: graph branches only */
+  int persistent;            /* 2 (default): the persistent kernel for the
+                                small gather-only networks when they are at
+                                least 3/4 of the batch; 1: always for them;
+                                0: graph branches only                       */
   uint64_t wait_limit_ns;    /* bound of the persistent kernel's dependency
                                 waits; 0 = 2 s, at most 10 s                 */
   int test_stall_network;    /* test hook: >= 0 makes one dependency of that
@@ -356,6 +364,61 @@ qtpu_status qtpu_htn_sync(qtpu_htn* h);
  * qtpu_htn_sync returns QTPU_ETIMEOUT.  Nothing faults, traps or hangs, and
  * the handle stays usable. */
 qtpu_status qtpu_htn_selftest_timeout(qtpu_htn* h, uint64_t limit_ns);
+
+/* ---- QPD sampling and h-TN simplification (section 4.3; Step 1 of
+ * section 6.1) ----
+ * A gate-cut CT is a rank-1 tensor added with kind QTPU_CT whose index is
+ * carried by exactly two QTs (kind QTPU_QT) and by no other tensor, and is
+ * not an output index.  A group is the set of gate-cut CTs between the same
+ * two QTs (tensor ids a < b); groups are ordered by (a, b), the CTs of a
+ * group by tensor id.  Wire-cut tensors (rank 2) and every other tensor are
+ * not sampled.
+ *
+ * qtpu_htn_qpd_groups: the number of groups of the network (works on
+ * host-only handles). */
+qtpu_status qtpu_htn_qpd_groups(const qtpu_htn* h, int* n_groups);
+
+/* Sample the network into a new, unplanned network *out on the same device
+ * and stream, with the same output indices:
+ *  1. each group is fused: one CT over one new index (id = the largest id of
+ *     the network + 1 + group number), its entries the tensor product of the
+ *     group's CTs (the first CT's index slowest), products in FP64 left to
+ *     right; in each of the two QTs the group's axes become one axis at the
+ *     place of the first of them (groups applied in order);
+ *  2. each fused CT c (length D) is sampled s_qpd times: draw j of group x
+ *     takes u = dev_uniforms[x * s_qpd + j] (uniform in [0, 1), FP64, on the
+ *     device, n_groups * s_qpd of them, read only during this call) and
+ *     picks the first i with P_i > u * gamma, where P_i = |c_0| + ... + |c_i|
+ *     is accumulated left to right in FP64 and gamma = P_{D-1} (the last
+ *     nonzero entry if there is none); the sampled CT is
+ *     c'_i = sign(c_i) * ((gamma * count_i) / s_qpd);
+ *  3. values never drawn are dropped: the fused CT keeps the drawn values in
+ *     ascending order, and both QTs are copied (dtype kept, C order)
+ *     restricted to them.
+ * The contraction of *out is an unbiased estimate of the source's.  Tensor
+ * order of *out: the source's tensors other than the group CTs, in order
+ * (untouched ones borrowed: the source's device memory must stay valid while
+ * *out is used), then the fused CTs in group order.  *out owns the device
+ * memory of its fused CTs and truncated QTs (freed by qtpu_htn_destroy); the
+ * copies run on the stream after this call returns, which waits only for the
+ * kept sizes (one small device-to-host copy).  QTPU_EINVAL on s_qpd outside
+ * 1..2^32 or NULL arguments, QTPU_ENOTSUP on a host-only handle, more than 8
+ * CTs in a group or a fused length of 2^31 or more, QTPU_ENOMEM /
+ * QTPU_ECUDA on device errors. */
+qtpu_status qtpu_htn_qpd_sample(const qtpu_htn* h, uint64_t s_qpd, const double* dev_uniforms, qtpu_htn** out);
+
+/* For a network made by qtpu_htn_qpd_sample: per group x < max, the fused
+ * length before sampling and the number of values kept; *n_groups receives
+ * the number of groups (0 for any other network). */
+qtpu_status qtpu_htn_qpd_info(const qtpu_htn* h, int max, int64_t* dim_before, int64_t* dim_kept, int* n_groups);
+
+/* The network's tensors: their number, and tensor t's rank, index ids, dims,
+ * element strides, dtype, kind and device pointer (each output may be NULL;
+ * the arrays need max_rank >= rank entries, else QTPU_EINVAL). */
+qtpu_status qtpu_htn_num_tensors(const qtpu_htn* h, int* n);
+qtpu_status qtpu_htn_tensor_info(const qtpu_htn* h, int t, int max_rank, int* rank, int64_t* index_ids,
+                                 int64_t* dims, int64_t* strides, qtpu_dtype* dtype, qtpu_kind* kind,
+                                 const void** dev_ptr);
 
 qtpu_status qtpu_htn_destroy(qtpu_htn* h);
 

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <set>
@@ -18,6 +19,7 @@
 
 #include "../../include/qtpu_htn.h"
 #include "exec.h"
+#include "qpd.h"
 #include "planner.h"
 
 using namespace qtpu;
@@ -40,6 +42,11 @@ struct qtpu_htn {
   cudaStream_t up_stream = nullptr;
   std::vector<cudaEvent_t> leaf_ev;
   cudaEvent_t up_start = nullptr;
+  // a network made by qtpu_htn_qpd_sample: the device memory it owns (its
+  // fused CTs, truncated QTs and sampling scratch) and, per group, the fused
+  // length before sampling and the values kept
+  std::vector<void*> owned;
+  std::vector<std::pair<int64_t, int64_t>> qpd;
 };
 
 // message of the last failed create or allocation-free call, per thread
@@ -53,6 +60,43 @@ static qtpu_status fail(qtpu_htn* h, qtpu_status s, const std::string& msg) {
   if (h) h->err = msg;
   return s;
 }
+
+namespace {
+// QPD sampling groups (section 4.3): the gate-cut CTs (rank 1, kind CT,
+// index on exactly two QTs and nothing else, not an output index) between
+// the same QT pair, pairs ascending, CTs ascending within a pair.
+struct QpdGroupHost {
+  int qa = -1, qb = -1;
+  std::vector<int> cts;
+  std::vector<int64_t> ids, dims;
+  int64_t D = 1;
+};
+std::vector<QpdGroupHost> qpd_groups_of(const qtpu_htn* h) {
+  std::map<int64_t, std::vector<int>> carriers;
+  for (size_t t = 0; t < h->leaves.size(); ++t)
+    for (int64_t i : h->leaves[t].ids) carriers[i].push_back((int)t);
+  const std::set<int64_t> outs(h->output.begin(), h->output.end());
+  std::map<std::pair<int, int>, QpdGroupHost> by_pair;
+  for (size_t t = 0; t < h->leaves.size(); ++t) {
+    const Leaf& L = h->leaves[t];
+    if (L.kind != QTPU_CT || L.ids.size() != 1 || outs.count(L.ids[0])) continue;
+    std::vector<int> others;
+    for (int u : carriers[L.ids[0]])
+      if (u != (int)t) others.push_back(u);
+    if (others.size() != 2 || h->leaves[others[0]].kind != QTPU_QT || h->leaves[others[1]].kind != QTPU_QT) continue;
+    const int a = std::min(others[0], others[1]), b = std::max(others[0], others[1]);
+    QpdGroupHost& G = by_pair[{a, b}];
+    G.qa = a, G.qb = b;
+    G.cts.push_back((int)t);
+    G.ids.push_back(L.ids[0]);
+    G.dims.push_back(L.dims[0]);
+    G.D *= L.dims[0];
+  }
+  std::vector<QpdGroupHost> out;
+  for (auto& kv : by_pair) out.push_back(kv.second);
+  return out;
+}
+}  // namespace
 
 extern "C" {
 
@@ -127,6 +171,7 @@ qtpu_status qtpu_htn_add_tensor(qtpu_htn* h, qtpu_kind kind, int rank, const int
   }
   L.dt = dtype == QTPU_F64 ? DT_F64 : DT_F32;
   L.ptr = dev_ptr;
+  L.kind = kind;
   h->leaves.push_back(L);
   if (tensor_id) *tensor_id = (int)h->leaves.size() - 1;
   return QTPU_OK;
@@ -227,6 +272,223 @@ qtpu_status qtpu_htn_autotune(qtpu_htn* h, int device, const char* table_path, i
   m = save_tile_table(table_path, t);
   if (!m.empty()) return fail(h, QTPU_EINVAL, m);
   if (n_problems) *n_problems = n;
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_qpd_groups(const qtpu_htn* h, int* n_groups) {
+  if (!h || !n_groups) return QTPU_EINVAL;
+  *n_groups = (int)qpd_groups_of(h).size();
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_qpd_sample(const qtpu_htn* h, uint64_t s_qpd, const double* dev_uniforms, qtpu_htn** out) {
+  if (!out) return QTPU_EINVAL;
+  *out = nullptr;
+  if (!h) return QTPU_EINVAL;
+  qtpu_htn* hs = const_cast<qtpu_htn*>(h);  // only its error message is written
+  if (h->host_only) return fail(hs, QTPU_ENOTSUP, "host-only handle cannot sample");
+  if (s_qpd < 1 || s_qpd > (1ull << 32)) return fail(hs, QTPU_EINVAL, "s_qpd outside 1..2^32");
+  const std::vector<QpdGroupHost> gs = qpd_groups_of(h);
+  const int ng = (int)gs.size();
+  if (ng > 0 && !dev_uniforms) return fail(hs, QTPU_EINVAL, "dev_uniforms NULL");
+  int64_t total = 0, maxD = 0;
+  for (const QpdGroupHost& G : gs) {
+    if ((int)G.cts.size() > kQpdMaxCts) return fail(hs, QTPU_ENOTSUP, "more than 8 gate cuts between two QTs");
+    if (G.D > 0x7FFFFFFF) return fail(hs, QTPU_ENOTSUP, "fused CT of 2^31 entries or more");
+    total += G.D;
+    maxD = std::max(maxD, G.D);
+  }
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return fail(hs, QTPU_ECUDA, cudaGetErrorString(e));
+  qtpu_htn* nh = new (std::nothrow) qtpu_htn();
+  if (!nh) return fail(hs, QTPU_ENOMEM, "host allocation failed");
+  nh->device = h->device;
+  nh->stream = h->stream;
+  nh->host_only = false;
+  nh->output = h->output;
+  cudaStream_t st = h->stream;
+  auto bail = [&](cudaError_t x, const char* what) {
+    cudaGetLastError();
+    qtpu_htn_destroy(nh);
+    return fail(hs, x == cudaErrorMemoryAllocation ? QTPU_ENOMEM : QTPU_ECUDA,
+                std::string("qpd_sample: ") + what + ": " + cudaGetErrorString(x));
+  };
+  auto dalloc = [&](size_t bytes, void** p) {
+    *p = nullptr;
+    cudaError_t x = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    if (x == cudaSuccess) nh->owned.push_back(*p);
+    return x;
+  };
+  // scratch: groups, fused values, prefix sums, gamma, counts, kept values
+  // and coefficients, kept counts (8-byte fields first)
+  const size_t n8 = (size_t)std::max<int64_t>(total, 1);
+  const size_t off_groups = 0, off_fused = (sizeof(QpdGroup) * std::max(ng, 1) + 255) / 256 * 256;
+  const size_t off_prefix = off_fused + n8 * 8, off_gamma = off_prefix + n8 * 8;
+  const size_t off_keptct = off_gamma + std::max(ng, 1) * 8, off_counts = off_keptct + n8 * 8;
+  const size_t off_keptidx = off_counts + n8 * 4, off_nkept = off_keptidx + n8 * 4;
+  const size_t scratch_bytes = off_nkept + std::max(ng, 1) * 4;
+  void* scratch = nullptr;
+  if ((e = dalloc(scratch_bytes, &scratch)) != cudaSuccess) return bail(e, "scratch");
+  uint8_t* sb = (uint8_t*)scratch;
+  QpdGroup* d_groups = (QpdGroup*)(sb + off_groups);
+  double* fused = (double*)(sb + off_fused);
+  double* prefix = (double*)(sb + off_prefix);
+  double* gamma = (double*)(sb + off_gamma);
+  double* kept_ct = (double*)(sb + off_keptct);
+  uint32_t* counts = (uint32_t*)(sb + off_counts);
+  int32_t* kept_idx = (int32_t*)(sb + off_keptidx);
+  int32_t* n_kept = (int32_t*)(sb + off_nkept);
+  std::vector<QpdGroup> hg(ng);
+  int64_t base = 0;
+  for (int x = 0; x < ng; ++x) {
+    QpdGroup& G = hg[x];
+    G.n_ct = (int)gs[x].cts.size();
+    G.D = gs[x].D;
+    G.base = base;
+    base += G.D;
+    for (int j = 0; j < G.n_ct; ++j) {
+      const Leaf& L = h->leaves[gs[x].cts[j]];
+      G.ct[j] = L.ptr;
+      G.dt[j] = L.dt;
+      G.dim[j] = L.dims[0];
+      G.stride[j] = L.strides[0];
+    }
+  }
+  std::vector<int32_t> kept(ng, 0);
+  if (ng > 0) {
+    if ((e = cudaMemcpyAsync(d_groups, hg.data(), sizeof(QpdGroup) * ng, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return bail(e, "group upload");
+    if ((e = cudaMemsetAsync(counts, 0, (size_t)total * 4, st)) != cudaSuccess) return bail(e, "counts");
+    if ((e = qpd_fuse(d_groups, ng, maxD, fused, st)) != cudaSuccess) return bail(e, "fuse");
+    if ((e = qpd_draw(d_groups, ng, fused, prefix, gamma, dev_uniforms, s_qpd, counts, st)) != cudaSuccess)
+      return bail(e, "draw");
+    if ((e = qpd_compact(d_groups, ng, fused, gamma, counts, s_qpd, kept_idx, kept_ct, n_kept, st)) != cudaSuccess)
+      return bail(e, "compact");
+    // the kept counts fix the new shapes
+    if ((e = cudaMemcpyAsync(kept.data(), n_kept, (size_t)ng * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return bail(e, "kept counts");
+  }
+  int sm = 148;
+  cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, h->device);
+  int64_t max_id = -1;
+  for (const Leaf& L : h->leaves)
+    for (int64_t i : L.ids) max_id = std::max(max_id, i);
+  std::set<int> dropped;
+  for (const QpdGroupHost& G : gs) dropped.insert(G.cts.begin(), G.cts.end());
+  for (size_t t = 0; t < h->leaves.size(); ++t) {
+    if (dropped.count((int)t)) continue;
+    const Leaf& L = h->leaves[t];
+    std::vector<int> mine;
+    for (int x = 0; x < ng; ++x)
+      if (gs[x].qa == (int)t || gs[x].qb == (int)t) mine.push_back(x);
+    if (mine.empty()) {
+      nh->leaves.push_back(L);  // borrowed
+      continue;
+    }
+    // the axis list of the truncated copy: groups applied in order, each
+    // group's axes replaced by its fused axis at the first of their places
+    struct Ax {
+      int64_t id, dim, stride;
+      int group;
+    };
+    std::vector<Ax> ax;
+    for (size_t a = 0; a < L.ids.size(); ++a) ax.push_back({L.ids[a], L.dims[a], L.strides[a], -1});
+    for (int x : mine) {
+      std::vector<size_t> pos;
+      for (int64_t id : gs[x].ids)
+        for (size_t a = 0; a < ax.size(); ++a)
+          if (ax[a].group < 0 && ax[a].id == id) pos.push_back(a);
+      const size_t first = *std::min_element(pos.begin(), pos.end());
+      std::vector<Ax> nx;
+      for (size_t a = 0; a < ax.size(); ++a) {
+        if (a == first) nx.push_back({max_id + 1 + x, kept[x], 0, x});
+        if (std::find(pos.begin(), pos.end(), a) == pos.end()) nx.push_back(ax[a]);
+      }
+      ax = nx;
+    }
+    QpdGather g;
+    g.src = L.ptr;
+    g.dt = L.dt;
+    g.n_axes = (int)ax.size();
+    g.n_out = 1;
+    for (size_t a = 0; a < ax.size(); ++a) {
+      g.dim[a] = ax[a].dim;
+      g.stride[a] = ax[a].stride;
+      g.n_out *= ax[a].dim;
+      if (ax[a].group < 0) continue;
+      const int x = ax[a].group;
+      std::vector<int64_t> qstride;
+      for (int64_t id : gs[x].ids)
+        for (size_t b = 0; b < L.ids.size(); ++b)
+          if (L.ids[b] == id) qstride.push_back(L.strides[b]);
+      void* tab = nullptr;
+      if ((e = dalloc((size_t)kept[x] * 8, &tab)) != cudaSuccess) return bail(e, "table");
+      if ((e = qpd_table((int)gs[x].dims.size(), gs[x].dims.data(), qstride.data(), kept_idx + hg[x].base, kept[x],
+                         (int64_t*)tab, st)) != cudaSuccess)
+        return bail(e, "table");
+      g.table[a] = (const int64_t*)tab;
+    }
+    void* dst = nullptr;
+    if ((e = dalloc((size_t)g.n_out * (L.dt == DT_F64 ? 8 : 4), &dst)) != cudaSuccess) return bail(e, "QT copy");
+    g.dst = dst;
+    if ((e = qpd_gather(g, sm, st)) != cudaSuccess) return bail(e, "gather");
+    Leaf N;
+    N.kind = L.kind;
+    N.dt = L.dt;
+    N.ptr = dst;
+    int64_t stc = 1;
+    N.strides.assign(ax.size(), 1);
+    for (int a = (int)ax.size() - 1; a >= 0; --a) N.strides[a] = stc, stc *= ax[a].dim;
+    for (const Ax& a : ax) N.ids.push_back(a.id), N.dims.push_back(a.dim);
+    nh->leaves.push_back(N);
+  }
+  for (int x = 0; x < ng; ++x) {
+    Leaf C;
+    C.kind = QTPU_CT;
+    C.dt = DT_F64;
+    C.ptr = kept_ct + hg[x].base;
+    C.ids = {max_id + 1 + x};
+    C.dims = {(int64_t)kept[x]};
+    C.strides = {1};
+    nh->leaves.push_back(C);
+    nh->qpd.push_back({gs[x].D, (int64_t)kept[x]});
+  }
+  for (const Leaf& L : nh->leaves)
+    for (size_t a = 0; a < L.ids.size(); ++a) nh->dims.set(L.ids[a], L.dims[a]);
+  *out = nh;
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_qpd_info(const qtpu_htn* h, int max, int64_t* dim_before, int64_t* dim_kept, int* n_groups) {
+  if (!h || !n_groups || max < 0 || (max > 0 && (!dim_before || !dim_kept))) return QTPU_EINVAL;
+  *n_groups = (int)h->qpd.size();
+  for (int x = 0; x < max && x < (int)h->qpd.size(); ++x) dim_before[x] = h->qpd[x].first, dim_kept[x] = h->qpd[x].second;
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_tensor_info(const qtpu_htn* h, int t, int max_rank, int* rank, int64_t* index_ids,
+                                 int64_t* dims, int64_t* strides, qtpu_dtype* dtype, qtpu_kind* kind,
+                                 const void** dev_ptr) {
+  if (!h || !rank) return QTPU_EINVAL;
+  if (t < 0 || t >= (int)h->leaves.size()) return QTPU_EINVAL;
+  const Leaf& L = h->leaves[t];
+  *rank = (int)L.ids.size();
+  if (max_rank < *rank && (index_ids || dims || strides)) return QTPU_EINVAL;
+  for (int a = 0; a < *rank; ++a) {
+    if (index_ids) index_ids[a] = L.ids[a];
+    if (dims) dims[a] = L.dims[a];
+    if (strides) strides[a] = L.strides[a];
+  }
+  if (dtype) *dtype = L.dt == DT_F64 ? QTPU_F64 : QTPU_F32;
+  if (kind) *kind = (qtpu_kind)L.kind;
+  if (dev_ptr) *dev_ptr = L.ptr;
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_num_tensors(const qtpu_htn* h, int* n) {
+  if (!h || !n) return QTPU_EINVAL;
+  *n = (int)h->leaves.size();
   return QTPU_OK;
 }
 
@@ -500,17 +762,23 @@ void batch_forget(qtpu_htn* h) {
 // network's previous task.  Returns a CUDA error; eligible[i] is set for the
 // networks the kernel contracts.
 cudaError_t batch_build_tasks(BatchGraph* b, qtpu_htn* const* hs, int n, double* const* dev_out, int stall,
-                              std::vector<char>* eligible) {
+                              int mode, std::vector<char>* eligible) {
   std::vector<std::vector<BatchTask>> per(n);
   eligible->assign(n, 0);
   size_t max_len = 0;
-  for (int i = 0; i < n; ++i) {
-    if (exec_batch_tasks(&hs[i]->ex, hs[i]->leaves, dev_out[i], &per[i])) {
-      (*eligible)[i] = 1;
+  int n_el = 0;
+  for (int i = 0; i < n; ++i)
+    if (exec_batch_tasks(&hs[i]->ex, hs[i]->leaves, dev_out[i], &per[i])) (*eligible)[i] = 1, ++n_el;
+  // mode 2: only a batch that is mostly small networks (launch-bound)
+  if (mode == 2 && 4 * n_el < 3 * n) {
+    eligible->assign(n, 0);
+    return cudaSuccess;
+  }
+  for (int i = 0; i < n; ++i)
+    if ((*eligible)[i]) {
       max_len = std::max(max_len, per[i].size());
       b->n_persistent++;
     }
-  }
   std::vector<BatchTask> tasks;
   std::vector<uint64_t> start(1, 0);
   std::vector<int> last(n, -1);
@@ -549,8 +817,9 @@ qtpu_status qtpu_htn_contract_batch_ex(qtpu_htn* const* hs, int n, double* const
                                        const qtpu_batch_opts* opts) {
   if (n < 0 || (n > 0 && (!hs || !dev_out))) return QTPU_EINVAL;
   if (n == 0) return QTPU_OK;
-  qtpu_batch_opts o{1, 0, -1};
+  qtpu_batch_opts o{2, 0, -1};
   if (opts) o = *opts;
+  if (o.persistent < 0 || o.persistent > 2) return fail(hs[0], QTPU_EINVAL, "persistent must be 0, 1 or 2");
   if (o.wait_limit_ns == 0) o.wait_limit_ns = 2000000000ull;
   if (o.wait_limit_ns > 10000000000ull) return fail(hs[0], QTPU_EINVAL, "wait limit above 10 s");
   for (int i = 0; i < n; ++i) {
@@ -573,7 +842,7 @@ qtpu_status qtpu_htn_contract_batch_ex(qtpu_htn* const* hs, int n, double* const
   BatchGraph* b = nullptr;
   for (BatchGraph* c : g_batch.cache)
     if (c->device == dev && (int)c->hs.size() == n && std::equal(c->hs.begin(), c->hs.end(), hs) &&
-        std::equal(c->outs.begin(), c->outs.end(), dev_out) && c->persistent == (o.persistent != 0) &&
+        std::equal(c->outs.begin(), c->outs.end(), dev_out) && c->persistent == o.persistent &&
         c->limit_ns == o.wait_limit_ns && c->stall == o.test_stall_network)
       b = c;
   if (!b) {
@@ -581,12 +850,12 @@ qtpu_status qtpu_htn_contract_batch_ex(qtpu_htn* const* hs, int n, double* const
     b->hs.assign(hs, hs + n);
     b->outs.assign(dev_out, dev_out + n);
     b->device = dev;
-    b->persistent = o.persistent != 0;
+    b->persistent = o.persistent;
     b->limit_ns = o.wait_limit_ns;
     b->stall = o.test_stall_network;
     std::vector<char> eligible(n, 0);
     if (b->persistent) {
-      e = batch_build_tasks(b, hs, n, dev_out, o.test_stall_network, &eligible);
+      e = batch_build_tasks(b, hs, n, dev_out, o.test_stall_network, o.persistent, &eligible);
       if (e != cudaSuccess) {
         cudaGetLastError();
         batch_free(b);
@@ -716,6 +985,11 @@ qtpu_status qtpu_htn_destroy(qtpu_htn* h) {
   for (cudaEvent_t ev : h->leaf_ev) cudaEventDestroy(ev);
   if (h->up_start) cudaEventDestroy(h->up_start);
   if (h->up_stream) cudaStreamDestroy(h->up_stream);
+  if (!h->owned.empty()) {
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);  // gathers into owned memory may be in flight
+    for (void* p : h->owned) cudaFree(p);
+  }
   delete h;
   return QTPU_OK;
 }

@@ -21,6 +21,7 @@ struct Leaf {
   std::vector<int64_t> dims, strides;  // strides in elements
   int dt = DT_F64;
   const void* ptr = nullptr;
+  int kind = 0;  // QTPU_QT or QTPU_CT
 };
 
 enum KernelClass { KC_CONTRACT = 0, KC_SPLIT = 1, KC_GEMM = 2, KC_REDUCE = 3, KC_COUNT = 4 };

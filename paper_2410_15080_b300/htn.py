@@ -21,7 +21,8 @@ PREC = {"fp64": 0, "tf32": 1, "3xtf32": 2, "bf16x3": 3}
 QTPU_QT, QTPU_CT = 0, 1
 
 SYMBOLS = ["qtpu_htn_create", "qtpu_htn_add_tensor", "qtpu_htn_set_output", "qtpu_htn_plan",
-           "qtpu_htn_plan_info", "qtpu_htn_autotune", "qtpu_htn_lowering_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats",
+           "qtpu_htn_plan_info", "qtpu_htn_autotune", "qtpu_htn_qpd_groups", "qtpu_htn_qpd_sample",
+           "qtpu_htn_qpd_info", "qtpu_htn_num_tensors", "qtpu_htn_tensor_info", "qtpu_htn_lowering_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats",
            "qtpu_htn_exec_stats", "qtpu_htn_launch_features", "qtpu_htn_profile_launches", "qtpu_htn_contract",
            "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_contract_batch_ex", "qtpu_htn_batch_info", "qtpu_htn_contract_slices", "qtpu_htn_sync", "qtpu_htn_selftest_timeout", "qtpu_htn_destroy",
            "qtpu_htn_profile", "qtpu_htn_profile_read", "qtpu_pairwise_contract_noalloc",
@@ -277,6 +278,64 @@ class HTN:
     def sync(self):
         self._check(self._L.qtpu_htn_sync(self._h))
 
+    # ---- QPD sampling and h-TN simplification (section 4.3)
+    def qpd_groups(self) -> int:
+        """Number of gate-cut groups (rank-1 CTs between the same two QTs)."""
+        n = C.c_int(0)
+        self._check(self._L.qtpu_htn_qpd_groups(self._h, C.byref(n)))
+        return n.value
+
+    def qpd_sample(self, s_qpd: int, uniforms) -> "HTN":
+        """The sampled, truncated network (unplanned, same output): uniforms is
+        a CUDA float64 tensor of qpd_groups() * s_qpd values in [0, 1),
+        group-major."""
+        ptr = 0
+        if uniforms is not None:
+            import torch
+            assert uniforms.device.type == "cuda" and uniforms.dtype == torch.float64 and uniforms.is_contiguous()
+            assert uniforms.numel() >= self.qpd_groups() * s_qpd
+            ptr = uniforms.data_ptr()
+        out = C.c_void_p()
+        self._check(self._L.qtpu_htn_qpd_sample(self._h, C.c_uint64(s_qpd), C.c_void_p(ptr), C.byref(out)))
+        h = HTN.__new__(HTN)
+        h._L, h._h, h.device = self._L, out, self.device
+        h._keep = [self]  # the untouched tensors are borrowed from this network
+        n = C.c_int(0)
+        h._check(self._L.qtpu_htn_num_tensors(out, C.byref(n)))
+        h.n_tensors = n.value
+        return h
+
+    def qpd_info(self):
+        """[(fused length, values kept)] per group of a sampled network."""
+        n = C.c_int(0)
+        self._check(self._L.qtpu_htn_qpd_info(self._h, 0, None, None, C.byref(n)))
+        a, b = (C.c_int64 * max(1, n.value))(), (C.c_int64 * max(1, n.value))()
+        self._check(self._L.qtpu_htn_qpd_info(self._h, n.value, a, b, C.byref(n)))
+        return [(a[i], b[i]) for i in range(n.value)]
+
+    def tensor_info(self, t: int) -> dict:
+        r = C.c_int(0)
+        ids, dims, st = (C.c_int64 * 16)(), (C.c_int64 * 16)(), (C.c_int64 * 16)()
+        dt, kd, ptr = C.c_int(0), C.c_int(0), C.c_void_p()
+        self._check(self._L.qtpu_htn_tensor_info(self._h, t, 16, C.byref(r), ids, dims, st, C.byref(dt),
+                                                 C.byref(kd), C.byref(ptr)))
+        n = r.value
+        return {"inds": tuple(ids[:n]), "dims": tuple(dims[:n]), "strides": tuple(st[:n]),
+                "dtype": "f64" if dt.value == QTPU_F64 else "f32", "kind": kd.value, "ptr": ptr.value or 0}
+
+    def tensor_view(self, t: int):
+        """Tensor t as a CUDA torch tensor viewing the library's (or the
+        caller's) device memory -- valid while this network lives."""
+        import torch
+        i = self.tensor_info(t)
+        es = 8 if i["dtype"] == "f64" else 4
+
+        class _View:
+            __cuda_array_interface__ = {
+                "shape": i["dims"], "typestr": "<f8" if es == 8 else "<f4", "data": (i["ptr"], True),
+                "strides": tuple(x * es for x in i["strides"]), "version": 2}
+        return torch.as_tensor(_View(), device=f"cuda:{self.device}")
+
     def close(self):
         if self._h:
             self._L.qtpu_htn_destroy(self._h)
@@ -289,13 +348,16 @@ class HTN:
             pass
 
 
-def contract_batch(htns: Sequence[HTN], outs, stream: int | None = None, persistent: bool = True,
+def contract_batch(htns: Sequence[HTN], outs, stream: int | None = None, persistent: bool | None = None,
                    wait_limit_ns: int = 0, test_stall_network: int = -1):
-    """Contract many planned networks in one CUDA graph (see the C header)."""
+    """Contract many planned networks in one CUDA graph (see the C header).
+    persistent: None = the library's choice (the persistent kernel when the
+    small gather-only networks are at least 3/4 of the batch), True = always
+    for them, False = graph branches only."""
     L = lib()
     hs = (C.c_void_p * len(htns))(*[h._h.value for h in htns])
     ps = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
-    o = BatchOpts(1 if persistent else 0, wait_limit_ns, test_stall_network)
+    o = BatchOpts(2 if persistent is None else (1 if persistent else 0), wait_limit_ns, test_stall_network)
     st = L.qtpu_htn_contract_batch_ex(hs, len(htns), ps, C.c_void_p(stream or 0), C.byref(o))
     if st != QTPU_OK:
         raise QtpuError(st, "contract_batch failed: " + htns[0]._L.qtpu_last_error(htns[0]._h).decode())

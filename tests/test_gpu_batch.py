@@ -49,7 +49,7 @@ def test_batch_of_uneven_networks():
     # the persistent kernel for the gather-only networks
     for o in outs:
         o.fill_(float("nan"))
-    contract_batch(hs, outs)
+    contract_batch(hs, outs, persistent=True)
     torch.cuda.synchronize()
     for h in hs:
         h.sync()
@@ -62,7 +62,7 @@ def test_batch_of_uneven_networks():
     # replay of the cached graph: the same bits
     for o in outs:
         o.fill_(float("nan"))
-    contract_batch(hs, outs)
+    contract_batch(hs, outs, persistent=True)
     torch.cuda.synchronize()
     for o, s in zip(outs, first):
         np.testing.assert_array_equal(o.cpu().numpy(), s)
@@ -74,7 +74,8 @@ def test_batch_of_512_networks():
     """The batched workload at its full size: 512 random networks (2-12
     subcircuits, 2-20 cuts, k 1-64, FP32/FP64, QTs up to 2^22 entries) in one
     graph with the persistent kernel; every output matches the graph-branch
-    schedule and a sample of 32 matches the FP64 oracle."""
+    schedule and a sample of 32 matches the FP64 oracle.  By default (about
+    half the networks small) the batch runs as graph branches only."""
     import torch
     from paper_2410_15080_b300 import batch_info, contract_batch
     nets = synth.random_batch(512, seed=0, max_qt_entries=QT_CAP)
@@ -82,12 +83,18 @@ def test_batch_of_512_networks():
     outs = [torch.empty(h.output_size(), dtype=torch.float64, device="cuda") for h in hs]
     ref = [torch.empty_like(o) for o in outs]
     contract_batch(hs, ref, persistent=False)
-    contract_batch(hs, outs)
+    contract_batch(hs, outs, persistent=True)
     torch.cuda.synchronize()
     for h in hs:
         h.sync()
     info = batch_info(hs, outs)
     assert info["persistent_networks"] >= 200
+    d = [torch.empty_like(o) for o in outs]
+    contract_batch(hs, d)
+    torch.cuda.synchronize()
+    assert batch_info(hs, d)["persistent_networks"] == 0
+    for o, r in zip(d, ref):
+        assert torch.equal(o, r)
     for o, r in zip(outs, ref):
         assert rel_err(o.cpu().numpy(), r.cpu().numpy()) <= 2 * REL_TOL
     for i in range(0, 512, 16):
@@ -110,7 +117,8 @@ def test_persistent_wait_gives_up_and_reports_timeout():
     contract_batch(hs, outs)
     torch.cuda.synchronize()
     info = batch_info(hs, outs)
-    assert info["persistent_networks"] == len(nets)  # small: every network is gather-only
+    # small: every network is gather-only, so the default takes them all
+    assert info["persistent_networks"] == len(nets)
     stalled = 3
     contract_batch(hs, outs, wait_limit_ns=50_000_000, test_stall_network=stalled)
     torch.cuda.synchronize()
