@@ -48,6 +48,9 @@ WORKLOADS = {
     "100q-free": "100-qubit ring+chords h-TN: 12 QTs, 28 gate + 12 wire cuts, k=64, peak intermediate <= 8 GB, "
                  "slices chosen by the planner, order: best of 256 planner candidates by exact FLOPs",
     "gemm": "one pairwise step C[b,m,n] = sum_k A[b,m,k] B[b,k,n] of the given --shape (FP64 leaves)",
+    "qpd": "QPD sampling + h-TN simplification (section 4.3) of the 100-qubit ring+chords h-TN (20 gate-cut "
+           "groups: 12 ring edges with 1 gate cut, 8 chords with 2) for s_QPD draws per group, then planning and "
+           "contraction of the sampled network",
     "batch": "512 independent random h-TNs (ring / 2-D grid, 2-12 subcircuits, 2-20 cuts, k 1-64, FP32/FP64, "
              "QTs <= 2^22 entries, peak intermediate <= 2^23 entries) in one CUDA graph (small gather-only "
              "networks in one persistent kernel when they are >= 3/4 of the batch, graph branches otherwise)",
@@ -452,6 +455,88 @@ def run_batch(args, rank, world):
         h.close()
 
 
+def run_qpd(args, rank, world):
+    """QPD sampling of the 100-qubit network for several draw counts: the
+    qtpu_htn_qpd_sample call (fuse, draw, truncate, QT copies) timed with CUDA
+    events, then the sampled network planned and contracted."""
+    import torch
+    import synth
+    from paper_2410_15080_b300.htn import HTN, QTPU_CT, QTPU_QT
+    dev = torch.device("cuda", torch.cuda.current_device())
+    net = synth.ring_chords_htn(k=args.observables)
+    h = HTN(dev.index)
+    for t in net.tensors:
+        h.add_tensor(t.inds, data=torch.from_numpy(np.ascontiguousarray(t.data)).to(dev),
+                     kind=QTPU_CT if t.kind == "CT" else QTPU_QT)
+    h.set_output(net.output)
+    ng = h.qpd_groups()
+    qt_bytes = sum(t.data.nbytes for t in net.tensors if t.kind == "QT")
+    peaks = load_peaks()
+    gen = torch.Generator(device=dev).manual_seed(0)
+    sweep = []
+    for s_qpd in [int(x) for x in args.s_qpd.split(",")]:
+        u = torch.rand(ng * s_qpd, dtype=torch.float64, device=dev, generator=gen)
+        ts, hs = [], None
+        for r in range(args.warmup + args.steps):
+            if hs is not None:
+                hs.close()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            hs = h.qpd_sample(s_qpd, u)
+            e1.record()
+            torch.cuda.synchronize()
+            if r >= args.warmup:
+                ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        info = hs.qpd_info()
+        kept_qt = 0
+        for t in range(hs.n_tensors):
+            ti = hs.tensor_info(t)
+            if ti["kind"] == QTPU_QT:
+                kept_qt += int(np.prod(ti["dims"])) * (8 if ti["dtype"] == "f64" else 4)
+        t0 = time.perf_counter()
+        hs.plan(args.prec, max_intermediate_bytes=8 << 30, n_candidates=64)
+        plan_s = time.perf_counter() - t0
+        st = hs.exec_stats()
+        for _ in range(2):
+            hs.contract()
+        tc = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record()
+            hs.contract()
+            c1.record()
+            torch.cuda.synchronize()
+            tc.append(c0.elapsed_time(c1))
+        hs.sync()
+        sweep.append({"s_qpd": s_qpd, "sample_ms": ms, "groups_kept_of": [list(x) for x in info],
+                      "qt_bytes_after": kept_qt, "qt_bytes_before": qt_bytes,
+                      "plan_s": plan_s, "contract_ms": statistics.median(tc),
+                      "contract_flops": st["flops_executed"]})
+        hs.close()
+    h.close()
+    base = sweep[-1]
+    line = {
+        "metric": "QPD sample + simplify (ms per call) of the 100-qubit h-TN", "value": sweep[0]["sample_ms"],
+        "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sweep[0]["sample_ms"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS["qpd"], "s_qpd": sweep[0]["s_qpd"], "groups": ng},
+        "roofline": {"bound": "hbm", "kernel": "whole qtpu_htn_qpd_sample call (QT copies dominate)",
+                     "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": None, "traffic": None},
+        "sweep": sweep, "gpu_launches": None,
+    }
+    # the QT copies read and write the kept entries of the copied QTs
+    moved = 2 * base["qt_bytes_after"]
+    line["roofline"]["achieved"] = moved / (base["sample_ms"] * 1e-3) / 1e9
+    line["roofline"]["frac"] = line["roofline"]["achieved"] / peaks["hbm_gbs"]
+    line["roofline"]["note"] = f"2 x kept QT bytes at s_qpd = {base['s_qpd']} / call time"
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def run_ours(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -674,6 +759,7 @@ def main():
     ap.add_argument("--shape", default="8x1024x1024x1024", help="gemm workload: batch x M x N x K")
     ap.add_argument("--extras", default="all", choices=["all", "none"],
                     help="none: only the warm-up and timed contractions (for profiler launch lists and captures)")
+    ap.add_argument("--s-qpd", default="10,100,1000,100000", help="qpd workload: draws per group, comma-separated")
     ap.add_argument("--observables", type=int, default=64,
                     help="100q workloads: size k of the observable index (64 = the benchmark; smaller for ncu captures)")
     args = ap.parse_args()
@@ -691,6 +777,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     if args.workload == "batch":
         run_batch(args, rank, world)
+    elif args.workload == "qpd":
+        run_qpd(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1:

@@ -332,7 +332,7 @@ class HTN:
 
         class _View:
             __cuda_array_interface__ = {
-                "shape": i["dims"], "typestr": "<f8" if es == 8 else "<f4", "data": (i["ptr"], True),
+                "shape": i["dims"], "typestr": "<f8" if es == 8 else "<f4", "data": (i["ptr"], False),
                 "strides": tuple(x * es for x in i["strides"]), "version": 2}
         return torch.as_tensor(_View(), device=f"cuda:{self.device}")
 
