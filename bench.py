@@ -51,6 +51,9 @@ WORKLOADS = {
     "qpd": "QPD sampling + h-TN simplification (section 4.3) of the 100-qubit ring+chords h-TN (20 gate-cut "
            "groups: 12 ring edges with 1 gate cut, 8 chords with 2) for s_QPD draws per group, then planning and "
            "contraction of the sampled network",
+    "knit": "naive circuit knitting (Eq. knitting: every global instance summed, FP64) against the h-TN "
+            "contraction of the same network: rings of 3, 4, 5 subcircuits with 1 gate + 1 wire cut per edge, "
+            "k = 8 observables",
     "batch": "512 independent random h-TNs (ring / 2-D grid, 2-12 subcircuits, 2-20 cuts, k 1-64, FP32/FP64, "
              "QTs <= 2^22 entries, peak intermediate <= 2^23 entries) in one CUDA graph (small gather-only "
              "networks in one persistent kernel when they are >= 3/4 of the batch, graph branches otherwise)",
@@ -537,6 +540,76 @@ def run_qpd(args, rank, world):
         print(json.dumps(line))
 
 
+def run_knit(args, rank, world):
+    """Naive knitting (qtpu_htn_knit_naive) vs the contraction, on rings of
+    growing size; both timed with CUDA events after warm-up."""
+    import torch
+    import synth
+    from paper_2410_15080_b300.htn import HTN, QTPU_CT, QTPU_QT
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sweep = []
+    for n_sub in (3, 4, 5):
+        net = synth.ring_htn(n_sub=n_sub, gates_per_edge=1, wires_per_edge=1, k=8, seed=n_sub)
+        h = HTN(dev.index)
+        for t in net.tensors:
+            h.add_tensor(t.inds, data=torch.from_numpy(np.ascontiguousarray(t.data)).to(dev),
+                         kind=QTPU_CT if t.kind == "CT" else QTPU_QT)
+        h.set_output(net.output)
+        out, ninst = h.knit_naive()
+        reps = 3 if n_sub < 5 else 1
+        tn_ = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            h.knit_naive(out)
+            e1.record()
+            torch.cuda.synchronize()
+            tn_.append(e0.elapsed_time(e1))
+        naive = out.cpu().numpy()
+        h.plan("fp64")
+        for _ in range(3):
+            c = h.contract()
+        tc = []
+        for _ in range(5):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            c = h.contract()
+            e1.record()
+            torch.cuda.synchronize()
+            tc.append(e0.elapsed_time(e1))
+        h.sync()
+        rel = float(np.linalg.norm(c.cpu().numpy() - naive) / np.linalg.norm(naive))
+        n_t = len(net.tensors)
+        # FP64 operations of the naive sum: per instance and output, n_t - 1
+        # multiplies and one add
+        ops = ninst * len(naive) * n_t
+        ms_n = statistics.median(tn_)
+        sweep.append({"n_sub": n_sub, "cuts": 2 * n_sub, "instances": ninst, "outputs": len(naive),
+                      "naive_ms": ms_n, "naive_fp64_gops": ops / (ms_n * 1e-3) / 1e9,
+                      "contract_fp64_ms": statistics.median(tc), "speedup_of_contraction": ms_n / statistics.median(tc),
+                      "rel_diff": rel})
+        h.close()
+    last = sweep[-1]
+    # DMUL / DADD issue at the DFMA rate: half the FMA-counted FP64 peak
+    fp64_peak = 1050.0 / 2
+    line = {
+        "metric": "naive knitting vs h-TN contraction (time ratio) on a 5-subcircuit ring", "value":
+        last["speedup_of_contraction"], "unit": "x", "n_gpus": world, "steps": 1, "warmup": 1,
+        "ms_per_step": last["naive_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOADS["knit"]},
+        "roofline": {"bound": "alu", "kernel": "k_knit_terms", "achieved": last["naive_fp64_gops"],
+                     "peak": fp64_peak, "unit": "GFLOP/s", "frac": last["naive_fp64_gops"] / fp64_peak,
+                     "traffic": None,
+                     "peak_note": "FP64 multiplies and adds at the DFMA issue rate: half the measured FP64 "
+                                  "matmul rate (1.05 TFLOP/s FMA-counted, BASELINE.md)"},
+        "sweep": sweep, "gpu_launches": None,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def run_ours(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -779,6 +852,8 @@ def main():
         run_batch(args, rank, world)
     elif args.workload == "qpd":
         run_qpd(args, rank, world)
+    elif args.workload == "knit":
+        run_knit(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1:

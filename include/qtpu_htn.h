@@ -412,6 +412,20 @@ qtpu_status qtpu_htn_qpd_sample(const qtpu_htn* h, uint64_t s_qpd, const double*
  * the number of groups (0 for any other network). */
 qtpu_status qtpu_htn_qpd_info(const qtpu_htn* h, int max, int64_t* dim_before, int64_t* dim_kept, int* n_groups);
 
+/* Naive circuit knitting (Eq. knitting, section 2.1), the baseline the
+ * contraction is measured against: dev_out (FP64, output_size entries, the
+ * output in set_output order) receives, for each output entry, the sum over
+ * every global instance -- every assignment of every non-output index, the
+ * summed index ids in ascending order as one mixed-radix number, last
+ * fastest -- of the product of one entry of every tensor (QTs and CTs),
+ * products and sums in FP64, partial sums added in a fixed order.  The work
+ * is the product of all summed dimensions times the output size (returned in
+ * *n_instances as instances, may be NULL).  Works on any device handle,
+ * planned or not; runs on the handle's stream and returns when the sum is
+ * complete.  QTPU_ENOTSUP on a host-only handle, more than 32 tensors, 40
+ * summed or 8 output indices, 4e18 instances or 65535 outputs or more. */
+qtpu_status qtpu_htn_knit_naive(qtpu_htn* h, double* dev_out, double* n_instances);
+
 /* The network's tensors: their number, and tensor t's rank, index ids, dims,
  * element strides, dtype, kind and device pointer (each output may be NULL;
  * the arrays need max_rank >= rank entries, else QTPU_EINVAL). */

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -19,6 +20,7 @@
 
 #include "../../include/qtpu_htn.h"
 #include "exec.h"
+#include "knit.h"
 #include "qpd.h"
 #include "planner.h"
 
@@ -483,6 +485,77 @@ qtpu_status qtpu_htn_tensor_info(const qtpu_htn* h, int t, int max_rank, int* ra
   if (dtype) *dtype = L.dt == DT_F64 ? QTPU_F64 : QTPU_F32;
   if (kind) *kind = (qtpu_kind)L.kind;
   if (dev_ptr) *dev_ptr = L.ptr;
+  return QTPU_OK;
+}
+
+qtpu_status qtpu_htn_knit_naive(qtpu_htn* h, double* dev_out, double* n_instances) {
+  if (!h) return QTPU_EINVAL;
+  if (n_instances) *n_instances = 0;
+  if (h->host_only) return fail(h, QTPU_ENOTSUP, "host-only handle cannot contract");
+  if (!dev_out) return fail(h, QTPU_EINVAL, "dev_out NULL");
+  if (h->leaves.empty()) return fail(h, QTPU_ESTATE, "no tensors");
+  if ((int)h->leaves.size() > kKnitMaxT) return fail(h, QTPU_ENOTSUP, "more than 32 tensors");
+  for (int64_t i : h->output)
+    if (!h->dims.has(i)) return fail(h, QTPU_EINVAL, "output index " + std::to_string(i) + " is on no tensor");
+  const std::set<int64_t> outs(h->output.begin(), h->output.end());
+  std::set<int64_t> summed;
+  for (const Leaf& L : h->leaves)
+    for (int64_t i : L.ids)
+      if (!outs.count(i)) summed.insert(i);
+  if ((int)summed.size() > kKnitMaxSum) return fail(h, QTPU_ENOTSUP, "more than 40 summed indices");
+  if ((int)h->output.size() > kKnitMaxOut) return fail(h, QTPU_ENOTSUP, "more than 8 output indices");
+  KnitTable T;
+  T.n_t = (int)h->leaves.size();
+  T.n_sum = (int)summed.size();
+  T.n_outi = (int)h->output.size();
+  double ninst = 1, nout = 1;
+  for (int t = 0; t < T.n_t; ++t) T.ptr[t] = h->leaves[t].ptr, T.dt[t] = h->leaves[t].dt;
+  auto strides_of = [&](int64_t id, int64_t* row) {
+    for (int t = 0; t < T.n_t; ++t) {
+      const Leaf& L = h->leaves[t];
+      row[t] = 0;
+      for (size_t a = 0; a < L.ids.size(); ++a)
+        if (L.ids[a] == id) row[t] = L.strides[a];
+    }
+  };
+  int m = 0;
+  for (int64_t i : summed) {
+    T.dim[m] = h->dims.get(i);
+    ninst *= (double)T.dim[m];
+    strides_of(i, T.stride[m]);
+    ++m;
+  }
+  for (int a = 0; a < T.n_outi; ++a) {
+    T.out_dim[a] = h->dims.get(h->output[a]);
+    nout *= (double)T.out_dim[a];
+    strides_of(h->output[a], T.out_stride[a]);
+  }
+  if (ninst >= 4.0e18 || nout > 65535) return fail(h, QTPU_ENOTSUP, "instance or output count too large");
+  T.n_inst = (uint64_t)ninst;
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
+  int sm = 148;
+  cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, h->device);
+  // about 8 blocks per SM in all, at least 256 instances per block
+  uint64_t chunks = (uint64_t)std::ceil(sm * 8.0 / nout);
+  chunks = std::max<uint64_t>(1, std::min<uint64_t>(chunks, (T.n_inst + 255) / 256));
+  cudaStream_t st = h->stream;
+  KnitTable* dT = nullptr;
+  double* part = nullptr;
+  e = cudaMallocAsync((void**)&dT, sizeof(KnitTable), st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&part, (size_t)nout * chunks * 8, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dT, &T, sizeof(KnitTable), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_knit(dT, T.n_inst, (uint64_t)nout, part, chunks, dev_out, st);
+  // the table is copied from this stack frame: finish the copy before returning
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (dT) cudaFreeAsync(dT, st);
+  if (part) cudaFreeAsync(part, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, e == cudaErrorMemoryAllocation ? QTPU_ENOMEM : QTPU_ECUDA,
+                std::string("knit_naive: ") + cudaGetErrorString(e));
+  }
+  if (n_instances) *n_instances = ninst;
   return QTPU_OK;
 }
 

@@ -21,8 +21,9 @@
 //                  indices);
 //   k_qpd_gather   the truncated QT: every entry of the new C-order layout
 //                  read from the source QT through plain strides and the
-//                  fused tables (HBM-bound: one read and one write per kept
-//                  entry).
+//                  fused tables, the trailing axes' offsets tabulated once
+//                  per block in shared memory (HBM-bound: one read and one
+//                  write per kept entry).
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -133,18 +134,38 @@ __global__ void k_qpd_table(TableArgs a, const int32_t* __restrict__ kept_idx, i
   }
 }
 
+// Output axes [0, split) are the outer axes, [split, n_axes) the inner ones
+// (at most kQpdInner entries together).  Each block builds the source offsets
+// of the inner entries once in shared memory; then per outer row (grid-
+// stride) one offset from the outer coordinates, and the row's entries are
+// copied with contiguous writes.
+constexpr int kQpdInner = 4096;
+
 template <typename T>
-__global__ void k_qpd_gather(const __grid_constant__ QpdGather a) {
+__global__ void __launch_bounds__(256) k_qpd_gather(const __grid_constant__ QpdGather a, int split, int64_t inner) {
+  __shared__ int64_t tab[kQpdInner];
   const T* __restrict__ src = (const T*)a.src;
   T* __restrict__ dst = (T*)a.dst;
-  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < a.n_out; o += (int64_t)gridDim.x * blockDim.x) {
-    int64_t r = o, off = 0;
-    for (int m = a.n_axes - 1; m >= 0; --m) {
+  for (int64_t j = threadIdx.x; j < inner; j += blockDim.x) {
+    int64_t r = j, off = 0;
+    for (int m = a.n_axes - 1; m >= split; --m) {
       const int64_t i = r % a.dim[m];
       r /= a.dim[m];
       off += a.table[m] ? a.table[m][i] : i * a.stride[m];
     }
-    dst[o] = src[off];
+    tab[j] = off;
+  }
+  __syncthreads();
+  const int64_t rows = a.n_out / inner;
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    int64_t r = row, base = 0;
+    for (int m = split - 1; m >= 0; --m) {
+      const int64_t i = r % a.dim[m];
+      r /= a.dim[m];
+      base += a.table[m] ? a.table[m][i] : i * a.stride[m];
+    }
+    T* d = dst + row * inner;
+    for (int64_t j = threadIdx.x; j < inner; j += blockDim.x) d[j] = src[base + tab[j]];
   }
 }
 
@@ -187,13 +208,17 @@ cudaError_t qpd_table(int n_ct, const int64_t* dims, const int64_t* qstride, con
 cudaError_t qpd_gather(const QpdGather& a, int sm_count, cudaStream_t st) {
   if (a.n_out <= 0) return cudaSuccess;
   if (a.n_axes < 0 || a.n_axes > kQpdMaxAxes) return cudaErrorInvalidValue;
-  const int64_t b = (a.n_out + 255) / 256;
-  const int64_t cap = (int64_t)sm_count * 8;
-  const unsigned grid = (unsigned)(b < cap ? b : cap);
+  // the longest run of trailing axes within kQpdInner entries
+  int split = a.n_axes;
+  int64_t inner = 1;
+  while (split > 0 && inner * a.dim[split - 1] <= kQpdInner) inner *= a.dim[--split];
+  const int64_t rows = a.n_out / inner;
+  const int64_t cap = (int64_t)sm_count * 4;
+  const unsigned grid = (unsigned)(rows < cap ? rows : cap);
   if (a.dt == DT_F64)
-    k_qpd_gather<double><<<grid, 256, 0, st>>>(a);
+    k_qpd_gather<double><<<grid, 256, 0, st>>>(a, split, inner);
   else
-    k_qpd_gather<float><<<grid, 256, 0, st>>>(a);
+    k_qpd_gather<float><<<grid, 256, 0, st>>>(a, split, inner);
   return cudaGetLastError();
 }
 

@@ -22,7 +22,7 @@ QTPU_QT, QTPU_CT = 0, 1
 
 SYMBOLS = ["qtpu_htn_create", "qtpu_htn_add_tensor", "qtpu_htn_set_output", "qtpu_htn_plan",
            "qtpu_htn_plan_info", "qtpu_htn_autotune", "qtpu_htn_qpd_groups", "qtpu_htn_qpd_sample",
-           "qtpu_htn_qpd_info", "qtpu_htn_num_tensors", "qtpu_htn_tensor_info", "qtpu_htn_lowering_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats",
+           "qtpu_htn_qpd_info", "qtpu_htn_num_tensors", "qtpu_htn_tensor_info", "qtpu_htn_knit_naive", "qtpu_htn_lowering_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats",
            "qtpu_htn_exec_stats", "qtpu_htn_launch_features", "qtpu_htn_profile_launches", "qtpu_htn_contract",
            "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_contract_batch_ex", "qtpu_htn_batch_info", "qtpu_htn_contract_slices", "qtpu_htn_sync", "qtpu_htn_selftest_timeout", "qtpu_htn_destroy",
            "qtpu_htn_profile", "qtpu_htn_profile_read", "qtpu_pairwise_contract_noalloc",
@@ -157,6 +157,7 @@ class HTN:
 
     def set_output(self, inds: Sequence[int]):
         self._check(self._L.qtpu_htn_set_output(self._h, len(inds), _arr(inds)))
+        self._out_inds = list(inds)
 
     def plan(self, prec: str = "bf16x3", max_intermediate_bytes: int = 0, n_slices: int = 0,
              slice_dim: int = 0, seed: int = 0, n_candidates: int = 0, reuse_bytes: int = 0,
@@ -278,6 +279,28 @@ class HTN:
     def sync(self):
         self._check(self._L.qtpu_htn_sync(self._h))
 
+    def knit_naive(self, out=None):
+        """Naive circuit knitting (Eq. knitting): the FP64 sum over every global
+        instance; returns (output device tensor, number of instances)."""
+        import torch
+        n = 1
+        for i in self._output_dims():
+            n *= i
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=f"cuda:{self.device}")
+        ni = C.c_double(0)
+        self._check(self._L.qtpu_htn_knit_naive(self._h, C.c_void_p(out.data_ptr()), C.byref(ni)))
+        return out, ni.value
+
+    def _output_dims(self):
+        if not hasattr(self, "_out_inds"):
+            return []
+        dims = {}
+        for t in range(self.n_tensors):
+            i = self.tensor_info(t)
+            dims.update(zip(i["inds"], i["dims"]))
+        return [dims[x] for x in self._out_inds]
+
     # ---- QPD sampling and h-TN simplification (section 4.3)
     def qpd_groups(self) -> int:
         """Number of gate-cut groups (rank-1 CTs between the same two QTs)."""
@@ -299,6 +322,7 @@ class HTN:
         self._check(self._L.qtpu_htn_qpd_sample(self._h, C.c_uint64(s_qpd), C.c_void_p(ptr), C.byref(out)))
         h = HTN.__new__(HTN)
         h._L, h._h, h.device = self._L, out, self.device
+        h._out_inds = list(getattr(self, "_out_inds", []))
         h._keep = [self]  # the untouched tensors are borrowed from this network
         n = C.c_int(0)
         h._check(self._L.qtpu_htn_num_tensors(out, C.byref(n)))
