@@ -103,6 +103,10 @@ typedef struct qtpu_plan_opts {
                                       off); see qtpu_htn_plan                 */
   const char* cost_model_path;     /* cost_model = 1: weights file (NULL =
                                       costmodel_b300.bin next to the library) */
+  uint32_t search;                 /* order search (cost_model = 0 only):
+                                      0 = greedy (best of n_candidates by
+                                      plan FLOPs); 1 = hyper-search; 2 = the
+                                      exact tree alone (see qtpu_htn_plan)    */
 } qtpu_plan_opts;
 
 /* Create an empty network bound to CUDA device `device` and the CUDA stream
@@ -166,6 +170,22 @@ qtpu_status qtpu_htn_set_output(qtpu_htn* h, int n, const int64_t* index_ids);
  * changes a computed value: every plan is contracted by the same kernels.
  * QTPU_EINVAL if the weights file is missing or invalid, QTPU_ENOTSUP on a
  * host-only handle.
+ *
+ * Order search (search = 1 or 2): the exact tree contracts every small leaf
+ * (<= 256 entries: the CTs) first, in ascending id, into the lowest-id large
+ * leaf sharing an index with it, then finds the cheapest contraction tree
+ * over the tensors left (at most 16) by dynamic programming over subsets
+ * with the planner's step cost (ties to the smallest subset as a bit mask),
+ * emits it in post order and slices it like any plan; search = 2 returns it
+ * (QTPU_ENOTSUP above 16 tensors, 128 indices or a cost of 2^126), and its
+ * plan text ends with "search exact tensors=m".  search = 1 plans the exact
+ * tree (when possible) and n_candidates randomised greedy orders (64 if
+ * n_candidates <= 1) on the host cores in parallel, lowers each without
+ * device memory and keeps the one whose launch list executes the fewest
+ * FLOPs under slice reuse (ties: fewer plan FLOPs, then the exact tree, then
+ * the lower seed); its plan text ends with "search hyper candidates=N
+ * chosen=exact|seed:S executed_flops=F".  QTPU_EINVAL for search > 2 or
+ * search with cost_model = 1.
  *
  * GEMM tiles: each tensor-core step (a batched GEMM of the step's batch, m,
  * n and k index groups, section 4.2) runs with the 128-row M tile along m
@@ -399,9 +419,11 @@ qtpu_status qtpu_htn_qpd_groups(const qtpu_htn* h, int* n_groups);
  * order of *out: the source's tensors other than the group CTs, in order
  * (untouched ones borrowed: the source's device memory must stay valid while
  * *out is used), then the fused CTs in group order.  *out owns the device
- * memory of its fused CTs and truncated QTs (freed by qtpu_htn_destroy); the
- * copies run on the stream after this call returns, which waits only for the
- * kept sizes (one small device-to-host copy).  QTPU_EINVAL on s_qpd outside
+ * memory of its fused CTs and truncated QTs, taken from a per-device
+ * stream-ordered pool of the library that keeps freed memory for the next
+ * sampling (qtpu_htn_destroy returns it in stream order); the copies run on
+ * the stream after this call returns, which waits only for the kept sizes
+ * (one small device-to-host copy).  QTPU_EINVAL on s_qpd outside
  * 1..2^32 or NULL arguments, QTPU_ENOTSUP on a host-only handle, more than 8
  * CTs in a group or a fused length of 2^31 or more, QTPU_ENOMEM /
  * QTPU_ECUDA on device errors. */

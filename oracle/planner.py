@@ -240,6 +240,8 @@ def plan_text(plan, tensors_inds) -> str:
                  f"peak={peak}")
     if getattr(plan, "search", None):
         lines.append(f"search candidates={plan.search[0]} seed={plan.search[1]}")
+    if getattr(plan, "search_dp", None) is not None:
+        lines.append(f"search exact tensors={plan.search_dp}")
     return "\n".join(lines) + "\n"
 
 

@@ -73,6 +73,31 @@ struct QpdGroupHost {
   std::vector<int64_t> ids, dims;
   int64_t D = 1;
 };
+// Device memory of sampled networks comes from one stream-ordered pool per
+// device that keeps freed memory (release threshold: never), so repeated
+// sampling reuses it instead of mapping fresh pages on every call.
+cudaMemPool_t qpd_pool(int dev) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> g(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
 std::vector<QpdGroupHost> qpd_groups_of(const qtpu_htn* h) {
   std::map<int64_t, std::vector<int>> carriers;
   for (size_t t = 0; t < h->leaves.size(); ++t)
@@ -199,6 +224,8 @@ qtpu_status qtpu_htn_plan(qtpu_htn* h, const qtpu_plan_opts* opts) {
   if (opts) o = *opts;
   if (o.prec < QTPU_PREC_FP64 || o.prec > QTPU_PREC_BF16X3) return fail(h, QTPU_EINVAL, "bad precision");
   if (o.cost_model != 0 && o.cost_model != 1) return fail(h, QTPU_EINVAL, "cost_model must be 0 or 1");
+  if (o.search > 2) return fail(h, QTPU_EINVAL, "search must be 0, 1 or 2");
+  if (o.search && o.cost_model) return fail(h, QTPU_EINVAL, "search and cost_model exclude each other");
   if (o.cost_model == 1 && h->host_only)
     return fail(h, QTPU_ENOTSUP, "the learned cost model runs its perceptron on the device");
   for (int64_t i : h->output)
@@ -227,6 +254,15 @@ qtpu_status qtpu_htn_plan(qtpu_htn* h, const qtpu_plan_opts* opts) {
                                       &h->plan, &err);
     if (st != QTPU_OK) return fail(h, (qtpu_status)st, err);
     r = PLAN_OK;
+  } else if (o.search == 1) {
+    std::string err;
+    const int st = plan_hyper(li, h->dims, h->output, o, h->leaves, &tiles, &h->plan, &err);
+    if (st != QTPU_OK) return fail(h, (qtpu_status)st, err);
+    r = PLAN_OK;
+  } else if (o.search == 2) {
+    r = make_plan_exact(li, h->dims, h->output, o.max_intermediate_bytes, o.n_slices, o.slice_dim, &h->plan);
+    if (r == PLAN_TOO_MANY)
+      return fail(h, QTPU_ENOTSUP, "exact search: more than 16 tensors after absorption, 128 indices or 2^126");
   } else if (o.n_candidates > 1) {
     uint64_t chosen = 0;
     r = make_plan_best(li, h->dims, h->output, o.max_intermediate_bytes, o.n_slices, o.slice_dim, o.seed,
@@ -315,9 +351,14 @@ qtpu_status qtpu_htn_qpd_sample(const qtpu_htn* h, uint64_t s_qpd, const double*
     return fail(hs, x == cudaErrorMemoryAllocation ? QTPU_ENOMEM : QTPU_ECUDA,
                 std::string("qpd_sample: ") + what + ": " + cudaGetErrorString(x));
   };
+  cudaMemPool_t pool = qpd_pool(h->device);
+  if (!pool) {
+    qtpu_htn_destroy(nh);
+    return fail(hs, QTPU_ECUDA, "qpd_sample: memory pool");
+  }
   auto dalloc = [&](size_t bytes, void** p) {
     *p = nullptr;
-    cudaError_t x = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    cudaError_t x = cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 16), pool, st);
     if (x == cudaSuccess) nh->owned.push_back(*p);
     return x;
   };
@@ -1059,9 +1100,9 @@ qtpu_status qtpu_htn_destroy(qtpu_htn* h) {
   if (h->up_start) cudaEventDestroy(h->up_start);
   if (h->up_stream) cudaStreamDestroy(h->up_stream);
   if (!h->owned.empty()) {
+    // pool memory, freed in stream order after the work that uses it
     cudaSetDevice(h->device);
-    cudaStreamSynchronize(h->stream);  // gathers into owned memory may be in flight
-    for (void* p : h->owned) cudaFree(p);
+    for (void* p : h->owned) cudaFreeAsync(p, h->stream);
   }
   delete h;
   return QTPU_OK;

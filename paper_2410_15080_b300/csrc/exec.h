@@ -243,6 +243,11 @@ void set_global_error(const char* msg);
 int plan_by_cost_model(const std::vector<Inds>& li, const DimMap& dims, const Inds& output,
                        const qtpu_plan_opts& o, const std::vector<Leaf>& leaves, int device, void* stream,
                        const TileTable* tiles, Plan* chosen, std::string* err);
+// Hyper-search over the exact tree and randomised greedy candidates, ranked
+// by the FLOPs their lowered launch lists execute (search.cpp).  Returns a
+// qtpu_status.
+int plan_hyper(const std::vector<Inds>& li, const DimMap& dims, const Inds& output, const qtpu_plan_opts& o,
+               const std::vector<Leaf>& leaves, const TileTable* tiles, Plan* chosen, std::string* err);
 // Sum the timed launches per class (after a stream sync) and reset.
 std::string exec_profile_read(Executor* ex, double* ms, int64_t* launches, double* flops, double* bytes);
 // Every timed launch (launch index, ms) in order (after a stream sync), and reset.

@@ -22,6 +22,7 @@
 #include "planner.h"
 
 #include <algorithm>
+#include <functional>
 #include <map>
 #include <set>
 #include <sstream>
@@ -222,8 +223,14 @@ int make_plan(const std::vector<Inds>& leaves, const DimMap& dims, const Inds& o
   p.final_inds = live.begin()->second;
   for (int64_t i : p.final_inds)
     if (!contains(output, i)) p.final_sum.push_back(i);
+  return finish_plan(dims, output, max_bytes, n_slices, slice_dim, &p);
+}
 
-  // slicing on the fixed tree
+// Slicing on the fixed tree, then the per-slice accounting.
+int finish_plan(const DimMap& dims, const Inds& output, uint64_t max_bytes, uint64_t n_slices, int64_t slice_dim,
+                Plan* plan) {
+  Plan& p = *plan;
+  Ctx c{&dims};
   std::set<int64_t> sl;
   U256 nsl(1);
   std::vector<int64_t> all_ix = dims.ids();
@@ -330,7 +337,166 @@ std::string plan_text(const Plan& p) {
   o << "cost flops_per_slice=" << p.flops_per_slice.str() << " flops_total=" << p.flops_total.str()
     << " peak=" << p.peak.str() << "\n";
   if (p.search) o << "search candidates=" << p.search << " seed=" << p.search_seed << "\n";
+  if (p.search_exact >= 0) o << "search exact tensors=" << p.search_exact << "\n";
+  if (!p.search_note.empty()) o << p.search_note << "\n";
   return o.str();
+}
+
+// ------------------------------------------------------------ exact search
+namespace {
+using u128 = unsigned __int128;
+constexpr u128 kCostCap = (u128)1 << 126;
+
+struct Bits {
+  uint64_t w[2] = {0, 0};
+  void set(int i) { w[i >> 6] |= 1ull << (i & 63); }
+  bool any() const { return w[0] | w[1]; }
+  Bits operator|(const Bits& o) const { Bits r; r.w[0] = w[0] | o.w[0]; r.w[1] = w[1] | o.w[1]; return r; }
+  Bits operator&(const Bits& o) const { Bits r; r.w[0] = w[0] & o.w[0]; r.w[1] = w[1] & o.w[1]; return r; }
+  Bits operator~() const { Bits r; r.w[0] = ~w[0]; r.w[1] = ~w[1]; return r; }
+};
+
+// product of the dims of the set bits; false when it reaches the cap
+bool prod_bits(const Bits& b, const std::vector<int64_t>& dim, u128* out) {
+  u128 r = 1;
+  for (int q = 0; q < 2; ++q) {
+    uint64_t x = b.w[q];
+    while (x) {
+      const int i = q * 64 + __builtin_ctzll(x);
+      x &= x - 1;
+      r *= (u128)dim[i];
+      if (r >= kCostCap) return false;
+    }
+  }
+  *out = r;
+  return true;
+}
+
+// one pairwise step with the planner's keep rule (count-based)
+void apply_step(std::map<int, Inds>& live, std::map<int64_t, int>& count, int x, int y, int nxt, Plan* p) {
+  const Inds& ia = live[x];
+  const Inds& ib = live[y];
+  std::set<int64_t> keep;
+  for (int64_t i : ia) if (count[i] - 1 - (contains(ib, i) ? 1 : 0) > 0) keep.insert(i);
+  for (int64_t i : ib) if (count[i] - 1 - (contains(ia, i) ? 1 : 0) > 0) keep.insert(i);
+  PlanStep st;
+  st.x = x; st.y = y; st.out = nxt;
+  classify(ia, ib, keep, &st);
+  for (int64_t i : std::set<int64_t>(ia.begin(), ia.end())) count[i]--;
+  for (int64_t i : std::set<int64_t>(ib.begin(), ib.end())) count[i]--;
+  live.erase(x);
+  live.erase(y);
+  Inds ni = st.out_inds();
+  live[nxt] = ni;
+  for (int64_t i : std::set<int64_t>(ni.begin(), ni.end())) count[i]++;
+  p->steps.push_back(st);
+  p->tensor_inds.push_back(ni);
+}
+}  // namespace
+
+int make_plan_exact(const std::vector<Inds>& leaves, const DimMap& dims, const Inds& output, uint64_t max_bytes,
+                    uint64_t n_slices, int64_t slice_dim, Plan* plan) {
+  Plan& p = *plan;
+  p = Plan();
+  p.n_leaves = (int)leaves.size();
+  p.output = output;
+  p.tensor_inds = leaves;
+  const int n = (int)leaves.size();
+  std::map<int, Inds> live;
+  std::map<int64_t, int> count;
+  for (int t = 0; t < n; ++t) {
+    live[t] = leaves[t];
+    for (int64_t i : std::set<int64_t>(leaves[t].begin(), leaves[t].end())) count[i]++;
+  }
+  for (int64_t i : output) count[i]++;
+  // 1. absorption of the small leaves
+  std::vector<int> small, large;
+  for (int t = 0; t < n; ++t) {
+    double sz = 1;
+    for (int64_t i : leaves[t]) sz *= (double)dims.get(i);
+    (sz <= 256.0 ? small : large).push_back(t);
+  }
+  std::map<int, int> cur;
+  for (int t : large) cur[t] = t;
+  int nxt = n;
+  for (int t : small) {
+    int h = -1;
+    for (int q : large) {
+      bool share = false;
+      for (int64_t i : leaves[t]) if (contains(leaves[q], i)) { share = true; break; }
+      if (share) { h = q; break; }  // large is ascending: the lowest id
+    }
+    if (h < 0) continue;
+    const int x = std::min(cur[h], t), y = std::max(cur[h], t);
+    apply_step(live, count, x, y, nxt, &p);
+    cur[h] = nxt++;
+  }
+  // 2. exact tree over the live tensors
+  std::vector<int> ids;
+  for (auto& kv : live) ids.push_back(kv.first);
+  const int m = (int)ids.size();
+  if (m > kExactMax) return PLAN_TOO_MANY;
+  std::vector<int64_t> all = dims.ids();
+  if (all.size() > 128) return PLAN_TOO_MANY;
+  std::map<int64_t, int> pos;
+  std::vector<int64_t> dim(all.size());
+  for (size_t q = 0; q < all.size(); ++q) pos[all[q]] = (int)q, dim[q] = dims.get(all[q]);
+  Bits outb;
+  for (int64_t i : output) outb.set(pos[i]);
+  std::vector<Bits> carried(m);
+  for (int j = 0; j < m; ++j)
+    for (int64_t i : live[ids[j]]) carried[j].set(pos[i]);
+  const uint32_t full = m ? (1u << m) - 1 : 0;
+  std::vector<Bits> uni(full + 1), tup(full + 1);
+  std::vector<u128> size(full + 1, 0), cost(full + 1, 0);
+  std::vector<uint32_t> split(full + 1, 0);
+  for (uint32_t s = 1; s <= full; ++s) uni[s] = uni[s & (s - 1)] | carried[__builtin_ctz(s)];
+  auto kept = [&](uint32_t s) { return uni[s] & (uni[full ^ s] | outb); };
+  for (uint32_t s = 1; s <= full; ++s) {
+    tup[s] = (s & (s - 1)) ? kept(s) : carried[__builtin_ctz(s)];
+    if (!prod_bits(tup[s], dim, &size[s])) return PLAN_TOO_MANY;
+  }
+  for (uint32_t s = 1; s <= full; ++s) {
+    if (!(s & (s - 1))) continue;
+    const uint32_t low = s & (~s + 1), rest = s ^ low;
+    const Bits keep = kept(s);
+    bool have = false;
+    u128 best = 0;
+    uint32_t besta = 0;
+    for (uint32_t sub = rest;; sub = (sub - 1) & rest) {
+      const uint32_t a = low | sub;
+      if (a != s) {
+        const uint32_t b = s ^ a;
+        const Bits& ia = tup[a];
+        const Bits& ib = tup[b];
+        const Bits sa = ia & ~ib & ~keep, sb = ib & ~ia & ~keep;
+        u128 core;
+        if (!prod_bits((ia | ib) & ~(sa | sb), dim, &core)) return PLAN_TOO_MANY;
+        u128 f = 2 * core + (sa.any() ? size[a] : 0) + (sb.any() ? size[b] : 0);
+        const u128 c = cost[a] + cost[b] + f;
+        if (c >= kCostCap) return PLAN_TOO_MANY;
+        if (!have || c < best || (c == best && a < besta)) best = c, besta = a, have = true;
+      }
+      if (sub == 0) break;
+    }
+    cost[s] = best;
+    split[s] = besta;
+  }
+  // 3. the tree in post order
+  std::function<int(uint32_t)> build = [&](uint32_t s) -> int {
+    if (!(s & (s - 1))) return ids[__builtin_ctz(s)];
+    const uint32_t a = split[s];
+    const int xa = build(a);
+    const int xb = build(s ^ a);
+    apply_step(live, count, std::min(xa, xb), std::max(xa, xb), nxt, &p);
+    return nxt++;
+  };
+  if (m > 1) build(full);
+  p.final_inds = live.begin()->second;
+  for (int64_t i : p.final_inds)
+    if (!contains(output, i)) p.final_sum.push_back(i);
+  p.search_exact = m;
+  return finish_plan(dims, output, max_bytes, n_slices, slice_dim, &p);
 }
 
 }  // namespace qtpu

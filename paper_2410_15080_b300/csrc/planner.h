@@ -40,6 +40,8 @@ struct Plan {
   U256 flops_per_slice, flops_total, peak;
   uint32_t search = 0;     // candidates searched (0: a single plan)
   uint64_t search_seed = 0;
+  int search_exact = -1;   // >= 0: an exact-search plan over this many tensors
+  std::string search_note; // a hyper-search's choice (plan text line)
 };
 
 // index id -> dim lookup
@@ -51,7 +53,7 @@ struct DimMap {
   std::vector<int64_t> ids() const;
 };
 
-enum PlanErr { PLAN_OK = 0, PLAN_OVERFLOW = 1, PLAN_LIMIT = 2 };
+enum PlanErr { PLAN_OK = 0, PLAN_OVERFLOW = 1, PLAN_LIMIT = 2, PLAN_TOO_MANY = 3 };
 
 // Greedy order then slicing.  Returns PLAN_OK, PLAN_OVERFLOW (a size >= 2^255)
 // or PLAN_LIMIT (peak limit unreachable).
@@ -66,6 +68,25 @@ int make_plan(const std::vector<Inds>& leaves, const DimMap& dims, const Inds& o
 // lower seed.  *chosen receives the winning seed.
 int make_plan_best(const std::vector<Inds>& leaves, const DimMap& dims, const Inds& output, uint64_t max_bytes,
                    uint64_t n_slices, int64_t slice_dim, uint64_t seed, uint32_t n, Plan* plan, uint64_t* chosen);
+
+// Slice a plan's fixed tree (same rule as make_plan) and fill its accounting.
+int finish_plan(const DimMap& dims, const Inds& output, uint64_t max_bytes, uint64_t n_slices, int64_t slice_dim,
+                Plan* plan);
+
+// Exact order search (section 6.1 step 3, beyond greedy): every small leaf
+// (<= 256 entries) is first contracted, in ascending id, into the lowest-id
+// large leaf sharing an index with it; over the m tensors left (ascending
+// id) the cheapest contraction tree is found by dynamic programming over
+// subsets with the planner's step cost: cost(S) = min over A (containing S's
+// lowest member, A != S) of cost(A) + cost(S \ A) + flops(A, S \ A), an
+// index kept when carried outside S or by the output, ties to the smallest
+// A as a bit mask; the tree is emitted in post order (A's subtree first,
+// operands as (min id, max id)) and sliced by finish_plan.  PLAN_TOO_MANY
+// when m > kExactMax or the network has more than 128 indices or a cost
+// above 2^126.
+constexpr int kExactMax = 16;
+int make_plan_exact(const std::vector<Inds>& leaves, const DimMap& dims, const Inds& output, uint64_t max_bytes,
+                    uint64_t n_slices, int64_t slice_dim, Plan* plan);
 
 std::string plan_text(const Plan& plan);
 

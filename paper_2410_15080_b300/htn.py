@@ -43,7 +43,7 @@ class PlanOpts(C.Structure):
     _fields_ = [("max_intermediate_bytes", C.c_uint64), ("n_slices", C.c_uint32),
                 ("slice_dim", C.c_uint32), ("prec", C.c_int), ("cost_model", C.c_int),
                 ("seed", C.c_uint64), ("autotune_table", C.c_char_p), ("n_candidates", C.c_uint32),
-                ("reuse_bytes", C.c_uint64), ("cost_model_path", C.c_char_p)]
+                ("reuse_bytes", C.c_uint64), ("cost_model_path", C.c_char_p), ("search", C.c_uint32)]
 
 
 class BatchOpts(C.Structure):
@@ -161,12 +161,14 @@ class HTN:
 
     def plan(self, prec: str = "bf16x3", max_intermediate_bytes: int = 0, n_slices: int = 0,
              slice_dim: int = 0, seed: int = 0, n_candidates: int = 0, reuse_bytes: int = 0,
-             cost_model: int = 0, cost_model_path: str | None = None, autotune_table: str | None = None):
+             cost_model: int = 0, cost_model_path: str | None = None, autotune_table: str | None = None,
+             search: int = 0):
         """autotune_table: GEMM tile table file (None: the measured table next
-        to the library if present; "": the padding rule alone)."""
+        to the library if present; "": the padding rule alone).  search: 0
+        greedy, 1 hyper-search, 2 the exact tree alone."""
         o = PlanOpts(max_intermediate_bytes, n_slices, slice_dim, PREC[prec], cost_model, seed,
                      None if autotune_table is None else autotune_table.encode(), n_candidates,
-                     reuse_bytes, cost_model_path.encode() if cost_model_path else None)
+                     reuse_bytes, cost_model_path.encode() if cost_model_path else None, search)
         self._check(self._L.qtpu_htn_plan(self._h, C.byref(o)))
 
     def autotune(self, table_path: str, reps: int = 5, device: int = -1) -> int:

@@ -409,3 +409,58 @@ def test_padding_rule_on_the_100_qubit_plan():
     assert (7776, 216, 216, 112) in shapes
     assert (1296, 1296, 576, 128) in shapes
     assert (5184, 144, 36, 80) in shapes
+
+
+def test_exact_order_search_matches_the_oracle():
+    """search = 2: the exact tree (absorption, subset DP, post order, slicing)
+    has the oracle's plan text byte for byte."""
+    import synth
+    from oracle import order_search
+    cases = [(synth.ring_htn(), {}),
+             (synth.ring_htn(n_sub=4, gates_per_edge=1, wires_per_edge=1, k=2), {"max_intermediate_bytes": 4096}),
+             (synth.ring_chords_htn(materialize=False),
+              {"max_intermediate_bytes": 8 << 30, "n_slices": 1024, "slice_dim": 4})]
+    for net, kw in cases:
+        h = _host_handle(net, search=2, **kw)
+        txt = h.plan_info()
+        h.close()
+        op, _ = order_search.dp_plan(net.inds(), net.dims(), net.output, kw.get("max_intermediate_bytes", 0),
+                                     kw.get("n_slices", 0), kw.get("slice_dim", 0))
+        assert txt == planner.plan_text(op, net.inds())
+        assert txt.rstrip().endswith("search exact tensors=%d" % op.search_dp)
+
+
+def test_hyper_search_never_executes_more_than_its_candidates():
+    """search = 1 keeps the candidate whose lowered launch list executes the
+    fewest FLOPs: never more than the greedy best-of-n or the exact tree."""
+    from paper_2410_15080_b300 import costmodel
+    nets = costmodel.eval_networks(10)
+    gains = []
+    for net in (nets[0], nets[9]):
+        g = _host_handle(net, n_candidates=16)
+        fg = g.exec_stats()["flops_executed"]
+        g.close()
+        e = _host_handle(net, search=2)
+        fe = e.exec_stats()["flops_executed"]
+        e.close()
+        hh = _host_handle(net, n_candidates=16, search=1)
+        fh = hh.exec_stats()["flops_executed"]
+        note = hh.plan_info().rstrip().splitlines()[-1]
+        hh.close()
+        assert note.startswith("search hyper candidates=17 chosen=")
+        assert fh <= fg and fh <= fe
+        gains.append(fg / fh)
+    assert max(gains) > 1.1  # the exact tree wins on the second network
+
+
+def test_search_option_errors():
+    import synth
+    net = synth.ring_htn(n_sub=4, gates_per_edge=1, wires_per_edge=1, k=2)
+    for kw in ({"search": 3}, {"search": 1, "cost_model": 1}):
+        with pytest.raises(htn.QtpuError) as e:
+            _host_handle(net, **kw)
+        assert e.value.status in (htn.QTPU_EINVAL, htn.QTPU_ENOTSUP)
+    big = synth.ring_htn(n_sub=17, gates_per_edge=1, wires_per_edge=1, k=2)
+    with pytest.raises(htn.QtpuError) as e:
+        _host_handle(big, search=2)
+    assert e.value.status == htn.QTPU_ENOTSUP
