@@ -456,6 +456,64 @@ qtpu_status qtpu_htn_tensor_info(const qtpu_htn* h, int t, int max_rank, int* ra
                                  int64_t* dims, int64_t* strides, qtpu_dtype* dtype, qtpu_kind* kind,
                                  const void** dev_ptr);
 
+/* ---- QT evaluation: a statevector simulator of subcircuit instances
+ * (section 4.1: a subcircuit is a QT whose entries are its instances'
+ * expectation values; section 6.2 Step 2 evaluates them -- here exactly, as a
+ * mock QPU) ----
+ * Qubit 0 is the most significant bit of a basis state's index. */
+typedef enum {
+  QTPU_OP_U1 = 0,       /* u: 2x2 unitary on q0, row-major (re, im) pairs      */
+  QTPU_OP_CZ = 1,       /* CZ on q0, q1                                        */
+  QTPU_OP_GATE_CUT = 2  /* on q0: the local operation of gate cut `cut` for its
+                           index value g, factor `side` (0 first, 1 second) of
+                           the CZ decomposition (section 2.1): side 0 takes
+                           I, Z, M, M, e^{+i pi/4 Z}, e^{-i pi/4 Z} for g = 0..5,
+                           side 1 takes I, Z, e^{+i pi/4 Z}, e^{-i pi/4 Z}, M, M;
+                           each is followed by e^{-i pi/4 Z}; M is the signed Z
+                           measurement rho -> P0 rho P0 - P1 rho P1            */
+} qtpu_op_kind;
+typedef enum {
+  QTPU_CUT_GATE = 0,     /* dim 6: the index of one QTPU_OP_GATE_CUT          */
+  QTPU_CUT_MEASURE = 1,  /* dim 4: the wire leaves at cut_qubit, measured in
+                            A = I, Z, X, Y (the observable carries A there)    */
+  QTPU_CUT_PREPARE = 2   /* dim 4: the wire enters at cut_qubit, prepared in
+                            |0>, |1>, |+>, |i> before the first operation      */
+} qtpu_cut_kind;
+typedef struct {
+  int kind;        /* qtpu_op_kind */
+  int q0, q1;
+  int cut, side;   /* QTPU_OP_GATE_CUT */
+  double u[8];     /* QTPU_OP_U1 */
+} qtpu_qop;
+typedef struct {
+  int n_qubits;            /* 1..15 */
+  int n_ops;               /* 0..4096 */
+  const qtpu_qop* ops;     /* host memory */
+  int n_cuts;              /* 0..16: the QT's axes after the observable axis */
+  const int* cut_kind;     /* qtpu_cut_kind per cut */
+  const int* cut_qubit;    /* per wire cut its qubit (distinct); ignored for gate cuts */
+  int n_obs;               /* 1..64 observables */
+  const char* paulis;      /* n_obs * n_qubits characters I, X, Y, Z (observable
+                              k on qubit q at k * n_qubits + q); I on measured
+                              wire qubits */
+} qtpu_qt_program;
+
+/* Evaluate the QT of one subcircuit on CUDA device `device` and stream
+ * cuda_stream: dev_out[k][v_0][v_1]... (FP64, C order, dims n_obs, then 6 or 4
+ * per cut) = Re Tr(O_k' E_v(rho_0)), rho_0 the product of the prepared wire
+ * states and |0> elsewhere, E_v the operations with cut values v, O_k' the
+ * observable k with A_{v_c} on each measured wire qubit -- the layout
+ * qtpu_htn_add_tensor takes for the QT with index ids (k, cut_0, cut_1, ...).
+ * Pure-state simulation in FP64: a signed measurement is carried as its two
+ * projected branches, added with sign -1 for outcome 1.  Each instance is one
+ * thread block, its state in shared memory up to 12 qubits (in device memory
+ * the call allocates beyond); results are deterministic.  Returns when the QT
+ * is written; *n_instances (may be NULL) receives the number of instances.
+ * QTPU_EINVAL on a malformed program (qtpu_last_error(NULL) says which
+ * rule), QTPU_ENOMEM / QTPU_ECUDA on device errors. */
+qtpu_status qtpu_qt_evaluate(int device, void* cuda_stream, const qtpu_qt_program* prog, double* dev_out,
+                             double* n_instances);
+
 qtpu_status qtpu_htn_destroy(qtpu_htn* h);
 
 /* Message of the last failure on h (or, when h is NULL, of the calling

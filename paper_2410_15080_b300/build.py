@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libqtpu_htn.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
-SOURCES = ["planner.cpp", "api.cpp", "costmodel.cpp", "search.cpp", "exec.cu", "kernels_generic.cu", "kernels_gather.cu", "kernels_fast.cu", "kernels_gemm.cu", "batch.cu", "autotune.cu", "qpd.cu", "knit.cu", "noalloc.cu", "mlp.cu"]
+SOURCES = ["planner.cpp", "api.cpp", "costmodel.cpp", "search.cpp", "exec.cu", "kernels_generic.cu", "kernels_gather.cu", "kernels_fast.cu", "kernels_gemm.cu", "batch.cu", "autotune.cu", "qpd.cu", "knit.cu", "qteval.cu", "noalloc.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -22,7 +22,8 @@ QTPU_QT, QTPU_CT = 0, 1
 
 SYMBOLS = ["qtpu_htn_create", "qtpu_htn_add_tensor", "qtpu_htn_set_output", "qtpu_htn_plan",
            "qtpu_htn_plan_info", "qtpu_htn_autotune", "qtpu_htn_qpd_groups", "qtpu_htn_qpd_sample",
-           "qtpu_htn_qpd_info", "qtpu_htn_num_tensors", "qtpu_htn_tensor_info", "qtpu_htn_knit_naive", "qtpu_htn_lowering_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats",
+           "qtpu_htn_qpd_info", "qtpu_htn_num_tensors", "qtpu_htn_tensor_info", "qtpu_htn_knit_naive",
+           "qtpu_qt_evaluate", "qtpu_htn_lowering_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats",
            "qtpu_htn_exec_stats", "qtpu_htn_launch_features", "qtpu_htn_profile_launches", "qtpu_htn_contract",
            "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_contract_batch_ex", "qtpu_htn_batch_info", "qtpu_htn_contract_slices", "qtpu_htn_sync", "qtpu_htn_selftest_timeout", "qtpu_htn_destroy",
            "qtpu_htn_profile", "qtpu_htn_profile_read", "qtpu_pairwise_contract_noalloc",
@@ -372,6 +373,58 @@ class HTN:
             self.close()
         except Exception:
             pass
+
+
+class QOp(C.Structure):
+    _fields_ = [("kind", C.c_int), ("q0", C.c_int), ("q1", C.c_int), ("cut", C.c_int), ("side", C.c_int),
+                ("u", C.c_double * 8)]
+
+
+class QtProgram(C.Structure):
+    _fields_ = [("n_qubits", C.c_int), ("n_ops", C.c_int), ("ops", C.POINTER(QOp)), ("n_cuts", C.c_int),
+                ("cut_kind", C.POINTER(C.c_int)), ("cut_qubit", C.POINTER(C.c_int)), ("n_obs", C.c_int),
+                ("paulis", C.c_char_p)]
+
+
+QTPU_OP_U1, QTPU_OP_CZ, QTPU_OP_GATE_CUT = 0, 1, 2
+QTPU_CUT_GATE, QTPU_CUT_MEASURE, QTPU_CUT_PREPARE = 0, 1, 2
+
+
+def qt_evaluate(prog: dict, device: int = 0, stream: int | None = None):
+    """The QT of one subcircuit program on the GPU (see qtpu_qt_evaluate):
+    prog = {"n": qubits, "ops": [("u1", q, U) | ("cz", q0, q1) |
+    ("gate_cut", q, cut, side)], "cuts": [("gate",) | ("measure", q) |
+    ("prepare", q)], "paulis": [str per observable]}.  Returns a CUDA FP64
+    tensor [observables, 6 or 4 per cut]."""
+    import numpy as np
+    import torch
+    L = lib()
+    ops = (QOp * max(1, len(prog["ops"])))()
+    for i, op in enumerate(prog["ops"]):
+        o = ops[i]
+        if op[0] == "u1":
+            o.kind, o.q0 = QTPU_OP_U1, op[1]
+            U = np.asarray(op[2], dtype=np.complex128).ravel()
+            for j in range(4):
+                o.u[2 * j], o.u[2 * j + 1] = float(U[j].real), float(U[j].imag)
+        elif op[0] == "cz":
+            o.kind, o.q0, o.q1 = QTPU_OP_CZ, op[1], op[2]
+        else:
+            o.kind, o.q0, o.cut, o.side = QTPU_OP_GATE_CUT, op[1], op[2], op[3]
+    kinds = {"gate": QTPU_CUT_GATE, "measure": QTPU_CUT_MEASURE, "prepare": QTPU_CUT_PREPARE}
+    ck = _arr([kinds[c[0]] for c in prog["cuts"]], C.c_int)
+    cq = _arr([c[1] if len(c) > 1 else -1 for c in prog["cuts"]], C.c_int)
+    pa = "".join(prog["paulis"]).encode()
+    p = QtProgram(prog["n"], len(prog["ops"]), ops, len(prog["cuts"]), ck, cq, len(prog["paulis"]), pa)
+    dims = [6 if c[0] == "gate" else 4 for c in prog["cuts"]]
+    out = torch.empty([len(prog["paulis"])] + dims, dtype=torch.float64, device=f"cuda:{device}")
+    if stream is None:
+        stream = torch.cuda.current_stream(device).cuda_stream
+    ni = C.c_double(0)
+    st = L.qtpu_qt_evaluate(device, C.c_void_p(stream), C.byref(p), C.c_void_p(out.data_ptr()), C.byref(ni))
+    if st != QTPU_OK:
+        raise QtpuError(st, L.qtpu_last_error(None).decode())
+    return out
 
 
 def contract_batch(htns: Sequence[HTN], outs, stream: int | None = None, persistent: bool | None = None,
