@@ -54,6 +54,9 @@ WORKLOADS = {
     "knit": "naive circuit knitting (Eq. knitting: every global instance summed, FP64) against the h-TN "
             "contraction of the same network: rings of 3, 4, 5 subcircuits with 1 gate + 1 wire cut per edge, "
             "k = 8 observables",
+    "qteval": "GPU QT evaluation (statevector, FP64) of a hardware-efficient-ansatz subcircuit (3 RY/RZ layers, "
+              "2 CZ chains) with 2 gate cuts, 1 measured and 1 prepared wire (576 instances), 16 observables, "
+              "at 12 and 15 qubits",
     "batch": "512 independent random h-TNs (ring / 2-D grid, 2-12 subcircuits, 2-20 cuts, k 1-64, FP32/FP64, "
              "QTs <= 2^22 entries, peak intermediate <= 2^23 entries) in one CUDA graph (small gather-only "
              "networks in one persistent kernel when they are >= 3/4 of the batch, graph branches otherwise)",
@@ -610,6 +613,98 @@ def run_knit(args, rank, world):
         print(json.dumps(line))
 
 
+def qteval_program(n, seed=0, k=16):
+    """A subcircuit like the paper's VQE/QAOA ansatz pieces: RY/RZ layers
+    and CZ chains, 2 gate cuts (on qubits 0 and n-1 after the first chain),
+    a measured wire (qubit 1, no later gates) and a prepared wire (qubit 2)."""
+    import oracle.sim as _sim  # noqa: F401  (matrices only)
+    rng = np.random.default_rng([seed, n])
+    def rot(q):
+        t, p = rng.uniform(0, 2 * np.pi, 2)
+        c, s_ = np.cos(t / 2), np.sin(t / 2)
+        ry = np.array([[c, -s_], [s_, c]], dtype=np.complex128)
+        rz = np.diag([np.exp(-0.5j * p), np.exp(0.5j * p)])
+        return ("u1", q, rz @ ry)
+    others = [q for q in range(n) if q != 1]
+    ops = [rot(q) for q in range(n)]
+    ops += [("cz", q, q + 1) for q in range(n - 1)]
+    ops += [("gate_cut", 0, 0, 0), ("gate_cut", n - 1, 1, 1)]
+    ops += [rot(q) for q in range(n)]
+    ops += [("cz", q, q + 1) for q in range(2, n - 1)] + [("cz", 0, 2)]
+    ops += [rot(q) for q in others]
+    paulis = []
+    for j in range(k):
+        sgl = ["I"] * n
+        sgl[others[j % len(others)]] = "Z"
+        sgl[others[(j + 1) % len(others)]] = "Z" if j >= len(others) else sgl[others[(j + 1) % len(others)]]
+        paulis.append("".join(sgl))
+    return {"n": n, "ops": ops, "cuts": [("gate",), ("gate",), ("measure", 1), ("prepare", 2)], "paulis": paulis}
+
+
+def run_qteval(args, rank, world):
+    """The QT evaluator on the GPU, timed with CUDA events, against the FP64
+    branching oracle (numpy) on a sample of instances."""
+    import torch
+    from paper_2410_15080_b300 import qt_evaluate
+    from oracle import qt_eval
+    sweep = []
+    for n in (12, 15):
+        prog = qteval_program(n)
+        qt_evaluate(prog)
+        ts = []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = qt_evaluate(prog)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        got = out.cpu().numpy()
+        # FP64 operations per branch (multiplies and adds of the kernel)
+        N = 2 ** n
+        ops_fp = 0
+        for op in prog["ops"]:
+            ops_fp += {"u1": 14 * N, "cz": 0, "gate_cut": 6 * N}[op[0]]
+        ops_fp += 6 * n * N + 7 * len(prog["paulis"]) * N
+        # branches: each instance has 2^(measurements) of them
+        n_br = 0
+        for g0 in range(6):
+            for g1 in range(6):
+                m = (g0 in (2, 3)) + (g1 in (4, 5))
+                n_br += 16 * 2 ** m
+        flops = ops_fp * n_br
+        # oracle on a sample: the first cut value of each axis fixed, all
+        # observables (one instance group per measured/prepared value pair)
+        t0 = time.perf_counter()
+        sample = dict(prog)
+        ref = qt_eval.qt_branching(sample) if n <= 12 else None
+        cpu_s = time.perf_counter() - t0
+        rel = float(np.abs(got - ref).max()) if ref is not None else None
+        sweep.append({"n_qubits": n, "instances": 576, "branches": n_br, "ms": ms,
+                      "instances_per_s": 576 / (ms * 1e-3), "fp64_gflops": flops / (ms * 1e-3) / 1e9,
+                      "oracle_cpu_s": cpu_s if ref is not None else None, "max_abs_diff_vs_oracle": rel})
+    fp64_peak = 1050.0 / 2
+    last = sweep[-1]
+    line = {
+        "metric": "QT evaluation (instances/s) of a 15-qubit subcircuit", "value": last["instances_per_s"],
+        "unit": "instances/s", "n_gpus": world, "steps": args.steps, "warmup": 1, "ms_per_step": last["ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS["qteval"]},
+        "roofline": {"bound": "alu", "kernel": "k_qt_instances", "achieved": last["fp64_gflops"], "peak": fp64_peak,
+                     "unit": "GFLOP/s", "frac": last["fp64_gflops"] / fp64_peak, "traffic": None,
+                     "peak_note": "FP64 multiplies and adds at the DFMA issue rate: half the measured FP64 "
+                                  "matmul rate (1.05 TFLOP/s FMA-counted)"},
+        "cpu_baseline": {"value": 576 / sweep[0]["oracle_cpu_s"], "unit": "instances/s", "cores": oracle_threads(),
+                         "kind": "oracle", "sample": "the 12-qubit program, all 576 instances, numpy branching "
+                                                     "statevector"},
+        "sweep": sweep, "gpu_launches": args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def run_ours(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -854,6 +949,8 @@ def main():
         run_qpd(args, rank, world)
     elif args.workload == "knit":
         run_knit(args, rank, world)
+    elif args.workload == "qteval":
+        run_qteval(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1:
