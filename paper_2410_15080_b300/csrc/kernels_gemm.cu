@@ -73,20 +73,20 @@ struct Cfg;
 template <>
 struct Cfg<3> {  // BF16x3: pieces of 8 significant bits, products of weight >= 2^-16
   static constexpr int NP = 3, NPROD = 6, ES = 2, KB = 64, UK = 16, FMT = 1, KC = 16;
-  __device__ static int pa(int i) { const int t[6] = {0, 0, 1, 0, 1, 2}; return t[i]; }
-  __device__ static int pb(int i) { const int t[6] = {0, 1, 0, 2, 1, 0}; return t[i]; }
+  __host__ __device__ static constexpr int pa(int i) { return i == 2 || i == 4 ? 1 : (i == 5 ? 2 : 0); }
+  __host__ __device__ static constexpr int pb(int i) { return i == 1 || i == 4 ? 1 : (i == 3 ? 2 : 0); }
 };
 template <>
 struct Cfg<2> {  // 3xTF32: pieces of 11 significant bits, products of weight >= 2^-11
   static constexpr int NP = 2, NPROD = 3, ES = 4, KB = 32, UK = 8, FMT = 2, KC = 4;
-  __device__ static int pa(int i) { const int t[3] = {0, 0, 1}; return t[i]; }
-  __device__ static int pb(int i) { const int t[3] = {0, 1, 0}; return t[i]; }
+  __host__ __device__ static constexpr int pa(int i) { return i == 2 ? 1 : 0; }
+  __host__ __device__ static constexpr int pb(int i) { return i == 1 ? 1 : 0; }
 };
 template <>
 struct Cfg<1> {  // TF32: one piece, one product
   static constexpr int NP = 1, NPROD = 1, ES = 4, KB = 32, UK = 8, FMT = 2, KC = 32;
-  __device__ static int pa(int) { return 0; }
-  __device__ static int pb(int) { return 0; }
+  __host__ __device__ static constexpr int pa(int) { return 0; }
+  __host__ __device__ static constexpr int pb(int) { return 0; }
 };
 
 // Shared memory: the pipeline stages (as many as fit, at most 4), the
@@ -108,8 +108,9 @@ struct Layout {
   static_assert(STAGES >= 2, "two pipeline stages must fit");
   static_assert(BN % 16 == 0 && BN >= 16 && 4 * BN <= (int)kTmemCols, "UMMA N tile");
   static constexpr int BAR_OFF = STAGES * STAGE;
-  // full[S], empty[S], accfull[2], accempty[2], mma_done
-  static constexpr int N_BARS = 2 * STAGES + 5;
+  // full[S][NP] (one per piece of a stage), empty[S], accfull[2],
+  // accempty[2], mma_done
+  static constexpr int N_BARS = STAGES * C::NP + STAGES + 5;
   static constexpr int FUSE_OFF = (BAR_OFF + N_BARS * 8 + 16 + 15) / 16 * 16;
   static constexpr int SMEM = FUSE_OFF + FUSE_BYTES + 1024;
   static_assert(SMEM <= kSmemLimit, "shared memory");
@@ -310,9 +311,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + L::BAR_OFF);
-  uint64_t* full = bars;
-  uint64_t* empty = bars + L::STAGES;
-  uint64_t* accfull = bars + 2 * L::STAGES;
+  uint64_t* full = bars;  // [stage * NP + piece]
+  uint64_t* empty = bars + L::STAGES * C::NP;
+  uint64_t* accfull = empty + L::STAGES;
   uint64_t* accempty = accfull + 2;
   uint64_t* mma_done = accempty + 2;
   uint32_t* tmem_holder = (uint32_t*)(bars + L::N_BARS);
@@ -333,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < L::STAGES; ++s) {
-      mbar_init(&full[s], 1);
+      for (int p = 0; p < C::NP; ++p) mbar_init(&full[s * C::NP + p], 1);
       mbar_init(&empty[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
@@ -398,14 +399,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(&full[stage], L::STAGE);
           uint8_t* sA = smem + stage * L::STAGE;
           uint8_t* sB = sA + C::NP * L::A_PIECE;
           const int v = kb / nkb1, kb1 = kb - v * nkb1;
+          // piece by piece, each on its own barrier, so the MMAs of the
+          // leading pieces start while the later ones are in flight
 #pragma unroll
           for (int p = 0; p < C::NP; ++p) {
-            tma_load_4d(sA + p * L::A_PIECE, &maps.a[v], &full[stage], kb1 * C::KB, mtile * BM, b, p);
-            tma_load_4d(sB + p * L::B_PIECE, &maps.b[v], &full[stage], kb1 * C::KB, ntile * BN, b, p);
+            uint64_t* fb = &full[stage * C::NP + p];
+            mbar_arrive_expect_tx(fb, L::A_PIECE + L::B_PIECE);
+            tma_load_4d(sA + p * L::A_PIECE, &maps.a[v], fb, kb1 * C::KB, mtile * BM, b, p);
+            tma_load_4d(sB + p * L::B_PIECE, &maps.b[v], fb, kb1 * C::KB, ntile * BN, b, p);
           }
           issued[stage] = 1;
           issued_phase[stage] = phase;
@@ -416,7 +420,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int s = 0; s < L::STAGES; ++s)
           if (issued[s]) {
             volatile int no_abort = 0;
-            mbar_wait_bounded(&full[s], issued_phase[s], limit_ns, &no_abort);
+            for (int p = 0; p < C::NP; ++p) mbar_wait_bounded(&full[s * C::NP + p], issued_phase[s], limit_ns, &no_abort);
           }
       }
     }
@@ -441,34 +445,43 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t dX = tmem + (uint32_t)(acc * 2 * BN);
           const uint32_t dY = dX + BN;
           const int kb0 = ch * kc, kb1 = min(nkb, kb0 + kc);
-          for (int kb = kb0; kb < kb1; ++kb) {
-            if (!mbar_wait_bounded(&full[stage], phase, limit_ns, abort)) {
-              set_abort(abort, status, ST_TIMEOUT_MMA);
-              ok = false;
-              break;
-            }
-            tc_fence_after();
+          for (int kb = kb0; kb < kb1 && ok; ++kb) {
             const uint32_t sA = smem_u32(smem + stage * L::STAGE);
             const uint32_t sB = sA + C::NP * L::A_PIECE;
             // descriptors of the stage's pieces; each K-step and piece adds its
             // byte offset / 16 to the start-address field (the stage lies
             // below 256 KB of shared memory, so the 14-bit field cannot carry)
             const uint64_t dA0 = smem_desc_k<L::ROW>(sA), dB0 = smem_desc_k<L::ROW>(sB);
+            // piece p's barrier releases the products whose later piece is p
+            // (x0y0; then x0y1, x1y0, x1y1; then x0y2, x2y0), so the leading
+            // products run while the smaller pieces still arrive
 #pragma unroll
-            for (int kk = 0; kk < C::KB / C::UK; ++kk) {
-              const bool first = (kb == kb0 && kk == 0);
-#pragma unroll
-              for (int pr = 0; pr < C::NPROD; ++pr) {
-                const uint64_t ad = dA0 + (uint64_t)((C::pa(pr) * L::A_PIECE + kk * C::UK * C::ES) >> 4);
-                const uint64_t bd = dB0 + (uint64_t)((C::pb(pr) * L::B_PIECE + kk * C::UK * C::ES) >> 4);
-                const uint32_t accum = (first && pr <= 1) ? 0u : 1u;
-                const uint32_t d = pr == 0 ? dX : dY;
-                if (C::FMT == 1)
-                  umma_f16(d, ad, bd, idesc, accum);
-                else
-                  umma_tf32(d, ad, bd, idesc, accum);
+            for (int p = 0; p < C::NP; ++p) {
+              if (!mbar_wait_bounded(&full[stage * C::NP + p], phase, limit_ns, abort)) {
+                set_abort(abort, status, ST_TIMEOUT_MMA);
+                ok = false;
+                break;
               }
+              tc_fence_after();
+#pragma unroll
+              for (int kk = 0; kk < C::KB / C::UK; ++kk) {
+                const bool first = (kb == kb0 && kk == 0);
+#pragma unroll
+                for (int pr = 0; pr < C::NPROD; ++pr) {
+                  if ((C::pa(pr) > C::pb(pr) ? C::pa(pr) : C::pb(pr)) != p) continue;
+                  const uint64_t ad = dA0 + (uint64_t)((C::pa(pr) * L::A_PIECE + kk * C::UK * C::ES) >> 4);
+                  const uint64_t bd = dB0 + (uint64_t)((C::pb(pr) * L::B_PIECE + kk * C::UK * C::ES) >> 4);
+                  const uint32_t accum = (first && pr <= 1) ? 0u : 1u;
+                  const uint32_t d = pr == 0 ? dX : dY;
+                  if (C::FMT == 1)
+                    umma_f16(d, ad, bd, idesc, accum);
+                  else
+                    umma_tf32(d, ad, bd, idesc, accum);
+                }
+              }
+              any = true;
             }
+            if (!ok) break;
             umma_commit(&empty[stage]);
             any = true;
             if (++stage == L::STAGES) stage = 0, phase ^= 1;
