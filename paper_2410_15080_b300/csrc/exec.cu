@@ -167,6 +167,7 @@ namespace {
 constexpr int64_t kSmallLeaf = 256;   // leaves up to this size are absorbed
 constexpr int kMaxVirtualOps = 5;     // operands of one virtual tensor
 constexpr int64_t kMaxVirtualLoop = 256;
+constexpr size_t kKeptSplitBudget = (size_t)8 << 30;  // device bytes for kept split results
 
 size_t dt_bytes(int dt) { return dt == DT_F32 ? 4 : 8; }
 
@@ -1330,6 +1331,9 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
   }
   // group loop orders and executions per contraction
   const double blocks = count_of(F);
+  size_t kept_total = 0;
+  bool kept_on = true;
+  if (const char* e = std::getenv("QTPU_NO_KEPT_SPLITS")) kept_on = std::atoi(e) == 0;
   ex->flops_executed = ex->flops_no_reuse = 0;
   ex->launches_per_contract = 1;
   ex->n_split_slots = 1;
@@ -1367,6 +1371,23 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       double r = 1;
       for (int j = 0; j <= last_j; ++j) r *= (double)sd[outer_order[j]];
       if (S.din & G.sum_pos) r *= V;
+      // a split that would rerun for values it has already produced (an
+      // outer position it does not depend on varies before its own) keeps
+      // one result per value of its own positions instead, within a budget
+      const double distinct = count_of(S.din & ~F);
+      if (r > distinct && !fp64 && kept_on && (S.dst == DST_SPLIT_A || S.dst == DST_SPLIT_B)) {
+        const GatherArgs& g = S.has_fast ? S.gf : S.g;
+        const size_t slot_bytes = align_up((size_t)np * g.n_rows * g.Kp * es, 1024);
+        if (kept_total + slot_bytes * (size_t)distinct <= kKeptSplitBudget) {
+          S.kept_slots = (int64_t)distinct;
+          S.kept_slot_bytes = slot_bytes;
+          S.kept_off = kept_total;
+          S.kept_side = S.dst == DST_SPLIT_A ? 0 : 1;
+          S.dst = DST_KEPT;
+          kept_total += slot_bytes * (size_t)distinct;
+          r = distinct;
+        }
+      }
       S.runs = (int64_t)(r * blocks);
       launches_of[sp] = (double)S.runs;
     }
@@ -1417,6 +1438,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     }
   }
   ex->side_bytes = side_total;
+  ex->kept_split_bytes = kept_total;
   // large W tables are computed once per launch into a buffer of their own
   ex->wbuf_bytes = 0;
   for (auto& L : ex->launches)
@@ -1453,7 +1475,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       !dalloc((void**)&ex->partial, (size_t)std::max<int64_t>(ex->final_size, 1) * 8) ||
       !dalloc((void**)&ex->status, 16) || !dalloc((void**)&ex->out_stage, (size_t)R.g.n_out * 8 + 8) ||
       !dalloc((void**)&ex->dot_scratch, dot_scratch_entries(ex->sm_count) * sizeof(float2)) ||
-      !dalloc((void**)&ex->wbuf, ex->wbuf_bytes)) {
+      !dalloc((void**)&ex->wbuf, ex->wbuf_bytes) || !dalloc((void**)&ex->keptbuf, ex->kept_split_bytes)) {
     exec_free(ex);
     return fail(QTPU_ENOMEM, "device workspace allocation failed");
   }
@@ -1502,6 +1524,23 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     for (int side = 0; side < 2; ++side) {
       L.opnd_owner[side] = -1;
       L.tm_copies[side].clear();
+      L.kept_maps[side].clear();
+      if (L.opnd_split[side] >= 0 && ex->launches[L.opnd_split[side]].kept_slots) {
+        // one map per kept result
+        const Launch& S = ex->launches[L.opnd_split[side]];
+        base[side] = ex->keptbuf + S.kept_off;
+        kp[side] = S.g.Kp;
+        const int64_t rows = side ? L.gemm.N : L.gemm.M;
+        const int box = side ? L.gemm.bn : 128;
+        L.kept_maps[side].resize((size_t)S.kept_slots);
+        for (int64_t c = 0; c < S.kept_slots; ++c)
+          if (!make_operand_map(&L.kept_maps[side][c], base[side] + (size_t)c * S.kept_slot_bytes, prec,
+                                L.gemm.batch, rows, L.gemm.K, kp[side], box)) {
+            exec_free(ex);
+            return fail(QTPU_ECUDA, "cuTensorMapEncodeTiled failed");
+          }
+        continue;
+      }
       if (L.opnd_split[side] >= 0) {
         const Launch& S = ex->launches[L.opnd_split[side]];
         base[side] = S.side >= 0 ? ex->sidebuf + S.side_off : ex->splitbuf + (side ? ex->split_a_bytes : 0);
@@ -1870,6 +1909,7 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
   auto dst_ptr = [&](int d) -> void* {
     switch (d) {
       case DST_SIDE: return ex->sidebuf + cur->side_off;
+      case DST_KEPT: return ex->keptbuf + cur->kept_off + (size_t)cur_slot * cur->kept_slot_bytes;
       case DST_PARTIAL: return ex->partial;
       case DST_SPLIT_A: return ex->splitbuf + (size_t)cur_slot * ex->split_slot[0];
       case DST_SPLIT_B: return ex->splitbuf + ex->split_a_bytes + (size_t)cur_slot * ex->split_slot[1];
@@ -2013,7 +2053,8 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
       for (int q = 0; q < nsp; ++q)
         if ((M.din >> q) & 1) digit[q] = B.lo[q];
       for (int sp : G.split)
-        if (sp >= 0) split_epoch[sp].assign((size_t)ex->n_split_slots, -1);
+        if (sp >= 0)
+          split_epoch[sp].assign((size_t)std::max<int64_t>(ex->launches[sp].kept_slots, ex->n_split_slots), -1);
       int64_t n_outer = 1, n_inner = 1;
       for (int q : outer) n_outer *= B.hi[q] - B.lo[q];
       for (int q : inner) n_inner *= B.hi[q] - B.lo[q];
@@ -2031,7 +2072,13 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
               const int sp = G.split[side];
               if (sp < 0) continue;
               const Launch& S = ex->launches[sp];
-              const int slot = (S.din & inner_mask) ? j : 0;
+              int slot = (S.din & inner_mask) ? j : 0;
+              if (S.kept_slots) {  // the kept result of the current values of its positions
+                int64_t k = 0;
+                for (int q = 0; q < nsp; ++q)
+                  if (((S.din >> q) & 1) && B.hi[q] - B.lo[q] > 1) k = k * (B.hi[q] - B.lo[q]) + (digit[q] - B.lo[q]);
+                slot = (int)k;
+              }
               slot_of[side] = slot;
               int64_t ep = 0;  // the values of the split's own positions
               for (int q = 0; q < nsp; ++q)
@@ -2046,7 +2093,9 @@ cudaError_t enqueue_all(Executor* ex, const std::vector<Leaf>& leaves, double* o
             if (M.kind == LK_GEMM) {
               for (int side = 0; side < 2; ++side) {
                 const CUtensorMap* m;
-                if (M.opnd_split[side] >= 0)
+                if (!M.kept_maps[side].empty())
+                  m = &M.kept_maps[side][(size_t)slot_of[side]];
+                else if (M.opnd_split[side] >= 0)
                   m = side ? &M.gemm.maps.b[slot_of[side]] : &M.gemm.maps.a[slot_of[side]];
                 else if (M.opnd_owner[side] >= 0)
                   m = &M.tm_copies[side][(size_t)copy_of(ex->stored[M.opnd_owner[side] - nl])];
@@ -2239,6 +2288,8 @@ void exec_free(Executor* ex) {
   ex->dot_scratch = nullptr;
   if (ex->wbuf) cudaFree(ex->wbuf);
   ex->wbuf = nullptr;
+  if (ex->keptbuf) cudaFree(ex->keptbuf);
+  ex->keptbuf = nullptr;
   ex->arena = ex->splitbuf = ex->partial = nullptr;
   ex->status = nullptr;
   ex->out_stage = nullptr;

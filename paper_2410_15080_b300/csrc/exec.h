@@ -29,7 +29,7 @@ enum KernelClass { KC_CONTRACT = 0, KC_SPLIT = 1, KC_GEMM = 2, KC_REDUCE = 3, KC
 enum LaunchKind { LK_GATHER = 0, LK_GEMM = 1, LK_CONTRACT64 = 2 };
 
 // Destinations of a launch's output
-enum : int { DST_PARTIAL = -1, DST_SPLIT_A = -2, DST_SPLIT_B = -3, DST_OUT = -4, DST_SIDE = -5 };
+enum : int { DST_PARTIAL = -1, DST_SPLIT_A = -2, DST_SPLIT_B = -3, DST_OUT = -4, DST_SIDE = -5, DST_KEPT = -6 };
 
 struct Launch {
   int kind = LK_GATHER;
@@ -76,6 +76,13 @@ struct Launch {
   // orientation and N tile are fixed (by a fused-split consumer)
   int64_t tile_key[5] = {};
   bool tile_fixed = false;
+  // a split whose result is kept per value of its own sliced positions
+  // (DST_KEPT): the slot count, bytes per slot, its region in keptbuf and the
+  // GEMM side it feeds; the GEMM it feeds holds one map per slot
+  int64_t kept_slots = 0;
+  size_t kept_slot_bytes = 0, kept_off = 0;
+  int kept_side = 0;
+  std::vector<CUtensorMap> kept_maps[2];
 };
 
 // One unit of the slice-reuse schedule: a launch, preceded (for a GEMM) by
@@ -158,6 +165,9 @@ struct Executor {
   int n_side = 0;
   uint8_t* sidebuf = nullptr;
   size_t side_bytes = 0;
+  // kept split results (sliced plans): one region per kept split
+  uint8_t* keptbuf = nullptr;
+  size_t kept_split_bytes = 0;
   cudaStream_t side_stream = nullptr;
   std::vector<cudaEvent_t> side_ev;  // one per side launch, plus fork and join
   double planned_side_bytes = 0;
@@ -171,7 +181,8 @@ struct Executor {
   double flops_executed = 0;     // useful FLOPs one full contraction executes
   double flops_no_reuse = 0;     // the same with every slice computed in full
   size_t workspace_bytes() const {
-    return arena_bytes + split_bytes + side_bytes + wbuf_bytes + (size_t)std::max<int64_t>(final_size, 1) * 8;
+    return arena_bytes + split_bytes + side_bytes + kept_split_bytes + wbuf_bytes +
+           (size_t)std::max<int64_t>(final_size, 1) * 8;
   }
 };
 

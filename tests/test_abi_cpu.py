@@ -464,3 +464,37 @@ def test_search_option_errors():
     with pytest.raises(htn.QtpuError) as e:
         _host_handle(big, search=2)
     assert e.value.status == htn.QTPU_ENOTSUP
+
+
+def test_kept_split_results_remove_reruns(monkeypatch):
+    """Slice reuse on the 100-qubit plan: an operand split whose own sliced
+    positions vary inside an outer loop it does not depend on keeps one
+    result per value of its positions, so every split runs once per distinct
+    value (16 here) instead of once per visit (64)."""
+    import synth
+    net = synth.ring_chords_htn(materialize=False)
+    kw = dict(max_intermediate_bytes=8 << 30, n_slices=1024, slice_dim=4, n_candidates=256)
+
+    def runs(h):
+        out = {}
+        for line in h.lowering_info().splitlines():
+            f = line.split()
+            if len(f) > 3 and f[0] == "launch" and f[2] == "split":
+                d = dict(w.split("=", 1) for w in f if "=" in w)
+                out[int(f[1])] = (d["din"], int(d["runs"]))
+        return out
+
+    h = _host_handle(net, **kw)
+    kept = runs(h)
+    n_kept = h.exec_stats()["launches"]
+    h.close()
+    monkeypatch.setenv("QTPU_NO_KEPT_SPLITS", "1")
+    h = _host_handle(net, **kw)
+    plain = runs(h)
+    n_plain = h.exec_stats()["launches"]
+    h.close()
+    for i, (din, r) in kept.items():
+        distinct = 4 ** (0 if din == "-" else len(din.split(",")))
+        assert r == distinct, (i, din, r)
+    assert any(r > 4 ** len(d.split(",")) for d, r in plain.values() if d != "-")
+    assert n_kept < n_plain
