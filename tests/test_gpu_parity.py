@@ -368,12 +368,16 @@ def _reuse_net():
 
 
 @pytest.mark.parametrize("reuse", ["all copies", "blocked", "off"])
-def test_slice_reuse_matches_oracle(reuse):
+def test_slice_reuse_matches_oracle(reuse, monkeypatch):
     """Slice reuse with every copy kept, with some sliced indices held fixed
     in an outer loop (a small budget), and off (one slice at a time): all
     give the oracle's value, and the same bits on a second call; with reuse
-    the contraction executes fewer FLOPs than the plan's total."""
+    the contraction executes fewer FLOPs than the plan's total.  (The blocked
+    case sizes its budget from the workspace, so kept split results, which
+    the workspace also holds, are off there.)"""
     from paper_2410_15080_b300.htn import HTN, lowering_text
+    if reuse == "blocked":
+        monkeypatch.setenv("QTPU_NO_KEPT_SPLITS", "1")
     net = _reuse_net()
     ref = oracle_value(net)
     kw = dict(n_slices=256, slice_dim=4)
