@@ -59,7 +59,7 @@ WORKLOADS = {
               "at 12 and 15 qubits",
     "batch": "512 independent random h-TNs (ring / 2-D grid, 2-12 subcircuits, 2-20 cuts, k 1-64, FP32/FP64, "
              "QTs <= 2^22 entries, peak intermediate <= 2^23 entries) in one CUDA graph (small gather-only "
-             "networks in one persistent kernel when they are >= 3/4 of the batch, graph branches otherwise)",
+             "networks in one persistent kernel when they are >= 1/2 of the batch, graph branches otherwise)",
 }
 
 
@@ -441,7 +441,7 @@ def run_batch(args, rank, world):
                      "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                      "kernel": "whole batch (aggregate leaf bytes / batch time)"},
         "default_schedule": {"persistent_kernel_networks": info["persistent_networks"], "tasks": info["tasks"],
-                             "rule": "persistent kernel when small gather-only networks are >= 3/4 of the batch"},
+                             "rule": "persistent kernel when small gather-only networks are >= 1/2 of the batch"},
         "graph_branches_only": {"ms_per_step": ms_graph, "value": flops / (ms_graph * 1e-3) / 1e12},
         "persistent_kernel_forced": {"ms_per_step": ms_pers, "networks": info_p["persistent_networks"],
                                      "tasks": info_p["tasks"], "value": flops / (ms_pers * 1e-3) / 1e12},

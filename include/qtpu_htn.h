@@ -320,9 +320,9 @@ qtpu_status qtpu_htn_contract_host(qtpu_htn* h, const void* const* host_ptrs,
  * All n contractions run as ONE CUDA graph.  Small networks whose launches
  * are all gathers (unsliced, no tensor-core step, no launch above 2^16 terms)
  * can become tasks of one persistent kernel -- by default when they are at
- * least 3/4 of the batch (a launch-bound batch; on B300 a batch of 512 such
- * networks ran 2.5x faster so, while in a batch bound by networks with
- * tensor-core steps it lengthened the batch by 2.5 %): its blocks claim work
+ * least half of the batch (on B300, batches of 512 random networks in which
+ * 52-80 % qualify ran 1.06-1.99x faster than as graph branches): its
+ * blocks claim work
  * units (256 outputs of a launch, or
  * one output of a long sum) in task order, level by level across the
  * networks, and each unit first waits -- bounded by a time limit -- until the
@@ -341,7 +341,7 @@ qtpu_status qtpu_htn_contract_batch(qtpu_htn* const* hs, int n,
 typedef struct {
   int persistent;            /* 2 (default): the persistent kernel for the
                                 small gather-only networks when they are at
-                                least 3/4 of the batch; 1: always for them;
+                                least half of the batch; 1: always for them;
                                 0: graph branches only                       */
   uint64_t wait_limit_ns;    /* bound of the persistent kernel's dependency
                                 waits; 0 = 2 s, at most 10 s                 */

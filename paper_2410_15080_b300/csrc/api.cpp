@@ -883,8 +883,8 @@ cudaError_t batch_build_tasks(BatchGraph* b, qtpu_htn* const* hs, int n, double*
   int n_el = 0;
   for (int i = 0; i < n; ++i)
     if (exec_batch_tasks(&hs[i]->ex, hs[i]->leaves, dev_out[i], &per[i])) (*eligible)[i] = 1, ++n_el;
-  // mode 2: only a batch that is mostly small networks (launch-bound)
-  if (mode == 2 && 4 * n_el < 3 * n) {
+  // mode 2: only a batch that is at least half small networks
+  if (mode == 2 && 2 * n_el < n) {
     eligible->assign(n, 0);
     return cudaSuccess;
   }

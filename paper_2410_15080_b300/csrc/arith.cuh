@@ -178,5 +178,29 @@ __device__ __forceinline__ void offsets(uint32_t o, const GModes& t, int64_t* of
   }
 }
 
+// digits of position l over the modes of t (outermost first) and the
+// operand offsets they add: the start state of an odometer walk from l
+template <int NOPS>
+__device__ __forceinline__ void digits(uint32_t l, const GModes& t, uint32_t* idx, int64_t* off) {
+  for (int m = t.n - 1; m >= 0; --m) {
+    const uint32_t q = fdiv(l, t.div[m]);
+    const uint32_t i = l - q * t.dim[m];
+    l = q;
+    idx[m] = i;
+#pragma unroll
+    for (int j = 0; j < NOPS; ++j) off[j] += (int64_t)i * t.stride[m][j];
+  }
+}
+
+// lanes per output for a sum of n_loop terms over few outputs: groups of
+// 2^lg consecutive lanes share an output (each lane a contiguous run of at
+// least 8 terms) while the outputs leave most of the GPU's lanes idle
+inline int lanes_for_long_sum(uint32_t n_out, uint32_t n_loop, int sm_count) {
+  int lg = 0;
+  if (n_out > (uint32_t)sm_count * 64) return 0;
+  while (lg < 5 && (8u << (lg + 1)) <= n_loop && ((uint64_t)n_out << (lg + 1)) <= (uint64_t)sm_count * 2048) ++lg;
+  return lg;
+}
+
 }  // namespace arith
 }  // namespace qtpu

@@ -931,10 +931,18 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     const double big_size = sx ? prod(live_inds[ps.y]) : prod(live_inds[ps.x]);
     Inds vL = X.L;
     vL.insert(vL.end(), Y.L.begin(), Y.L.end());
-    for (const Inds* g : {&k, &sa, &sb}) vL.insert(vL.end(), g->begin(), g->end());
+    Inds stepL;
+    for (const Inds* g : {&k, &sa, &sb}) stepL.insert(stepL.end(), g->begin(), g->end());
+    vL.insert(vL.end(), stepL.begin(), stepL.end());
+    // A virtual result sums prod(vL) terms per entry where it is finally read;
+    // evaluating its parts step by step sums prod(X.L) + prod(Y.L) +
+    // prod(stepL) at a comparable output size.  Keep it virtual only when
+    // the product is not larger than that sum: a QT absorbing five 4 x 4
+    // wire CTs at once would sum 4^5 = 1024 terms per entry instead of 5 x 4.
+    const bool loop_ok = prod(vL) <= prod(X.L) + prod(Y.L) + prod(stepL);
     if (!last && (sx || sy) && !(sx && sy && nb * nm * nn > 4 * kSmallLeaf) &&
         nb * nm * nn <= 4.0 * big_size && (int)(X.ops.size() + Y.ops.size()) <= kMaxVirtualOps &&
-        prod(vL) <= (double)kMaxVirtualLoop) {
+        prod(vL) <= (double)kMaxVirtualLoop && loop_ok) {
       Repr V;
       V.ops = X.ops;
       V.ops.insert(V.ops.end(), Y.ops.begin(), Y.ops.end());
@@ -1116,12 +1124,18 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     extra.insert(extra.end(), sa.begin(), sa.end());
     extra.insert(extra.end(), sb.begin(), sb.end());
     // a virtual operand is materialised first when it has too many factors
-    // for one gather, or when this step would recompute each of its entries
-    // many times (every output reads it over the whole loop)
+    // for one gather, when this step would recompute each of its entries
+    // many times (every output reads it over the whole loop), or when the
+    // product of its loop and this step's sums more terms than the two
+    // done one after the other
     for (Repr* r : {&X, &Y}) {
       const double vsize = r->virt ? prod(live_inds[r == &X ? ps.x : ps.y]) : 1.0;
       const double reuse = r->virt ? (nb * nm * nn) * prod(extra) / vsize : 0.0;
-      if (r->virt && ((int)(X.ops.size() + Y.ops.size()) > kMaxOps || reuse > 4.0)) {
+      // terms summed by this gather with r virtual, and by materialising r
+      // first (its own loop once per entry) and then gathering without it
+      const double fused_terms = (nb * nm * nn) * prod(X.L) * prod(Y.L) * prod(extra);
+      const double split_terms = vsize * prod(r->L) + fused_terms / prod(r->L);
+      if (r->virt && ((int)(X.ops.size() + Y.ops.size()) > kMaxOps || reuse > 4.0 || fused_terms > split_terms)) {
         const int tid = next_tmp++;
         const Inds vin = live_inds[r == &X ? ps.x : ps.y];
         tout[tid] = toutof(r == &X ? ps.x : ps.y);

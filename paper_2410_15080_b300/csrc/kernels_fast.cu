@@ -120,9 +120,27 @@ struct Op {
       }
       return acc;
     }
+    walk(a, W, off, 0, a.n_loop, acc);
+    return acc;
+  }
+  // loop positions [l0, l1) of the entry at base as an odometer walk over the
+  // loop modes, started from the digits of l0
+  template <typename ACC>
+  __device__ static __forceinline__ void range(const GatherArgs& a, const float2* W, const int64_t* base,
+                                               uint32_t l0, uint32_t l1, ACC& acc) {
+    if (l0 >= l1) return;
+    int64_t off[NOPS];
+#pragma unroll
+    for (int j = 0; j < NOPS; ++j) off[j] = base[j];
+    walk(a, W, off, l0, l1, acc);
+  }
+  template <typename ACC>
+  __device__ static __forceinline__ void walk(const GatherArgs& a, const float2* W, int64_t* off, uint32_t l0,
+                                              uint32_t l1, ACC& acc) {
     uint32_t idx[kMaxModes];
     for (int m = 0; m < a.loop.n; ++m) idx[m] = 0;
-    for (uint32_t l = 0; l < a.n_loop; ++l) {
+    if (l0 > 0) digits<NOPS>(l0, a.loop, idx, off);
+    for (uint32_t l = l0; l < l1; ++l) {
       acc.add(term(a, W, off));
       int m = a.loop.n - 1;
       ++idx[m];
@@ -138,7 +156,6 @@ struct Op {
         for (int j = 0; j < NOPS; ++j) off[j] += a.loop.stride[m][j];
       }
     }
-    return acc;
   }
 };
 
@@ -217,12 +234,16 @@ __global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __
   pdl_wait();
   pdl_launch_dependents();
   if (lanes_log2 > 0) {
-    // few outputs with a short tabulated loop: 2^lanes_log2 consecutive lanes
-    // share an output, each summing every 2^lanes_log2-th term, then the
-    // partial sums meet by shuffles (compensated pairs, or FP64)
+    // few outputs: 2^lanes_log2 consecutive lanes share an output, each
+    // summing every 2^lanes_log2-th term of a tabulated loop, or a contiguous
+    // run of a longer one; the partial sums then meet by shuffles
+    // (compensated pairs, or FP64)
     const uint32_t S = 1u << lanes_log2;
+    const bool tab = use_loop_tab(a);
+    const uint32_t per = (a.n_loop + S - 1) / S;
     const uint64_t total = (uint64_t)a.n_out << lanes_log2;
     const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+    // i0 is the same for the 32 lanes of a warp: every lane takes part in the shuffles
     for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < total; i0 += step) {
       const uint64_t i = i0 + (threadIdx.x & 31u);
       const uint32_t o = (uint32_t)(i >> lanes_log2), sub = (uint32_t)(i & (S - 1));
@@ -230,12 +251,17 @@ __global__ void __launch_bounds__(256) k_dense_fast(const GatherArgs a, void* __
       if (o < a.n_out) {
         int64_t base[O::NOPS];
         offsets<O::NOPS>(o, a.out, base);
+        if (tab) {
 #pragma unroll 2
-        for (uint32_t l = sub; l < a.n_loop; l += S) {
-          int64_t off[O::NOPS];
+          for (uint32_t l = sub; l < a.n_loop; l += S) {
+            int64_t off[O::NOPS];
 #pragma unroll
-          for (int j = 0; j < O::NOPS; ++j) off[j] = base[j] + lt[l][j];
-          acc.add(O::term(a, W, off));
+            for (int j = 0; j < O::NOPS; ++j) off[j] = base[j] + lt[l][j];
+            acc.add(O::term(a, W, off));
+          }
+        } else {
+          const uint32_t l0 = (uint32_t)min((uint64_t)a.n_loop, (uint64_t)sub * per);
+          O::range(a, W, base, l0, (uint32_t)min((uint64_t)a.n_loop, (uint64_t)l0 + per), acc);
         }
       }
       if (F64OUT) {
@@ -797,10 +823,13 @@ template <int NB, int DT0, int DT1, bool HW>
 cudaError_t dense_dt(const GatherArgs& a, void* out, int sm, cudaStream_t st) {
   if (a.n_out == 0) return cudaSuccess;
   // lanes per output: up to 8 while the SMs are not yet full and each lane
-  // keeps at least 4 terms of a tabulated loop
+  // keeps at least 4 terms of a tabulated loop; for a longer loop, up to 32
+  // when the outputs are few (each lane a run of at least 8 terms)
   int lg = 0;
   if (a.loop.n > 0 && a.n_loop <= kLoopTab)
     while (lg < 3 && (4u << (lg + 1)) <= a.n_loop && ((uint64_t)a.n_out << (lg + 1)) <= (uint64_t)sm * 4096) ++lg;
+  else if (a.loop.n > 0)
+    lg = lanes_for_long_sum(a.n_out, a.n_loop, sm);
   int64_t g = (((int64_t)a.n_out << lg) + 255) / 256;
   if (g > (int64_t)sm * 8) g = (int64_t)sm * 8;
   const size_t sm_bytes = HW ? a.w_size * sizeof(float2) : 0;

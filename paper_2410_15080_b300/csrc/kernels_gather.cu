@@ -35,6 +35,35 @@ __device__ __forceinline__ float2 term(const GatherArgs& a, const int64_t* off) 
   return v;
 }
 
+// loop positions [l0, l1) of one output entry (base offsets) as an odometer
+// walk over the loop modes, started from the digits of l0
+template <int NOPS, typename ACC>
+__device__ __forceinline__ void entry_range(const GatherArgs& a, const int64_t* base, uint32_t l0, uint32_t l1,
+                                            ACC& acc) {
+  if (l0 >= l1) return;
+  uint32_t idx[kMaxModes];
+  int64_t off[NOPS];
+#pragma unroll
+  for (int j = 0; j < NOPS; ++j) off[j] = base[j];
+  digits<NOPS>(l0, a.loop, idx, off);
+  for (uint32_t l = l0; l < l1; ++l) {
+    acc.add(term<NOPS>(a, off));
+    int m = a.loop.n - 1;
+    ++idx[m];
+#pragma unroll
+    for (int j = 0; j < NOPS; ++j) off[j] += a.loop.stride[m][j];
+    while (m > 0 && idx[m] == a.loop.dim[m]) {
+#pragma unroll
+      for (int j = 0; j < NOPS; ++j) off[j] -= (int64_t)a.loop.dim[m] * a.loop.stride[m][j];
+      idx[m] = 0;
+      --m;
+      ++idx[m];
+#pragma unroll
+      for (int j = 0; j < NOPS; ++j) off[j] += a.loop.stride[m][j];
+    }
+  }
+}
+
 // value of one output entry: base offsets + sum over the loop modes, in the
 // accumulator ACC (FP32 pairs for intermediates, FP64 for output values)
 template <int NOPS, typename ACC>
@@ -81,12 +110,48 @@ __device__ __forceinline__ ACC entry(const GatherArgs& a, const int64_t* base) {
 
 // ------------------------------------------------------------ dense writers
 // out[o] for o < n_out, one thread per entry (FP32 pair, or FP64 output
-// accumulated in FP64)
+// accumulated in FP64).  With lanes_log2 > 0 (few outputs, a long loop),
+// 2^lanes_log2 consecutive lanes share an entry, each summing a contiguous
+// run of the loop, and the runs' sums meet by shuffles in a fixed order.
 template <int NOPS, bool F64OUT>
-__global__ void __launch_bounds__(256) k_gather_dense(const GatherArgs a, void* __restrict__ out) {
+__global__ void __launch_bounds__(256) k_gather_dense(const GatherArgs a, void* __restrict__ out, int lanes_log2) {
   using ACC = typename AccSel<F64OUT>::T;
   pdl_wait();
   pdl_launch_dependents();
+  if (lanes_log2 > 0) {
+    const uint32_t S = 1u << lanes_log2;
+    const uint32_t per = (a.n_loop + S - 1) / S;
+    const uint64_t total = (uint64_t)a.n_out << lanes_log2;
+    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+    // i0 is the same for the 32 lanes of a warp: every lane takes part in the shuffles
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < total; i0 += step) {
+      const uint64_t i = i0 + (threadIdx.x & 31u);
+      const uint32_t o = (uint32_t)(i >> lanes_log2), sub = (uint32_t)(i & (S - 1));
+      ACC acc;
+      if (o < a.n_out) {
+        int64_t base[NOPS];
+        offsets<NOPS>(o, a.out, base);
+        const uint32_t l0 = (uint32_t)min((uint64_t)a.n_loop, (uint64_t)sub * per);
+        entry_range<NOPS, ACC>(a, base, l0, (uint32_t)min((uint64_t)a.n_loop, (uint64_t)l0 + per), acc);
+      }
+      if (F64OUT) {
+        double v = acc.as_double();
+        for (uint32_t d = S >> 1; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+        if (o < a.n_out && sub == 0) store_out((double*)out, o, v, a.accum);
+        continue;
+      }
+      float2 v = acc.get();
+      for (uint32_t d = S >> 1; d > 0; d >>= 1) {
+        Acc t;
+        t.hi = v.x;
+        t.lo = v.y;
+        t.add(make_float2(__shfl_xor_sync(0xffffffffu, v.x, d), __shfl_xor_sync(0xffffffffu, v.y, d)));
+        v = t.get();
+      }
+      if (o < a.n_out && sub == 0) store_out((float2*)out, o, v, a.accum);
+    }
+    return;
+  }
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t o = blockIdx.x * blockDim.x + threadIdx.x; o < a.n_out; o += stride) {
     int64_t base[NOPS];
@@ -286,10 +351,11 @@ cudaError_t launch_n(const GatherArgs& a, void* out, int sm, cudaStream_t st) {
     if (f64) return launch_k(k_gather_block<NOPS, true>, dim3(g), dim3(256), 0, st, a, out);
     return launch_k(k_gather_block<NOPS, false>, dim3(g), dim3(256), 0, st, a, out);
   }
-  int64_t g = ((int64_t)a.n_out + 255) / 256;
+  const int lg = a.loop.n > 0 ? lanes_for_long_sum(a.n_out, a.n_loop, sm) : 0;
+  int64_t g = (((int64_t)a.n_out << lg) + 255) / 256;
   if (g > (int64_t)sm * 32) g = (int64_t)sm * 32;
-  if (f64) return launch_k(k_gather_dense<NOPS, true>, dim3((unsigned)g), dim3(256), 0, st, a, out);
-  return launch_k(k_gather_dense<NOPS, false>, dim3((unsigned)g), dim3(256), 0, st, a, out);
+  if (f64) return launch_k(k_gather_dense<NOPS, true>, dim3((unsigned)g), dim3(256), 0, st, a, out, lg);
+  return launch_k(k_gather_dense<NOPS, false>, dim3((unsigned)g), dim3(256), 0, st, a, out, lg);
 }
 
 }  // namespace

@@ -431,7 +431,7 @@ def contract_batch(htns: Sequence[HTN], outs, stream: int | None = None, persist
                    wait_limit_ns: int = 0, test_stall_network: int = -1):
     """Contract many planned networks in one CUDA graph (see the C header).
     persistent: None = the library's choice (the persistent kernel when the
-    small gather-only networks are at least 3/4 of the batch), True = always
+    small gather-only networks are at least half of the batch), True = always
     for them, False = graph branches only."""
     L = lib()
     hs = (C.c_void_p * len(htns))(*[h._h.value for h in htns])

@@ -74,8 +74,9 @@ def test_batch_of_512_networks():
     """The batched workload at its full size: 512 random networks (2-12
     subcircuits, 2-20 cuts, k 1-64, FP32/FP64, QTs up to 2^22 entries) in one
     graph with the persistent kernel; every output matches the graph-branch
-    schedule and a sample of 32 matches the FP64 oracle.  By default (about
-    half the networks small) the batch runs as graph branches only."""
+    schedule and a sample of 32 matches the FP64 oracle.  By default (more
+    than half the networks small) the batch takes the persistent kernel; a
+    batch of mostly larger networks runs as graph branches only."""
     import torch
     from paper_2410_15080_b300 import batch_info, contract_batch
     nets = synth.random_batch(512, seed=0, max_qt_entries=QT_CAP)
@@ -92,9 +93,18 @@ def test_batch_of_512_networks():
     d = [torch.empty_like(o) for o in outs]
     contract_batch(hs, d)
     torch.cuda.synchronize()
-    assert batch_info(hs, d)["persistent_networks"] == 0
-    for o, r in zip(d, ref):
-        assert torch.equal(o, r)
+    assert batch_info(hs, d)["persistent_networks"] == info["persistent_networks"]
+    for o, p in zip(d, outs):
+        assert torch.equal(o, p)
+    # mostly networks with tensor-core steps: the default is graph branches
+    big = [i for i, h in enumerate(hs) if h.plan_stats()["n_tensor_core_steps"] > 0]
+    mixed = big + [i for i in range(512) if i not in big][: len(big) // 2]
+    dm = [torch.empty_like(outs[i]) for i in mixed]
+    contract_batch([hs[i] for i in mixed], dm)
+    torch.cuda.synchronize()
+    assert batch_info([hs[i] for i in mixed], dm)["persistent_networks"] == 0
+    for o, i in zip(dm, mixed):
+        assert torch.equal(o, ref[i])
     for o, r in zip(outs, ref):
         assert rel_err(o.cpu().numpy(), r.cpu().numpy()) <= 2 * REL_TOL
     for i in range(0, 512, 16):
@@ -136,4 +146,27 @@ def test_persistent_wait_gives_up_and_reports_timeout():
         h.sync()
         assert rel_err(o.cpu().numpy(), oracle_value(n)) <= REL_TOL
     for h in hs:
+        h.close()
+
+
+def test_few_outputs_with_long_sums():
+    """Networks of the batched workload whose last step sums 576-864 terms
+    into 5-46 outputs (FP64): lanes share an output, each summing a
+    contiguous run of the loop, in the typed fast kernel and in the generic
+    one; each network matches the FP64 oracle."""
+    import re
+    from paper_2410_15080_b300.htn import lowering_text
+    nets = synth.random_batch(512, seed=0, max_qt_entries=QT_CAP)
+    pick = [nets[i] for i in (15, 148, 205, 339)]
+    kinds = set()
+    for n in pick:
+        dts = ["f32" if t.data.dtype == np.float32 else "f64" for t in n.tensors]
+        t = lowering_text(n.inds(), n.dims(), n.output, dtypes=dts, max_intermediate_bytes=PEAK_BYTES)
+        last = next(l for l in t.splitlines() if l.startswith("launch ") and " dst=-1 " in l)
+        out, loop = (int(re.search(k + r"=(\d+)", last).group(1)) for k in ("out", "loop"))
+        assert out <= 64 and loop >= 512, last
+        kinds.add(last.split()[3])
+    assert kinds == {"fast", "generic"}
+    for n, h in zip(pick, _handles(pick)):
+        assert rel_err(h.contract().cpu().numpy(), oracle_value(n)) <= REL_TOL
         h.close()
