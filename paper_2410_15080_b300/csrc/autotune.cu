@@ -61,17 +61,19 @@ std::string load_tile_table(const std::string& path, TileTable* t) {
     while (*c == ' ' || *c == '\t') ++c;
     if (*c == '#' || *c == '\n' || *c == 0) continue;
     long long k[5];
-    int swap = 0, bn = 0;
+    int swap = 0, bn = 0, pair = 0;
     double ms = 0, ms_rule = 0, ms_base = 0;
-    const int got = std::sscanf(c, "%lld %lld %lld %lld %lld : %d %d %lf %lf %lf", &k[0], &k[1], &k[2], &k[3],
-                                &k[4], &swap, &bn, &ms, &ms_rule, &ms_base);
-    if (got < 7 || (swap != 0 && swap != 1) || !gemm_bn_supported(bn) || k[0] < 0 || k[0] > 3) {
+    const int got = std::sscanf(c, "%lld %lld %lld %lld %lld : %d %d %lf %lf %lf %d", &k[0], &k[1], &k[2], &k[3],
+                                &k[4], &swap, &bn, &ms, &ms_rule, &ms_base, &pair);
+    if (got < 7 || (swap != 0 && swap != 1) || !gemm_bn_supported(bn) || k[0] < 0 || k[0] > 3 ||
+        (pair != 0 && pair != 1) || (pair && k[0] != 3)) {
       err = path + ":" + std::to_string(ln) + ": not a tile table line";
       break;
     }
     TileChoice ch;
     ch.swap = swap;
     ch.bn = bn;
+    ch.pair = pair;
     ch.ms = ms;
     ch.ms_rule = ms_rule;
     ch.ms_base = ms_base;
@@ -85,14 +87,14 @@ std::string save_tile_table(const std::string& path, const TileTable& t) {
   FILE* fp = std::fopen(path.c_str(), "w");
   if (!fp) return "cannot write the tile table " + path;
   std::fprintf(fp,
-               "# GEMM tile table: prec batch m n k : swap bn ms ms_rule ms_base\n"
+               "# GEMM tile table: prec batch m n k : swap bn ms ms_rule ms_base pair\n"
                "# (m, n: the step's index-group sizes; swap 1: m runs along the N tile of bn columns;\n"
                "#  median times in ms of that choice, of the padding rule's choice, and of 128-column\n"
-               "#  tiles with m along M unless m < 64)\n");
+               "#  tiles with m along M unless m < 64; pair 1: 256-row tiles on a pair of CTAs)\n");
   for (const auto& kv : t)
-    std::fprintf(fp, "%lld %lld %lld %lld %lld : %d %d %.6f %.6f %.6f\n", (long long)kv.first[0],
+    std::fprintf(fp, "%lld %lld %lld %lld %lld : %d %d %.6f %.6f %.6f %d\n", (long long)kv.first[0],
                  (long long)kv.first[1], (long long)kv.first[2], (long long)kv.first[3], (long long)kv.first[4],
-                 kv.second.swap, kv.second.bn, kv.second.ms, kv.second.ms_rule, kv.second.ms_base);
+                 kv.second.swap, kv.second.bn, kv.second.ms, kv.second.ms_rule, kv.second.ms_base, kv.second.pair);
   const bool ok = std::fclose(fp) == 0;
   return ok ? "" : "cannot write the tile table " + path;
 }
@@ -107,18 +109,22 @@ std::string default_tile_table_path() {
   return "gemm_tiles_b300.txt";
 }
 
-void choose_tile(const TileTable* t, int prec, double nb, double nm, double nn, double nk, bool* swap, int* bn) {
+void choose_tile(const TileTable* t, int prec, double nb, double nm, double nn, double nk, bool* swap, int* bn,
+                 int* pair) {
+  *pair = 0;
   if (t && !t->empty()) {
     auto it = t->find(TileKey{prec, (int64_t)nb, (int64_t)nm, (int64_t)nn, (int64_t)nk});
     if (it != t->end() && valid_tile(nm, nn, it->second.swap != 0, it->second.bn)) {
       *swap = it->second.swap != 0;
       *bn = it->second.bn;
+      *pair = prec == 3 ? it->second.pair : 0;
       return;
     }
     it = t->find(TileKey{prec, (int64_t)nb, (int64_t)nn, (int64_t)nm, (int64_t)nk});
     if (it != t->end() && valid_tile(nm, nn, it->second.swap == 0, it->second.bn)) {
       *swap = it->second.swap == 0;
       *bn = it->second.bn;
+      *pair = prec == 3 ? it->second.pair : 0;
       return;
     }
   }
@@ -198,14 +204,16 @@ std::string exec_autotune(const Executor* ex, int reps, TileTable* t, int* n, in
     if (err.empty() && (e = cudaMalloc(&C, c_bytes)) != cudaSuccess) cuda_fail(e);
     const bool base_swap = nm < 64 && nn >= 64;
     bool rule_swap = base_swap;
-    int rule_bn = 128;
-    choose_tile(nullptr, prec, (double)nb, (double)nm, (double)nn, (double)nk, &rule_swap, &rule_bn);
+    int rule_bn = 128, rule_pair = 0;
+    choose_tile(nullptr, prec, (double)nb, (double)nm, (double)nn, (double)nk, &rule_swap, &rule_bn, &rule_pair);
     TileChoice best;
     best.ms = std::numeric_limits<double>::infinity();
-    for (int o = 0; o < 2 && err.empty(); ++o)
+    for (int o = 0; o < 4 && err.empty(); ++o)
       for (int bn : kGemmBlockN) {
         if (!err.empty()) break;
-        const bool sw = o == 1;
+        const bool sw = (o & 1) != 0;
+        const int pair = o >> 1;  // CTA pairs: BF16x3 only
+        if (pair && prec != 3) continue;
         if (!valid_tile((double)nm, (double)nn, sw, bn)) continue;
         GemmArgs g;
         g.nval = nval;
@@ -217,11 +225,12 @@ std::string exec_autotune(const Executor* ex, int reps, TileTable* t, int* n, in
         g.kc_blocks = ex->kc_blocks;
         g.prec = prec;
         g.bn = bn;
+        g.pair = pair;
         g.status = status;
         bool ok = true;
         for (int v = 0; v < nval && ok; ++v)
           ok = make_operand_map(&g.maps.a[v], bufs[2 * v], prec, nb, g.M, nk, Kp, 128) &&
-               make_operand_map(&g.maps.b[v], bufs[2 * v + 1], prec, nb, g.N, nk, Kp, bn);
+               make_operand_map(&g.maps.b[v], bufs[2 * v + 1], prec, nb, g.N, nk, Kp, pair ? bn / 2 : bn);
         if (!ok) {
           *code = QTPU_ECUDA;
           err = "cuTensorMapEncodeTiled failed";
@@ -241,9 +250,9 @@ std::string exec_autotune(const Executor* ex, int reps, TileTable* t, int* n, in
         if (!err.empty()) break;
         std::sort(ms.begin(), ms.end());
         const double med = ms[ms.size() / 2];
-        if (sw == rule_swap && bn == rule_bn) best.ms_rule = med;
-        if (sw == base_swap && bn == 128) best.ms_base = med;
-        if (med < best.ms) best.ms = med, best.swap = sw ? 1 : 0, best.bn = bn;
+        if (sw == rule_swap && bn == rule_bn && !pair) best.ms_rule = med;
+        if (sw == base_swap && bn == 128 && !pair) best.ms_base = med;
+        if (med < best.ms) best.ms = med, best.swap = sw ? 1 : 0, best.bn = bn, best.pair = pair;
       }
     uint32_t hs = 0;
     if (err.empty() && (e = cudaMemcpy(&hs, status, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) cuda_fail(e);

@@ -167,6 +167,17 @@ namespace {
 constexpr int64_t kSmallLeaf = 256;   // leaves up to this size are absorbed
 constexpr int kMaxVirtualOps = 5;     // operands of one virtual tensor
 constexpr int64_t kMaxVirtualLoop = 256;
+// QTPU_GEMM_PAIR=0/1 sets the CTA-pair form of every BF16x3 GEMM whose tile
+// the lowering chooses (unset: the tile table's choice)
+int gemm_pair_override() {
+  static const int v = [] {
+    const char* e = std::getenv("QTPU_GEMM_PAIR");
+    return e ? (std::atoi(e) != 0 ? 1 : 0) : -1;
+  }();
+  return v;
+}
+// rows of B one TMA box loads: a CTA of a pair stages half of the N tile
+int gemm_b_box(const GemmArgs& g) { return g.pair ? g.bn / 2 : g.bn; }
 constexpr size_t kKeptSplitBudget = (size_t)8 << 30;  // device bytes for kept split results
 
 size_t dt_bytes(int dt) { return dt == DT_F32 ? 4 : 8; }
@@ -790,7 +801,8 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     if (T < 0 || it == gemm_out.end()) return false;
     const GemmOut& P = it->second;
     const Launch& LP = ex->launches[P.li];
-    if (LP.kind != LK_GEMM || LP.gemm.fuse.on || LP.gemm.prec != 3 || LP.gemm.bn != 128 || (P.K + 63) / 64 > 16)
+    if (LP.kind != LK_GEMM || LP.gemm.fuse.on || LP.gemm.prec != 3 || LP.gemm.bn != 128 || LP.gemm.pair ||
+        (P.K + 63) / 64 > 16)
       return false;
     // pieces cannot be added up: the producer must not sum over slice values
     if (LP.din != LP.dout) return false;
@@ -959,7 +971,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     // C^T = B^T A^T, so the 128-row tile runs along the longer dimension)
     const double lim = 2147483647.0;
     bool swap = nm < 64 && nn >= 64;
-    int bn = 128;
+    int bn = 128, pair = 0;
     bool oriented = false;  // fixed by the fused split of the consumer
     // when the next GEMM will contract this result over exactly the m (or n)
     // indices, make that group the stored outer (N) one: the epilogue then
@@ -978,7 +990,11 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
         oriented = true;
       }
     }
-    if (!oriented) choose_tile(tiles, prec, nb, nm, nn, nk, &swap, &bn);
+    if (!oriented) {
+      choose_tile(tiles, prec, nb, nm, nn, nk, &swap, &bn, &pair);
+      if (gemm_pair_override() >= 0) pair = gemm_pair_override();
+    }
+    if (prec != 3) pair = 0;
     const double gM = swap ? nn : nm, gN = swap ? nm : nn;
     const bool tc = sa.empty() && sb.empty() && gM >= 64 && gN >= 16 && nk >= 8 &&
                     nb * nm * nn * nk >= (double)(1 << 22) && nb < lim && nm < lim && nn < lim && nk < lim &&
@@ -1075,6 +1091,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
         LG.gemm.K = (int)Ka;
         LG.gemm.prec = prec;
         LG.gemm.bn = bn;
+        LG.gemm.pair = pair;
         LG.tile_key[0] = prec, LG.tile_key[1] = (int64_t)nb, LG.tile_key[2] = (int64_t)nm;
         LG.tile_key[3] = (int64_t)nn, LG.tile_key[4] = (int64_t)nk;
         LG.tile_fixed = oriented;
@@ -1545,7 +1562,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
         base[side] = ex->keptbuf + S.kept_off;
         kp[side] = S.g.Kp;
         const int64_t rows = side ? L.gemm.N : L.gemm.M;
-        const int box = side ? L.gemm.bn : 128;
+        const int box = side ? gemm_b_box(L.gemm) : 128;
         L.kept_maps[side].resize((size_t)S.kept_slots);
         for (int64_t c = 0; c < S.kept_slots; ++c)
           if (!make_operand_map(&L.kept_maps[side][c], base[side] + (size_t)c * S.kept_slot_bytes, prec,
@@ -1561,7 +1578,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
         kp[side] = S.g.Kp;
         // one map per split slot (slot 0 is the map set below)
         const int64_t rows = side ? L.gemm.N : L.gemm.M;
-        const int box = side ? L.gemm.bn : 128;
+        const int box = side ? gemm_b_box(L.gemm) : 128;
         for (int v = 1; v < ex->n_split_slots && S.side < 0; ++v) {
           CUtensorMap* m = side ? &L.gemm.maps.b[v] : &L.gemm.maps.a[v];
           if (!make_operand_map(m, base[side] + (size_t)v * ex->split_slot[side], prec, L.gemm.batch, rows, L.gemm.K,
@@ -1581,7 +1598,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       if (nc > 1) {
         L.opnd_owner[side] = T;
         const int64_t rows = side ? L.gemm.N : L.gemm.M;
-        const int box = side ? L.gemm.bn : 128;
+        const int box = side ? gemm_b_box(L.gemm) : 128;
         L.tm_copies[side].resize((size_t)nc);
         for (int64_t c = 0; c < nc; ++c)
           if (!make_operand_map(&L.tm_copies[side][c], base[side] + (size_t)c * St.bytes, prec, L.gemm.batch, rows,
@@ -1593,7 +1610,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     }
     if (!make_operand_map(&L.gemm.maps.a[0], base[0], prec, L.gemm.batch, L.gemm.M, L.gemm.K, kp[0], 128) ||
         !make_operand_map(&L.gemm.maps.b[0], base[1], prec, L.gemm.batch, L.gemm.N, L.gemm.K, kp[1],
-                          L.gemm.bn)) {
+                          gemm_b_box(L.gemm))) {
       exec_free(ex);
       return fail(QTPU_ECUDA, "cuTensorMapEncodeTiled failed");
     }
@@ -1649,7 +1666,7 @@ std::string exec_describe(const Executor* ex) {
     o << "launch " << i << " " << cls[L.kclass] << " ";
     if (L.kind == LK_GEMM) {
       o << "gemm batch=" << L.gemm.batch << " M=" << L.gemm.M << " N=" << L.gemm.N << " K=" << L.gemm.K
-        << " bn=" << L.gemm.bn;
+        << " bn=" << L.gemm.bn << (L.gemm.pair ? " pair" : "");
       if (L.gemm.fuse.on) o << " writes-pieces k=" << (L.gemm.fuse.k_is_m ? "M" : "N") << " w=" << L.gemm.fuse.w_size;
     } else if (L.kind == LK_CONTRACT64) {
       o << "fp64 out=" << L.c64.n_out << " loop=" << L.c64.n_loop;
@@ -1767,7 +1784,7 @@ void exec_launch_features(const Executor* ex, size_t i, float* f) {
     f[15] = lg(g.K);
     f[16] = lg(g.batch);
     f[17] = (float)nv;
-    const double mt = std::ceil(g.M / 128.0), nt = std::ceil(g.N / (double)g.bn);
+    const double mt = std::ceil(g.M / (g.pair ? 256.0 : 128.0)), nt = std::ceil(g.N / (double)g.bn);
     f[18] = (float)(g.M / (128.0 * mt));
     f[19] = (float)(g.N / ((double)g.bn * nt));
     f[20] = (float)(g.K / (64.0 * std::ceil(g.K / 64.0)));

@@ -196,6 +196,7 @@ struct Executor {
 struct TileChoice {
   int swap = 0;
   int bn = 128;
+  int pair = 0;  // BF16x3: 256-row tiles on a CTA pair
   double ms = 0, ms_rule = 0, ms_base = 0;
 };
 using TileKey = std::array<int64_t, 5>;
@@ -212,7 +213,8 @@ std::string default_tile_table_path();
 // than its width (112-column tiles of a 1296 x 1296 x 576 step took 0.98 of
 // the time of 128-column ones) -- ties keeping *swap as given and the wider
 // tile.
-void choose_tile(const TileTable* t, int prec, double nb, double nm, double nn, double nk, bool* swap, int* bn);
+void choose_tile(const TileTable* t, int prec, double nb, double nm, double nn, double nk, bool* swap, int* bn,
+                 int* pair);
 
 std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& leaves, const DimMap& dims,
                        int prec, int* code, bool dry_run = false, uint64_t reuse_bytes = 0,

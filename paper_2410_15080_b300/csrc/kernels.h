@@ -157,6 +157,8 @@ struct GemmArgs {
   GemmFuse fuse;         // fuse.on: C receives the consumer's piece planes
   int accum = 0;         // add the product to the stored (hi, lo) result (not with fuse)
   int bn = 128;          // N tile, one of kGemmBlockN (fuse: 128 only)
+  int pair = 0;          // BF16x3 without fuse: 256-row tiles on a cluster of two CTAs
+                         // (cta_group::2), each staging BN/2 rows of B (the B map's box)
 };
 cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st);
 // one warp waiting (bounded) on a barrier nothing completes: sets ST_TIMEOUT_DEP

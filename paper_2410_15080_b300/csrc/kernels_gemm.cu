@@ -24,11 +24,19 @@
 // table or by padding): a 216-wide side fills two 112-column tiles to 96 %
 // where 128-column tiles fill 84 %.  The M tile is 128 rows.  Every k-block
 // issues all its K-steps, zero-filled past K: on B300 skipping the K-steps
-// past K (a bound check in the MMA issue loop) made every launch slower,
-// even those with no partial k-block (1296 x 1296 x 576: 0.675 ms with the
-// check, 0.597 ms without).
+// past K made every launch slower, even those with no partial k-block
+// (1296 x 1296 x 576: 0.675 ms with a bound check in the MMA issue loop and
+// 0.660 ms with unrolled per-count variants, 0.591-0.597 ms without).
 //
-// One CTA per SM, persistent over (batch, m-tile, n-tile) tiles:
+// BF16x3 GEMMs can also run on CTA pairs (clusters of two, cta_group::2
+// MMAs of M = 256): each CTA stages its 128 rows of A and half of B's BN
+// rows, so a stage is 25 % smaller and three fit instead of two; the tile
+// table picks the form per problem (on B300 the 4-pair 216 x 7776 x 216 step
+// of the 100-qubit plan runs 12 % faster on pairs, 1296 x 1296 x 576 is
+// fastest on single CTAs).
+//
+// One CTA (or CTA pair) per SM (pair of SMs), persistent over (batch,
+// m-tile, n-tile) tiles:
 //   warp 0      TMA producer (one lane): pieces of A and B for one k-block
 //               (KB k: 64 for BF16x3, 32 for TF32) per pipeline stage, each
 //               piece p (A_p and B_p) counted on its own mbarrier; as many
@@ -91,17 +99,24 @@ struct Cfg<1> {  // TF32: one piece, one product
   __host__ __device__ static constexpr int pb(int) { return 0; }
 };
 
-// Shared memory: the pipeline stages (as many as fit, at most 4), the
-// barriers and, for the fused-split epilogue (BF16x3, BN = 128 only), its
-// tables.
-template <int PREC, int BN>
+// Shared memory: the pipeline stages (as many as fit, at most 8), the
+// barriers and, for the fused-split epilogue (BF16x3, BN = 128, one CTA per
+// tile only), its tables.  In a CTA pair each CTA stages its own 128 rows of
+// A and half of B's BN rows.
+template <int PREC, int BN, bool PAIR = false>
 struct Layout {
   using C = Cfg<PREC>;
-  static constexpr bool FUSE = PREC == 3 && BN == kFuseBN;
+  static constexpr bool FUSE = PREC == 3 && BN == kFuseBN && !PAIR;
   static constexpr int ROW = C::KB * C::ES;  // bytes per smem row (= swizzle span)
   static_assert(ROW == 64 || ROW == 128, "64- or 128-byte swizzle rows");
+  static constexpr int B_ROWS = PAIR ? BN / 2 : BN;  // B rows staged by one CTA
+  static_assert(B_ROWS % 8 == 0, "B rows in whole 8-row swizzle atoms");
+  static constexpr int TM = PAIR ? 2 * BM : BM;      // rows of a tile
+  // TMEM columns allocated: 2 buffers x (X, Y) x BN, a power of two; a
+  // pair's allocation covers both CTAs
+  static constexpr uint32_t TMEM_COLS = !PAIR || 4 * BN > 256 ? kTmemCols : 256;
   static constexpr int A_PIECE = BM * ROW;
-  static constexpr int B_PIECE = BN * ROW;
+  static constexpr int B_PIECE = B_ROWS * ROW;
   static constexpr int STAGE = C::NP * (A_PIECE + B_PIECE);
   static constexpr int FUSE_W = (int)kFuseMaxW * 8;
   static constexpr int FUSE_BYTES = FUSE ? FUSE_W + 4 * 128 * 4 + 4 * 128 * 4 + 16 : 0;
@@ -302,13 +317,47 @@ __device__ void fused_epilogue(const GemmFuse& fz, const float2* fW, uint8_t* sm
   }
 }
 
-template <int PREC, int BN>
+// The MMAs of one stage (all its K-steps) for the products whose later
+// piece is p (p is a constant after the caller's unrolling).
+template <int PREC, int BN, bool PAIR>
+__device__ __forceinline__ void issue_piece(int p, uint64_t dA0, uint64_t dB0, uint32_t dX, uint32_t dY,
+                                            uint32_t idesc, bool first_kb) {
+  using C = Cfg<PREC>;
+  using L = Layout<PREC, BN, PAIR>;
+#pragma unroll
+  for (int kk = 0; kk < C::KB / C::UK; ++kk) {
+    const bool first = first_kb && kk == 0;
+#pragma unroll
+    for (int pr = 0; pr < C::NPROD; ++pr) {
+      if ((C::pa(pr) > C::pb(pr) ? C::pa(pr) : C::pb(pr)) != p) continue;
+      const uint64_t ad = dA0 + (uint64_t)((C::pa(pr) * L::A_PIECE + kk * C::UK * C::ES) >> 4);
+      const uint64_t bd = dB0 + (uint64_t)((C::pb(pr) * L::B_PIECE + kk * C::UK * C::ES) >> 4);
+      const uint32_t accum = (first && pr <= 1) ? 0u : 1u;
+      const uint32_t d = pr == 0 ? dX : dY;
+      if constexpr (PAIR)
+        umma_f16_pair(d, ad, bd, idesc, accum);
+      else if (C::FMT == 1)
+        umma_f16(d, ad, bd, idesc, accum);
+      else
+        umma_tf32(d, ad, bd, idesc, accum);
+    }
+  }
+}
+
+// PAIR: a cluster of two CTAs computes each 256 x BN tile with cta_group::2
+// MMAs issued by rank 0 (the leader): each CTA loads its 128 rows of A and
+// BN/2 rows of B into its own shared memory and completes the bytes on the
+// leader's stage barriers; the leader's commits arrive on the stage and
+// accumulator barriers of both CTAs; each CTA's epilogue drains its own TMEM
+// (its 128 rows) and hands the accumulator back on the leader's barrier.
+template <int PREC, int BN, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ GemmMaps maps, int nval,
               float2* __restrict__ Cout, int batch, int M, int N, int K, int kc_blocks, uint32_t* status,
               uint64_t limit_ns, const __grid_constant__ GemmFuse fz, int accum) {
   using C = Cfg<PREC>;
-  using L = Layout<PREC, BN>;
+  using L = Layout<PREC, BN, PAIR>;
+  static_assert(!PAIR || PREC == 3, "CTA pairs for BF16x3 only");
   constexpr int NG = BN / 8;  // 8-column groups of a tile
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -323,7 +372,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
+  const uint32_t rank = PAIR ? cluster_rank() : 0u;
+  const bool leader = rank == 0;
+  // tiles are dealt to CTAs (or CTA pairs) round robin
+  const int tile0 = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int tstep = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  const int mt = (M + L::TM - 1) / L::TM, nt = (N + BN - 1) / BN;
   const int n_tiles = batch * mt * nt;  // host checks n_tiles < 2^31
   // k-blocks of one operand pair, and of all nval pairs in sequence (pair v
   // owns k-blocks [v * nkb1, (v + 1) * nkb1))
@@ -341,22 +395,31 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&accfull[a], 1);
-      mbar_init(&accempty[a], kEpiWarps);
+      // a pair's accumulator is free once the epilogue warps of both CTAs are done
+      mbar_init(&accempty[a], PAIR ? 2 * kEpiWarps : kEpiWarps);
     }
     mbar_init(mma_done, 1);
     *abort = 0;
     mbar_fence_init();
   }
   if (warp == 1) {
-    tmem_alloc(tmem_holder, kTmemCols);
-    tmem_relinquish();
+    if constexpr (PAIR) {
+      tmem_alloc_pair(tmem_holder, L::TMEM_COLS);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(tmem_holder, kTmemCols);
+      tmem_relinquish();
+    }
   }
   if (warp == 0 && lane < nval) {
     tma_prefetch_desc(&maps.a[lane]);
     tma_prefetch_desc(&maps.b[lane]);
   }
   tc_fence_before();
-  __syncthreads();
+  if constexpr (PAIR)
+    cluster_sync();  // the peer's barriers are initialised before either CTA signals them
+  else
+    __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
   float2* fW = reinterpret_cast<float2*>(smem + L::FUSE_OFF);
@@ -390,11 +453,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t issued_phase[L::STAGES];
       for (int s = 0; s < L::STAGES; ++s) issued[s] = 0, issued_phase[s] = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+      for (int t = tile0; t < n_tiles && ok; t += tstep) {
         const int ntile = (int)(t % nt);
         const int r = t / nt;
         const int mtile = (int)(r % mt);
         const int b = (int)(r / mt);
+        // this CTA's rows of A and of B
+        const int arow = mtile * L::TM + (int)rank * BM;
+        const int brow = ntile * BN + (int)rank * L::B_ROWS;
         for (int kb = 0; kb < nkb; ++kb) {
           if (!mbar_wait_bounded(&empty[stage], phase ^ 1, limit_ns, abort)) {
             set_abort(abort, status, ST_TIMEOUT_TMA);
@@ -409,9 +475,18 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int p = 0; p < C::NP; ++p) {
             uint64_t* fb = &full[stage * C::NP + p];
-            mbar_arrive_expect_tx(fb, L::A_PIECE + L::B_PIECE);
-            tma_load_4d(sA + p * L::A_PIECE, &maps.a[v], fb, kb1 * C::KB, mtile * BM, b, p);
-            tma_load_4d(sB + p * L::B_PIECE, &maps.b[v], fb, kb1 * C::KB, ntile * BN, b, p);
+            if constexpr (PAIR) {
+              // the leader expects both CTAs' bytes; the peer's copies may
+              // complete before that (the barrier's pending count goes below zero)
+              if (leader) mbar_arrive_expect_tx(fb, 2 * (L::A_PIECE + L::B_PIECE));
+              const uint32_t cfb = cluster_addr(fb, 0);
+              tma_load_4d_pair(sA + p * L::A_PIECE, &maps.a[v], cfb, kb1 * C::KB, arow, b, p);
+              tma_load_4d_pair(sB + p * L::B_PIECE, &maps.b[v], cfb, kb1 * C::KB, brow, b, p);
+            } else {
+              mbar_arrive_expect_tx(fb, L::A_PIECE + L::B_PIECE);
+              tma_load_4d(sA + p * L::A_PIECE, &maps.a[v], fb, kb1 * C::KB, arow, b, p);
+              tma_load_4d(sB + p * L::B_PIECE, &maps.b[v], fb, kb1 * C::KB, brow, b, p);
+            }
           }
           issued[stage] = 1;
           issued_phase[stage] = phase;
@@ -419,26 +494,38 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       if (!ok) {  // let copies already in flight land before the CTA exits
-        for (int s = 0; s < L::STAGES; ++s)
-          if (issued[s]) {
-            volatile int no_abort = 0;
-            for (int p = 0; p < C::NP; ++p) mbar_wait_bounded(&full[s * C::NP + p], issued_phase[s], limit_ns, &no_abort);
+        if constexpr (PAIR) {
+          // the pair's copies complete on the leader's barriers, whose phases
+          // the peer does not see: give them a fixed time (copies of a stage
+          // take microseconds)
+          const uint64_t t0 = global_ns();
+          while (global_ns() - t0 < 2000000ull) {
           }
+        } else {
+          for (int s = 0; s < L::STAGES; ++s)
+            if (issued[s]) {
+              volatile int no_abort = 0;
+              for (int p = 0; p < C::NP; ++p)
+                mbar_wait_bounded(&full[s * C::NP + p], issued_phase[s], limit_ns, &no_abort);
+            }
+        }
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    if (lane == 0 && leader) {
       // ------------------------------------------------------------ MMA issuer
-      const uint32_t idesc = make_idesc(C::FMT, BM, BN);
+      const uint32_t idesc = make_idesc(C::FMT, L::TM, BN);
       int stage = 0;
       uint32_t phase = 0;
       int item = 0;
       bool ok = true, any = false;
-      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+      for (int t = tile0; t < n_tiles && ok; t += tstep) {
         for (int ch = 0; ch < nchunks && ok; ++ch, ++item) {
           const int acc = (int)(item & 1);
           const uint32_t aph = (uint32_t)((item >> 1) & 1);
-          if (!mbar_wait_bounded(&accempty[acc], aph ^ 1, limit_ns, abort)) {
+          const bool free_acc = PAIR ? mbar_wait_bounded_cluster(&accempty[acc], aph ^ 1, limit_ns, abort)
+                                     : mbar_wait_bounded(&accempty[acc], aph ^ 1, limit_ns, abort);
+          if (!free_acc) {
             set_abort(abort, status, ST_TIMEOUT_MMA);
             ok = false;
             break;
@@ -465,34 +552,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
               }
               tc_fence_after();
-#pragma unroll
-              for (int kk = 0; kk < C::KB / C::UK; ++kk) {
-                const bool first = (kb == kb0 && kk == 0);
-#pragma unroll
-                for (int pr = 0; pr < C::NPROD; ++pr) {
-                  if ((C::pa(pr) > C::pb(pr) ? C::pa(pr) : C::pb(pr)) != p) continue;
-                  const uint64_t ad = dA0 + (uint64_t)((C::pa(pr) * L::A_PIECE + kk * C::UK * C::ES) >> 4);
-                  const uint64_t bd = dB0 + (uint64_t)((C::pb(pr) * L::B_PIECE + kk * C::UK * C::ES) >> 4);
-                  const uint32_t accum = (first && pr <= 1) ? 0u : 1u;
-                  const uint32_t d = pr == 0 ? dX : dY;
-                  if (C::FMT == 1)
-                    umma_f16(d, ad, bd, idesc, accum);
-                  else
-                    umma_tf32(d, ad, bd, idesc, accum);
-                }
-              }
+              issue_piece<PREC, BN, PAIR>(p, dA0, dB0, dX, dY, idesc, kb == kb0);
               any = true;
             }
             if (!ok) break;
-            umma_commit(&empty[stage]);
+            if constexpr (PAIR)
+              umma_commit_pair(&empty[stage], 3);
+            else
+              umma_commit(&empty[stage]);
             any = true;
             if (++stage == L::STAGES) stage = 0, phase ^= 1;
           }
-          if (ok) umma_commit(&accfull[acc]);
+          if (ok) {
+            if constexpr (PAIR)
+              umma_commit_pair(&accfull[acc], 3);
+            else
+              umma_commit(&accfull[acc]);
+          }
         }
       }
       if (!ok && any) {  // let issued MMAs finish before TMEM is freed
-        umma_commit(mma_done);
+        if constexpr (PAIR)
+          umma_commit_pair(mma_done, 1);
+        else
+          umma_commit(mma_done);
         volatile int no_abort = 0;
         mbar_wait_bounded(mma_done, 0, limit_ns, &no_abort);
       }
@@ -519,14 +602,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int h = ew >> 2;
     int item = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+    for (int t = tile0; t < n_tiles && ok; t += tstep) {
       const int ntile = (int)(t % nt);
       const int r = t / nt;
       const int mtile = (int)(r % mt);
       const int b = (int)(r / mt);
       // C is stored [batch][N][M] (M fastest): for a fixed column the 32
       // lanes of a warp write 32 consecutive rows, 256 contiguous bytes
-      const int row = mtile * BM + q * 32 + lane;
+      const int row = mtile * L::TM + (int)rank * BM + q * 32 + lane;
       float2* cb = Cout + (long long)b * M * N + row;
       const int n0 = ntile * BN;
       for (int ch = 0; ch < nchunks; ++ch, ++item) {
@@ -552,7 +635,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (g + 4 >= NG) {  // this warp's last group: the accumulator is free for the next chunk
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&accempty[acc]);
+            if (lane == 0) {
+              if constexpr (PAIR)
+                mbar_arrive_cluster(cluster_addr(&accempty[acc], 0));
+              else
+                mbar_arrive(&accempty[acc]);
+            }
           }
           if (row < M) {
             const int c0 = n0 + g * 8;
@@ -573,49 +661,94 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 
   tc_fence_before();
-  __syncthreads();
+  if constexpr (PAIR)
+    cluster_sync();  // neither CTA frees TMEM or exits while the pair still works
+  else
+    __syncthreads();
   tc_fence_after();
   if (warp == 1) {
     __syncwarp();
-    tmem_dealloc(tmem, kTmemCols);
+    if constexpr (PAIR)
+      tmem_dealloc_pair(tmem, L::TMEM_COLS);
+    else
+      tmem_dealloc(tmem, kTmemCols);
   }
 }
 
+// clusters of two that can be resident at once, per device (measured once
+// by gemm_prepare; half the SMs when unknown)
+constexpr int kMaxDevices = 64;
 template <int PREC, int BN>
+int* pair_clusters() {
+  static int n[kMaxDevices] = {};
+  return n;
+}
+
+template <int PREC, int BN, bool PAIR>
 cudaError_t launch_t(const GemmArgs& a, int sm_count, cudaStream_t st) {
-  using L = Layout<PREC, BN>;
-  const long long tiles = (long long)a.batch * ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
+  using L = Layout<PREC, BN, PAIR>;
+  const long long tiles = (long long)a.batch * ((a.M + L::TM - 1) / L::TM) * ((a.N + BN - 1) / BN);
   if (tiles <= 0) return cudaSuccess;
-  const int grid = (int)(tiles < sm_count ? tiles : sm_count);
   if (a.fuse.on && (!L::FUSE || a.fuse.w_size > kFuseMaxW || a.accum || a.nval != 1)) return cudaErrorInvalidValue;
   if (a.nval < 1 || a.nval > kGemmVals) return cudaErrorInvalidValue;
-  return launch_k(k_gemm_tc<PREC, BN>, dim3(grid), dim3(kThreads), (size_t)L::SMEM, st, a.maps, a.nval,
-                  (float2*)a.C, a.batch, a.M, a.N, a.K, a.kc_blocks, a.status, a.limit_ns, a.fuse, a.accum);
+  if constexpr (PAIR) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
+    int ncl = dev >= 0 && dev < kMaxDevices ? pair_clusters<PREC, BN>()[dev] : 0;
+    if (ncl <= 0) ncl = sm_count / 2;
+    const int grid = 2 * (int)(tiles < ncl ? tiles : ncl);
+    return launch_k_pair(k_gemm_tc<PREC, BN, true>, dim3(grid), dim3(kThreads), (size_t)L::SMEM, st, a.maps, a.nval,
+                         (float2*)a.C, a.batch, a.M, a.N, a.K, a.kc_blocks, a.status, a.limit_ns, a.fuse, a.accum);
+  } else {
+    const int grid = (int)(tiles < sm_count ? tiles : sm_count);
+    return launch_k(k_gemm_tc<PREC, BN, false>, dim3(grid), dim3(kThreads), (size_t)L::SMEM, st, a.maps, a.nval,
+                    (float2*)a.C, a.batch, a.M, a.N, a.K, a.kc_blocks, a.status, a.limit_ns, a.fuse, a.accum);
+  }
 }
 
-template <int PREC, int BN>
+template <int PREC, int BN, bool PAIR>
 cudaError_t prepare_t() {
-  return cudaFuncSetAttribute(k_gemm_tc<PREC, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Layout<PREC, BN>::SMEM);
+  using L = Layout<PREC, BN, PAIR>;
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<PREC, BN, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+  if (e != cudaSuccess || !PAIR) return e;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * (unsigned)(sms / 2));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = L::SMEM;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if ((e = cudaOccupancyMaxActiveClusters(&n, k_gemm_tc<PREC, BN, PAIR>, &cfg)) != cudaSuccess) return e;
+  if (dev >= 0 && dev < kMaxDevices) pair_clusters<PREC, BN>()[dev] = n > 0 ? n : sms / 2;
+  return cudaSuccess;
 }
 
-// the N tiles instantiated, in kGemmBlockN order
-template <int PREC>
+// the N tiles instantiated, in kGemmBlockN order; CTA pairs for BF16x3 only
+template <int PREC, bool PAIR>
 cudaError_t launch_p(const GemmArgs& a, int sm_count, cudaStream_t st) {
   switch (a.bn) {
-    case 128: return launch_t<PREC, 128>(a, sm_count, st);
-    case 112: return launch_t<PREC, 112>(a, sm_count, st);
-    case 96: return launch_t<PREC, 96>(a, sm_count, st);
-    case 80: return launch_t<PREC, 80>(a, sm_count, st);
-    case 64: return launch_t<PREC, 64>(a, sm_count, st);
-    case 48: return launch_t<PREC, 48>(a, sm_count, st);
+    case 128: return launch_t<PREC, 128, PAIR>(a, sm_count, st);
+    case 112: return launch_t<PREC, 112, PAIR>(a, sm_count, st);
+    case 96: return launch_t<PREC, 96, PAIR>(a, sm_count, st);
+    case 80: return launch_t<PREC, 80, PAIR>(a, sm_count, st);
+    case 64: return launch_t<PREC, 64, PAIR>(a, sm_count, st);
+    case 48: return launch_t<PREC, 48, PAIR>(a, sm_count, st);
     default: return cudaErrorInvalidValue;
   }
 }
-template <int PREC>
+template <int PREC, bool PAIR>
 cudaError_t prepare_p() {
   cudaError_t e = cudaSuccess;
-  for (cudaError_t x : {prepare_t<PREC, 128>(), prepare_t<PREC, 112>(), prepare_t<PREC, 96>(), prepare_t<PREC, 80>(),
-                        prepare_t<PREC, 64>(), prepare_t<PREC, 48>()})
+  for (cudaError_t x : {prepare_t<PREC, 128, PAIR>(), prepare_t<PREC, 112, PAIR>(), prepare_t<PREC, 96, PAIR>(),
+                        prepare_t<PREC, 80, PAIR>(), prepare_t<PREC, 64, PAIR>(), prepare_t<PREC, 48, PAIR>()})
     if (e == cudaSuccess) e = x;
   return e;
 }
@@ -651,18 +784,20 @@ bool gemm_bn_supported(int bn) {
 }
 
 cudaError_t gemm_prepare() {
-  cudaError_t e = prepare_p<1>();
-  if (e == cudaSuccess) e = prepare_p<2>();
-  if (e == cudaSuccess) e = prepare_p<3>();
+  cudaError_t e = prepare_p<1, false>();
+  if (e == cudaSuccess) e = prepare_p<2, false>();
+  if (e == cudaSuccess) e = prepare_p<3, false>();
+  if (e == cudaSuccess) e = prepare_p<3, true>();
   return e;
 }
 int gemm_k_block(int prec) { return prec == 3 ? Cfg<3>::KB : Cfg<1>::KB; }
 
 cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st) {
+  if (a.pair && (a.prec != 3 || a.fuse.on)) return cudaErrorInvalidValue;
   switch (a.prec) {
-    case 1: return launch_p<1>(a, sm_count, st);
-    case 2: return launch_p<2>(a, sm_count, st);
-    case 3: return launch_p<3>(a, sm_count, st);
+    case 1: return launch_p<1, false>(a, sm_count, st);
+    case 2: return launch_p<2, false>(a, sm_count, st);
+    case 3: return a.pair ? launch_p<3, true>(a, sm_count, st) : launch_p<3, false>(a, sm_count, st);
     default: return cudaErrorInvalidValue;
   }
 }

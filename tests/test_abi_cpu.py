@@ -343,8 +343,10 @@ def _gemm_launches(h):
     for line in h.lowering_info().splitlines():
         f = line.split()
         if len(f) > 2 and f[2] == "gemm":
-            out.append({k: int(v) for k, v in (w.split("=", 1) for w in f if "=" in w)
-                        if k in ("batch", "M", "N", "K", "bn")})
+            d = {k: int(v) for k, v in (w.split("=", 1) for w in f if "=" in w)
+                 if k in ("batch", "M", "N", "K", "bn")}
+            d["pair"] = int("pair" in f)
+            out.append(d)
     return out
 
 
@@ -371,12 +373,27 @@ def test_tile_table_sets_orientation_and_n_tile(tmp_path):
     h = _host_handle(net, autotune_table="")
     g = _gemm_launches(h)
     h.close()
-    assert g[0]["bn"] == 112 and g[0]["M"] == 300
+    assert g[0]["bn"] == 112 and g[0]["M"] == 300 and g[0]["pair"] == 0
+
+
+def test_tile_table_sets_the_cta_pair_form(tmp_path):
+    """The table's last field selects 256-row tiles on a pair of CTAs for a
+    BF16x3 GEMM; an entry without it, and the padding rule, keep one CTA per
+    tile."""
+    net = _one_gemm_net()
+    for pair in (0, 1):
+        path = tmp_path / "t.txt"
+        path.write_text(f"3 2 300 200 333 : 0 64 0.1 0.2 0.3 {pair}\n")
+        h = _host_handle(net, autotune_table=str(path))
+        g = _gemm_launches(h)
+        h.close()
+        assert len(g) == 1 and g[0]["bn"] == 64 and g[0]["M"] == 300 and g[0]["pair"] == pair, g
 
 
 def test_malformed_tile_table_is_rejected(tmp_path):
     net = _one_gemm_net()
-    for text in ["3 2 300 200 333 : 1 100\n", "3 2 300 200 : 1 128\n", "3 2 300 200 333 : 2 128\n"]:
+    for text in ["3 2 300 200 333 : 1 100\n", "3 2 300 200 : 1 128\n", "3 2 300 200 333 : 2 128\n",
+                 "3 2 300 200 333 : 0 128 1 1 1 2\n", "1 2 300 200 333 : 0 128 1 1 1 1\n"]:
         path = tmp_path / "bad.txt"
         path.write_text(text)
         with pytest.raises(htn.QtpuError) as e:

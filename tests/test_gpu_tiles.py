@@ -14,9 +14,9 @@ pytestmark = pytest.mark.gpu
 BNS = (128, 112, 96, 80, 64, 48)
 PREC_CODE = {"tf32": 1, "3xtf32": 2, "bf16x3": 3}
 TOL = {"bf16x3": REL_TOL, "3xtf32": 1e-5, "tf32": 1e-2}
-# ragged M/N against 128-row tiles and every N tile; K = 333 and 1100 end
-# inside a k-block (the K-steps past K are skipped) and K = 1100 takes two
-# accumulator chunks in BF16x3
+# ragged M/N against 128-row (and 256-row CTA-pair) tiles and every N tile;
+# K = 333 and 1100 end inside a k-block (zero-filled past K) and K = 1100
+# takes two accumulator chunks in BF16x3
 SHAPES = [(3, 300, 200, 333), (2, 520, 144, 1100), (4, 216, 776, 216)]
 
 
@@ -30,12 +30,13 @@ def _cuda():
 
 
 def _gemm_lines(h):
-    """batch, M, N, K and bn of every GEMM launch of the lowered plan"""
+    """batch, M, N, K, bn and the CTA-pair form of every GEMM launch of the
+    lowered plan"""
     out = []
     for line in h.lowering_info().splitlines():
         f = line.split()
         if len(f) > 2 and f[2] == "gemm":
-            d = {}
+            d = {"pair": int("pair" in f)}
             for w in f:
                 if "=" in w:
                     k, v = w.split("=", 1)
@@ -58,24 +59,26 @@ def test_every_orientation_and_n_tile(shape, prec, tmp_path):
     ref = np.matmul(A, B).ravel()
     dev = to_device(net)
     seen = set()
-    for swap in (0, 1):
-        for bn in BNS:
-            # the entry keyed both ways, so it applies whichever operand the
-            # plan takes first (the other key's swap is the complement)
-            path = tmp_path / f"t_{swap}_{bn}.txt"
-            p = PREC_CODE[prec]
-            path.write_text(f"{p} {b} {m} {n} {k} : {swap} {bn}\n{p} {b} {n} {m} {k} : {1 - swap} {bn}\n")
-            h = from_network(dev, net.output, prec=prec, autotune_table=str(path))
-            g = _gemm_lines(h)
-            assert len(g) == 1 and g[0]["bn"] == bn and g[0]["M"] == (n if swap else m), g
-            out = h.contract()
-            h.sync()
-            torch.cuda.synchronize()
-            err = rel_err(out.cpu().numpy(), ref)
-            h.close()
-            assert err <= TOL[prec], (swap, bn, err)
-            seen.add((swap, bn))
-    assert len(seen) == 12
+    cases = [(sw, c, q) for q in ((0, 1) if prec == "bf16x3" else (0,)) for sw in (0, 1) for c in BNS]
+    for swap, bn, pair in cases:
+        # the entry keyed both ways, so it applies whichever operand the
+        # plan takes first (the other key's swap is the complement)
+        path = tmp_path / f"t_{swap}_{bn}_{pair}.txt"
+        p = PREC_CODE[prec]
+        path.write_text(f"{p} {b} {m} {n} {k} : {swap} {bn} 0 0 0 {pair}\n"
+                        f"{p} {b} {n} {m} {k} : {1 - swap} {bn} 0 0 0 {pair}\n")
+        h = from_network(dev, net.output, prec=prec, autotune_table=str(path))
+        g = _gemm_lines(h)
+        assert len(g) == 1 and g[0]["bn"] == bn and g[0]["M"] == (n if swap else m), g
+        assert g[0]["pair"] == pair, g
+        out = h.contract()
+        h.sync()
+        torch.cuda.synchronize()
+        err = rel_err(out.cpu().numpy(), ref)
+        h.close()
+        assert err <= TOL[prec], (swap, bn, pair, err)
+        seen.add((swap, bn, pair))
+    assert len(seen) == len(cases) == (24 if prec == "bf16x3" else 12)
 
 
 def test_autotune_writes_a_table_the_plan_follows(tmp_path):
@@ -97,20 +100,21 @@ def test_autotune_writes_a_table_the_plan_follows(tmp_path):
             continue
         key, val = line.split(":")
         kk = tuple(int(x) for x in key.split())
-        sw, bn, ms, ms_rule, ms_base = val.split()
-        assert int(bn) in BNS and int(sw) in (0, 1)
+        sw, bn, ms, ms_rule, ms_base, pair = val.split()
+        assert int(bn) in BNS and int(sw) in (0, 1) and int(pair) in (0, 1)
         # the padding rule's choice and the 128-column one are among those timed
         assert 0 < float(ms) <= min(float(ms_rule), float(ms_base))
-        rows[kk] = (int(sw), int(bn))
+        rows[kk] = (int(sw), int(bn), int(pair))
     assert len(rows) == n
     h2 = from_network(dev, net.output, prec="bf16x3", autotune_table=str(path))
     # every GEMM launch runs its problem's tuned choice (or is a fixed
     # 128-column producer of a fused split)
     for g in _gemm_lines(h2):
-        match = [(sw, bn) for (p, b, m, n_, k), (sw, bn) in rows.items()
+        match = [(sw, bn, pair) for (p, b, m, n_, k), (sw, bn, pair) in rows.items()
                  if p == 3 and b == g["batch"] and k == g["K"] and {m, n_} == {g["M"], g["N"]}
                  and g["M"] == (n_ if sw else m)]
-        assert any(bn == g["bn"] for _, bn in match) or g["bn"] == 128, (g, rows)
+        assert any(bn == g["bn"] and pair == g["pair"] for _, bn, pair in match) or \
+            (g["bn"] == 128 and g["pair"] == 0), (g, rows)
     out = h2.contract()
     h2.sync()
     torch.cuda.synchronize()
