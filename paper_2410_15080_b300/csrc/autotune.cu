@@ -17,6 +17,7 @@
 #include <cstring>
 #include <limits>
 #include <set>
+#include <vector>
 
 #include "exec.h"
 
@@ -24,9 +25,9 @@ namespace qtpu {
 
 namespace {
 
-bool valid_tile(double nm, double nn, bool swap, int bn) {
+bool valid_tile(double nm, double nn, bool swap, int bn, int pair = 0) {
   const double gM = swap ? nn : nm, gN = swap ? nm : nn;
-  return gM >= 64 && gN >= 16 && gemm_bn_supported(bn);
+  return gM >= 64 && gN >= 16 && gemm_bn_supported(bn, pair);
 }
 
 // synthetic operand pieces: values uniform in [-1, 1) from a 32-bit hash of
@@ -65,8 +66,8 @@ std::string load_tile_table(const std::string& path, TileTable* t) {
     double ms = 0, ms_rule = 0, ms_base = 0;
     const int got = std::sscanf(c, "%lld %lld %lld %lld %lld : %d %d %lf %lf %lf %d", &k[0], &k[1], &k[2], &k[3],
                                 &k[4], &swap, &bn, &ms, &ms_rule, &ms_base, &pair);
-    if (got < 7 || (swap != 0 && swap != 1) || !gemm_bn_supported(bn) || k[0] < 0 || k[0] > 3 ||
-        (pair != 0 && pair != 1) || (pair && k[0] != 3)) {
+    if (got < 7 || (swap != 0 && swap != 1) || (pair != 0 && pair != 1) || !gemm_bn_supported(bn, pair) ||
+        k[0] < 0 || k[0] > 3 || (pair && k[0] != 3)) {
       err = path + ":" + std::to_string(ln) + ": not a tile table line";
       break;
     }
@@ -114,14 +115,14 @@ void choose_tile(const TileTable* t, int prec, double nb, double nm, double nn, 
   *pair = 0;
   if (t && !t->empty()) {
     auto it = t->find(TileKey{prec, (int64_t)nb, (int64_t)nm, (int64_t)nn, (int64_t)nk});
-    if (it != t->end() && valid_tile(nm, nn, it->second.swap != 0, it->second.bn)) {
+    if (it != t->end() && valid_tile(nm, nn, it->second.swap != 0, it->second.bn, it->second.pair)) {
       *swap = it->second.swap != 0;
       *bn = it->second.bn;
       *pair = prec == 3 ? it->second.pair : 0;
       return;
     }
     it = t->find(TileKey{prec, (int64_t)nb, (int64_t)nn, (int64_t)nm, (int64_t)nk});
-    if (it != t->end() && valid_tile(nm, nn, it->second.swap == 0, it->second.bn)) {
+    if (it != t->end() && valid_tile(nm, nn, it->second.swap == 0, it->second.bn, it->second.pair)) {
       *swap = it->second.swap == 0;
       *bn = it->second.bn;
       *pair = prec == 3 ? it->second.pair : 0;
@@ -208,13 +209,15 @@ std::string exec_autotune(const Executor* ex, int reps, TileTable* t, int* n, in
     choose_tile(nullptr, prec, (double)nb, (double)nm, (double)nn, (double)nk, &rule_swap, &rule_bn, &rule_pair);
     TileChoice best;
     best.ms = std::numeric_limits<double>::infinity();
+    std::vector<int> widths(std::begin(kGemmPairWideN), std::end(kGemmPairWideN));
+    widths.insert(widths.end(), std::begin(kGemmBlockN), std::end(kGemmBlockN));
     for (int o = 0; o < 4 && err.empty(); ++o)
-      for (int bn : kGemmBlockN) {
+      for (int bn : widths) {
         if (!err.empty()) break;
         const bool sw = (o & 1) != 0;
         const int pair = o >> 1;  // CTA pairs: BF16x3 only
         if (pair && prec != 3) continue;
-        if (!valid_tile((double)nm, (double)nn, sw, bn)) continue;
+        if (!valid_tile((double)nm, (double)nn, sw, bn, pair)) continue;
         GemmArgs g;
         g.nval = nval;
         g.C = C;

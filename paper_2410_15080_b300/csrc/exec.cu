@@ -995,6 +995,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       if (gemm_pair_override() >= 0) pair = gemm_pair_override();
     }
     if (prec != 3) pair = 0;
+    if (!pair && bn > 128) bn = 128;  // the wider tiles exist on CTA pairs only
     const double gM = swap ? nn : nm, gN = swap ? nm : nn;
     const bool tc = sa.empty() && sb.empty() && gM >= 64 && gN >= 16 && nk >= 8 &&
                     nb * nm * nn * nk >= (double)(1 << 22) && nb < lim && nm < lim && nn < lim && nk < lim &&

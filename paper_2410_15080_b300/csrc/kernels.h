@@ -156,7 +156,7 @@ struct GemmArgs {
   uint64_t limit_ns = 2000000000ull;
   GemmFuse fuse;         // fuse.on: C receives the consumer's piece planes
   int accum = 0;         // add the product to the stored (hi, lo) result (not with fuse)
-  int bn = 128;          // N tile, one of kGemmBlockN (fuse: 128 only)
+  int bn = 128;          // N tile, one of kGemmBlockN, or of kGemmPairWideN with pair (fuse: 128 only)
   int pair = 0;          // BF16x3 without fuse: 256-row tiles on a cluster of two CTAs
                          // (cta_group::2), each staging BN/2 rows of B (the B map's box)
 };
@@ -192,7 +192,9 @@ bool make_operand_map(CUtensorMap* map, void* base, int prec, int64_t batch, int
 // N tiles of the GEMM kernel (the M tile is 128 rows); B operand maps use a
 // box of bn rows
 constexpr int kGemmBlockN[6] = {128, 112, 96, 80, 64, 48};
-bool gemm_bn_supported(int bn);
+// wider N tiles, on CTA pairs only (one TMEM accumulator buffer)
+constexpr int kGemmPairWideN[2] = {256, 224};
+bool gemm_bn_supported(int bn, int pair = 0);
 int gemm_k_block(int prec);  // K elements per pipeline stage
 
 }  // namespace qtpu

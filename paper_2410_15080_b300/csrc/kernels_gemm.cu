@@ -112,9 +112,11 @@ struct Layout {
   static constexpr int B_ROWS = PAIR ? BN / 2 : BN;  // B rows staged by one CTA
   static_assert(B_ROWS % 8 == 0, "B rows in whole 8-row swizzle atoms");
   static constexpr int TM = PAIR ? 2 * BM : BM;      // rows of a tile
-  // TMEM columns allocated: 2 buffers x (X, Y) x BN, a power of two; a
-  // pair's allocation covers both CTAs
-  static constexpr uint32_t TMEM_COLS = !PAIR || 4 * BN > 256 ? kTmemCols : 256;
+  // TMEM accumulator buffers of (X, Y) x BN columns: two (the epilogue of a
+  // chunk overlaps the next chunk's MMAs) while they fit in 512 columns
+  static constexpr int ACC_BUFS = 4 * BN <= (int)kTmemCols ? 2 : 1;
+  // TMEM columns allocated, a power of two; a pair's allocation covers both CTAs
+  static constexpr uint32_t TMEM_COLS = !PAIR || 2 * ACC_BUFS * BN > 256 ? kTmemCols : 256;
   static constexpr int A_PIECE = BM * ROW;
   static constexpr int B_PIECE = B_ROWS * ROW;
   static constexpr int STAGE = C::NP * (A_PIECE + B_PIECE);
@@ -123,7 +125,8 @@ struct Layout {
   static constexpr int FIT = (kSmemLimit - 1024 - 256 - FUSE_BYTES) / STAGE;
   static constexpr int STAGES = FIT < 8 ? FIT : 8;
   static_assert(STAGES >= 2, "two pipeline stages must fit");
-  static_assert(BN % 16 == 0 && BN >= 16 && 4 * BN <= (int)kTmemCols, "UMMA N tile");
+  static_assert(BN % 16 == 0 && BN >= 16 && 2 * ACC_BUFS * BN <= (int)kTmemCols, "UMMA N tile");
+  static_assert(BN <= 128 || PAIR, "N tiles above 128 columns on CTA pairs only");
   static constexpr int BAR_OFF = STAGES * STAGE;
   // full[S][NP] (one per piece of a stage), empty[S], accfull[2],
   // accempty[2], mma_done
@@ -521,8 +524,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true, any = false;
       for (int t = tile0; t < n_tiles && ok; t += tstep) {
         for (int ch = 0; ch < nchunks && ok; ++ch, ++item) {
-          const int acc = (int)(item & 1);
-          const uint32_t aph = (uint32_t)((item >> 1) & 1);
+          const int acc = item % L::ACC_BUFS;
+          const uint32_t aph = (uint32_t)((item / L::ACC_BUFS) & 1);
           const bool free_acc = PAIR ? mbar_wait_bounded_cluster(&accempty[acc], aph ^ 1, limit_ns, abort)
                                      : mbar_wait_bounded(&accempty[acc], aph ^ 1, limit_ns, abort);
           if (!free_acc) {
@@ -613,8 +616,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       float2* cb = Cout + (long long)b * M * N + row;
       const int n0 = ntile * BN;
       for (int ch = 0; ch < nchunks; ++ch, ++item) {
-        const int acc = (int)(item & 1);
-        const uint32_t aph = (uint32_t)((item >> 1) & 1);
+        const int acc = item % L::ACC_BUFS;
+        const uint32_t aph = (uint32_t)((item / L::ACC_BUFS) & 1);
         // every lane waits, then the warp agrees (tcgen05.ld is warp-collective)
         const bool got = mbar_wait_bounded(&accfull[acc], aph, limit_ns, abort);
         if (!__all_sync(0xffffffffu, got)) {
@@ -734,6 +737,10 @@ cudaError_t prepare_t() {
 // the N tiles instantiated, in kGemmBlockN order; CTA pairs for BF16x3 only
 template <int PREC, bool PAIR>
 cudaError_t launch_p(const GemmArgs& a, int sm_count, cudaStream_t st) {
+  if constexpr (PAIR) {
+    if (a.bn == 256) return launch_t<PREC, 256, PAIR>(a, sm_count, st);
+    if (a.bn == 224) return launch_t<PREC, 224, PAIR>(a, sm_count, st);
+  }
   switch (a.bn) {
     case 128: return launch_t<PREC, 128, PAIR>(a, sm_count, st);
     case 112: return launch_t<PREC, 112, PAIR>(a, sm_count, st);
@@ -750,6 +757,10 @@ cudaError_t prepare_p() {
   for (cudaError_t x : {prepare_t<PREC, 128, PAIR>(), prepare_t<PREC, 112, PAIR>(), prepare_t<PREC, 96, PAIR>(),
                         prepare_t<PREC, 80, PAIR>(), prepare_t<PREC, 64, PAIR>(), prepare_t<PREC, 48, PAIR>()})
     if (e == cudaSuccess) e = x;
+  if constexpr (PAIR) {
+    if (e == cudaSuccess) e = prepare_t<PREC, 256, PAIR>();
+    if (e == cudaSuccess) e = prepare_t<PREC, 224, PAIR>();
+  }
   return e;
 }
 
@@ -777,9 +788,12 @@ cudaError_t launch_bounded_wait_probe(uint32_t* status, uint64_t limit_ns, cudaS
   return cudaGetLastError();
 }
 
-bool gemm_bn_supported(int bn) {
+bool gemm_bn_supported(int bn, int pair) {
   for (int b : kGemmBlockN)
     if (b == bn) return true;
+  if (pair)
+    for (int b : kGemmPairWideN)
+      if (b == bn) return true;
   return false;
 }
 
