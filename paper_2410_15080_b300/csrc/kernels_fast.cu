@@ -11,6 +11,7 @@
 // load and one compensated multiply-add.
 #include <cuda_bf16.h>
 
+
 #include "arith.cuh"
 #include "common.cuh"
 #include "kernels.h"
@@ -638,52 +639,55 @@ __global__ void __launch_bounds__(256) k_split_fast(const GatherArgs a, void* __
 }
 
 // ------------------------------------------------------------ split, one term
-// The same tiles as k_split_fast for entries of one term (a large operand,
-// times W when small factors are absorbed), software-pipelined: a block loads
+// Tiles like k_split_fast's (but 64 rows high) for entries of one term (a
+// large operand, times W when small factors are absorbed), software-pipelined: a block loads
 // its next tile into registers before it writes the current one, so the load
 // latency overlaps the piece arithmetic, the stores and the barriers.  The
 // index tables of the next tile are built during the current write.
-template <int DT0, bool HW, int KIND, int NP>
-__global__ void __launch_bounds__(256) k_split_pipe(const GatherArgs a, void* __restrict__ dst) {
+// Tiles of TR rows x 64 k: with 64 rows each block has 32 KB of loads in
+// flight, and three blocks per SM (80 registers a thread) 96 KB.
+constexpr int kPipeTR = 64;
+template <int DT0, bool HW, int KIND, int NP, int TR>
+__global__ void __launch_bounds__(256, 3) k_split_pipe(const GatherArgs a, void* __restrict__ dst) {
   constexpr int NOPS = 1 + (HW ? 1 : 0);
-  constexpr int PER = kTR * kTK / 256;
+  constexpr int PER = TR * kTK / 256;
   extern __shared__ float2 W[];  // w_size entries (dynamic shared memory)
-  __shared__ int64_t rowoff[2][kTR][NOPS];
+  __shared__ int64_t rowoff[2][TR][NOPS];
   __shared__ int64_t koff[2][kTK][NOPS];
-  __shared__ float2 tile[kTR][kTK + 1];
+  __shared__ float2 tile[TR][kTK + 1];
   if (HW) build_w(a, W);
   __syncthreads();
   pdl_wait();
   pdl_launch_dependents();
-  const uint32_t n_rt = (a.n_rows + kTR - 1) / kTR;
+  const uint32_t n_rt = (a.n_rows + TR - 1) / TR;
   const uint32_t n_kt = (a.Kp + kTK - 1) / kTK;
   const uint32_t n_tiles = n_rt * n_kt;
   const int64_t piece = (int64_t)a.n_rows * a.Kp;
   const int tid = threadIdx.x;
   auto tables = [&](uint32_t t, int buf) {
     const uint32_t rt = t / n_kt, kt = t - rt * n_kt;
-    const uint32_t r0 = rt * kTR, k0 = kt * kTK;
-    if (tid < kTR) {
+    const uint32_t r0 = rt * TR, k0 = kt * kTK;
+    if (tid < TR) {
       int64_t o[NOPS];
       offsets<NOPS>(min(r0 + tid, a.n_rows - 1), a.out, o);
 #pragma unroll
       for (int j = 0; j < NOPS; ++j) rowoff[buf][tid][j] = o[j];
-    } else if (tid < kTR + kTK) {
+    } else if (tid < TR + kTK) {
       int64_t o[NOPS];
-      offsets<NOPS>(min(k0 + (tid - kTR), a.K - 1), a.kmodes, o);
+      offsets<NOPS>(min(k0 + (tid - TR), a.K - 1), a.kmodes, o);
 #pragma unroll
-      for (int j = 0; j < NOPS; ++j) koff[buf][tid - kTR][j] = o[j];
+      for (int j = 0; j < NOPS; ++j) koff[buf][tid - TR][j] = o[j];
     }
   };
   float2 v[PER];
   auto load = [&](uint32_t t, int buf) {
     const uint32_t rt = t / n_kt, kt = t - rt * n_kt;
-    const uint32_t r0 = rt * kTR, k0 = kt * kTK;
+    const uint32_t r0 = rt * TR, k0 = kt * kTK;
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       const int e = tid + u * 256;
-      const int r = a.row_fast ? e % kTR : e / kTK;
-      const int k = a.row_fast ? e / kTR : e % kTK;
+      const int r = a.row_fast ? e % TR : e / kTK;
+      const int k = a.row_fast ? e / TR : e % kTK;
       v[u] = r0 + r < a.n_rows && k0 + k < a.K ? load_pair<DT0>(a.ptr[0], rowoff[buf][r][0] + koff[buf][k][0])
                                                 : make_float2(0.f, 0.f);
     }
@@ -692,8 +696,8 @@ __global__ void __launch_bounds__(256) k_split_pipe(const GatherArgs a, void* __
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       const int e = tid + u * 256;
-      const int r = a.row_fast ? e % kTR : e / kTK;
-      const int k = a.row_fast ? e / kTR : e % kTK;
+      const int r = a.row_fast ? e % TR : e / kTK;
+      const int k = a.row_fast ? e / TR : e % kTK;
       float2 x = v[u];
       if (HW) x = mul_pair(x, W[rowoff[buf][r][NOPS - 1] + koff[buf][k][NOPS - 1]]);
       tile[r][k] = x;
@@ -713,9 +717,10 @@ __global__ void __launch_bounds__(256) k_split_pipe(const GatherArgs a, void* __
     const bool more = nt < n_tiles;
     if (more) load(nt, buf ^ 1);  // in flight during this tile's write
     const uint32_t rt = t / n_kt, kt = t - rt * n_kt;
-    const uint32_t r0 = rt * kTR, k0 = kt * kTK;
-    {
-      const int r = tid >> 3, kk = (tid & 7) * 8;
+    const uint32_t r0 = rt * TR, k0 = kt * kTK;
+#pragma unroll
+    for (int rr = 0; rr < TR; rr += 32) {
+      const int r = (tid >> 3) + rr, kk = (tid & 7) * 8;
       const uint32_t row = r0 + r, kb = k0 + kk;
       const bool in = row < a.n_rows && kb < a.Kp;
       if (KIND == 0) {
@@ -806,13 +811,14 @@ cudaError_t split_dt(const GatherArgs& a, void* out, int sm, cudaStream_t st) {
         cudaError_t e = allow_smem(kernel);
         if (e != cudaSuccess) return e;
       }
-      // ~64 registers a thread: 4 blocks of 256 per SM stay resident
-      const int gp = (int)(tiles < (int64_t)sm * 4 ? tiles : (int64_t)sm * 4);
+      // 64-row tiles, 80 registers a thread: 3 blocks of 256 per SM stay resident
+      const int64_t tp = (int64_t)((a.n_rows + kPipeTR - 1) / kPipeTR) * ((a.Kp + kTK - 1) / kTK);
+      const int gp = (int)(tp < (int64_t)sm * 3 ? tp : (int64_t)sm * 3);
       return launch_k(kernel, dim3(gp), dim3(256), sm_bytes, st, a, out);
     };
-    if (a.mode == GW_SPLIT_BF16X3) return go(k_split_pipe<DT0, HW, 0, 3>);
-    if (a.mode == GW_SPLIT_TF32X2) return go(k_split_pipe<DT0, HW, 1, 2>);
-    return go(k_split_pipe<DT0, HW, 1, 1>);
+    if (a.mode == GW_SPLIT_BF16X3) return go(k_split_pipe<DT0, HW, 0, 3, kPipeTR>);
+    if (a.mode == GW_SPLIT_TF32X2) return go(k_split_pipe<DT0, HW, 1, 2, kPipeTR>);
+    return go(k_split_pipe<DT0, HW, 1, 1, kPipeTR>);
   }
   if (HW && a.fan && a.fan_f == 4) return split_f<DT0, HW, 4>(a, out, g, st);
   if (HW && a.fan && a.fan_f == 2) return split_f<DT0, HW, 2>(a, out, g, st);
