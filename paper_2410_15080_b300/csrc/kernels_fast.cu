@@ -313,9 +313,9 @@ __host__ __device__ __forceinline__ uint32_t dot_slot(uint32_t u) { return u + (
 // B300) runs once per kDotFold tuples instead of once per term.
 constexpr int kDotFold = 8;
 
-template <int DT0, int DT1, bool F64>
+template <int DT0, int DT1, bool F64, int PER>
 __global__ void __launch_bounds__(256) k_dot_fast(const GatherArgs a) {
-  constexpr int PER = kDotMaxTile / 256;
+  // PER >= tile_n / 256 entries of the tile per thread
   extern __shared__ float2 dsm[];
   const uint32_t T = a.tile_n;
   float2* sX = dsm;                                                   // T + T/16 slots
@@ -343,12 +343,13 @@ __global__ void __launch_bounds__(256) k_dot_fast(const GatherArgs a) {
   Acc acc;
   double accd = 0.0;
   int fold = 0;
-  // register double buffer: the next tuple's loads are in flight while the
-  // current tuple is multiplied
-  float2 xv[PER], yv[PER];
-  if (t0 < t1) {
+  // two register buffers: the loads of the next two tuples are in flight
+  // while the current tuple is multiplied (the buffers alternate, so no
+  // register copy waits on a load)
+  float2 xa[PER], ya[PER], xb[PER], yb[PER];
+  auto load = [&](uint32_t t, float2* xv, float2* yv) {
     int64_t ot[2];
-    offsets<2>(t0, a.loop, ot);
+    offsets<2>(t, a.loop, ot);
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const uint32_t v = threadIdx.x + k * 256;
@@ -357,8 +358,8 @@ __global__ void __launch_bounds__(256) k_dot_fast(const GatherArgs a) {
         yv[k] = load_pair<DT1>(Y, base[1] + ot[1] + ty[v]);
       }
     }
-  }
-  for (uint32_t t = t0; t < t1; ++t) {
+  };
+  auto step = [&](uint32_t t, float2* xv, float2* yv) {
     __syncthreads();  // the previous tuple's tile is consumed
     float2 yc[PER];
 #pragma unroll
@@ -368,18 +369,7 @@ __global__ void __launch_bounds__(256) k_dot_fast(const GatherArgs a) {
       yc[k] = yv[k];
     }
     __syncthreads();
-    if (t + 1 < t1) {
-      int64_t ot[2];
-      offsets<2>(t + 1, a.loop, ot);
-#pragma unroll
-      for (int k = 0; k < PER; ++k) {
-        const uint32_t v = threadIdx.x + k * 256;
-        if (v < T) {
-          xv[k] = load_pair<DT0>(X, base[0] + ot[0] + tx[v].y);
-          yv[k] = load_pair<DT1>(Y, base[1] + ot[1] + ty[v]);
-        }
-      }
-    }
+    if (t + 2 < t1) load(t + 2, xv, yv);
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const uint32_t u = threadIdx.x + k * 256;
@@ -390,6 +380,12 @@ __global__ void __launch_bounds__(256) k_dot_fast(const GatherArgs a) {
       acc = Acc();
       fold = 0;
     }
+  };
+  if (t0 < t1) load(t0, xa, ya);
+  if (t0 + 1 < t1) load(t0 + 1, xb, yb);
+  for (uint32_t t = t0; t < t1; t += 2) {
+    step(t, xa, ya);
+    if (t + 1 < t1) step(t + 1, xb, yb);
   }
   if (F64) {
     // FP64 block sum -> scratch[o][c] (the scratch holds doubles here)
@@ -449,15 +445,25 @@ __global__ void __launch_bounds__(256) k_dot_finish(const float2* __restrict__ p
 
 size_t dot_smem_bytes(uint32_t T) { return (dot_slot(T) + 1) * sizeof(float2) + T * (sizeof(int2) + sizeof(int)); }
 
+template <int DT0, int DT1, int PER>
+cudaError_t dot_main(const GatherArgs& a, size_t sm_bytes, bool f64, cudaStream_t st) {
+  auto kern = f64 ? k_dot_fast<DT0, DT1, true, PER> : k_dot_fast<DT0, DT1, false, PER>;
+  cudaError_t e = cudaSuccess;
+  if (sm_bytes > 40960) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_bytes);
+  if (e != cudaSuccess) return e;
+  return launch_k(kern, dim3(a.chunks, a.n_out), dim3(256), sm_bytes, st, a);
+}
+
 template <int DT0, int DT1>
 cudaError_t dot_launch(const GatherArgs& a, void* out, cudaStream_t st) {
   const size_t sm_bytes = dot_smem_bytes(a.tile_n);
   const bool f64 = a.mode == GW_DENSE_F64;
-  auto kern = f64 ? k_dot_fast<DT0, DT1, true> : k_dot_fast<DT0, DT1, false>;
-  cudaError_t e = cudaSuccess;
-  if (sm_bytes > 40960) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_bytes);
-  if (e != cudaSuccess) return e;
-  e = launch_k(kern, dim3(a.chunks, a.n_out), dim3(256), sm_bytes, st, a);
+  // tile entries per thread, rounded up to an instantiated count
+  const uint32_t per = (a.tile_n + 255) / 256;
+  cudaError_t e = per <= 2   ? dot_main<DT0, DT1, 2>(a, sm_bytes, f64, st)
+                  : per <= 4 ? dot_main<DT0, DT1, 4>(a, sm_bytes, f64, st)
+                  : per <= 6 ? dot_main<DT0, DT1, 6>(a, sm_bytes, f64, st)
+                             : dot_main<DT0, DT1, kDotMaxTile / 256>(a, sm_bytes, f64, st);
   if (e != cudaSuccess) return e;
   const uint32_t g = (a.n_out + 255) / 256;
   const float2* part = a.scratch;
