@@ -192,13 +192,13 @@ __device__ __forceinline__ void digits(uint32_t l, const GModes& t, uint32_t* id
   }
 }
 
-// lanes per output for a sum of n_loop terms over few outputs: groups of
-// 2^lg consecutive lanes share an output (each lane a contiguous run of at
-// least 8 terms) while the outputs leave most of the GPU's lanes idle
+// lanes per output for a sum of n_loop terms: groups of 2^lg consecutive
+// lanes share an output (each lane a contiguous run of at least 8 terms)
+// while the lanes stay within half of what the SMs hold at once (1024 a
+// SM); with more outputs than that, one lane per output already fills them
 inline int lanes_for_long_sum(uint32_t n_out, uint32_t n_loop, int sm_count) {
   int lg = 0;
-  if (n_out > (uint32_t)sm_count * 64) return 0;
-  while (lg < 5 && (8u << (lg + 1)) <= n_loop && ((uint64_t)n_out << (lg + 1)) <= (uint64_t)sm_count * 2048) ++lg;
+  while (lg < 5 && (8u << (lg + 1)) <= n_loop && ((uint64_t)n_out << (lg + 1)) <= (uint64_t)sm_count * 1024) ++lg;
   return lg;
 }
 
