@@ -1786,7 +1786,7 @@ void exec_launch_features(const Executor* ex, size_t i, float* f) {
     f[16] = lg(g.batch);
     f[17] = (float)nv;
     const double mt = std::ceil(g.M / (g.pair ? 256.0 : 128.0)), nt = std::ceil(g.N / (double)g.bn);
-    f[18] = (float)(g.M / (128.0 * mt));
+    f[18] = (float)(g.M / ((g.pair ? 256.0 : 128.0) * mt));
     f[19] = (float)(g.N / ((double)g.bn * nt));
     f[20] = (float)(g.K / (64.0 * std::ceil(g.K / 64.0)));
     f[21] = g.fuse.on ? 1.f : 0.f;
