@@ -36,7 +36,9 @@ QTPU_ENOTSUP at the same point).
 Pinned by tests/test_oracle_planner.py: a plan's cost never exceeds the naive
 knitting cost (section 4.2, worst case equals naive), the paper's 432 and 20
 FLOP components, the plan executes through ``oracle.tn`` to the brute-force
-value, and brute-force enumeration of orders on tiny nets.
+value, brute-force enumeration of orders on tiny nets, the slicer's choice
+against peaks measured by a numpy contraction of one slice, and the greedy
+key's tie-breaks on networks built to tie every earlier component.
 """
 from __future__ import annotations
 

@@ -515,3 +515,16 @@ def test_kept_split_results_remove_reruns(monkeypatch):
         assert r == distinct, (i, din, r)
     assert any(r > 4 ** len(d.split(",")) for d, r in plain.values() if d != "-")
     assert n_kept < n_plain
+
+
+def test_greedy_tie_breaks_match_the_oracle():
+    """The C++ planner resolves the greedy key's ties like the oracle (FLOPs,
+    then x, then y): same plan text on networks built to tie each component."""
+    from tests.test_oracle_planner import FLOP_TIE, ID_TIE_X, ID_TIE_Y, _tiny
+    for case in (FLOP_TIE, ID_TIE_X, ID_TIE_Y):
+        net = _tiny(*case)
+        h = _host_handle(net)
+        txt = h.plan_info()
+        h.close()
+        op = planner.make_plan(net.inds(), net.dims(), net.output)
+        assert txt == planner.plan_text(op, net.inds())

@@ -93,3 +93,74 @@ def test_slicing_targets():
     assert planner.slice_stats(p2, net.inds(), p2.sliced)[0] * 8 <= lim
     with pytest.raises(ValueError):
         planner.make_plan(net.inds(), net.dims(), net.output, max_bytes=8)
+
+
+def _measured_peak(tensors, output, order, fixed):
+    """Largest step result (entries) of a pairwise contraction along ``order``
+    with the indices in ``fixed`` held at the given values, contracted here
+    with numpy einsum (independent of the planner's size bookkeeping)."""
+    live = {}
+    for t, (inds, arr) in enumerate(tensors):
+        sl = tuple(fixed.get(i, slice(None)) for i in inds)
+        live[t] = ([i for i in inds if i not in fixed], np.asarray(arr)[sl])
+    nxt, peak = len(tensors), 0
+    letters = {}
+    sym = lambda v: "".join(letters.setdefault(i, chr(ord("a") + len(letters))) for i in v)  # noqa: E731
+    for x, y in order:
+        (ia, A), (ib, B) = live.pop(x), live.pop(y)
+        elsewhere = set(output).union(*[set(v[0]) for v in live.values()])
+        keep = [i for i in dict.fromkeys(ia + ib) if i in elsewhere]
+        R = np.einsum(f"{sym(ia)},{sym(ib)}->{sym(keep)}", A, B)
+        peak = max(peak, R.size)
+        live[nxt] = (keep, R)
+        nxt += 1
+    return peak
+
+
+@pytest.mark.parametrize("seed", [2, 10, 14, 33, 39])
+def test_slicer_takes_the_index_with_the_smallest_peak(seed):
+    """Slicing on the fixed tree takes the gate index whose slicing leaves the
+    smallest peak intermediate, as measured by contracting slice 0 along the
+    plan's order with numpy.  On these small random networks the candidates'
+    peaks differ and the minimum is unique, so a slicer that maximised (or
+    ignored) the peak picks another index."""
+    net = synth.random_htn(seed, n_sub_range=(3, 5), n_cuts_range=(4, 8), k_range=(2, 4), max_qt_entries=1 << 12)
+    inds, dims, out = net.inds(), net.dims(), net.output
+    p0 = planner.make_plan(inds, dims, out)
+    order = planner.order_of(p0)
+    cands = [i for i in sorted(dims) if i not in out and dims[i] == 6]
+    peaks = {i: _measured_peak(net.pairs(), out, order, {i: 0}) for i in cands}
+    p1 = planner.make_plan(inds, dims, out, n_slices=6, slice_dim=6)
+    assert planner.order_of(p1) == order and len(p1.sliced) == 1
+    assert sorted(peaks.values()).count(min(peaks.values())) == 1
+    assert peaks[p1.sliced[0]] == min(peaks.values())
+    # the unsliced peak, measured the same way, is the planner's own figure
+    assert _measured_peak(net.pairs(), out, order, {}) == planner.slice_stats(p0, inds, ())[0]
+
+
+def _tiny(shapes, output):
+    """An h-TN of zero-filled QTs with the given (indices, dims) (values
+    play no part in planning)."""
+    return synth.HTN([synth.Tensor("QT", tuple(i), np.zeros(d)) for i, d in shapes], tuple(output))
+
+
+# two disjoint pairs whose contraction changes the live size by the same -4
+# entries: (0, 1) costs 2*2*4*2 = 32 FLOPs, (2, 3) costs 2*2*2*2 = 16
+FLOP_TIE = ([((0, 1), (2, 2)), ((1, 2), (2, 4)), ((3, 4), (2, 2)), ((4, 5), (2, 2))], (0, 2, 3, 5))
+# two identical disjoint pairs: every key component but the ids ties
+ID_TIE_X = ([((0, 1), (2, 3)), ((1, 2), (3, 2)), ((3, 4), (2, 3)), ((4, 5), (3, 2))], (0, 2, 3, 5))
+# one tensor sharing one index with each of two others, symmetric: the pairs
+# (0, 1) and (0, 2) tie on size change, FLOPs and x
+ID_TIE_Y = ([((0, 1, 2), (2, 3, 3)), ((1, 3), (3, 2)), ((2, 4), (3, 2))], (0, 3, 4))
+
+
+@pytest.mark.parametrize("case,first", [(FLOP_TIE, (2, 3)), (ID_TIE_X, (0, 1)), (ID_TIE_Y, (0, 1))],
+                         ids=["flops", "x", "y"])
+def test_greedy_tie_breaks(case, first):
+    """The greedy key after the size change: fewer FLOPs first, then the
+    smaller x, then the smaller y (the rule in the module header); each case
+    ties every component before the one it tests, so reordering or dropping
+    that component picks the other pair."""
+    net = _tiny(*case)
+    p = planner.make_plan(net.inds(), net.dims(), net.output)
+    assert (p.steps[0].x, p.steps[0].y) == first
