@@ -40,13 +40,15 @@
 //   warp 0      TMA producer (one lane): pieces of A and B for one k-block
 //               (KB k: 64 for BF16x3, 32 for TF32) per pipeline stage, each
 //               piece p (A_p and B_p) counted on its own mbarrier; as many
-//               stages as fit (2 for BF16x3 with 128-column tiles, 3 with 64
-//               or 48);
-//   warp 1      TMEM owner and MMA issuer (one lane): per k-block and piece
-//               p as it lands, the K-steps of the products whose later piece
-//               is p (x0*y0; x0*y1, x1*y0, x1*y1; x0*y2, x2*y0), into one of
-//               two TMEM accumulators (double-buffered so the epilogue of one
-//               chunk overlaps the MMAs of the next);
+//               stages as fit (BF16x3: 2 with 128-column tiles on one CTA,
+//               3 with 64 or 48 columns or on a pair, 2 with a pair's 224 or
+//               256 columns);
+//   warp 1      TMEM owner and MMA issuer (one lane; rank 0 of a pair): per
+//               k-block and piece p as it lands, the K-steps of the products
+//               whose later piece is p (x0*y0; x0*y1, x1*y0, x1*y1; x0*y2,
+//               x2*y0), into one of two TMEM accumulator buffers
+//               (double-buffered so the epilogue of one chunk overlaps the
+//               MMAs of the next; one buffer for N tiles above 128 columns);
 //   warps 2..17 epilogue: tcgen05.ld 32 lanes x 8-column groups of both
 //               accumulators, X + Y as an exact (hi, lo) float pair (TwoSum)
 //               stored, or added to the stored pair for later chunks.
