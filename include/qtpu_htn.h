@@ -386,6 +386,16 @@ qtpu_status qtpu_htn_sync(qtpu_htn* h);
  * the handle stays usable. */
 qtpu_status qtpu_htn_selftest_timeout(qtpu_htn* h, uint64_t limit_ns);
 
+/* Failure-path self-test of the tensor-core GEMM itself: enqueue on the
+ * handle's stream one BF16x3 GEMM launch (256 x 128 x 64, on one CTA per
+ * tile with pair = 0 or on a CTA pair with pair = 1) whose producer issues no
+ * copies.  The MMA issuer's and the epilogue's bounded waits give up after
+ * limit_ns (at most 10 s); the kernel lets nothing in flight, frees its TMEM
+ * and returns, and the next qtpu_htn_sync returns QTPU_ETIMEOUT.  Nothing
+ * faults, traps or hangs, and the handle stays usable.  QTPU_ESTATE before a
+ * device plan, QTPU_EINVAL for a bad pair or limit. */
+qtpu_status qtpu_htn_selftest_gemm_timeout(qtpu_htn* h, int pair, uint64_t limit_ns);
+
 /* ---- QPD sampling and h-TN simplification (section 4.3; Step 1 of
  * section 6.1) ----
  * A gate-cut CT is a rank-1 tensor added with kind QTPU_CT whose index is

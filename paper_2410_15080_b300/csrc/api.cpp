@@ -1089,6 +1089,48 @@ qtpu_status qtpu_htn_selftest_timeout(qtpu_htn* h, uint64_t limit_ns) {
   return QTPU_OK;
 }
 
+qtpu_status qtpu_htn_selftest_gemm_timeout(qtpu_htn* h, int pair, uint64_t limit_ns) {
+  if (!h) return QTPU_EINVAL;
+  if (h->host_only || !h->built) return fail(h, QTPU_ESTATE, "needs a planned device handle");
+  if (limit_ns == 0 || limit_ns > 10000000000ull) return fail(h, QTPU_EINVAL, "limit must be in (0, 10 s]");
+  if (pair != 0 && pair != 1) return fail(h, QTPU_EINVAL, "pair must be 0 or 1");
+  // one 256 x 128 x 64 BF16x3 problem on zeroed operand pieces, in memory
+  // ordered on the handle's stream
+  const int M = 256, N = 128, K = 64;
+  const size_t a_bytes = (size_t)3 * M * K * 2, b_bytes = (size_t)3 * N * K * 2, c_bytes = (size_t)M * N * 8;
+  void *A = nullptr, *B = nullptr, *Cb = nullptr;
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e == cudaSuccess) e = gemm_prepare();
+  if (e == cudaSuccess) e = cudaMallocAsync(&A, a_bytes, h->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync(&B, b_bytes, h->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync(&Cb, c_bytes, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A, 0, a_bytes, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(B, 0, b_bytes, h->stream);
+  if (e == cudaSuccess) {
+    GemmArgs g;
+    g.nval = 1;
+    g.C = Cb;
+    g.batch = 1;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.prec = 3;
+    g.bn = 128;
+    g.pair = pair;
+    g.status = h->ex.status;
+    g.limit_ns = limit_ns;
+    g.test_no_loads = 1;
+    if (!make_operand_map(&g.maps.a[0], A, 3, 1, M, K, K, 128) ||
+        !make_operand_map(&g.maps.b[0], B, 3, 1, N, K, K, pair ? 64 : 128))
+      e = cudaErrorInvalidValue;
+    if (e == cudaSuccess) e = launch_gemm(g, h->ex.sm_count, h->stream);
+  }
+  for (void* p : {A, B, Cb})
+    if (p) cudaFreeAsync(p, h->stream);
+  if (e != cudaSuccess) return fail(h, QTPU_ECUDA, cudaGetErrorString(e));
+  return QTPU_OK;
+}
+
 qtpu_status qtpu_htn_destroy(qtpu_htn* h) {
   if (!h) return QTPU_EINVAL;
   batch_forget(h);

@@ -159,6 +159,7 @@ struct GemmArgs {
   int bn = 128;          // N tile, one of kGemmBlockN, or of kGemmPairWideN with pair (fuse: 128 only)
   int pair = 0;          // BF16x3 without fuse: 256-row tiles on a cluster of two CTAs
                          // (cta_group::2), each staging BN/2 rows of B (the B map's box)
+  int test_no_loads = 0;  // failure-path self-test: no copies are issued, every wait gives up
 };
 cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st);
 // one warp waiting (bounded) on a barrier nothing completes: sets ST_TIMEOUT_DEP

@@ -25,7 +25,7 @@ SYMBOLS = ["qtpu_htn_create", "qtpu_htn_add_tensor", "qtpu_htn_set_output", "qtp
            "qtpu_htn_qpd_info", "qtpu_htn_num_tensors", "qtpu_htn_tensor_info", "qtpu_htn_knit_naive",
            "qtpu_qt_evaluate", "qtpu_htn_lowering_info", "qtpu_htn_output_size", "qtpu_htn_plan_stats",
            "qtpu_htn_exec_stats", "qtpu_htn_launch_features", "qtpu_htn_profile_launches", "qtpu_htn_contract",
-           "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_contract_batch_ex", "qtpu_htn_batch_info", "qtpu_htn_contract_slices", "qtpu_htn_sync", "qtpu_htn_selftest_timeout", "qtpu_htn_destroy",
+           "qtpu_htn_contract_host", "qtpu_htn_contract_batch", "qtpu_htn_contract_batch_ex", "qtpu_htn_batch_info", "qtpu_htn_contract_slices", "qtpu_htn_sync", "qtpu_htn_selftest_timeout", "qtpu_htn_selftest_gemm_timeout", "qtpu_htn_destroy",
            "qtpu_htn_profile", "qtpu_htn_profile_read", "qtpu_pairwise_contract_noalloc",
            "qtpu_pairwise_noalloc_scratch_bytes", "qtpu_noalloc_status", "qtpu_noalloc_selftest_timeout",
            "qtpu_last_error",
@@ -89,6 +89,7 @@ def lib():
         L.qtpu_htn_contract_slices.argtypes = [vp, C.c_int64, C.c_int64, vp]
         L.qtpu_htn_sync.argtypes = [vp]
         L.qtpu_htn_selftest_timeout.argtypes = [vp, C.c_uint64]
+        L.qtpu_htn_selftest_gemm_timeout.argtypes = [vp, C.c_int, C.c_uint64]
         L.qtpu_pairwise_contract_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]
         L.qtpu_pairwise_noalloc_scratch_bytes.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)]
         L.qtpu_noalloc_status.argtypes = [vp]
@@ -278,6 +279,10 @@ class HTN:
     def selftest_timeout(self, limit_ns: int):
         """Enqueue a bounded device wait that is bound to time out (see header)."""
         self._check(self._L.qtpu_htn_selftest_timeout(self._h, limit_ns))
+
+    def selftest_gemm_timeout(self, pair: int, limit_ns: int):
+        """Enqueue a GEMM launch whose waits are bound to time out (see header)."""
+        self._check(self._L.qtpu_htn_selftest_gemm_timeout(self._h, int(pair), limit_ns))
 
     def sync(self):
         self._check(self._L.qtpu_htn_sync(self._h))

@@ -110,6 +110,9 @@ def test_status_codes():
     import ctypes as C
     st = L.qtpu_htn_contract(h._h, C.c_void_p(1))
     assert st == htn.QTPU_ENOTSUP
+    # the failure-path self-tests need a device handle
+    assert L.qtpu_htn_selftest_timeout(h._h, 1000) == htn.QTPU_ESTATE
+    assert L.qtpu_htn_selftest_gemm_timeout(h._h, 0, 1000) == htn.QTPU_ESTATE
     h.close()
 
 

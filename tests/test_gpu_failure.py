@@ -42,6 +42,35 @@ def test_bounded_wait_times_out_and_context_stays_usable():
     h.close()
 
 
+@pytest.mark.parametrize("pair", [0, 1], ids=["one-cta", "cta-pair"])
+def test_gemm_waits_time_out_and_context_stays_usable(pair):
+    """The tensor-core GEMM's own bounded waits: a launch whose producer
+    issues no copies (the self-test flag) gives up in the MMA issuer and the
+    epilogue after 50 ms, frees its TMEM (on a CTA pair, both CTAs' share)
+    and returns; the host reads QTPU_ETIMEOUT, and the same handle then
+    contracts correctly through the GEMM path."""
+    import torch
+    from paper_2410_15080_b300 import from_network, htn
+    net = synth.ring_htn(n_sub=4, gates_per_edge=2, wires_per_edge=1, k=3, seed=6)
+    h = from_network(to_device(net), net.output, prec="bf16x3")
+    assert h.plan_stats()["n_tensor_core_steps"] > 0
+    h.contract()
+    h.sync()
+    t0 = time.perf_counter()
+    h.selftest_gemm_timeout(pair, 50_000_000)  # 50 ms
+    with pytest.raises(htn.QtpuError) as e:
+        h.sync()
+    dt = time.perf_counter() - t0
+    assert e.value.status == htn.QTPU_ETIMEOUT
+    assert 0.04 <= dt < 5.0
+    h.sync()  # reported once
+    out = h.contract()
+    h.sync()
+    torch.cuda.synchronize()
+    assert rel_err(out.cpu().numpy(), oracle_value(net)) <= REL_TOL
+    h.close()
+
+
 def test_injected_workspace_allocation_failure_is_enomem(monkeypatch):
     from paper_2410_15080_b300 import from_network, htn
     net = synth.ring_htn(n_sub=4, gates_per_edge=1, wires_per_edge=1, k=2, seed=1)
