@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tmem_alloc_pair(tmem_holder, L::TMEM_COLS);
       tmem_relinquish_pair();
     } else {
-      tmem_alloc(tmem_holder, kTmemCols);
+      tmem_alloc(tmem_holder, L::TMEM_COLS);
       tmem_relinquish();
     }
   }
@@ -678,7 +678,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if constexpr (PAIR)
       tmem_dealloc_pair(tmem, L::TMEM_COLS);
     else
-      tmem_dealloc(tmem, kTmemCols);
+      tmem_dealloc(tmem, L::TMEM_COLS);
   }
 }
 
