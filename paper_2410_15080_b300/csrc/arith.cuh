@@ -30,16 +30,14 @@ __device__ __forceinline__ float2 decode_f64(double x) {
   }
   const uint32_t mhi = ((uh & 0xFFFFFu) << 3) | (ul >> 29);  // top 23 mantissa bits
   const float hi = __uint_as_float(sign | ((uint32_t)(e + 127) << 23) | mhi);
-  uint32_t rem = ul & 0x1FFFFFFFu;  // remaining 29 mantissa bits, weight 2^(e-52)
-  float lo = 0.f;
-  if (rem) {
-    const int p = 31 - __clz(rem);  // leading one, 0..28
-    const int el = e - 52 + p;
-    if (el >= -126) {
-      const uint32_t m = p >= 23 ? (rem >> (p - 23)) : (rem << (23 - p));
-      lo = __uint_as_float(sign | ((uint32_t)(el + 127) << 23) | (m & 0x7FFFFFu));
-    }
-  }
+  const uint32_t rem = ul & 0x1FFFFFFFu;  // remaining 29 mantissa bits, weight 2^(e-52)
+  // lo without branches: its bits are formed whatever rem is and selected
+  // only when rem is nonzero and lo is a normal float
+  const int p = 31 - __clz(rem);  // leading one, 0..28 (-1 when rem is 0)
+  const int el = e - 52 + p;
+  const uint32_t m = p >= 23 ? (rem >> (p - 23)) : (rem << (23 - p));
+  const uint32_t lob = sign | ((uint32_t)(el + 127) << 23) | (m & 0x7FFFFFu);
+  const float lo = (rem != 0u && el >= -126) ? __uint_as_float(lob) : 0.f;
   return make_float2(hi, lo);
 }
 

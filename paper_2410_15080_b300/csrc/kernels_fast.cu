@@ -100,6 +100,16 @@ struct Op {
       return acc;
     }
     if (use_loop_tab(a)) {
+      if (a.n_loop == 4) {  // a wire CT's loop: unrolled, no loop control
+#pragma unroll
+        for (uint32_t l = 0; l < 4; ++l) {
+          int64_t off[NOPS];
+#pragma unroll
+          for (int j = 0; j < NOPS; ++j) off[j] = base[j] + lt[l][j];
+          acc.add(term(a, W, off));
+        }
+        return acc;
+      }
 #pragma unroll 4
       for (uint32_t l = 0; l < a.n_loop; ++l) {
         int64_t off[NOPS];
@@ -172,7 +182,15 @@ __device__ __forceinline__ void entry_fan(const GatherArgs& a, const float2* W, 
     for (int f = 0; f < F; ++f) v[f] = mul_pair(x, W[wof[f]]);
     return;
   }
-  if (use_loop_tab(a)) {
+  if (use_loop_tab(a) && a.n_loop == 4) {  // a wire CT's loop: unrolled, no loop control
+#pragma unroll
+    for (uint32_t l = 0; l < 4; ++l) {
+      const float2 x = load_pair<DT0>(a.ptr[0], xo + lt[l][0]);
+      const int ow = (int)lt[l][1];
+#pragma unroll
+      for (int f = 0; f < F; ++f) acc[f].add(mul_pair(x, W[wof[f] + ow]));
+    }
+  } else if (use_loop_tab(a)) {
 #pragma unroll 4
     for (uint32_t l = 0; l < a.n_loop; ++l) {
       const float2 x = load_pair<DT0>(a.ptr[0], xo + lt[l][0]);
