@@ -325,8 +325,16 @@ bool dot_setup(GatherArgs& g, int sm) {
     tx.div[tx.n] = make_fastdiv(L.dim[m]);
     tx.n++;
   }
-  for (int m = 0; m < L.n; ++m) {
-    if (in_tile[m]) continue;
+  // outer tuples: the mode with the smallest strides runs fastest, so a
+  // block's consecutive tuples read neighbouring runs of both operands while
+  // their cache lines are still in L2
+  std::vector<int> om;
+  for (int m = 0; m < L.n; ++m)
+    if (!in_tile[m]) om.push_back(m);
+  std::stable_sort(om.begin(), om.end(), [&](int a, int b) {
+    return L.stride[a][0] + L.stride[a][1] > L.stride[b][0] + L.stride[b][1];
+  });
+  for (int m : om) {
     outer.dim[outer.n] = L.dim[m];
     for (int q = 0; q < kMaxOps; ++q) outer.stride[outer.n][q] = L.stride[m][q];
     outer.n++;
