@@ -987,7 +987,12 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     // (with QTPU_FUSE_KEEP_LAYOUT the default orientation stays).  Such a
     // result keeps the 128-column tile the fused epilogue needs: dropping a
     // split launch saves more than a narrower tile.
-    if (!fuse_off && prec == 3 && !last) {
+    // (a result summed over slice values never becomes pieces in the
+    // epilogue: such a step takes its tile like any other)
+    uint64_t din_step = 0;
+    for (const Repr* R : {&X, &Y})
+      for (int o : R->ops) din_step |= toutof(o);
+    if (!fuse_off && prec == 3 && !last && din_step == toutof(ps.out)) {
       const Inds ck = consumer_k(ps.out, s);
       const std::set<int64_t> cks(ck.begin(), ck.end());
       int pref = -1;

@@ -124,3 +124,34 @@ def test_autotune_writes_a_table_the_plan_follows(tmp_path):
     err = rel_err(out.cpu().numpy(), oracle_value(net))
     h2.close()
     assert err <= REL_TOL
+
+
+def test_summed_operand_pairs_on_cta_pairs(tmp_path):
+    """A GEMM that sums four operand pairs in TMEM (the mid-size ring sliced
+    over 16 wire-index values: the step that contracts a sliced index runs
+    once per value of the other), forced onto CTA pairs by a tile table: the
+    contraction matches the oracle."""
+    import re
+    import torch
+    from paper_2410_15080_b300 import from_network
+    net = synth.ring_htn()
+    kw = dict(n_slices=16, slice_dim=4)
+    dev = to_device(net)
+    h = from_network(dev, net.output, prec="bf16x3", **kw)
+    lines = [l for l in h.lowering_info().splitlines() if " gemm " in l]
+    h.close()
+    multi = [l for l in lines if re.search(r"runs=(\d+) launches=(\d+)", l).groups() == ("16", "4")]
+    assert multi, lines
+    g = {k: int(re.search(k + r"=(\d+)", multi[0]).group(1)) for k in ("batch", "M", "N", "K", "bn")}
+    path = tmp_path / "pair.txt"
+    path.write_text(f"3 {g['batch']} {g['M']} {g['N']} {g['K']} : 0 {g['bn']} 0 0 0 1\n"
+                    f"3 {g['batch']} {g['N']} {g['M']} {g['K']} : 1 {g['bn']} 0 0 0 1\n")
+    h = from_network(dev, net.output, prec="bf16x3", autotune_table=str(path), **kw)
+    lines = [l for l in h.lowering_info().splitlines() if " gemm " in l]
+    assert any(" pair " in l and "runs=16 launches=4" in l for l in lines), lines
+    out = h.contract()
+    h.sync()
+    torch.cuda.synchronize()
+    err = rel_err(out.cpu().numpy(), oracle_value(net))
+    h.close()
+    assert err <= REL_TOL
