@@ -809,8 +809,11 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     if (T < 0 || it == gemm_out.end()) return false;
     const GemmOut& P = it->second;
     const Launch& LP = ex->launches[P.li];
-    if (LP.kind != LK_GEMM || LP.gemm.fuse.on || LP.gemm.prec != 3 || LP.gemm.bn != 128 || LP.gemm.pair ||
-        (P.K + 63) / 64 > 16)
+    // the fused epilogue's tiles: 128 columns, or one 160-column tile over the
+    // whole N side (its k-blocks then never cross a tile)
+    const bool fuse_tile = !LP.gemm.pair && (LP.gemm.bn == 128 || (LP.gemm.bn == kFuseWideBN && LP.gemm.N <= kFuseWideBN));
+    const uint32_t w_cap = LP.gemm.bn == kFuseWideBN ? kFuseMaxWWide : kFuseMaxW;
+    if (LP.kind != LK_GEMM || LP.gemm.fuse.on || LP.gemm.prec != 3 || !fuse_tile || (P.K + 63) / 64 > 16)
       return false;
     // pieces cannot be added up: the producer must not sum over slice values
     if (LP.din != LP.dout) return false;
@@ -841,7 +844,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       wsz *= dims.get(U[j]);
     }
     if (small.empty()) wsz = 0;
-    if (wsz > (int64_t)kFuseMaxW || (int)small.size() > kMaxOps) return false;
+    if (wsz > (int64_t)w_cap || (int)small.size() > kMaxOps) return false;
     for (int64_t i : U)
       if (!mine.count(i)) return false;
     std::map<int64_t, int64_t> rst;
@@ -1010,6 +1013,16 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
     if (prec != 3) pair = 0;
     if (!pair && bn > 128) bn = 128;  // the wider tiles exist on CTA pairs only
     const double gM = swap ? nn : nm, gN = swap ? nm : nn;
+    // a result the next GEMM may take in piece form keeps a tile the fused
+    // epilogue has: 128 columns, or one 160-column tile when the N side is
+    // 129-160 wide and that fits the problem in one wave of CTAs where
+    // 128-column tiles need two or more (small latency-bound steps)
+    if (oriented && prec == 3 && gN > 128 && gN <= kFuseWideBN) {
+      const double sms = ex->sm_count;
+      const double t128 = nb * std::ceil(gM / 128.0) * std::ceil(gN / 128.0);
+      const double t160 = nb * std::ceil(gM / 128.0);
+      if (t128 > sms && t160 <= sms) bn = kFuseWideBN;
+    }
     const bool tc = sa.empty() && sb.empty() && gM >= 64 && gN >= 16 && nk >= 8 &&
                     nb * nm * nn * nk >= (double)(1 << 22) && nb < lim && nm < lim && nn < lim && nk < lim &&
                     nb * std::ceil(gM / 128.0) * std::ceil(gN / (double)bn) < lim;

@@ -121,6 +121,11 @@ cudaError_t launch_contract(const void* A, int dtA, const void* B, int dtB, doub
 // per-digit row strides, and absorbed small factors multiply each entry
 // through a table W over their joint indices (per-digit W strides).
 constexpr uint32_t kFuseMaxW = 1024;
+// a fused-epilogue producer whose N side is 129-160 wide may run one 160-column
+// tile instead of two of 128 (one CTA, one TMEM buffer); its table of small
+// factors holds at most kFuseMaxWWide entries (shared memory)
+constexpr int kFuseWideBN = 160;
+constexpr uint32_t kFuseMaxWWide = 256;
 struct GemmFuse {
   int on = 0;
   int k_is_m = 1;

@@ -19,7 +19,8 @@
 // stored result with compensated (TwoSum) FP32 arithmetic; FP64 math is
 // avoided (FP64 throughput on B300 is ~1/64 of FP32).
 //
-// The N tile BN is a template parameter (128, 112, 96, 80, 64 or 48 columns;
+// The N tile BN is a template parameter (128, 112, 96, 80, 64 or 48 columns,
+// and 160 for a fused-split producer whose N side is at most 160 wide;
 // the executor picks it per GEMM, with the orientation, from a measured tile
 // table or by padding): a 216-wide side fills two 112-column tiles to 96 %
 // where 128-column tiles fill 84 %.  The M tile is 128 rows.  Every k-block
@@ -69,7 +70,6 @@ namespace {
 constexpr int BM = 128;
 constexpr int kFuseBN = 128;                   // N tile of the fused-split epilogue
 constexpr int kEpiWarps = 16;
-constexpr int kFuseEpiCols = kFuseBN / (kEpiWarps / 4);  // columns per fused-epilogue thread
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer, MMA, 16 epilogue warps
 constexpr uint32_t kTmemCols = 512;            // 2 buffers x (X, Y) x BN columns (BN <= 128)
 constexpr int kSmemLimit = 232448;             // dynamic shared memory per CTA (227 KB)
@@ -102,13 +102,13 @@ struct Cfg<1> {  // TF32: one piece, one product
 };
 
 // Shared memory: the pipeline stages (as many as fit, at most 8), the
-// barriers and, for the fused-split epilogue (BF16x3, BN = 128, one CTA per
-// tile only), its tables.  In a CTA pair each CTA stages its own 128 rows of
+// barriers and, for the fused-split epilogue (BF16x3, one CTA per tile, BN =
+// 128, or 160 for an N side of at most 160 columns), its tables.  In a CTA pair each CTA stages its own 128 rows of
 // A and half of B's BN rows.
 template <int PREC, int BN, bool PAIR = false>
 struct Layout {
   using C = Cfg<PREC>;
-  static constexpr bool FUSE = PREC == 3 && BN == kFuseBN && !PAIR;
+  static constexpr bool FUSE = PREC == 3 && !PAIR && (BN == kFuseBN || BN == kFuseWideBN);
   static constexpr int ROW = C::KB * C::ES;  // bytes per smem row (= swizzle span)
   static_assert(ROW == 64 || ROW == 128, "64- or 128-byte swizzle rows");
   static constexpr int B_ROWS = PAIR ? BN / 2 : BN;  // B rows staged by one CTA
@@ -122,13 +122,17 @@ struct Layout {
   static constexpr int A_PIECE = BM * ROW;
   static constexpr int B_PIECE = B_ROWS * ROW;
   static constexpr int STAGE = C::NP * (A_PIECE + B_PIECE);
-  static constexpr int FUSE_W = (int)kFuseMaxW * 8;
-  static constexpr int FUSE_BYTES = FUSE ? FUSE_W + 4 * 128 * 4 + 4 * 128 * 4 + 16 : 0;
+  static constexpr int FUSE_W = (BN == kFuseBN ? (int)kFuseMaxW : (int)kFuseMaxWWide) * 8;
+  // maxima: [4][BN] per lane quarter and column (k along the rows), or per
+  // column group and row: [4][128] (BN 128), [4][2][128] (BN 160: a group of
+  // 40 columns meets two 64-entry k-blocks)
+  static constexpr int FUSE_XF = BN == kFuseBN ? 4 * 128 : (4 * BN > 8 * 128 ? 4 * BN : 8 * 128);
+  static constexpr int FUSE_BYTES = FUSE ? FUSE_W + 2 * 128 * 4 + 2 * BN * 4 + FUSE_XF * 4 + 16 : 0;
   static constexpr int FIT = (kSmemLimit - 1024 - 256 - FUSE_BYTES) / STAGE;
   static constexpr int STAGES = FIT < 8 ? FIT : 8;
   static_assert(STAGES >= 2, "two pipeline stages must fit");
   static_assert(BN % 16 == 0 && BN >= 16 && 2 * ACC_BUFS * BN <= (int)kTmemCols, "UMMA N tile");
-  static_assert(BN <= 128 || PAIR, "N tiles above 128 columns on CTA pairs only");
+  static_assert(BN <= 128 || PAIR || BN == kFuseWideBN, "N tiles above 128 columns: CTA pairs, or the fused 160");
   static constexpr int BAR_OFF = STAGES * STAGE;
   // full[S][NP] (one per piece of a stage), empty[S], accfull[2],
   // accempty[2], mma_done
@@ -186,19 +190,22 @@ __device__ void fused_epilogue(const GemmFuse& fz, const float2* fW, uint8_t* sm
                                uint64_t* accempty, volatile int* abort, uint32_t* status, uint64_t limit_ns, int batch,
                                int M, int N, int mt, int nt, int n_tiles, __nv_bfloat16* out) {
   using L = Layout<PREC, BN>;
-  static_assert(BN == kFuseBN, "the fused epilogue's tables are laid out for 128-column tiles");
-  constexpr int kEpiCols = kFuseEpiCols;
+  static_assert(L::FUSE, "the fused epilogue has 128- or 160-column tiles");
+  constexpr int kEpiCols = BN / (kEpiWarps / 4);  // columns per thread (4 column groups)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ew = warp - 2, q = warp & 3, h = ew >> 2;
   const int et = threadIdx.x - 64;
   int* rm = reinterpret_cast<int*>(smem + L::FUSE_OFF + L::FUSE_W);
   int* wm = rm + 128;
   int* rn = wm + 128;
-  int* wn = rn + 128;
-  float* xmax = reinterpret_cast<float*>(wn + 128);  // [4][128]
+  int* wn = rn + BN;
+  float* xmax = reinterpret_cast<float*>(wn + BN);  // L::FUSE_XF entries
   // set only by epilogue threads, and only before a tile's last barrier, so
   // every epilogue warp reads the same value after it
-  volatile int* epi_abort = reinterpret_cast<volatile int*>(xmax + 4 * 128);
+  volatile int* epi_abort = reinterpret_cast<volatile int*>(xmax + L::FUSE_XF);
+  // BN 160: the 64-entry k-blocks (columns) a group of 40 columns meets,
+  // first and last (the only N tile starts at column 0)
+  const int blk0 = h * kEpiCols / 64, blk1 = (h * kEpiCols + kEpiCols - 1) / 64;
   if (et == 0) *epi_abort = 0;
   const bool hasW = fz.w_size != 0;
   const uint32_t Kp = fz.Kp;
@@ -213,7 +220,7 @@ __device__ void fused_epilogue(const GemmFuse& fz, const float2* fW, uint8_t* sm
       const int m = mtile * BM + et;
       rm[et] = wm[et] = 0;
       if (m < M) digits((uint32_t)m, fz.mmodes, &rm[et], &wm[et]);
-    } else if (et < 256) {
+    } else if (et < 128 + BN) {
       const int n = ntile * BN + (et - 128);
       rn[et - 128] = wn[et - 128] = 0;
       if (n < N) digits((uint32_t)n, fz.nmodes, &rn[et - 128], &wn[et - 128]);
@@ -221,8 +228,8 @@ __device__ void fused_epilogue(const GemmFuse& fz, const float2* fW, uint8_t* sm
     int rb, wb;
     digits((uint32_t)b, fz.bmodes, &rb, &wb);
     epi_bar();
-    const int acc = item & 1;
-    const uint32_t aph = (uint32_t)((item >> 1) & 1);
+    const int acc = item % L::ACC_BUFS;
+    const uint32_t aph = (uint32_t)((item / L::ACC_BUFS) & 1);
     const bool got = mbar_wait_bounded(&accfull[acc], aph, limit_ns, abort);
     const bool all = __all_sync(0xffffffffu, got);
     if (!all && lane == 0) {
@@ -234,7 +241,7 @@ __device__ void fused_epilogue(const GemmFuse& fz, const float2* fW, uint8_t* sm
     const int ml = q * 32 + lane;
     const int m = mtile * BM + ml;
     // pass 1: maxima of |X + Y| * W
-    float tmax = 0.f;
+    float tmax = 0.f, tmax1 = 0.f;  // (tmax1: BN 160, the group's second k-block)
 #pragma unroll 1
     for (int g = 0; g < kEpiCols / 8 && all; ++g) {
       uint32_t rx[8], ry[8];
@@ -250,13 +257,22 @@ __device__ void fused_epilogue(const GemmFuse& fz, const float2* fW, uint8_t* sm
         if (fz.k_is_m) {  // k runs over the lanes: maximum per column over the warp
 #pragma unroll
           for (int s = 16; s > 0; s >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, s));
-          if (lane == 0) xmax[q * 128 + cl] = a;
-        } else {
+          if (lane == 0) xmax[q * BN + cl] = a;
+        } else if (BN == kFuseBN || cl / 64 == blk0) {
           tmax = fmaxf(tmax, a);
+        } else {
+          tmax1 = fmaxf(tmax1, a);
         }
       }
     }
-    if (!fz.k_is_m) xmax[h * 128 + ml] = tmax;
+    if (!fz.k_is_m) {
+      if (BN == kFuseBN) {
+        xmax[h * 128 + ml] = tmax;
+      } else {
+        xmax[(h * 2) * 128 + ml] = tmax;
+        xmax[(h * 2 + 1) * 128 + ml] = tmax1;
+      }
+    }
     epi_bar();
     if (*epi_abort) break;
     // pass 2: pieces
@@ -275,7 +291,7 @@ __device__ void fused_epilogue(const GemmFuse& fz, const float2* fW, uint8_t* sm
           float2 v = two_sum(__uint_as_float(rx[j]), __uint_as_float(ry[j]));
           if (hasW) v = arith::mul_pair(v, fW[wb + wm[ml] + wn[cl]]);
           const int qb = q & 2;  // the two lane quarters of this 64-entry k-block
-          const int E = arith::grid_exp(fmaxf(xmax[qb * 128 + cl], xmax[(qb + 1) * 128 + cl]));
+          const int E = arith::grid_exp(fmaxf(xmax[qb * BN + cl], xmax[(qb + 1) * BN + cl]));
           float pc[3];
           arith::grid_pieces(v, E, pc);
           const int64_t dst = (int64_t)(rb + rn[cl]) * Kp + m;
@@ -284,8 +300,29 @@ __device__ void fused_epilogue(const GemmFuse& fz, const float2* fW, uint8_t* sm
         }
       }
     } else {
-      const int hb = h & ~1;  // the two column groups of this 64-entry k-block
-      const int E = arith::grid_exp(fmaxf(xmax[hb * 128 + ml], xmax[(hb + 1) * 128 + ml]));
+      // the grid exponent of each k-block this thread's columns meet: BN 128,
+      // the two column groups of the one block; BN 160, every group's
+      // partial maximum for the block (0, the neutral maximum, where a group
+      // does not meet it)
+      int E0, E1 = 0;
+      if (BN == kFuseBN) {
+        const int hb = h & ~1;
+        E0 = arith::grid_exp(fmaxf(xmax[hb * 128 + ml], xmax[(hb + 1) * 128 + ml]));
+      } else {
+        float m0 = 0.f, m1 = 0.f;
+#pragma unroll
+        for (int hh = 0; hh < 4; ++hh) {
+          const int b0 = hh * kEpiCols / 64;
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {
+            const float v = xmax[(hh * 2 + s) * 128 + ml];
+            if (b0 + s == blk0) m0 = fmaxf(m0, v);
+            if (b0 + s == blk1) m1 = fmaxf(m1, v);
+          }
+        }
+        E0 = arith::grid_exp(m0);
+        E1 = arith::grid_exp(m1);
+      }
 #pragma unroll 1
       for (int g = 0; g < kEpiCols / 8; ++g) {
         uint32_t rx[8], ry[8];
@@ -295,6 +332,7 @@ __device__ void fused_epilogue(const GemmFuse& fz, const float2* fW, uint8_t* sm
         const int c0 = h * kEpiCols + g * 8;
         const int n0 = ntile * BN + c0;
         if (m >= M || n0 >= N) continue;
+        const int E = (BN == kFuseBN || c0 / 64 == blk0) ? E0 : E1;
         __nv_bfloat16 hp[3][8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -696,7 +734,8 @@ cudaError_t launch_t(const GemmArgs& a, int sm_count, cudaStream_t st) {
   using L = Layout<PREC, BN, PAIR>;
   const long long tiles = (long long)a.batch * ((a.M + L::TM - 1) / L::TM) * ((a.N + BN - 1) / BN);
   if (tiles <= 0) return cudaSuccess;
-  if (a.fuse.on && (!L::FUSE || a.fuse.w_size > kFuseMaxW || a.accum || a.nval != 1)) return cudaErrorInvalidValue;
+  if (a.fuse.on && (!L::FUSE || a.fuse.w_size > (uint32_t)(L::FUSE_W / 8) || a.accum || a.nval != 1))
+    return cudaErrorInvalidValue;
   if (a.nval < 1 || a.nval > kGemmVals) return cudaErrorInvalidValue;
   if constexpr (PAIR) {
     int dev = 0;
@@ -747,6 +786,8 @@ cudaError_t launch_p(const GemmArgs& a, int sm_count, cudaStream_t st) {
     if (a.bn == 256) return launch_t<PREC, 256, PAIR>(a, sm_count, st);
     if (a.bn == 224) return launch_t<PREC, 224, PAIR>(a, sm_count, st);
   }
+  if constexpr (PREC == 3 && !PAIR)
+    if (a.bn == kFuseWideBN) return launch_t<PREC, kFuseWideBN, PAIR>(a, sm_count, st);
   switch (a.bn) {
     case 128: return launch_t<PREC, 128, PAIR>(a, sm_count, st);
     case 112: return launch_t<PREC, 112, PAIR>(a, sm_count, st);
@@ -767,6 +808,8 @@ cudaError_t prepare_p() {
     if (e == cudaSuccess) e = prepare_t<PREC, 256, PAIR>();
     if (e == cudaSuccess) e = prepare_t<PREC, 224, PAIR>();
   }
+  if constexpr (PREC == 3 && !PAIR)
+    if (e == cudaSuccess) e = prepare_t<PREC, kFuseWideBN, PAIR>();
   return e;
 }
 
