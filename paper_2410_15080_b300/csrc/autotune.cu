@@ -8,6 +8,8 @@
 // rule below picks by counted tile area, and exec_autotune measures every
 // valid choice of a plan's GEMM problems on synthetic operand pieces and
 // records the fastest in a tile table, which the lowering then follows.
+// Each GEMM is timed alone: the layout its result leaves for the next step
+// (set by the orientation) is not part of the measurement.
 #include <cuda_runtime.h>
 #include <dlfcn.h>
 
@@ -25,9 +27,9 @@ namespace qtpu {
 
 namespace {
 
-bool valid_tile(double nm, double nn, bool swap, int bn, int pair = 0) {
+bool valid_tile(double nm, double nn, bool swap, int bn, int pair = 0, int prec = 3) {
   const double gM = swap ? nn : nm, gN = swap ? nm : nn;
-  return gM >= 64 && gN >= 16 && gemm_bn_supported(bn, pair);
+  return gM >= 64 && gN >= 16 && gemm_bn_supported(bn, pair, prec);
 }
 
 // synthetic operand pieces: values uniform in [-1, 1) from a 32-bit hash of
@@ -66,7 +68,7 @@ std::string load_tile_table(const std::string& path, TileTable* t) {
     double ms = 0, ms_rule = 0, ms_base = 0;
     const int got = std::sscanf(c, "%lld %lld %lld %lld %lld : %d %d %lf %lf %lf %d", &k[0], &k[1], &k[2], &k[3],
                                 &k[4], &swap, &bn, &ms, &ms_rule, &ms_base, &pair);
-    if (got < 7 || (swap != 0 && swap != 1) || (pair != 0 && pair != 1) || !gemm_bn_supported(bn, pair) ||
+    if (got < 7 || (swap != 0 && swap != 1) || (pair != 0 && pair != 1) || !gemm_bn_supported(bn, pair, (int)k[0]) ||
         k[0] < 0 || k[0] > 3 || (pair && k[0] != 3)) {
       err = path + ":" + std::to_string(ln) + ": not a tile table line";
       break;
@@ -115,14 +117,14 @@ void choose_tile(const TileTable* t, int prec, double nb, double nm, double nn, 
   *pair = 0;
   if (t && !t->empty()) {
     auto it = t->find(TileKey{prec, (int64_t)nb, (int64_t)nm, (int64_t)nn, (int64_t)nk});
-    if (it != t->end() && valid_tile(nm, nn, it->second.swap != 0, it->second.bn, it->second.pair)) {
+    if (it != t->end() && valid_tile(nm, nn, it->second.swap != 0, it->second.bn, it->second.pair, prec)) {
       *swap = it->second.swap != 0;
       *bn = it->second.bn;
       *pair = prec == 3 ? it->second.pair : 0;
       return;
     }
     it = t->find(TileKey{prec, (int64_t)nb, (int64_t)nn, (int64_t)nm, (int64_t)nk});
-    if (it != t->end() && valid_tile(nm, nn, it->second.swap == 0, it->second.bn, it->second.pair)) {
+    if (it != t->end() && valid_tile(nm, nn, it->second.swap == 0, it->second.bn, it->second.pair, prec)) {
       *swap = it->second.swap == 0;
       *bn = it->second.bn;
       *pair = prec == 3 ? it->second.pair : 0;
@@ -209,7 +211,10 @@ std::string exec_autotune(const Executor* ex, int reps, TileTable* t, int* n, in
     choose_tile(nullptr, prec, (double)nb, (double)nm, (double)nn, (double)nk, &rule_swap, &rule_bn, &rule_pair);
     TileChoice best;
     best.ms = std::numeric_limits<double>::infinity();
+    // every width on one CTA and on a CTA pair; valid_tile drops the ones a
+    // form lacks (224 and 256 on one CTA, 160 on pairs or outside BF16x3)
     std::vector<int> widths(std::begin(kGemmPairWideN), std::end(kGemmPairWideN));
+    widths.push_back(kFuseWideBN);
     widths.insert(widths.end(), std::begin(kGemmBlockN), std::end(kGemmBlockN));
     for (int o = 0; o < 4 && err.empty(); ++o)
       for (int bn : widths) {
@@ -217,7 +222,7 @@ std::string exec_autotune(const Executor* ex, int reps, TileTable* t, int* n, in
         const bool sw = (o & 1) != 0;
         const int pair = o >> 1;  // CTA pairs: BF16x3 only
         if (pair && prec != 3) continue;
-        if (!valid_tile((double)nm, (double)nn, sw, bn, pair)) continue;
+        if (!valid_tile((double)nm, (double)nn, sw, bn, pair, prec)) continue;
         GemmArgs g;
         g.nval = nval;
         g.C = C;

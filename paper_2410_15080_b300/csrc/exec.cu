@@ -1011,7 +1011,8 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       if (gemm_pair_override() >= 0) pair = gemm_pair_override();
     }
     if (prec != 3) pair = 0;
-    if (!pair && bn > 128) bn = 128;  // the wider tiles exist on CTA pairs only
+    // the tiles above 128 columns: 224 and 256 on CTA pairs, 160 on one CTA in BF16x3
+    if (!gemm_bn_supported(bn, pair, prec)) bn = 128;
     const double gM = swap ? nn : nm, gN = swap ? nm : nn;
     // a result the next GEMM may take in piece form keeps a tile the fused
     // epilogue has: 128 columns, or one 160-column tile when the N side is

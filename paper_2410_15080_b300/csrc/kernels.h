@@ -200,7 +200,8 @@ bool make_operand_map(CUtensorMap* map, void* base, int prec, int64_t batch, int
 constexpr int kGemmBlockN[6] = {128, 112, 96, 80, 64, 48};
 // wider N tiles, on CTA pairs only (one TMEM accumulator buffer)
 constexpr int kGemmPairWideN[2] = {256, 224};
-bool gemm_bn_supported(int bn, int pair = 0);
+// (BF16x3 on one CTA also takes kFuseWideBN)
+bool gemm_bn_supported(int bn, int pair = 0, int prec = 3);
 int gemm_k_block(int prec);  // K elements per pipeline stage
 
 }  // namespace qtpu
