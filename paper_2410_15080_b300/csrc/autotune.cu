@@ -212,9 +212,9 @@ std::string exec_autotune(const Executor* ex, int reps, TileTable* t, int* n, in
     TileChoice best;
     best.ms = std::numeric_limits<double>::infinity();
     // every width on one CTA and on a CTA pair; valid_tile drops the ones a
-    // form lacks (224 and 256 on one CTA, 160 on pairs or outside BF16x3)
+    // form lacks (224 and 256 on one CTA, 160 and 144 on pairs or outside BF16x3)
     std::vector<int> widths(std::begin(kGemmPairWideN), std::end(kGemmPairWideN));
-    widths.push_back(kFuseWideBN);
+    widths.insert(widths.end(), std::begin(kGemmWideN), std::end(kGemmWideN));
     widths.insert(widths.end(), std::begin(kGemmBlockN), std::end(kGemmBlockN));
     for (int o = 0; o < 4 && err.empty(); ++o)
       for (int bn : widths) {

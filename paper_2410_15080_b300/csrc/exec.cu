@@ -1011,7 +1011,7 @@ std::string exec_build(Executor* ex, const Plan& plan, const std::vector<Leaf>& 
       if (gemm_pair_override() >= 0) pair = gemm_pair_override();
     }
     if (prec != 3) pair = 0;
-    // the tiles above 128 columns: 224 and 256 on CTA pairs, 160 on one CTA in BF16x3
+    // the tiles above 128 columns: 224 and 256 on CTA pairs, 160 and 144 on one CTA in BF16x3
     if (!gemm_bn_supported(bn, pair, prec)) bn = 128;
     const double gM = swap ? nn : nm, gN = swap ? nm : nn;
     // a result the next GEMM may take in piece form keeps a tile the fused

@@ -200,7 +200,9 @@ bool make_operand_map(CUtensorMap* map, void* base, int prec, int64_t batch, int
 constexpr int kGemmBlockN[6] = {128, 112, 96, 80, 64, 48};
 // wider N tiles, on CTA pairs only (one TMEM accumulator buffer)
 constexpr int kGemmPairWideN[2] = {256, 224};
-// (BF16x3 on one CTA also takes kFuseWideBN)
+// wider N tiles of BF16x3 on one CTA (one TMEM accumulator buffer): 160 (also
+// the fused-split producer's), and 144 for N sides that are multiples of 144
+constexpr int kGemmWideN[2] = {kFuseWideBN, 144};
 bool gemm_bn_supported(int bn, int pair = 0, int prec = 3);
 int gemm_k_block(int prec);  // K elements per pipeline stage
 

@@ -20,8 +20,9 @@
 // avoided (FP64 throughput on B300 is ~1/64 of FP32).
 //
 // The N tile BN is a template parameter (128, 112, 96, 80, 64 or 48 columns,
-// and 160 for BF16x3 on one CTA: a fused-split producer whose N side is at
-// most 160 wide, or a plain GEMM whose tile table entry picks it;
+// and 160 or 144 for BF16x3 on one CTA: 160 for a fused-split producer whose
+// N side is at most 160 wide, and either for a plain GEMM whose tile table
+// entry picks it;
 // the executor picks it per GEMM, with the orientation, from a measured tile
 // table or by padding): a 216-wide side fills two 112-column tiles to 96 %
 // where 128-column tiles fill 84 %.  The M tile is 128 rows.  Every k-block
@@ -133,7 +134,8 @@ struct Layout {
   static constexpr int STAGES = FIT < 8 ? FIT : 8;
   static_assert(STAGES >= 2, "two pipeline stages must fit");
   static_assert(BN % 16 == 0 && BN >= 16 && 2 * ACC_BUFS * BN <= (int)kTmemCols, "UMMA N tile");
-  static_assert(BN <= 128 || PAIR || BN == kFuseWideBN, "N tiles above 128 columns: CTA pairs, or 160 in BF16x3");
+  static_assert(BN <= 128 || PAIR || (PREC == 3 && (BN == kGemmWideN[0] || BN == kGemmWideN[1])),
+                "N tiles above 128 columns: CTA pairs, or 160 and 144 in BF16x3");
   static constexpr int BAR_OFF = STAGES * STAGE;
   // full[S][NP] (one per piece of a stage), empty[S], accfull[2],
   // accempty[2], mma_done
@@ -787,8 +789,10 @@ cudaError_t launch_p(const GemmArgs& a, int sm_count, cudaStream_t st) {
     if (a.bn == 256) return launch_t<PREC, 256, PAIR>(a, sm_count, st);
     if (a.bn == 224) return launch_t<PREC, 224, PAIR>(a, sm_count, st);
   }
-  if constexpr (PREC == 3 && !PAIR)
-    if (a.bn == kFuseWideBN) return launch_t<PREC, kFuseWideBN, PAIR>(a, sm_count, st);
+  if constexpr (PREC == 3 && !PAIR) {
+    if (a.bn == kGemmWideN[0]) return launch_t<PREC, kGemmWideN[0], PAIR>(a, sm_count, st);
+    if (a.bn == kGemmWideN[1]) return launch_t<PREC, kGemmWideN[1], PAIR>(a, sm_count, st);
+  }
   switch (a.bn) {
     case 128: return launch_t<PREC, 128, PAIR>(a, sm_count, st);
     case 112: return launch_t<PREC, 112, PAIR>(a, sm_count, st);
@@ -809,8 +813,10 @@ cudaError_t prepare_p() {
     if (e == cudaSuccess) e = prepare_t<PREC, 256, PAIR>();
     if (e == cudaSuccess) e = prepare_t<PREC, 224, PAIR>();
   }
-  if constexpr (PREC == 3 && !PAIR)
-    if (e == cudaSuccess) e = prepare_t<PREC, kFuseWideBN, PAIR>();
+  if constexpr (PREC == 3 && !PAIR) {
+    if (e == cudaSuccess) e = prepare_t<PREC, kGemmWideN[0], PAIR>();
+    if (e == cudaSuccess) e = prepare_t<PREC, kGemmWideN[1], PAIR>();
+  }
   return e;
 }
 
@@ -841,7 +847,9 @@ cudaError_t launch_bounded_wait_probe(uint32_t* status, uint64_t limit_ns, cudaS
 bool gemm_bn_supported(int bn, int pair, int prec) {
   for (int b : kGemmBlockN)
     if (b == bn) return true;
-  if (!pair && prec == 3 && bn == kFuseWideBN) return true;
+  if (!pair && prec == 3)
+    for (int b : kGemmWideN)
+      if (b == bn) return true;
   if (pair)
     for (int b : kGemmPairWideN)
       if (b == bn) return true;

@@ -393,23 +393,26 @@ def test_tile_table_sets_the_cta_pair_form(tmp_path):
         assert len(g) == 1 and g[0]["bn"] == 64 and g[0]["M"] == 300 and g[0]["pair"] == pair, g
 
 
-def test_tile_table_takes_the_one_cta_160_column_tile(tmp_path):
-    """BF16x3 on one CTA also runs 160-column tiles (the width of the
-    fused-split producer): a table entry selects it for a plain GEMM."""
+@pytest.mark.parametrize("bn", [160, 144])
+def test_tile_table_takes_the_wide_one_cta_tiles(tmp_path, bn):
+    """BF16x3 on one CTA also runs 160-column (the width of the fused-split
+    producer) and 144-column tiles: a table entry selects one for a plain
+    GEMM."""
     net = _one_gemm_net()
-    path = tmp_path / "t160.txt"
-    path.write_text("3 2 300 200 333 : 0 160 0.1 0.2 0.3 0\n")
+    path = tmp_path / f"t{bn}.txt"
+    path.write_text(f"3 2 300 200 333 : 0 {bn} 0.1 0.2 0.3 0\n")
     h = _host_handle(net, autotune_table=str(path))
     g = _gemm_launches(h)
     h.close()
-    assert len(g) == 1 and g[0]["bn"] == 160 and g[0]["M"] == 300 and g[0]["pair"] == 0, g
+    assert len(g) == 1 and g[0]["bn"] == bn and g[0]["M"] == 300 and g[0]["pair"] == 0, g
 
 
 def test_malformed_tile_table_is_rejected(tmp_path):
     net = _one_gemm_net()
     for text in ["3 2 300 200 333 : 1 100\n", "3 2 300 200 : 1 128\n", "3 2 300 200 333 : 2 128\n",
                  "3 2 300 200 333 : 0 128 1 1 1 2\n", "1 2 300 200 333 : 0 128 1 1 1 1\n",
-                 "1 2 300 200 333 : 0 160 1 1 1 0\n", "3 2 300 200 333 : 0 160 1 1 1 1\n"]:
+                 "1 2 300 200 333 : 0 160 1 1 1 0\n", "3 2 300 200 333 : 0 160 1 1 1 1\n",
+                 "2 2 300 200 333 : 0 144 1 1 1 0\n", "3 2 300 200 333 : 0 144 1 1 1 1\n"]:
         path = tmp_path / "bad.txt"
         path.write_text(text)
         with pytest.raises(htn.QtpuError) as e:

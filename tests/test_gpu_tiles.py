@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 BNS = (128, 112, 96, 80, 64, 48)
 PAIR_WIDE = (256, 224)
-WIDE_ONE_CTA = 160  # BF16x3 on one CTA (the fused-split producer's wide tile)
+WIDE_ONE_CTA = (160, 144)  # BF16x3 on one CTA (160: also the fused-split producer's wide tile)
 PREC_CODE = {"tf32": 1, "3xtf32": 2, "bf16x3": 3}
 TOL = {"bf16x3": REL_TOL, "3xtf32": 1e-5, "tf32": 1e-2}
 # ragged M/N against 128-row (and 256-row CTA-pair) tiles and every N tile;
@@ -62,8 +62,8 @@ def test_every_orientation_and_n_tile(shape, prec, tmp_path):
     dev = to_device(net)
     seen = set()
     cases = [(sw, c, 0) for sw in (0, 1) for c in BNS]
-    if prec == "bf16x3":  # one CTA's 160-column tile; CTA pairs, with the two wider tiles only they have
-        cases += [(sw, WIDE_ONE_CTA, 0) for sw in (0, 1)]
+    if prec == "bf16x3":  # one CTA's 160- and 144-column tiles; CTA pairs, with the two wider tiles only they have
+        cases += [(sw, c, 0) for sw in (0, 1) for c in WIDE_ONE_CTA]
         cases += [(sw, c, 1) for sw in (0, 1) for c in BNS + PAIR_WIDE]
     for swap, bn, pair in cases:
         # the entry keyed both ways, so it applies whichever operand the
@@ -83,7 +83,7 @@ def test_every_orientation_and_n_tile(shape, prec, tmp_path):
         h.close()
         assert err <= TOL[prec], (swap, bn, pair, err)
         seen.add((swap, bn, pair))
-    assert len(seen) == len(cases) == (30 if prec == "bf16x3" else 12)
+    assert len(seen) == len(cases) == (32 if prec == "bf16x3" else 12)
 
 
 def test_autotune_writes_a_table_the_plan_follows(tmp_path):
@@ -106,7 +106,7 @@ def test_autotune_writes_a_table_the_plan_follows(tmp_path):
         key, val = line.split(":")
         kk = tuple(int(x) for x in key.split())
         sw, bn, ms, ms_rule, ms_base, pair = val.split()
-        assert int(pair) in (0, 1) and int(bn) in BNS + (PAIR_WIDE if int(pair) else (WIDE_ONE_CTA,)) \
+        assert int(pair) in (0, 1) and int(bn) in BNS + (PAIR_WIDE if int(pair) else WIDE_ONE_CTA) \
             and int(sw) in (0, 1)
         # the padding rule's choice and the 128-column one are among those timed
         assert 0 < float(ms) <= min(float(ms_rule), float(ms_base))
