@@ -9,7 +9,8 @@
 // valid choice of a plan's GEMM problems on synthetic operand pieces and
 // records the fastest in a tile table, which the lowering then follows.
 // Each GEMM is timed alone: the layout its result leaves for the next step
-// (set by the orientation) is not part of the measurement.
+// (set by the orientation) is not part of the measurement, so the tuner
+// keeps a problem's orientation unless the other one is clearly faster.
 #include <cuda_runtime.h>
 #include <dlfcn.h>
 
@@ -26,6 +27,10 @@
 namespace qtpu {
 
 namespace {
+
+// the least gain (fraction of the time) for which the tuner changes a
+// problem's orientation
+constexpr double kSwapGain = 0.03;
 
 bool valid_tile(double nm, double nn, bool swap, int bn, int pair = 0, int prec = 3) {
   const double gM = swap ? nn : nm, gN = swap ? nm : nn;
@@ -209,8 +214,21 @@ std::string exec_autotune(const Executor* ex, int reps, TileTable* t, int* n, in
     bool rule_swap = base_swap;
     int rule_bn = 128, rule_pair = 0;
     choose_tile(nullptr, prec, (double)nb, (double)nm, (double)nn, (double)nk, &rule_swap, &rule_bn, &rule_pair);
-    TileChoice best;
-    best.ms = std::numeric_limits<double>::infinity();
+    // the orientation also sets the layout the next step reads, which a GEMM
+    // timed alone does not show: the other orientation replaces the one of
+    // the problem's present entry (else the padding rule's) only when it is
+    // more than kSwapGain faster
+    bool ref_swap = rule_swap;
+    {
+      const auto it = t->find(key);
+      const auto jt = t->find(TileKey{key[0], key[1], key[3], key[2], key[4]});
+      if (it != t->end())
+        ref_swap = it->second.swap != 0;
+      else if (jt != t->end())
+        ref_swap = jt->second.swap == 0;
+    }
+    TileChoice best, best_ref;
+    best.ms = best_ref.ms = std::numeric_limits<double>::infinity();
     // every width on one CTA and on a CTA pair; valid_tile drops the ones a
     // form lacks (224 and 256 on one CTA, 160 and 144 on pairs or outside BF16x3)
     std::vector<int> widths(std::begin(kGemmPairWideN), std::end(kGemmPairWideN));
@@ -261,7 +279,14 @@ std::string exec_autotune(const Executor* ex, int reps, TileTable* t, int* n, in
         if (sw == rule_swap && bn == rule_bn && !pair) best.ms_rule = med;
         if (sw == base_swap && bn == 128 && !pair) best.ms_base = med;
         if (med < best.ms) best.ms = med, best.swap = sw ? 1 : 0, best.bn = bn, best.pair = pair;
+        if (sw == ref_swap && med < best_ref.ms) best_ref.ms = med, best_ref.swap = sw ? 1 : 0, best_ref.bn = bn,
+                                                 best_ref.pair = pair;
       }
+    if ((best.swap != 0) != ref_swap && best_ref.ms <= best.ms * (1.0 + kSwapGain)) {
+      best_ref.ms_rule = best.ms_rule;
+      best_ref.ms_base = best.ms_base;
+      best = best_ref;
+    }
     uint32_t hs = 0;
     if (err.empty() && (e = cudaMemcpy(&hs, status, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) cuda_fail(e);
     if (err.empty() && hs) {
