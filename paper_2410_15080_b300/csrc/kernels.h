@@ -161,7 +161,7 @@ struct GemmArgs {
   uint64_t limit_ns = 2000000000ull;
   GemmFuse fuse;         // fuse.on: C receives the consumer's piece planes
   int accum = 0;         // add the product to the stored (hi, lo) result (not with fuse)
-  int bn = 128;          // N tile, one of kGemmBlockN, or of kGemmPairWideN with pair (fuse: 128 only)
+  int bn = 128;          // N tile: kGemmBlockN, kGemmPairWideN with pair, kGemmWideN in BF16x3 without (fuse: 128, 160)
   int pair = 0;          // BF16x3 without fuse: 256-row tiles on a cluster of two CTAs
                          // (cta_group::2), each staging BN/2 rows of B (the B map's box)
   int test_no_loads = 0;  // failure-path self-test: no copies are issued, every wait gives up
